@@ -1,0 +1,120 @@
+"""Pins for the oracle's J/K steps: symmetry, positivity, energies two ways,
+invariance under aux rescaling, under the choice of whitening and under the
+orthonormalisation of C_occ (J and K depend on C only through D = C C^T)."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2404_09452_gb300 import inputs as I
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "water_dfjk.json")
+
+
+def system(name):
+    m = I.water() if name == "water" else I.molecule(4, seed=1004)
+    nocc = 5 if name == "water" else I.default_nocc(m.nao)
+    S = O.overlap(m.orb, m.coords)
+    C = I.orthonormalize(I.c_occ_raw(m.nao, nocc, 3000), S)
+    T = O.three_center(m.orb, m.aux, m.coords)
+    V = O.metric(m.aux, m.coords)
+    return m, S, C, T, V
+
+
+@pytest.fixture(scope="module", params=["water", "mol4"])
+def sys_(request):
+    m, S, C, T, V = system(request.param)
+    return m, S, C, T, V, O.dfjk(m.orb, m.aux, m.coords, C, T=T, V=V)
+
+
+def test_c_orthonormal(sys_):
+    _, S, C, *_ = sys_
+    assert np.max(np.abs(C.T @ S @ C - np.eye(C.shape[1]))) < 1e-12
+
+
+def test_J_K_symmetric_and_K_psd(sys_):
+    r = sys_[5]
+    J, K = r["J"], r["K"]
+    assert np.max(np.abs(J - J.T)) < 1e-13 * np.abs(J).max()
+    assert np.max(np.abs(K - K.T)) < 1e-13 * np.abs(K).max()
+    assert np.linalg.eigvalsh(K).min() > -1e-12 * np.abs(K).max()
+
+
+def test_energies_two_ways(sys_):
+    m, S, C, T, V, r = sys_
+    ej2, ek2 = O.energies_second_way(T, V, r["B"], C)
+    assert r["E_J"] == pytest.approx(ej2, rel=1e-12)
+    assert r["E_K"] == pytest.approx(ek2, rel=1e-12)
+    assert r["E_J"] > 0 and r["E_K"] > 0
+    # E_J = rho.rho / 2 with rho = B vec(D)
+    assert r["E_J"] == pytest.approx(0.5 * r["rho"] @ r["rho"], rel=1e-12)
+
+
+def test_whitening_choice_invariance(sys_):
+    m, S, C, T, V, r = sys_
+    r2 = O.dfjk(m.orb, m.aux, m.coords, C, how="eigh", T=T, V=V)
+    assert np.max(np.abs(r2["J"] - r["J"])) < 1e-11 * np.abs(r["J"]).max()
+    assert np.max(np.abs(r2["K"] - r["K"])) < 1e-11 * np.abs(r["K"]).max()
+
+
+def test_aux_rescaling_invariance(sys_):
+    m, S, C, T, V, r = sys_
+    s = np.random.default_rng(1).uniform(0.3, 3.0, size=V.shape[0])
+    r2 = O.dfjk(m.orb, m.aux, m.coords, C, T=T * s[:, None, None], V=V * np.outer(s, s))
+    assert np.max(np.abs(r2["J"] - r["J"])) < 1e-11 * np.abs(r["J"]).max()
+    assert np.max(np.abs(r2["K"] - r["K"])) < 1e-11 * np.abs(r["K"]).max()
+
+
+def test_depends_on_C_only_through_D(sys_):
+    m, S, C, T, V, r = sys_
+    nocc = C.shape[1]
+    U, _ = np.linalg.qr(np.random.default_rng(2).standard_normal((nocc, nocc)))
+    r2 = O.dfjk(m.orb, m.aux, m.coords, C @ U, T=T, V=V)
+    assert np.max(np.abs(r2["K"] - r["K"])) < 1e-11 * np.abs(r["K"]).max()
+    # Cholesky (Gram-Schmidt) orthonormalisation of the same raw C0
+    C0 = I.c_occ_raw(m.nao, nocc, 3000)
+    R = np.linalg.cholesky(C0.T @ S @ C0).T
+    r3 = O.dfjk(m.orb, m.aux, m.coords, np.linalg.solve(R.T, C0.T).T, T=T, V=V)
+    assert np.max(np.abs(r3["J"] - r["J"])) < 1e-11 * np.abs(r["J"]).max()
+    assert np.max(np.abs(r3["K"] - r["K"])) < 1e-11 * np.abs(r["K"]).max()
+
+
+def test_exact_limit_complete_aux():
+    """With one centre and an aux set that spans every orbital product exactly
+    (products of s Gaussians are s Gaussians), density fitting is exact:
+    E_J equals the 4-centre (ii|jj) energy computed from the closed form."""
+    a1, a2 = 0.5, 1.3
+    orb = I.Basis([I.Shell(0, 0, np.array([a1]), np.array([1.0])), I.Shell(0, 0, np.array([a2]), np.array([1.0]))])
+    aux = I.Basis([I.Shell(0, 0, np.array([e]), np.array([1.0])) for e in (2 * a1, a1 + a2, 2 * a2)])
+    xyz = np.zeros((1, 3))
+    S = O.overlap(orb, xyz)
+    C = I.orthonormalize(np.array([[1.0], [0.4]]), S)
+    r = O.dfjk(orb, aux, xyz, C)
+    # exact (ab|cd) for s primitives at one centre: 2 pi^2.5/(p q sqrt(p+q))
+    ex = np.array([a1, a2])
+    nrm = (2 * ex / np.pi) ** 0.75
+    D = C @ C.T
+    E = 0.0
+    for i in range(2):
+        for j in range(2):
+            for k in range(2):
+                for l in range(2):
+                    p, q = ex[i] + ex[j], ex[k] + ex[l]
+                    v = 2 * np.pi**2.5 / (p * q * np.sqrt(p + q)) * nrm[i] * nrm[j] * nrm[k] * nrm[l]
+                    E += 0.5 * D[i, j] * D[k, l] * v
+    assert r["E_J"] == pytest.approx(E, rel=1e-12)
+    assert r["E_K"] == pytest.approx(E, rel=1e-12)  # one orbital: K = J
+
+
+def test_water_golden():
+    """Stored values written by tests/golden/make_golden.py from this oracle;
+    they catch any later drift of the oracle's arithmetic."""
+    g = json.load(open(GOLDEN))
+    m, S, C, T, V = system("water")
+    r = O.dfjk(m.orb, m.aux, m.coords, C, T=T, V=V)
+    assert r["E_J"] == pytest.approx(g["E_J"], rel=1e-13)
+    assert r["E_K"] == pytest.approx(g["E_K"], rel=1e-13)
+    assert np.allclose(r["J"], np.array(g["J"]), rtol=0, atol=1e-13)
+    assert np.allclose(r["K"], np.array(g["K"]), rtol=0, atol=1e-13)
