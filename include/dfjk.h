@@ -1,0 +1,164 @@
+/*
+ * dfjk.h -- C ABI of the GB300 density-fitted Coulomb/exchange (DF-J/K) build.
+ *
+ * The method (paper: Introduction, contribution 1; Sec. "Dataset and
+ * Performance" on keeping intermediates resident in GPU memory; Sec.
+ * "Improved Interfaces to External Libraries" on tensor-core contractions):
+ * 3-centre integrals (P|mu nu) over contracted Cartesian Gaussians, whitened
+ * with the Cholesky factor of the 2-centre metric (P|Q) = L L^T into
+ * B = L^-1 (P|mu nu), then
+ *     rho_P = sum_{mu nu} B[P][mu][nu] D[mu][nu],    J = B^T rho,
+ *     X_P   = B_P C_occ,                             K = sum_P X_P X_P^T,
+ *     E_J   = Tr(D J) / 2,  E_K = Tr(D K) / 2,       D = C_occ C_occ^T.
+ * For one spin-orbital set D the restricted two-electron energy is
+ * 4 E_J - 2 E_K (E_K here is the positive exchange energy of D).
+ *
+ * Conventions.  Units are bohr and hartree.  Shells are Cartesian with
+ * 0 <= l <= 2; components are ordered x,y,z (l=1) and xx,xy,xz,yy,yz,zz (l=2);
+ * AO order is shell order, then component.  Every Cartesian component is
+ * normalised to unit self-overlap: primitive norm
+ * (2a/pi)^(3/4) (4a)^(l/2) / sqrt((2i-1)!!(2j-1)!!(2k-1)!!), and the contraction
+ * is rescaled so <chi|chi> = 1.  Matrices are row-major FP64.
+ *
+ * Errors.  Every entry point returns an int status (DFJK_OK = 0).  A detail
+ * message for the last failure on the calling thread is available from
+ * dfjk_last_error().  No C++ exception crosses this boundary and device code
+ * never traps: device-side failures (a non-positive Cholesky pivot, an
+ * expired bounded wait) are written to a status word that the host reads.
+ *
+ * Streams.  `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ * stream).  dfjk_build enqueues work and returns without synchronising;
+ * outputs are valid once the stream reaches that point.  dfjk_setup
+ * synchronises its stream twice (to size the screened pair list and to read
+ * the Cholesky status) and returns with the handle's data resident.
+ */
+#ifndef DFJK_H
+#define DFJK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  DFJK_OK = 0,
+  DFJK_ERR_ARG = 1,         /* invalid argument (null pointer, bad size)       */
+  DFJK_ERR_UNSUPPORTED = 2, /* l > 2, nprim > 8, or a precision not built     */
+  DFJK_ERR_NOT_PD = 3,      /* (P|Q) has a non-positive Cholesky pivot         */
+  DFJK_ERR_OOM = 4,         /* device allocation failed                        */
+  DFJK_ERR_BUDGET = 5,      /* resident data would exceed hbm_budget_bytes     */
+  DFJK_ERR_TIMEOUT = 6,     /* a bounded device wait expired                   */
+  DFJK_ERR_CUDA = 7,        /* a CUDA runtime call failed                      */
+  DFJK_ERR_STATE = 8        /* handle used in the wrong state (e.g. evicted)   */
+};
+
+/* One contracted Cartesian shell (host memory, caller-owned; copied by
+ * dfjk_setup).  coefs multiply *unnormalised* primitives; the library
+ * applies the normalisation described above.                                */
+typedef struct {
+  int32_t atom;  /* index into coords                                       */
+  int32_t l;     /* 0..2                                                    */
+  int32_t nprim; /* 1..8                                                    */
+  const double *exps;
+  const double *coefs;
+} dfjk_shell;
+
+typedef struct {
+  int32_t nshell;
+  const dfjk_shell *shells;
+} dfjk_basis;
+
+typedef enum {
+  DFJK_FP64 = 0, /* every step in FP64 on the FP64 pipe (the plain path)     */
+  DFJK_MIXED = 1 /* integrals, Cholesky and energies FP64; B stored FP32 and the
+                    whitening and J/K contractions on tensor cores with exact
+                    sliced BF16 products and FP64 recombination                */
+} dfjk_precision;
+
+typedef struct {
+  int32_t precision;       /* dfjk_precision                                 */
+  double schwarz_thresh;   /* drop shell pair ab if sqrt(max(ab|ab)) *
+                              max_P sqrt((P|P)) < thresh; default 1e-12       */
+  size_t hbm_budget_bytes; /* 0 = no limit; else setup fails with
+                              DFJK_ERR_BUDGET if resident data would exceed it */
+  int64_t timeout_iters;   /* iteration limit of bounded device waits        */
+  int32_t energies_on_host;/* 1: E_J/E_K pointers of dfjk_build are host
+                              memory (the call then synchronises the stream);
+                              0: device memory                               */
+} dfjk_options;
+
+typedef struct dfjk_ctx *dfjk_handle;
+
+/* Fills *opt with the defaults: DFJK_FP64, 1e-12, no budget, 1<<26, host
+ * energies.                                                                  */
+void dfjk_default_options(dfjk_options *opt);
+
+/* Steps a0-a5: validates and normalises the bases, builds the shell-pair list
+ * with Schwarz screening, the metric (P|Q), its Cholesky factor and inverse,
+ * the 3-centre integrals and the whitened tensor B, which stays resident on
+ * the current device until dfjk_destroy/dfjk_evict.
+ *   orb, aux : host shell lists (copied).  natom, coords: natom x 3 host doubles.
+ *   opt      : may be NULL (defaults).  out: receives the handle.
+ * Errors: DFJK_ERR_ARG, _UNSUPPORTED, _NOT_PD, _OOM, _BUDGET, _CUDA.           */
+int dfjk_setup(const dfjk_basis *orb, const dfjk_basis *aux, int32_t natom,
+               const double *coords, const dfjk_options *opt, void *stream,
+               dfjk_handle *out);
+
+/* Sizes of a handle: number of AOs, aux functions, screened shell pairs, and
+ * device bytes it holds resident.  Any output pointer may be NULL.          */
+int dfjk_query(dfjk_handle h, int32_t *nao, int32_t *naux, int32_t *npair_kept,
+               size_t *device_bytes);
+
+/* Steps a6-a9 for nset occupied-orbital sets.
+ *   C_occ : device, nset x nao x nocc, row-major FP64 (caller-owned).
+ *   J, K  : device, nset x nao x nao FP64, written in full (symmetric).
+ *   E_J, E_K : nset doubles each, host or device per opt.energies_on_host.
+ * Work buffers are owned by the handle and reused across calls; calls on one
+ * handle must therefore be ordered on a stream.                              */
+int dfjk_build(dfjk_handle h, int32_t nset, int32_t nocc, const double *C_occ,
+               double *J, double *K, double *E_J, double *E_K, void *stream);
+
+/* Overlap matrix S (device, nao x nao), computed by a device kernel; used to
+ * orthonormalise occupied orbitals.                                           */
+int dfjk_overlap(dfjk_handle h, double *S, void *stream);
+
+/* Frees B and the work buffers but keeps the host copy of the inputs, so a
+ * later dfjk_build recomputes steps a0-a5 first (resident-set eviction).     */
+int dfjk_evict(dfjk_handle h);
+
+/* Releases everything the handle owns.  NULL is accepted.                    */
+int dfjk_destroy(dfjk_handle h);
+
+const char *dfjk_status_string(int code);
+const char *dfjk_last_error(void);
+
+/* Number of kernels this library has launched in this process.             */
+uint64_t dfjk_launch_count(void);
+
+/* ---- diagnostic accessors (tests and parity checks) ---------------------- */
+
+/* F_m(T) for m = 0..mmax at n points: T device [n], F device [n][mmax+1].
+ * mmax <= 8.                                                                 */
+int dfjk_boys(int32_t mmax, int32_t n, const double *T, double *F, void *stream);
+
+/* Copies of resident intermediates, in user AO / aux order, device FP64:
+ *   V, L : naux x naux (L lower triangular, zero above the diagonal)
+ *   B    : naux x nao x nao (whitened tensor, expanded to FP64)
+ *   keep : nshell_orb x nshell_orb int32, 1 where the shell pair survived
+ *          Schwarz screening (symmetric)                                     */
+int dfjk_get_metric(dfjk_handle h, double *V, void *stream);
+int dfjk_get_cholesky(dfjk_handle h, double *L, void *stream);
+int dfjk_get_B(dfjk_handle h, double *B, void *stream);
+int dfjk_get_pair_mask(dfjk_handle h, int32_t *keep, void *stream);
+
+/* Raw 3-centre integrals T[P][mu][nu] (before whitening), device FP64
+ * naux x nao x nao; recomputed on demand.                                    */
+int dfjk_get_three_center(dfjk_handle h, double *T, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DFJK_H */

@@ -1,0 +1,809 @@
+// C ABI of the DF-J/K build: handle lifetime, setup (steps a0-a5) and build
+// (steps a6-a9) orchestration, diagnostic accessors and error plumbing.
+// Paper: Introduction, contribution 1 (density fitting: 3-centre integrals,
+// then tensor contractions) and Sec. "Dataset and Performance" (intermediates
+// of small and medium molecules kept resident in GPU memory).
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "boys.cuh"
+#include "common.cuh"
+#include "integrals.cuh"
+#include "linalg.cuh"
+#include "mixed.cuh"
+
+namespace dfjk {
+
+static thread_local std::string g_last_error;
+void set_error(const std::string &msg) { g_last_error = msg; }
+std::atomic<uint64_t> &launch_counter() {
+  static std::atomic<uint64_t> c{0};
+  return c;
+}
+
+// ---- device buffers -------------------------------------------------------------
+
+template <class T>
+struct DBuf {
+  T *p = nullptr;
+  size_t n = 0;
+  void alloc(size_t count) {
+    release();
+    if (count == 0) return;
+    cudaError_t e = cudaMalloc((void **)&p, count * sizeof(T));
+    if (e != cudaSuccess) {
+      p = nullptr;
+      cudaGetLastError();
+      throw Error{DFJK_ERR_OOM, "cudaMalloc of " + std::to_string(count * sizeof(T)) + " bytes failed"};
+    }
+    n = count;
+  }
+  void upload(const std::vector<T> &v, cudaStream_t st) {
+    alloc(v.size());
+    if (!v.empty()) DFJK_CUDA_CHECK(cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st));
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+  size_t bytes() const { return n * sizeof(T); }
+  ~DBuf() { release(); }
+};
+
+// ---- Boys table per device ---------------------------------------------------------
+
+const double *boys_table_device() {
+  static std::mutex mu;
+  static std::map<int, double *> tabs;
+  int dev = 0;
+  DFJK_CUDA_CHECK(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = tabs.find(dev);
+  if (it != tabs.end()) return it->second;
+  std::vector<double> h((size_t)BOYS_NPT * (BOYS_NCOL + 1));
+  boys_table_host(h.data());
+  double *d = nullptr;
+  DFJK_CUDA_CHECK(cudaMalloc(&d, h.size() * sizeof(double)));
+  DFJK_CUDA_CHECK(cudaMemcpy(d, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice));
+  tabs[dev] = d;
+  return d;
+}
+
+// ---- host-side basis ---------------------------------------------------------------
+
+struct HostBasis {
+  int nshell = 0, nfunc = 0;
+  std::vector<int> l, nprim, prim_off, func_off;
+  std::vector<double> exps, coefs_raw, coefs, center;  // coefs: normalised radial
+};
+
+static void read_basis(const dfjk_basis *b, int natom, const double *coords, HostBasis &hb,
+                       const char *what) {
+  if (!b || b->nshell < 0 || (b->nshell > 0 && !b->shells))
+    throw Error{DFJK_ERR_ARG, std::string(what) + ": null basis"};
+  hb = HostBasis();
+  hb.nshell = b->nshell;
+  for (int s = 0; s < b->nshell; ++s) {
+    const dfjk_shell &sh = b->shells[s];
+    if (sh.l < 0 || sh.l > 2) throw Error{DFJK_ERR_UNSUPPORTED, std::string(what) + ": l must be 0..2"};
+    if (sh.nprim < 1 || sh.nprim > 8)
+      throw Error{DFJK_ERR_UNSUPPORTED, std::string(what) + ": nprim must be 1..8"};
+    if (sh.atom < 0 || sh.atom >= natom) throw Error{DFJK_ERR_ARG, std::string(what) + ": atom index"};
+    if (!sh.exps || !sh.coefs) throw Error{DFJK_ERR_ARG, std::string(what) + ": null exps/coefs"};
+    hb.l.push_back(sh.l);
+    hb.nprim.push_back(sh.nprim);
+    hb.prim_off.push_back((int)hb.exps.size());
+    hb.func_off.push_back(hb.nfunc);
+    hb.nfunc += ncart(sh.l);
+    for (int d = 0; d < 3; ++d) {
+      const double x = coords[3 * sh.atom + d];
+      if (!std::isfinite(x)) throw Error{DFJK_ERR_ARG, "non-finite coordinate"};
+      hb.center.push_back(x);
+    }
+    // <chi|chi> with per-component normalised primitives:
+    // sum_kl d_k d_l (2 sqrt(a_k a_l)/(a_k + a_l))^(l + 3/2)
+    double ss = 0.0;
+    for (int k = 0; k < sh.nprim; ++k) {
+      if (!(sh.exps[k] > 0.0) || !std::isfinite(sh.exps[k]) || !std::isfinite(sh.coefs[k]))
+        throw Error{DFJK_ERR_ARG, std::string(what) + ": exponents must be positive and finite"};
+      for (int q = 0; q < sh.nprim; ++q) {
+        const double a = sh.exps[k], c = sh.exps[q];
+        ss += sh.coefs[k] * sh.coefs[q] * std::pow(2.0 * std::sqrt(a * c) / (a + c), sh.l + 1.5);
+      }
+    }
+    if (!(ss > 0.0)) throw Error{DFJK_ERR_ARG, std::string(what) + ": contraction has zero norm"};
+    const double scale = 1.0 / std::sqrt(ss);
+    for (int k = 0; k < sh.nprim; ++k) {
+      const double a = sh.exps[k];
+      hb.exps.push_back(a);
+      hb.coefs_raw.push_back(sh.coefs[k]);
+      hb.coefs.push_back(sh.coefs[k] * scale * std::pow(2.0 * a / M_PI, 0.75) * std::pow(4.0 * a, 0.5 * sh.l));
+    }
+  }
+}
+
+}  // namespace dfjk
+
+using namespace dfjk;
+
+struct dfjk_ctx {
+  int device = 0;
+  dfjk_options opt{};
+  int natom = 0;
+  std::vector<double> coords;
+  HostBasis orb, aux;
+  int nao = 0, naux = 0, naux_pad = 0;
+  bool resident = false;
+
+  // device: bases
+  DBuf<double> o_center, o_exps, o_coefs, a_center, a_exps, a_cdiv, a_g1;
+  DBuf<int> o_prim_off, o_nprim, o_func_off, a_prim_off, a_nprim, a_func_off;
+  DBuf<int> aux_cls[3];
+  std::vector<int> aux_cls_n = std::vector<int>(3, 0);
+  // shell pairs (global ids in class order)
+  std::vector<int> cls_begin;  // 7 entries: ss ps pp ds dp dd
+  std::vector<int> pa_h, pb_h, npp_h;
+  DBuf<int> pair_a, pair_b, pair_npp, pair_keep, kept;
+  DBuf<long long> pair_rec_off, pair_col;
+  DBuf<double> rec, q, scal;
+  std::vector<int> kept_h;
+  std::vector<long long> pair_col_h;
+  std::vector<int> kept_cls_begin;  // 7 entries into kept list
+  long long ncol = 0;
+  int npair_kept = 0;
+  DBuf<int> colmu, colnu;
+  // metric
+  DBuf<double> V, L, Linv, Dinv;
+  DBuf<int> status;
+  // whitened tensor: FP64 B[(mu nao + nu) ldb + P] or the mixed representation
+  DBuf<double> B;
+  long long ldb = 0;
+  MixedB mixedB;
+  // build workspace
+  int ws_nocc = -1;
+  DBuf<double> D, rho, rho_work, X, Kpart, en_work, e;
+  int ksplit = 1;
+  MixedWork mixedW;
+};
+
+namespace {
+
+cudaStream_t S(void *s) { return (cudaStream_t)s; }
+
+int fail(const Error &e) {
+  set_error(e.msg);
+  return e.code;
+}
+
+// Orbital shell pairs (l_a >= l_b; equal l: a >= b), grouped by class.
+void enumerate_pairs(dfjk_ctx *h) {
+  static const int cls[6][2] = {{0, 0}, {1, 0}, {1, 1}, {2, 0}, {2, 1}, {2, 2}};
+  h->cls_begin.assign(7, 0);
+  h->pa_h.clear();
+  h->pb_h.clear();
+  h->npp_h.clear();
+  for (int c = 0; c < 6; ++c) {
+    h->cls_begin[c] = (int)h->pa_h.size();
+    for (int a = 0; a < h->orb.nshell; ++a) {
+      if (h->orb.l[a] != cls[c][0]) continue;
+      for (int b = 0; b < h->orb.nshell; ++b) {
+        if (h->orb.l[b] != cls[c][1]) continue;
+        if (cls[c][0] == cls[c][1] && b > a) continue;
+        h->pa_h.push_back(a);
+        h->pb_h.push_back(b);
+        h->npp_h.push_back(h->orb.nprim[a] * h->orb.nprim[b]);
+      }
+    }
+  }
+  h->cls_begin[6] = (int)h->pa_h.size();
+}
+
+size_t resident_estimate(const dfjk_ctx *h) {
+  const size_t np2 = (size_t)h->naux_pad * h->naux_pad;
+  size_t b = (h->opt.precision == DFJK_MIXED) ? mixed_B_bytes(h->nao, h->naux_pad)
+                                              : (size_t)h->nao * h->nao * h->naux_pad * sizeof(double);
+  return b + 3 * np2 * sizeof(double);
+}
+
+void upload_bases(dfjk_ctx *h, cudaStream_t st) {
+  h->o_center.upload(h->orb.center, st);
+  h->o_exps.upload(h->orb.exps, st);
+  h->o_coefs.upload(h->orb.coefs, st);
+  h->o_prim_off.upload(h->orb.prim_off, st);
+  h->o_nprim.upload(h->orb.nprim, st);
+  h->o_func_off.upload(h->orb.func_off, st);
+  std::vector<double> cdiv(h->aux.exps.size()), g1(h->aux.exps.size());
+  for (size_t k = 0; k < h->aux.exps.size(); ++k) {
+    cdiv[k] = h->aux.coefs[k] / h->aux.exps[k];
+    g1[k] = 0.5 / h->aux.exps[k];
+  }
+  h->a_center.upload(h->aux.center, st);
+  h->a_exps.upload(h->aux.exps, st);
+  h->a_cdiv.upload(cdiv, st);
+  h->a_g1.upload(g1, st);
+  h->a_prim_off.upload(h->aux.prim_off, st);
+  h->a_nprim.upload(h->aux.nprim, st);
+  h->a_func_off.upload(h->aux.func_off, st);
+  for (int c = 0; c < 3; ++c) {
+    std::vector<int> lst;
+    for (int s = 0; s < h->aux.nshell; ++s)
+      if (h->aux.l[s] == c) lst.push_back(s);
+    h->aux_cls_n[c] = (int)lst.size();
+    h->aux_cls[c].upload(lst, st);
+  }
+}
+
+OrbArgs orb_args(dfjk_ctx *h) {
+  return OrbArgs{h->o_center.p, h->o_prim_off.p, h->o_nprim.p, h->o_exps.p, h->o_coefs.p, h->o_func_off.p};
+}
+AuxArgs aux_args(dfjk_ctx *h) {
+  return AuxArgs{h->a_center.p, h->a_prim_off.p, h->a_nprim.p, h->a_exps.p,
+                 h->a_cdiv.p,   h->a_g1.p,       h->a_func_off.p};
+}
+
+__global__ void pad_identity_kernel(double *V, int n, int npad, int ld) {
+  const int i = n + blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < npad) V[(long long)i * ld + i] = 1.0;
+}
+
+__global__ void zero_upper_kernel(double *A, int n, int ld) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)n * n) return;
+  const int i = (int)(e / n), j = (int)(e % n);
+  if (j > i) A[(long long)i * ld + j] = 0.0;
+}
+
+// Metric (P|Q) into V (naux_pad^2, identity on the padding).
+void compute_metric(dfjk_ctx *h, const double *tab, cudaStream_t st) {
+  const int np = h->naux_pad;
+  h->V.alloc((size_t)np * np);
+  DFJK_CUDA_CHECK(cudaMemsetAsync(h->V.p, 0, h->V.bytes(), st));
+  if (np > h->naux) {
+    pad_identity_kernel<<<ceil_div(np - h->naux, 64), 64, 0, st>>>(h->V.p, h->naux, np, np);
+    DFJK_LAUNCHED();
+  }
+  static const int cls[6][2] = {{0, 0}, {1, 0}, {1, 1}, {2, 0}, {2, 1}, {2, 2}};
+  for (int c = 0; c < 6; ++c) {
+    std::vector<int> sp, sq;
+    for (int p = 0; p < h->aux.nshell; ++p) {
+      if (h->aux.l[p] != cls[c][0]) continue;
+      for (int q = 0; q < h->aux.nshell; ++q) {
+        if (h->aux.l[q] != cls[c][1]) continue;
+        if (cls[c][0] == cls[c][1] && q > p) continue;
+        sp.push_back(p);
+        sq.push_back(q);
+      }
+    }
+    if (sp.empty()) continue;
+    DBuf<int> dp, dq;
+    dp.upload(sp, st);
+    dq.upload(sq, st);
+    MetricArgs a{(int)sp.size(), dp.p, dq.p, h->V.p, np};
+    launch_metric(cls[c][0], cls[c][1], a, aux_args(h), tab, st);
+    DFJK_CUDA_CHECK(cudaStreamSynchronize(st));  // dp/dq go out of scope
+  }
+}
+
+// Steps a0-a5 on the device.
+void make_resident(dfjk_ctx *h, cudaStream_t st) {
+  const double *tab = boys_table_device();
+  const int np = h->naux_pad;
+  if (h->opt.hbm_budget_bytes > 0 && resident_estimate(h) > h->opt.hbm_budget_bytes)
+    throw Error{DFJK_ERR_BUDGET, "resident data (" + std::to_string(resident_estimate(h)) +
+                                     " bytes) exceeds hbm_budget_bytes"};
+  upload_bases(h, st);
+  h->status.alloc(1);
+  DFJK_CUDA_CHECK(cudaMemsetAsync(h->status.p, 0, sizeof(int), st));
+
+  // a2: metric
+  compute_metric(h, tab, st);
+
+  // a0: shell pairs, primitive-pair records, Schwarz factors
+  enumerate_pairs(h);
+  const int npair = h->cls_begin[6];
+  std::vector<long long> rec_off(npair);
+  long long tot = 0;
+  static const int cls[6][2] = {{0, 0}, {1, 0}, {1, 1}, {2, 0}, {2, 1}, {2, 2}};
+  for (int c = 0; c < 6; ++c)
+    for (int i = h->cls_begin[c]; i < h->cls_begin[c + 1]; ++i) {
+      rec_off[i] = tot;
+      tot += (long long)h->npp_h[i] * pair_record_len(cls[c][0], cls[c][1]);
+    }
+  h->pair_a.upload(h->pa_h, st);
+  h->pair_b.upload(h->pb_h, st);
+  h->pair_npp.upload(h->npp_h, st);
+  h->pair_rec_off.upload(rec_off, st);
+  h->rec.alloc((size_t)std::max<long long>(tot, 1));
+  h->q.alloc(std::max(npair, 1));
+  for (int c = 0; c < 6; ++c) {
+    const int b0 = h->cls_begin[c], n = h->cls_begin[c + 1] - b0;
+    PairClassArgs a{n, h->pair_a.p + b0, h->pair_b.p + b0, h->pair_rec_off.p + b0, h->rec.p, h->q.p + b0};
+    launch_pair_kernel(cls[c][0], cls[c][1], a, orb_args(h), tab, st);
+  }
+  h->scal.alloc(1);
+  max_sqrt_diag(h->V.p, h->naux, np, h->scal.p, st);
+  h->pair_keep.alloc(std::max(npair, 1));
+  screen_pairs(h->q.p, npair, h->scal.p, h->opt.schwarz_thresh, h->pair_keep.p, st);
+  std::vector<int> keep(npair);
+  if (npair) DFJK_CUDA_CHECK(cudaMemcpyAsync(keep.data(), h->pair_keep.p, npair * sizeof(int), cudaMemcpyDeviceToHost, st));
+  DFJK_CUDA_CHECK(cudaStreamSynchronize(st));
+
+  // kept list, columns, column -> (mu, nu) map (host bookkeeping)
+  h->kept_h.clear();
+  h->kept_cls_begin.assign(7, 0);
+  h->pair_col_h.assign(npair, -1);
+  std::vector<int> cmu, cnu;
+  long long col = 0;
+  for (int c = 0; c < 6; ++c) {
+    h->kept_cls_begin[c] = (int)h->kept_h.size();
+    const int na = ncart(cls[c][0]), nb = ncart(cls[c][1]);
+    for (int i = h->cls_begin[c]; i < h->cls_begin[c + 1]; ++i) {
+      if (!keep[i]) continue;
+      h->kept_h.push_back(i);
+      h->pair_col_h[i] = col;
+      const int sa = h->pa_h[i], sb = h->pb_h[i];
+      for (int ca = 0; ca < na; ++ca)
+        for (int cb = 0; cb < nb; ++cb) {
+          const bool dup = (sa == sb) && (ca < cb);
+          cmu.push_back(dup ? -1 : h->orb.func_off[sa] + ca);
+          cnu.push_back(dup ? -1 : h->orb.func_off[sb] + cb);
+        }
+      col += na * nb;
+    }
+  }
+  h->kept_cls_begin[6] = (int)h->kept_h.size();
+  h->npair_kept = (int)h->kept_h.size();
+  h->ncol = col;
+  h->kept.upload(h->kept_h, st);
+  h->pair_col.upload(h->pair_col_h, st);
+  h->colmu.upload(cmu, st);
+  h->colnu.upload(cnu, st);
+
+  // a3: Cholesky and inverse of the metric
+  h->L.alloc((size_t)np * np);
+  DFJK_CUDA_CHECK(cudaMemcpyAsync(h->L.p, h->V.p, h->V.bytes(), cudaMemcpyDeviceToDevice, st));
+  h->Dinv.alloc((size_t)(np / 64) * 4096);
+  cholesky_f64(h->L.p, np, np, h->Dinv.p, h->status.p, nullptr, st);
+  zero_upper_kernel<<<(unsigned)(((long long)np * np + 255) / 256), 256, 0, st>>>(h->L.p, np, np);
+  DFJK_LAUNCHED();
+  h->Linv.alloc((size_t)np * np);
+  {
+    DBuf<double> work;
+    work.alloc((size_t)np * np);
+    tri_inverse_f64(h->L.p, np, np, h->Dinv.p, h->Linv.p, work.p, st);
+    DFJK_CUDA_CHECK(cudaStreamSynchronize(st));
+  }
+
+  // a4 + a5: 3-centre integrals in column slabs, whitened into B
+  const bool mixed = h->opt.precision == DFJK_MIXED;
+  if (!mixed) {
+    h->ldb = np;
+    h->B.alloc((size_t)h->nao * h->nao * np);
+    DFJK_CUDA_CHECK(cudaMemsetAsync(h->B.p, 0, h->B.bytes(), st));
+  } else {
+    mixed_alloc_B(h->mixedB, h->nao, np, st);
+  }
+  const long long slab_budget = 4LL << 30;  // bytes of one T slab
+  long long slab_cols = std::max<long long>(36, slab_budget / ((long long)np * 8));
+  slab_cols = std::min<long long>(slab_cols, std::max<long long>(h->ncol, 1));
+  DBuf<double> T;
+  T.alloc((size_t)slab_cols * np);
+  DFJK_CUDA_CHECK(cudaMemsetAsync(T.p, 0, T.bytes(), st));
+  int r0 = 0;
+  while (r0 < h->npair_kept) {
+    const long long c0 = h->pair_col_h[h->kept_h[r0]];
+    int r1 = r0;
+    while (r1 < h->npair_kept) {
+      const int g = h->kept_h[r1];
+      const int c = [&] { int k = 0; while (g >= h->cls_begin[k + 1]) ++k; return k; }();
+      const long long cend = h->pair_col_h[g] + ncart(cls[c][0]) * ncart(cls[c][1]);
+      if (cend - c0 > slab_cols) break;
+      ++r1;
+    }
+    const long long c1 = (r1 < h->npair_kept) ? h->pair_col_h[h->kept_h[r1]] : h->ncol;
+    for (int c = 0; c < 6; ++c) {
+      const int lo = std::max(r0, h->kept_cls_begin[c]), hi = std::min(r1, h->kept_cls_begin[c + 1]);
+      if (hi <= lo) continue;
+      for (int lc = 0; lc < 3; ++lc) {
+        Eri3cArgs a{h->kept.p + lo, hi - lo, h->pair_rec_off.p, h->pair_npp.p, h->pair_col.p, h->rec.p,
+                    h->aux_cls[lc].p, h->aux_cls_n[lc], T.p, c0, np};
+        launch_eri3c(cls[c][0], cls[c][1], lc, a, aux_args(h), tab, st);
+      }
+    }
+    if (!mixed) {
+      GemmArgs g;  // B[(mu,nu)][P] = sum_Q T[col][Q] Linv[P][Q]
+      g.M = (int)(c1 - c0); g.N = np; g.K = np;
+      g.A = T.p; g.sAm = np; g.sAk = 1;
+      g.B = h->Linv.p; g.sBn = np; g.sBk = 1;
+      g.k_upto_n = 1;
+      g.colmu = h->colmu.p + c0; g.colnu = h->colnu.p + c0;
+      g.nao = h->nao; g.ldo = h->ldb; g.out = h->B.p;
+      gemm_f64(g, st);
+    } else {
+      mixed_whiten_slab(h->mixedB, T.p, (int)(c1 - c0), np, h->Linv.p, h->colmu.p + c0,
+                        h->colnu.p + c0, h->nao, st);
+    }
+    r0 = r1;
+  }
+  int status = 0;
+  DFJK_CUDA_CHECK(cudaMemcpyAsync(&status, h->status.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+  DFJK_CUDA_CHECK(cudaStreamSynchronize(st));
+  if (status & STATUS_NOT_PD)
+    throw Error{DFJK_ERR_NOT_PD, "(P|Q) metric is not positive definite (non-positive Cholesky pivot)"};
+  h->resident = true;
+}
+
+void release_device(dfjk_ctx *h) {
+  h->B.release();
+  mixed_release_B(h->mixedB);
+  h->V.release();
+  h->L.release();
+  h->Linv.release();
+  h->Dinv.release();
+  h->rec.release();
+  h->q.release();
+  h->colmu.release();
+  h->colnu.release();
+  h->D.release();
+  h->rho.release();
+  h->rho_work.release();
+  h->X.release();
+  h->Kpart.release();
+  h->en_work.release();
+  h->e.release();
+  mixed_release_work(h->mixedW);
+  h->ws_nocc = -1;
+  h->resident = false;
+}
+
+void ensure_workspace(dfjk_ctx *h, int nocc, int nset) {
+  const size_t nao2 = (size_t)h->nao * h->nao;
+  if (h->ws_nocc < nocc || !h->D.p) {
+    h->D.alloc(nao2);
+    h->rho.alloc(h->naux_pad);
+    h->rho_work.alloc((size_t)128 * ceil_div(h->naux_pad, 256) * 256);
+    if (h->opt.precision != DFJK_MIXED) h->X.alloc((size_t)h->nao * h->naux_pad * nocc);
+    const int t = ceil_div(h->nao, 64);
+    const int tiles = t * (t + 1) / 2;
+    h->ksplit = std::max(1, std::min(64, ceil_div(4 * 152, tiles)));
+    h->Kpart.alloc(nao2 * h->ksplit);
+    h->en_work.alloc(2 * 256);
+    h->ws_nocc = nocc;
+  }
+  if (!h->e.p || h->e.n < (size_t)(2 * nset)) h->e.alloc(2 * nset);
+}
+
+__global__ void split_energies_kernel(const double *e, int nset, double *EJ, double *EK) {
+  const int s = threadIdx.x + blockIdx.x * blockDim.x;
+  if (s < nset) {
+    EJ[s] = e[2 * s];
+    EK[s] = e[2 * s + 1];
+  }
+}
+
+void build_fp64(dfjk_ctx *h, int nocc, const double *C, double *J, double *Kout, double *e,
+                cudaStream_t st) {
+  const int nao = h->nao, np = h->naux_pad;
+  GemmArgs d;  // D = C C^T
+  d.M = nao; d.N = nao; d.K = nocc;
+  d.A = C; d.sAm = nocc; d.sAk = 1;
+  d.B = C; d.sBn = nocc; d.sBk = 1;
+  d.C = h->D.p; d.sCm = nao; d.sCn = 1;
+  gemm_f64(d, st);
+  rho_gemv_f64(h->B.p, h->ldb, nao, np, h->D.p, h->rho.p, h->rho_work.p, 128, st);
+  j_gemv_f64(h->B.p, h->ldb, nao, np, h->rho.p, J, st);
+  GemmArgs x;  // X[mu][P][i] = sum_nu B[(mu,nu)][P] C[nu][i]
+  x.M = np; x.N = nocc; x.K = nao; x.batch = nao;
+  x.A = h->B.p; x.sAm = 1; x.sAk = h->ldb; x.sAb = (long long)nao * h->ldb;
+  x.B = C; x.sBn = 1; x.sBk = nocc; x.sBb = 0;
+  x.C = h->X.p; x.sCm = nocc; x.sCn = 1; x.sCb = (long long)np * nocc;
+  gemm_f64(x, st);
+  const long long kt = (long long)np * nocc;
+  GemmArgs k;  // K[mu][nu] = sum_(P,i) X[mu][(P,i)] X[nu][(P,i)]
+  k.M = nao; k.N = nao; k.K = (int)kt;
+  k.A = h->X.p; k.sAm = kt; k.sAk = 1;
+  k.B = h->X.p; k.sBn = kt; k.sBk = 1;
+  k.C = h->Kpart.p; k.sCm = nao; k.sCn = 1; k.sCb = (long long)nao * nao;
+  k.k_split = (int)((kt + h->ksplit - 1) / h->ksplit);
+  k.k_split = ((k.k_split + 15) / 16) * 16;
+  k.lower_only = 1;
+  gemm_f64(k, st);
+  reduce_sym_f64(h->Kpart.p, ceil_div(kt, k.k_split), nao, Kout, st);
+  energies_f64(h->D.p, J, Kout, nao, e, h->en_work.p, st);
+}
+
+}  // namespace
+
+extern "C" {
+
+void dfjk_default_options(dfjk_options *opt) {
+  if (!opt) return;
+  opt->precision = DFJK_FP64;
+  opt->schwarz_thresh = 1e-12;
+  opt->hbm_budget_bytes = 0;
+  opt->timeout_iters = 1LL << 26;
+  opt->energies_on_host = 1;
+}
+
+const char *dfjk_status_string(int code) {
+  switch (code) {
+    case DFJK_OK: return "ok";
+    case DFJK_ERR_ARG: return "invalid argument";
+    case DFJK_ERR_UNSUPPORTED: return "unsupported input";
+    case DFJK_ERR_NOT_PD: return "metric not positive definite";
+    case DFJK_ERR_OOM: return "out of device memory";
+    case DFJK_ERR_BUDGET: return "HBM budget exceeded";
+    case DFJK_ERR_TIMEOUT: return "bounded device wait expired";
+    case DFJK_ERR_CUDA: return "CUDA error";
+    case DFJK_ERR_STATE: return "invalid handle state";
+    default: return "unknown status";
+  }
+}
+
+const char *dfjk_last_error(void) { return g_last_error.c_str(); }
+
+uint64_t dfjk_launch_count(void) { return launch_counter().load(); }
+
+int dfjk_setup(const dfjk_basis *orb, const dfjk_basis *aux, int32_t natom, const double *coords,
+               const dfjk_options *opt, void *stream, dfjk_handle *out) {
+  if (!out) return fail(Error{DFJK_ERR_ARG, "out is null"});
+  *out = nullptr;
+  dfjk_ctx *h = nullptr;
+  try {
+    if (natom <= 0 || !coords) throw Error{DFJK_ERR_ARG, "natom/coords"};
+    h = new dfjk_ctx();
+    DFJK_CUDA_CHECK(cudaGetDevice(&h->device));
+    if (opt) h->opt = *opt;
+    else dfjk_default_options(&h->opt);
+    if (h->opt.precision != DFJK_FP64 && h->opt.precision != DFJK_MIXED)
+      throw Error{DFJK_ERR_UNSUPPORTED, "precision"};
+    if (!(h->opt.schwarz_thresh >= 0.0)) throw Error{DFJK_ERR_ARG, "schwarz_thresh"};
+    h->natom = natom;
+    h->coords.assign(coords, coords + 3 * (size_t)natom);
+    read_basis(orb, natom, coords, h->orb, "orbital basis");
+    read_basis(aux, natom, coords, h->aux, "aux basis");
+    h->nao = h->orb.nfunc;
+    h->naux = h->aux.nfunc;
+    if (h->nao == 0 || h->naux == 0) throw Error{DFJK_ERR_ARG, "empty basis"};
+    h->naux_pad = ((h->naux + 63) / 64) * 64;
+    make_resident(h, S(stream));
+    *out = h;
+    return DFJK_OK;
+  } catch (const Error &e) {
+    delete h;
+    return fail(e);
+  } catch (const std::exception &e) {
+    delete h;
+    return fail(Error{DFJK_ERR_CUDA, e.what()});
+  }
+}
+
+int dfjk_query(dfjk_handle h, int32_t *nao, int32_t *naux, int32_t *npair_kept, size_t *bytes) {
+  if (!h) return fail(Error{DFJK_ERR_ARG, "null handle"});
+  if (nao) *nao = h->nao;
+  if (naux) *naux = h->naux;
+  if (npair_kept) *npair_kept = h->npair_kept;
+  if (bytes) *bytes = h->B.bytes() + mixed_B_resident_bytes(h->mixedB) + h->V.bytes() +
+                      h->L.bytes() + h->Linv.bytes() + h->rec.bytes();
+  return DFJK_OK;
+}
+
+int dfjk_build(dfjk_handle h, int32_t nset, int32_t nocc, const double *C, double *J, double *K,
+               double *EJ, double *EK, void *stream) {
+  try {
+    if (!h) throw Error{DFJK_ERR_ARG, "null handle"};
+    if (nset < 1 || nocc < 1 || !C || !J || !K || !EJ || !EK) throw Error{DFJK_ERR_ARG, "build arguments"};
+    cudaStream_t st = S(stream);
+    DFJK_CUDA_CHECK(cudaSetDevice(h->device));
+    if (!h->resident) make_resident(h, st);
+    ensure_workspace(h, nocc, nset);
+    const size_t nao2 = (size_t)h->nao * h->nao;
+    for (int s = 0; s < nset; ++s) {
+      const double *Cs = C + (size_t)s * h->nao * nocc;
+      if (h->opt.precision == DFJK_MIXED)
+        mixed_build(h->mixedB, h->mixedW, h->nao, h->naux_pad, nocc, Cs, h->D.p, h->rho.p,
+                    h->rho_work.p, J + s * nao2, K + s * nao2, h->Kpart.p, h->ksplit, st);
+      else
+        build_fp64(h, nocc, Cs, J + s * nao2, K + s * nao2, h->e.p + 2 * s, st);
+      if (h->opt.precision == DFJK_MIXED)
+        energies_f64(h->D.p, J + s * nao2, K + s * nao2, h->nao, h->e.p + 2 * s, h->en_work.p, st);
+    }
+    if (h->opt.energies_on_host) {
+      std::vector<double> e(2 * nset);
+      DFJK_CUDA_CHECK(cudaMemcpyAsync(e.data(), h->e.p, e.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+      DFJK_CUDA_CHECK(cudaStreamSynchronize(st));
+      for (int s = 0; s < nset; ++s) {
+        EJ[s] = e[2 * s];
+        EK[s] = e[2 * s + 1];
+      }
+    } else {
+      split_energies_kernel<<<ceil_div(nset, 64), 64, 0, st>>>(h->e.p, nset, EJ, EK);
+      DFJK_LAUNCHED();
+    }
+    return DFJK_OK;
+  } catch (const Error &e) {
+    return fail(e);
+  }
+}
+
+int dfjk_overlap(dfjk_handle h, double *Sout, void *stream) {
+  try {
+    if (!h || !Sout) throw Error{DFJK_ERR_ARG, "overlap arguments"};
+    cudaStream_t st = S(stream);
+    if (!h->o_center.p) upload_bases(h, st);
+    static const int cls[6][2] = {{0, 0}, {1, 0}, {1, 1}, {2, 0}, {2, 1}, {2, 2}};
+    for (int c = 0; c < 6; ++c) {
+      std::vector<int> sa, sb;
+      for (int a = 0; a < h->orb.nshell; ++a)
+        for (int b = 0; b < h->orb.nshell; ++b)
+          if (h->orb.l[a] == cls[c][0] && h->orb.l[b] == cls[c][1] && (cls[c][0] != cls[c][1] || b <= a)) {
+            sa.push_back(a);
+            sb.push_back(b);
+          }
+      if (sa.empty()) continue;
+      DBuf<int> da, db;
+      da.upload(sa, st);
+      db.upload(sb, st);
+      OverlapArgs a{(int)sa.size(), da.p, db.p, Sout, h->nao};
+      launch_overlap(cls[c][0], cls[c][1], a, orb_args(h), st);
+      DFJK_CUDA_CHECK(cudaStreamSynchronize(st));
+    }
+    return DFJK_OK;
+  } catch (const Error &e) {
+    return fail(e);
+  }
+}
+
+int dfjk_evict(dfjk_handle h) {
+  if (!h) return fail(Error{DFJK_ERR_ARG, "null handle"});
+  try {
+    DFJK_CUDA_CHECK(cudaSetDevice(h->device));
+    DFJK_CUDA_CHECK(cudaDeviceSynchronize());
+    release_device(h);
+    return DFJK_OK;
+  } catch (const Error &e) {
+    return fail(e);
+  }
+}
+
+int dfjk_destroy(dfjk_handle h) {
+  if (!h) return DFJK_OK;
+  cudaSetDevice(h->device);
+  cudaDeviceSynchronize();
+  delete h;
+  return DFJK_OK;
+}
+
+int dfjk_boys(int32_t mmax, int32_t n, const double *T, double *F, void *stream) {
+  try {
+    if (n < 0 || (n > 0 && (!T || !F))) throw Error{DFJK_ERR_ARG, "boys arguments"};
+    launch_boys(mmax, n, T, F, boys_table_device(), S(stream));
+    return DFJK_OK;
+  } catch (const Error &e) {
+    return fail(e);
+  }
+}
+
+int dfjk_get_metric(dfjk_handle h, double *Vout, void *stream) {
+  try {
+    if (!h || !Vout) throw Error{DFJK_ERR_ARG, "null argument"};
+    if (!h->resident) throw Error{DFJK_ERR_STATE, "handle evicted"};
+    DFJK_CUDA_CHECK(cudaMemcpy2DAsync(Vout, h->naux * 8, h->V.p, h->naux_pad * 8, h->naux * 8, h->naux,
+                                      cudaMemcpyDeviceToDevice, S(stream)));
+    return DFJK_OK;
+  } catch (const Error &e) {
+    return fail(e);
+  }
+}
+
+int dfjk_get_cholesky(dfjk_handle h, double *Lout, void *stream) {
+  try {
+    if (!h || !Lout) throw Error{DFJK_ERR_ARG, "null argument"};
+    if (!h->resident) throw Error{DFJK_ERR_STATE, "handle evicted"};
+    DFJK_CUDA_CHECK(cudaMemcpy2DAsync(Lout, h->naux * 8, h->L.p, h->naux_pad * 8, h->naux * 8, h->naux,
+                                      cudaMemcpyDeviceToDevice, S(stream)));
+    return DFJK_OK;
+  } catch (const Error &e) {
+    return fail(e);
+  }
+}
+
+int dfjk_get_B(dfjk_handle h, double *Bout, void *stream) {
+  try {
+    if (!h || !Bout) throw Error{DFJK_ERR_ARG, "null argument"};
+    if (!h->resident) throw Error{DFJK_ERR_STATE, "handle evicted"};
+    cudaStream_t st = S(stream);
+    std::vector<int> ident(h->naux);
+    for (int i = 0; i < h->naux; ++i) ident[i] = i;
+    DBuf<int> perm;
+    perm.upload(ident, st);
+    if (h->opt.precision == DFJK_MIXED) {
+      DBuf<double> tmp;
+      tmp.alloc((size_t)h->nao * h->nao * h->naux_pad);
+      mixed_expand_B(h->mixedB, h->nao, h->naux_pad, tmp.p, st);
+      gather_B_f64(tmp.p, h->naux_pad, h->nao, perm.p, h->naux, Bout, st);
+      DFJK_CUDA_CHECK(cudaStreamSynchronize(st));
+    } else {
+      gather_B_f64(h->B.p, h->ldb, h->nao, perm.p, h->naux, Bout, st);
+      DFJK_CUDA_CHECK(cudaStreamSynchronize(st));
+    }
+    return DFJK_OK;
+  } catch (const Error &e) {
+    return fail(e);
+  }
+}
+
+int dfjk_get_pair_mask(dfjk_handle h, int32_t *keep, void *stream) {
+  try {
+    if (!h || !keep) throw Error{DFJK_ERR_ARG, "null argument"};
+    const int ns = h->orb.nshell;
+    std::vector<int> m((size_t)ns * ns, 0);
+    for (int i = 0; i < (int)h->pa_h.size(); ++i)
+      if (h->pair_col_h[i] >= 0) {
+        m[(size_t)h->pa_h[i] * ns + h->pb_h[i]] = 1;
+        m[(size_t)h->pb_h[i] * ns + h->pa_h[i]] = 1;
+      }
+    DFJK_CUDA_CHECK(cudaMemcpyAsync(keep, m.data(), m.size() * sizeof(int), cudaMemcpyHostToDevice, S(stream)));
+    DFJK_CUDA_CHECK(cudaStreamSynchronize(S(stream)));
+    return DFJK_OK;
+  } catch (const Error &e) {
+    return fail(e);
+  }
+}
+
+}  // extern "C"
+
+namespace {
+__global__ void scatter_T_kernel(const double *T, int ldT, long long ncol, int naux, const int *colmu,
+                                 const int *colnu, int nao, double *out) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= ncol * naux) return;
+  const long long c = e / naux;
+  const int P = (int)(e % naux);
+  const int mu = colmu[c], nu = colnu[c];
+  if (mu < 0) return;
+  const double v = T[c * ldT + P];
+  const long long n2 = (long long)nao * nao;
+  out[P * n2 + (long long)mu * nao + nu] = v;
+  out[P * n2 + (long long)nu * nao + mu] = v;
+}
+}  // namespace
+
+extern "C" int dfjk_get_three_center(dfjk_handle h, double *Tout, void *stream) {
+  try {
+    if (!h || !Tout) throw Error{DFJK_ERR_ARG, "null argument"};
+    if (!h->resident) throw Error{DFJK_ERR_STATE, "handle evicted"};
+    cudaStream_t st = S(stream);
+    const int np = h->naux_pad;
+    const double *tab = boys_table_device();
+    DBuf<double> T;
+    T.alloc((size_t)std::max<long long>(h->ncol, 1) * np);
+    DFJK_CUDA_CHECK(cudaMemsetAsync(T.p, 0, T.bytes(), st));
+    DFJK_CUDA_CHECK(cudaMemsetAsync(Tout, 0, sizeof(double) * (size_t)h->naux * h->nao * h->nao, st));
+    static const int cls[6][2] = {{0, 0}, {1, 0}, {1, 1}, {2, 0}, {2, 1}, {2, 2}};
+    for (int c = 0; c < 6; ++c) {
+      const int lo = h->kept_cls_begin[c], hi = h->kept_cls_begin[c + 1];
+      if (hi <= lo) continue;
+      for (int lc = 0; lc < 3; ++lc) {
+        Eri3cArgs a{h->kept.p + lo, hi - lo, h->pair_rec_off.p, h->pair_npp.p, h->pair_col.p, h->rec.p,
+                    h->aux_cls[lc].p, h->aux_cls_n[lc], T.p, 0, np};
+        launch_eri3c(cls[c][0], cls[c][1], lc, a, aux_args(h), tab, st);
+      }
+    }
+    const long long n = h->ncol * h->naux;
+    if (n > 0) {
+      scatter_T_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(T.p, np, h->ncol, h->naux, h->colmu.p,
+                                                                     h->colnu.p, h->nao, Tout);
+      DFJK_LAUNCHED();
+    }
+    DFJK_CUDA_CHECK(cudaStreamSynchronize(st));
+    return DFJK_OK;
+  } catch (const Error &e) {
+    return fail(e);
+  }
+}

@@ -1,0 +1,485 @@
+// FP64 dense kernels of the DF-J/K build: a generic strided GEMM (64x64x16
+// tiles, 4x4 outputs per thread), blocked Cholesky and triangular inverse of
+// the metric, the two streaming GEMVs of J (rho = B vec(D), J = B^T rho) and
+// deterministic reductions.
+//
+// Paper: Introduction, contribution 1 (after the 3-centre integrals, density
+// fitting is tensor operations) and the accuracy passage of the PySCF
+// compatibility section (the fitting solve).  On this GPU FP64 runs at about
+// 1.2 TFLOP/s, 1/62 of FP32, so these SIMT kernels are bound by the FP64 pipe
+// at any reasonable tiling; they are the plain-FP64 reference path.
+#include <algorithm>
+#include <cmath>
+
+#include "common.cuh"
+#include "linalg.cuh"
+
+namespace dfjk {
+
+constexpr int GBM = 64, GBN = 64, GBK = 16;
+
+template <bool A_KC, bool B_KC, bool SCATTER>
+__global__ void __launch_bounds__(256) gemm_f64_kernel(GemmArgs g) {
+  __shared__ double As[GBK][GBM + 1];
+  __shared__ double Bs[GBK][GBN + 1];
+  const int m0 = blockIdx.y * GBM, n0 = blockIdx.x * GBN;
+  if (g.lower_only && n0 > m0 + GBM - 1) return;
+  const int z = blockIdx.z;
+  const double *A = g.A, *B = g.B;
+  double *C = g.C;
+  long long kbeg = 0, kend = g.K;
+  if (g.k_split > 0) {
+    kbeg = (long long)z * g.k_split;
+    kend = min((long long)g.K, kbeg + g.k_split);
+    C += z * g.sCb;
+  } else {
+    A += z * g.sAb;
+    B += z * g.sBb;
+    C += z * g.sCb;
+  }
+  if (g.k_upto_n) kend = min(kend, (long long)(n0 + GBN));
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  double acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+
+  for (long long k0 = kbeg; k0 < kend; k0 += GBK) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int e = tid + i * 256;
+      const int mm = A_KC ? (e >> 4) : (e & 63);
+      const int kk = A_KC ? (e & 15) : (e >> 6);
+      const long long gm = m0 + mm, gk = k0 + kk;
+      As[kk][mm] = (gm < g.M && gk < kend) ? A[gm * g.sAm + gk * g.sAk] : 0.0;
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int e = tid + i * 256;
+      const int nn = B_KC ? (e >> 4) : (e & 63);
+      const int kk = B_KC ? (e & 15) : (e >> 6);
+      const long long gn = n0 + nn, gk = k0 + kk;
+      Bs[kk][nn] = (gn < g.N && gk < kend) ? B[gn * g.sBn + gk * g.sBk] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < GBK; ++kk) {
+      double a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int m = m0 + ty * 4 + i;
+    if (m >= g.M) continue;
+    if (SCATTER) {
+      const int mu = g.colmu[m], nu = g.colnu[m];
+      if (mu < 0) continue;
+      double *o1 = g.out + ((long long)mu * g.nao + nu) * g.ldo;
+      double *o2 = g.out + ((long long)nu * g.nao + mu) * g.ldo;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int n = n0 + tx * 4 + j;
+        if (n < g.N) {
+          o1[n] = acc[i][j];
+          if (mu != nu) o2[n] = acc[i][j];
+        }
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int n = n0 + tx * 4 + j;
+        if (n >= g.N) continue;
+        double *c = C + m * g.sCm + n * g.sCn;
+        *c = (g.beta != 0.0) ? fma(g.alpha, acc[i][j], g.beta * *c) : g.alpha * acc[i][j];
+      }
+    }
+  }
+}
+
+void gemm_f64(const GemmArgs &g, cudaStream_t st) {
+  if (g.M <= 0 || g.N <= 0) return;
+  const int nz = g.k_split > 0 ? ceil_div(g.K, g.k_split) : g.batch;
+  if (nz <= 0) return;
+  dim3 grid(ceil_div(g.N, GBN), ceil_div(g.M, GBM), nz);
+  if (grid.y > 65535 || grid.z > 65535) throw Error{DFJK_ERR_ARG, "gemm grid too large"};
+  const bool akc = g.sAk == 1, bkc = g.sBk == 1, sc = g.out != nullptr;
+  if (sc) {
+    if (akc && bkc) gemm_f64_kernel<true, true, true><<<grid, 256, 0, st>>>(g);
+    else throw Error{DFJK_ERR_ARG, "scatter gemm needs K-contiguous operands"};
+  } else if (akc && bkc) {
+    gemm_f64_kernel<true, true, false><<<grid, 256, 0, st>>>(g);
+  } else if (akc && !bkc) {
+    gemm_f64_kernel<true, false, false><<<grid, 256, 0, st>>>(g);
+  } else if (!akc && bkc) {
+    gemm_f64_kernel<false, true, false><<<grid, 256, 0, st>>>(g);
+  } else {
+    gemm_f64_kernel<false, false, false><<<grid, 256, 0, st>>>(g);
+  }
+  DFJK_LAUNCHED();
+}
+
+// ---- Cholesky -------------------------------------------------------------------
+
+// Factors the 64x64 lower block at A in place (upper part zeroed) and writes
+// its inverse (lower triangular) to Dinv.  A non-positive or non-finite pivot
+// sets STATUS_NOT_PD and continues with pivot 1 so no NaN spreads.
+__global__ void __launch_bounds__(256) potrf_diag_kernel(double *A, int lda, double *Dinv,
+                                                         int *status) {
+  __shared__ double a[64][65];
+  const int tid = threadIdx.x;
+  for (int e = tid; e < 64 * 64; e += 256) {
+    const int i = e >> 6, j = e & 63;
+    a[i][j] = (j <= i) ? A[(long long)i * lda + j] : 0.0;
+  }
+  __syncthreads();
+  for (int j = 0; j < 64; ++j) {
+    if (tid == 0) {
+      double d = a[j][j];
+      if (!(d > 0.0) || !isfinite(d)) {
+        atomicOr(status, STATUS_NOT_PD);
+        d = 1.0;
+      }
+      a[j][j] = sqrt(d);
+    }
+    __syncthreads();
+    const double ljj = a[j][j];
+    for (int i = j + 1 + tid; i < 64; i += 256) a[i][j] /= ljj;
+    __syncthreads();
+    const int m = 63 - j;  // trailing size
+    for (int e = tid; e < m * m; e += 256) {
+      const int i = j + 1 + e / m, c = j + 1 + e % m;
+      if (c <= i) a[i][c] = fma(-a[i][j], a[c][j], a[i][c]);
+    }
+    __syncthreads();
+  }
+  if (tid < 64) {  // column tid of the inverse by forward substitution
+    const int c = tid;
+    double x[64];
+    for (int i = 0; i < 64; ++i) x[i] = 0.0;
+    x[c] = 1.0 / a[c][c];
+    for (int i = c + 1; i < 64; ++i) {
+      double s = 0.0;
+      for (int k = c; k < i; ++k) s = fma(a[i][k], x[k], s);
+      x[i] = -s / a[i][i];
+    }
+    for (int i = 0; i < 64; ++i) Dinv[i * 64 + c] = x[i];
+  }
+  for (int e = tid; e < 64 * 64; e += 256) {
+    const int i = e >> 6, j = e & 63;
+    A[(long long)i * lda + j] = a[i][j];
+  }
+}
+
+void cholesky_f64(double *A, int n, int lda, double *Dinv, int *status, double *work,
+                  cudaStream_t st) {
+  (void)work;
+  const int nb = n / 64;
+  for (int k = 0; k < nb; ++k) {
+    double *Akk = A + (long long)k * 64 * lda + k * 64;
+    potrf_diag_kernel<<<1, 256, 0, st>>>(Akk, lda, Dinv + (long long)k * 4096, status);
+    DFJK_LAUNCHED();
+    const int rows = n - (k + 1) * 64;
+    if (rows <= 0) continue;
+    double *panel = A + (long long)(k + 1) * 64 * lda + k * 64;
+    GemmArgs p;  // L_ik = A_ik Dinv_k^T, in place (one 64-wide tile owns its rows)
+    p.M = rows; p.N = 64; p.K = 64;
+    p.A = panel; p.sAm = lda; p.sAk = 1;
+    p.B = Dinv + (long long)k * 4096; p.sBn = 64; p.sBk = 1;
+    p.C = panel; p.sCm = lda; p.sCn = 1;
+    gemm_f64(p, st);
+    GemmArgs t;  // A_ij -= L_ik L_jk^T on the trailing lower triangle
+    t.M = rows; t.N = rows; t.K = 64;
+    t.A = panel; t.sAm = lda; t.sAk = 1;
+    t.B = panel; t.sBn = lda; t.sBk = 1;
+    t.C = A + (long long)(k + 1) * 64 * (lda + 1); t.sCm = lda; t.sCn = 1;
+    t.alpha = -1.0; t.beta = 1.0; t.lower_only = 1;
+    gemm_f64(t, st);
+  }
+}
+
+__global__ void place_diag_blocks(double *Linv, int ld, const double *Dinv, int nb) {
+  const int b = blockIdx.x;
+  for (int e = threadIdx.x; e < 4096; e += blockDim.x) {
+    const int i = e >> 6, j = e & 63;
+    Linv[((long long)b * 64 + i) * ld + b * 64 + j] = Dinv[(long long)b * 4096 + e];
+  }
+}
+
+static void tri_inv_rec(const double *L, int ld, double *Linv, double *work, int lo, int hi,
+                        cudaStream_t st) {
+  if (hi - lo <= 64) return;
+  const int half = (hi - lo) / 2;
+  const int mid = lo + ((half + 63) / 64) * 64;
+  tri_inv_rec(L, ld, Linv, work, lo, mid, st);
+  tri_inv_rec(L, ld, Linv, work, mid, hi, st);
+  const int n1 = mid - lo, n2 = hi - mid;
+  GemmArgs a;  // work = L21 Linv11   (n2 x n1)
+  a.M = n2; a.N = n1; a.K = n1;
+  a.A = L + (long long)mid * ld + lo; a.sAm = ld; a.sAk = 1;
+  a.B = Linv + (long long)lo * ld + lo; a.sBn = 1; a.sBk = ld;
+  a.C = work; a.sCm = n1; a.sCn = 1;
+  gemm_f64(a, st);
+  GemmArgs b;  // Linv21 = -Linv22 work
+  b.M = n2; b.N = n1; b.K = n2;
+  b.A = Linv + (long long)mid * ld + mid; b.sAm = ld; b.sAk = 1;
+  b.B = work; b.sBn = 1; b.sBk = n1;
+  b.C = Linv + (long long)mid * ld + lo; b.sCm = ld; b.sCn = 1;
+  b.alpha = -1.0;
+  gemm_f64(b, st);
+}
+
+void tri_inverse_f64(const double *L, int n, int ld, const double *Dinv, double *Linv,
+                     double *work, cudaStream_t st) {
+  DFJK_CUDA_CHECK(cudaMemsetAsync(Linv, 0, sizeof(double) * (size_t)n * ld, st));
+  const int nb = n / 64;
+  place_diag_blocks<<<nb, 256, 0, st>>>(Linv, ld, Dinv, nb);
+  DFJK_LAUNCHED();
+  tri_inv_rec(L, ld, Linv, work, 0, n, st);
+}
+
+// ---- J: rho = B vec(D), J = B^T rho ------------------------------------------------
+
+__device__ __forceinline__ void tri_row(long long r, int &mu, int &nu) {
+  int m = (int)((sqrt(8.0 * (double)r + 1.0) - 1.0) * 0.5);
+  while ((long long)m * (m + 1) / 2 > r) --m;
+  while ((long long)(m + 1) * (m + 2) / 2 <= r) ++m;
+  mu = m;
+  nu = (int)(r - (long long)m * (m + 1) / 2);
+}
+
+__global__ void __launch_bounds__(256) rho_partial_kernel(const double *__restrict__ B,
+                                                          long long ldb, int nao, int naux,
+                                                          const double *__restrict__ D,
+                                                          double *__restrict__ work, int ldw,
+                                                          long long rows_per) {
+  const int P = blockIdx.x * 256 + threadIdx.x;
+  const long long nrows = (long long)nao * (nao + 1) / 2;
+  const long long r0 = (long long)blockIdx.y * rows_per;
+  const long long r1 = min(nrows, r0 + rows_per);
+  double acc = 0.0;
+  if (r0 < r1) {
+    int mu, nu;
+    tri_row(r0, mu, nu);
+    for (long long r = r0; r < r1; ++r) {
+      const double w = D[(long long)mu * nao + nu] * (mu == nu ? 1.0 : 2.0);
+      if (P < naux) acc = fma(w, B[((long long)mu * nao + nu) * ldb + P], acc);
+      if (++nu > mu) {
+        ++mu;
+        nu = 0;
+      }
+    }
+  }
+  if (P < ldw) work[(long long)blockIdx.y * ldw + P] = acc;
+}
+
+__global__ void column_sum_kernel(const double *__restrict__ work, int ldw, int nrow, int n,
+                                  double *__restrict__ out) {
+  const int P = blockIdx.x * blockDim.x + threadIdx.x;
+  if (P >= n) return;
+  double s = 0.0;
+  for (int r = 0; r < nrow; ++r) s += work[(long long)r * ldw + P];
+  out[P] = s;
+}
+
+void rho_gemv_f64(const double *B, long long ldb, int nao, int naux, const double *D,
+                  double *rho, double *work, int nchunk, cudaStream_t st) {
+  const long long nrows = (long long)nao * (nao + 1) / 2;
+  const long long rows_per = (nrows + nchunk - 1) / nchunk;
+  const int gx = ceil_div(naux, 256), ldw = gx * 256;
+  rho_partial_kernel<<<dim3(gx, nchunk), 256, 0, st>>>(B, ldb, nao, naux, D, work, ldw, rows_per);
+  DFJK_LAUNCHED();
+  column_sum_kernel<<<ceil_div(naux, 256), 256, 0, st>>>(work, ldw, nchunk, naux, rho);
+  DFJK_LAUNCHED();
+}
+
+__global__ void __launch_bounds__(256) j_gemv_kernel(const double *__restrict__ B, long long ldb,
+                                                     int nao, int naux,
+                                                     const double *__restrict__ rho,
+                                                     double *__restrict__ J) {
+  const long long r = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  const long long nrows = (long long)nao * (nao + 1) / 2;
+  if (r >= nrows) return;
+  int mu, nu;
+  tri_row(r, mu, nu);
+  const double *row = B + ((long long)mu * nao + nu) * ldb;
+  double s = 0.0;
+  for (int P = lane; P < naux; P += 32) s = fma(row[P], __ldg(rho + P), s);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) {
+    J[(long long)mu * nao + nu] = s;
+    J[(long long)nu * nao + mu] = s;
+  }
+}
+
+void j_gemv_f64(const double *B, long long ldb, int nao, int naux, const double *rho, double *J,
+                cudaStream_t st) {
+  const long long nrows = (long long)nao * (nao + 1) / 2;
+  j_gemv_kernel<<<(unsigned)((nrows + 7) / 8), 256, 0, st>>>(B, ldb, nao, naux, rho, J);
+  DFJK_LAUNCHED();
+}
+
+// ---- reductions -----------------------------------------------------------------------
+
+__global__ void reduce_sym_kernel(const double *__restrict__ part, int nsplit, int n,
+                                  double *__restrict__ out) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)n * n) return;
+  const int mu = (int)(e / n), nu = (int)(e % n);
+  if (nu > mu) return;
+  double s = 0.0;
+  for (int k = 0; k < nsplit; ++k) s += part[(long long)k * n * n + e];
+  out[e] = s;
+  out[(long long)nu * n + mu] = s;
+}
+
+void reduce_sym_f64(const double *part, int nsplit, int n, double *out, cudaStream_t st) {
+  const long long n2 = (long long)n * n;
+  reduce_sym_kernel<<<(unsigned)((n2 + 255) / 256), 256, 0, st>>>(part, nsplit, n, out);
+  DFJK_LAUNCHED();
+}
+
+constexpr int EN_BLOCKS = 256;
+
+__global__ void __launch_bounds__(256) energy_partial_kernel(const double *__restrict__ D,
+                                                             const double *__restrict__ J,
+                                                             const double *__restrict__ K,
+                                                             long long n2, double *work) {
+  __shared__ double sj[256], sk[256];
+  double aj = 0.0, ak = 0.0;
+  for (long long e = (long long)blockIdx.x * 256 + threadIdx.x; e < n2; e += (long long)EN_BLOCKS * 256) {
+    aj = fma(D[e], J[e], aj);
+    ak = fma(D[e], K[e], ak);
+  }
+  sj[threadIdx.x] = aj;
+  sk[threadIdx.x] = ak;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      sj[threadIdx.x] += sj[threadIdx.x + s];
+      sk[threadIdx.x] += sk[threadIdx.x + s];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    work[2 * blockIdx.x] = sj[0];
+    work[2 * blockIdx.x + 1] = sk[0];
+  }
+}
+
+__global__ void energy_final_kernel(const double *__restrict__ work, double *e) {
+  __shared__ double sj[EN_BLOCKS], sk[EN_BLOCKS];
+  sj[threadIdx.x] = work[2 * threadIdx.x];
+  sk[threadIdx.x] = work[2 * threadIdx.x + 1];
+  __syncthreads();
+  for (int s = EN_BLOCKS / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      sj[threadIdx.x] += sj[threadIdx.x + s];
+      sk[threadIdx.x] += sk[threadIdx.x + s];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    e[0] = 0.5 * sj[0];
+    e[1] = 0.5 * sk[0];
+  }
+}
+
+void energies_f64(const double *D, const double *J, const double *K, int n, double *e,
+                  double *work, cudaStream_t st) {
+  energy_partial_kernel<<<EN_BLOCKS, 256, 0, st>>>(D, J, K, (long long)n * n, work);
+  DFJK_LAUNCHED();
+  energy_final_kernel<<<1, EN_BLOCKS, 0, st>>>(work, e);
+  DFJK_LAUNCHED();
+}
+
+__global__ void max_sqrt_diag_kernel(const double *V, int n, int ld, double *out) {
+  __shared__ double s[256];
+  double m = 0.0;
+  for (int i = threadIdx.x; i < n; i += 256) m = fmax(m, sqrt(fmax(V[(long long)i * ld + i], 0.0)));
+  s[threadIdx.x] = m;
+  __syncthreads();
+  for (int k = 128; k > 0; k >>= 1) {
+    if (threadIdx.x < k) s[threadIdx.x] = fmax(s[threadIdx.x], s[threadIdx.x + k]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = s[0];
+}
+
+void max_sqrt_diag(const double *V, int n, int ld, double *out, cudaStream_t st) {
+  max_sqrt_diag_kernel<<<1, 256, 0, st>>>(V, n, ld, out);
+  DFJK_LAUNCHED();
+}
+
+__global__ void screen_kernel(const double *q, int n, const double *maxdiag, double thresh,
+                              int *keep) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) keep[i] = (q[i] * (*maxdiag) >= thresh) ? 1 : 0;
+}
+
+void screen_pairs(const double *q, int n, const double *maxdiag, double thresh, int *keep,
+                  cudaStream_t st) {
+  if (n == 0) return;
+  screen_kernel<<<ceil_div(n, 256), 256, 0, st>>>(q, n, maxdiag, thresh, keep);
+  DFJK_LAUNCHED();
+}
+
+__global__ void fill_kernel(double *p, long long n, double v) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    p[i] = v;
+}
+
+void fill_f64(double *p, long long n, double v, cudaStream_t st) {
+  if (n == 0) return;
+  fill_kernel<<<(unsigned)std::min<long long>((n + 255) / 256, 4096), 256, 0, st>>>(p, n, v);
+  DFJK_LAUNCHED();
+}
+
+__global__ void gather2d_kernel(const double *in, long long ldi, const int *pr, const int *pc,
+                                int nr, int nc, double *out, long long ldo) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)nr * nc) return;
+  const int i = (int)(e / nc), j = (int)(e % nc);
+  out[i * ldo + j] = in[(long long)pr[i] * ldi + pc[j]];
+}
+
+void gather2d_f64(const double *in, long long ldi, const int *perm_r, const int *perm_c, int nr,
+                  int nc, double *out, long long ldo, cudaStream_t st) {
+  const long long n = (long long)nr * nc;
+  if (n == 0) return;
+  gather2d_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(in, ldi, perm_r, perm_c, nr, nc, out, ldo);
+  DFJK_LAUNCHED();
+}
+
+__global__ void gather_B_kernel(const double *Bint, long long ldb, int nao, const int *perm,
+                                int naux, double *out) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long n2 = (long long)nao * nao;
+  if (e >= n2 * naux) return;
+  const int P = (int)(e / n2);
+  const long long mn = e % n2;
+  out[e] = Bint[mn * ldb + perm[P]];
+}
+
+void gather_B_f64(const double *Bint, long long ldb, int nao, const int *perm, int naux,
+                  double *out, cudaStream_t st) {
+  const long long n = (long long)nao * nao * naux;
+  if (n == 0) return;
+  gather_B_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(Bint, ldb, nao, perm, naux, out);
+  DFJK_LAUNCHED();
+}
+
+}  // namespace dfjk

@@ -1,0 +1,69 @@
+// FP64 dense kernels of the DF-J/K build (linalg.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace dfjk {
+
+// C[b](m,n) = alpha sum_k A[b](m,k) B[b](n,k) + beta C[b](m,n), FP64, with
+// element (m,k) of A at A + b sAb + m sAm + k sAk (same scheme for B, C).
+struct GemmArgs {
+  int M = 0, N = 0, K = 0, batch = 1;
+  const double *A = nullptr;
+  long long sAm = 0, sAk = 0, sAb = 0;
+  const double *B = nullptr;
+  long long sBn = 0, sBk = 0, sBb = 0;
+  double *C = nullptr;
+  long long sCm = 0, sCn = 0, sCb = 0;
+  double alpha = 1.0, beta = 0.0;
+  int lower_only = 0;  // skip output tiles strictly above the diagonal
+  int k_upto_n = 0;    // K range of an output tile limited to k < n_tile_end
+                       // (B lower triangular in (n, k))
+  int k_split = 0;     // >0: blockIdx.z selects K range [z k_split, ...) and C += z sCb
+  // whitening epilogue: row m is column `m` of a T slab; writes
+  // out[(mu nao + nu) ldo + n] and out[(nu nao + mu) ldo + n]
+  const int *colmu = nullptr, *colnu = nullptr;
+  int nao = 0;
+  long long ldo = 0;
+  double *out = nullptr;
+};
+
+void gemm_f64(const GemmArgs &g, cudaStream_t st);
+
+// Cholesky of the lower triangle of A (n x n, n a multiple of 64, lda), in
+// place; Dinv receives the inverse of every 64x64 diagonal block of L.
+// A non-positive pivot sets STATUS_NOT_PD in *status.
+void cholesky_f64(double *A, int n, int lda, double *Dinv, int *status, double *work,
+                  cudaStream_t st);
+// Linv = L^-1 (lower triangular), n a multiple of 64; uses Dinv from
+// cholesky_f64 and `work` (n x n doubles).
+void tri_inverse_f64(const double *L, int n, int ld, const double *Dinv, double *Linv,
+                     double *work, cudaStream_t st);
+
+// rho[P] = sum_{mu >= nu} w D[mu][nu] B[(mu nao + nu) ldb + P], w = 2 off the
+// diagonal; partial sums in `work` (ceil(naux/256) x nchunk) then a fixed-order
+// reduction.
+void rho_gemv_f64(const double *B, long long ldb, int nao, int naux, const double *D,
+                  double *rho, double *work, int nchunk, cudaStream_t st);
+// J[mu][nu] = J[nu][mu] = sum_P B[(mu nao + nu) ldb + P] rho[P].
+void j_gemv_f64(const double *B, long long ldb, int nao, int naux, const double *rho, double *J,
+                cudaStream_t st);
+// out[mu][nu] = out[nu][mu] = sum_s part[s][mu][nu] (mu >= nu).
+void reduce_sym_f64(const double *part, int nsplit, int n, double *out, cudaStream_t st);
+// e[0] = Tr(D J)/2, e[1] = Tr(D K)/2 (fixed-order two-level reduction).
+void energies_f64(const double *D, const double *J, const double *K, int n, double *e,
+                  double *work, cudaStream_t st);
+// max_P sqrt(V[P][P]) over the first n diagonal entries.
+void max_sqrt_diag(const double *V, int n, int ld, double *out, cudaStream_t st);
+// keep[i] = q[i] * (*maxdiag) >= thresh
+void screen_pairs(const double *q, int n, const double *maxdiag, double thresh, int *keep,
+                  cudaStream_t st);
+void fill_f64(double *p, long long n, double v, cudaStream_t st);
+// out[i][j] = in[perm_r[i] * ldi + perm_c[j]] for an n_r x n_c gather.
+void gather2d_f64(const double *in, long long ldi, const int *perm_r, const int *perm_c, int nr,
+                  int nc, double *out, long long ldo, cudaStream_t st);
+// B user-order copy: out[P][mu][nu] = Bint[(mu nao + nu) ldb + perm[P]].
+void gather_B_f64(const double *Bint, long long ldb, int nao, const int *perm, int naux,
+                  double *out, cudaStream_t st);
+
+}  // namespace dfjk

@@ -1,0 +1,528 @@
+// McMurchie-Davidson kernel templates shared by the integral translation units.
+// The scheme and its equations are described in integrals.cu.
+#pragma once
+
+#include "boys.cuh"
+#include "common.cuh"
+#include "integrals.cuh"
+
+namespace dfjk {
+
+
+// ---- Hermite index helpers ---------------------------------------------------
+
+__host__ __device__ constexpr int ntuv(int L) { return (L + 1) * (L + 2) * (L + 3) / 6; }
+// Dense index of (t,u,v): levels n = t+u+v, then descending t, then descending u.
+__host__ __device__ constexpr int tuv_idx(int t, int u, int v) {
+  return (t + u + v) * (t + u + v + 1) * (t + u + v + 2) / 6 + (u + v) * (u + v + 1) / 2 + v;
+}
+
+// Number of (component pair, t, u, v) terms of a shell-pair class.
+__host__ __device__ constexpr int nterms(int LA, int LB) {
+  int n = 0;
+  for (int ca = 0; ca < ncart(LA); ++ca)
+    for (int cb = 0; cb < ncart(LB); ++cb)
+      n += (cart_x(LA, ca) + cart_x(LB, cb) + 1) * (cart_y(LA, ca) + cart_y(LB, cb) + 1) *
+           (cart_z(LA, ca) + cart_z(LB, cb) + 1);
+  return n;
+}
+
+
+// R^0_{tuv} for t+u+v <= L.
+template <int L>
+__device__ __forceinline__ void hermite_R(const double *F, double a, double X, double Y, double Z,
+                                          double *R) {
+  double pw[L + 1];
+  pw[0] = 1.0;
+#pragma unroll
+  for (int n = 1; n <= L; ++n) pw[n] = pw[n - 1] * (-2.0 * a);
+  double cur[ntuv(L)];
+  cur[0] = pw[L] * F[L];
+#pragma unroll
+  for (int n = L - 1; n >= 0; --n) {
+    double nxt[ntuv(L)];
+    nxt[0] = pw[n] * F[n];
+#pragma unroll
+    for (int N = 1; N <= L - n; ++N)
+#pragma unroll
+      for (int t = N; t >= 0; --t)
+#pragma unroll
+        for (int u = N - t; u >= 0; --u) {
+          const int v = N - t - u;
+          double r;
+          if (t > 0) {
+            r = X * cur[tuv_idx(t - 1, u, v)];
+            if (t > 1) r = fma((double)(t - 1), cur[tuv_idx(t - 2, u, v)], r);
+          } else if (u > 0) {
+            r = Y * cur[tuv_idx(t, u - 1, v)];
+            if (u > 1) r = fma((double)(u - 1), cur[tuv_idx(t, u - 2, v)], r);
+          } else {
+            r = Z * cur[tuv_idx(t, u, v - 1)];
+            if (v > 1) r = fma((double)(v - 1), cur[tuv_idx(t, u, v - 2)], r);
+          }
+          nxt[tuv_idx(t, u, v)] = r;
+        }
+#pragma unroll
+    for (int k = 0; k < ntuv(L - n); ++k) cur[k] = nxt[k];
+  }
+#pragma unroll
+  for (int k = 0; k < ntuv(L); ++k) R[k] = cur[k];
+}
+
+// Same recursion with a runtime order (L <= 8), loops not unrolled: used by
+// the Schwarz diagonal, where compile time matters more than speed.
+static __device__ __noinline__ void hermite_R_rt(int L, const double *F, double a, double X, double Y,
+                                          double Z, double *R) {
+  double cur[ntuv(8)], nxt[ntuv(8)];
+  double pw = 1.0;
+  for (int n = 0; n < L; ++n) pw *= -2.0 * a;
+  cur[0] = pw * F[L];
+#pragma unroll 1
+  for (int n = L - 1; n >= 0; --n) {
+    pw = 1.0;
+    for (int k = 0; k < n; ++k) pw *= -2.0 * a;
+    nxt[0] = pw * F[n];
+#pragma unroll 1
+    for (int N = 1; N <= L - n; ++N)
+#pragma unroll 1
+      for (int t = N; t >= 0; --t)
+#pragma unroll 1
+        for (int u = N - t; u >= 0; --u) {
+          const int v = N - t - u;
+          double r;
+          if (t > 0) {
+            r = X * cur[tuv_idx(t - 1, u, v)];
+            if (t > 1) r = fma((double)(t - 1), cur[tuv_idx(t - 2, u, v)], r);
+          } else if (u > 0) {
+            r = Y * cur[tuv_idx(t, u - 1, v)];
+            if (u > 1) r = fma((double)(u - 1), cur[tuv_idx(t, u - 2, v)], r);
+          } else {
+            r = Z * cur[tuv_idx(t, u, v - 1)];
+            if (v > 1) r = fma((double)(v - 1), cur[tuv_idx(t, u, v - 2)], r);
+          }
+          nxt[tuv_idx(t, u, v)] = r;
+        }
+    for (int k = 0; k < ntuv(L - n); ++k) cur[k] = nxt[k];
+  }
+  for (int k = 0; k < ntuv(L); ++k) R[k] = cur[k];
+}
+
+// E^{ij}_t for one direction, i <= LA, j <= LB (t <= i+j), with E^{00}_0 = 1.
+template <int LA, int LB>
+__device__ __forceinline__ void hermite_E(double inv2p, double XPA, double XPB,
+                                          double E[LA + 1][LB + 1][LA + LB + 1]) {
+#pragma unroll
+  for (int i = 0; i <= LA; ++i)
+#pragma unroll
+    for (int j = 0; j <= LB; ++j)
+#pragma unroll
+      for (int t = 0; t <= LA + LB; ++t) E[i][j][t] = 0.0;
+  E[0][0][0] = 1.0;
+#pragma unroll
+  for (int i = 0; i <= LA; ++i)
+#pragma unroll
+    for (int j = 0; j <= LB; ++j) {
+      if (i == 0 && j == 0) continue;
+      if (i > 0) {
+#pragma unroll
+        for (int t = 0; t <= i + j; ++t) {
+          double e = XPA * E[i - 1][j][t];
+          if (t > 0) e = fma(inv2p, E[i - 1][j][t - 1], e);
+          if (t + 1 <= i - 1 + j) e = fma((double)(t + 1), E[i - 1][j][t + 1], e);
+          E[i][j][t] = e;
+        }
+      } else {
+#pragma unroll
+        for (int t = 0; t <= j; ++t) {
+          double e = XPB * E[0][j - 1][t];
+          if (t > 0) e = fma(inv2p, E[0][j - 1][t - 1], e);
+          if (t + 1 <= j - 1) e = fma((double)(t + 1), E[0][j - 1][t + 1], e);
+          E[0][j][t] = e;
+        }
+      }
+    }
+}
+
+// ---- pair kernel: primitive-pair records and Schwarz diagonal ----------------
+
+// One thread per shell pair of class (LA, LB).  Record of a primitive pair:
+//   [0] p  [1..3] P  [4] c_a c_b K_ab 2 pi^(5/2)/p  [5..] E^x E^y E^z per term.
+// q[pair] = sqrt(max over components of (ab|ab)), the Schwarz factor.
+template <int LA, int LB>
+__global__ void __launch_bounds__(128) pair_kernel(PairClassArgs args, OrbArgs orb,
+                                                   const double *__restrict__ boys_tab) {
+  const int ip = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ip >= args.npair) return;
+  constexpr int NT = nterms(LA, LB);
+  constexpr int REC = REC_HDR + NT;
+  constexpr int NCA = ncart(LA), NCB = ncart(LB);
+  const int sa = args.shell_a[ip], sb = args.shell_b[ip];
+  const double Ax = orb.center[3 * sa], Ay = orb.center[3 * sa + 1], Az = orb.center[3 * sa + 2];
+  const double Bx = orb.center[3 * sb], By = orb.center[3 * sb + 1], Bz = orb.center[3 * sb + 2];
+  const double ABx = Ax - Bx, ABy = Ay - By, ABz = Az - Bz;
+  const double AB2 = ABx * ABx + ABy * ABy + ABz * ABz;
+  double *rec0 = args.rec + args.rec_off[ip];
+  const int pa0 = orb.prim_off[sa], na = orb.nprim[sa];
+  const int pb0 = orb.prim_off[sb], nb = orb.nprim[sb];
+  int npp = 0;
+  for (int ka = 0; ka < na; ++ka)
+    for (int kb = 0; kb < nb; ++kb, ++npp) {
+      const double a = orb.exps[pa0 + ka], b = orb.exps[pb0 + kb];
+      const double p = a + b, ip_ = 1.0 / p;
+      const double Px = (a * Ax + b * Bx) * ip_, Py = (a * Ay + b * By) * ip_,
+                   Pz = (a * Az + b * Bz) * ip_;
+      double *r = rec0 + (long long)npp * REC;
+      r[0] = p;
+      r[1] = Px;
+      r[2] = Py;
+      r[3] = Pz;
+      r[4] = orb.coefs[pa0 + ka] * orb.coefs[pb0 + kb] * exp(-a * b * ip_ * AB2) *
+             (2.0 * 17.493418327624862846 * ip_);  // 2 pi^(5/2) / p
+      double Ex[LA + 1][LB + 1][LA + LB + 1], Ey[LA + 1][LB + 1][LA + LB + 1],
+          Ez[LA + 1][LB + 1][LA + LB + 1];
+      const double inv2p = 0.5 * ip_;
+      hermite_E<LA, LB>(inv2p, Px - Ax, Px - Bx, Ex);
+      hermite_E<LA, LB>(inv2p, Py - Ay, Py - By, Ey);
+      hermite_E<LA, LB>(inv2p, Pz - Az, Pz - Bz, Ez);
+      int k = 0;
+#pragma unroll
+      for (int ca = 0; ca < NCA; ++ca)
+#pragma unroll
+        for (int cb = 0; cb < NCB; ++cb) {
+          const int ax = cart_x(LA, ca), ay = cart_y(LA, ca), az = cart_z(LA, ca);
+          const int bx = cart_x(LB, cb), by = cart_y(LB, cb), bz = cart_z(LB, cb);
+#pragma unroll
+          for (int t = 0; t <= ax + bx; ++t)
+#pragma unroll
+            for (int u = 0; u <= ay + by; ++u)
+#pragma unroll
+              for (int v = 0; v <= az + bz; ++v) r[REC_HDR + k++] = Ex[ax][bx][t] * Ey[ay][by][u] * Ez[az][bz][v];
+        }
+    }
+
+  // Schwarz: diagonal (ab|ab) per component from all primitive quadruples
+  // (runtime loops: a negligible share of the work).
+  constexpr int L4 = 2 * (LA + LB);
+  double diag[NCA * NCB];
+  for (int c = 0; c < NCA * NCB; ++c) diag[c] = 0.0;
+#pragma unroll 1
+  for (int i = 0; i < npp; ++i) {
+    const double *ri = rec0 + (long long)i * REC;
+#pragma unroll 1
+    for (int j = 0; j < npp; ++j) {
+      const double *rj = rec0 + (long long)j * REC;
+      const double p = ri[0], q = rj[0];
+      const double s = rsqrt(p + q);
+      const double al = p * q * s * s;
+      const double X = ri[1] - rj[1], Y = ri[2] - rj[2], Z = ri[3] - rj[3];
+      double F[L4 + 1];
+      boys_eval<L4>(al * (X * X + Y * Y + Z * Z), boys_tab, F);
+      double R[ntuv(8)];
+      hermite_R_rt(L4, F, al, X, Y, Z, R);
+      // ri[4] rj[4] = c c K c c K (2 pi^2.5)^2 / (p q); we need 2 pi^2.5 /(p q sqrt(p+q))
+      const double fac = ri[4] * rj[4] * s * (1.0 / (2.0 * 17.493418327624862846));
+      int k = 0;
+#pragma unroll 1
+      for (int ca = 0; ca < NCA; ++ca)
+#pragma unroll 1
+        for (int cb = 0; cb < NCB; ++cb) {
+          const int ax = cart_x(LA, ca), ay = cart_y(LA, ca), az = cart_z(LA, ca);
+          const int bx = cart_x(LB, cb), by = cart_y(LB, cb), bz = cart_z(LB, cb);
+          const int k0 = k;
+          double sum = 0.0;
+#pragma unroll 1
+          for (int t = 0; t <= ax + bx; ++t)
+#pragma unroll 1
+            for (int u = 0; u <= ay + by; ++u)
+#pragma unroll 1
+              for (int v = 0; v <= az + bz; ++v) {
+                double inner = 0.0;
+                int k2 = k0;
+#pragma unroll 1
+                for (int t2 = 0; t2 <= ax + bx; ++t2)
+#pragma unroll 1
+                  for (int u2 = 0; u2 <= ay + by; ++u2)
+#pragma unroll 1
+                    for (int v2 = 0; v2 <= az + bz; ++v2) {
+                      const double e2 = ((t2 + u2 + v2) & 1) ? -rj[REC_HDR + k2] : rj[REC_HDR + k2];
+                      inner = fma(e2, R[tuv_idx(t + t2, u + u2, v + v2)], inner);
+                      ++k2;
+                    }
+                sum = fma(ri[REC_HDR + k], inner, sum);
+                ++k;
+              }
+          diag[ca * NCB + cb] = fma(fac, sum, diag[ca * NCB + cb]);
+        }
+    }
+  }
+  double qmax = 0.0;
+#pragma unroll
+  for (int ca = 0; ca < NCA; ++ca)
+#pragma unroll
+    for (int cb = 0; cb < NCB; ++cb) {
+      const double f = comp_factor(LA, ca) * comp_factor(LB, cb);
+      qmax = fmax(qmax, diag[ca * NCB + cb] * f * f);
+    }
+  args.q[ip] = sqrt(fmax(qmax, 0.0));
+}
+
+// ---- 3-centre kernel ---------------------------------------------------------
+
+// Block: one shell pair of class (LA, LB) (blockIdx.x indexes the kept-pair
+// list), 128 aux shells of class LC (blockIdx.y).  Thread: one aux shell;
+// loops over the pair's primitive pairs (records staged in shared memory) and
+// the aux primitives, accumulating the ncart(LA) ncart(LB) ncart(LC) block,
+// then writes T[col - col_begin][P] (P contiguous).
+template <int LA, int LB, int LC>
+__global__ void __launch_bounds__(128) eri3c_kernel(Eri3cArgs args, AuxArgs aux,
+                                                    const double *__restrict__ boys_tab) {
+  constexpr int NT = nterms(LA, LB);
+  constexpr int REC = REC_HDR + NT;
+  constexpr int NCA = ncart(LA), NCB = ncart(LB), NCC = ncart(LC);
+  constexpr int LAB = LA + LB, L = LA + LB + LC;
+  __shared__ double srec[REC];
+  const int pair = args.pairs[blockIdx.x];
+  const int as = blockIdx.y * blockDim.x + threadIdx.x;
+  const bool active = as < args.naux_shells;
+  const int sc = active ? args.aux_shells[as] : 0;
+  const double Cx = aux.center[3 * sc], Cy = aux.center[3 * sc + 1], Cz = aux.center[3 * sc + 2];
+  const int pc0 = aux.prim_off[sc], nc = active ? aux.nprim[sc] : 0;
+  double acc[NCA * NCB * NCC];
+#pragma unroll
+  for (int i = 0; i < NCA * NCB * NCC; ++i) acc[i] = 0.0;
+  const double *rec0 = args.rec + args.rec_off[pair];
+  const int npp = args.npp[pair];
+  for (int ipp = 0; ipp < npp; ++ipp) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < REC; i += blockDim.x) srec[i] = rec0[(long long)ipp * REC + i];
+    __syncthreads();
+    for (int kc = 0; kc < nc; ++kc) {
+      const double g = aux.exps[pc0 + kc];
+      const double g1 = aux.g1[pc0 + kc];  // 1/(2g)
+      const double p = srec[0];
+      const double X = srec[1] - Cx, Y = srec[2] - Cy, Z = srec[3] - Cz;
+      const double s = rsqrt(p + g);
+      const double al = p * g * (s * s);
+      double F[L + 1];
+      boys_eval<L>(al * (X * X + Y * Y + Z * Z), boys_tab, F);
+      double R[ntuv(L)];
+      hermite_R<L>(F, al, X, Y, Z, R);
+      const double pt = srec[4] * aux.cdiv[pc0 + kc] * s;  // c_c / g folded in cdiv
+#pragma unroll
+      for (int cc = 0; cc < NCC; ++cc) {
+        const int cx = cart_x(LC, cc), cy = cart_y(LC, cc), cz = cart_z(LC, cc);
+        // W[tuv] for t+u+v <= LAB: aux Hermite expansion folded into shifts.
+        double W[ntuv(LAB)];
+        double scale = 1.0;
+        if (LC == 0) {
+#pragma unroll
+          for (int i = 0; i < ntuv(LAB); ++i) W[i] = R[i];
+        } else {
+          const int two = (cx == 2) ? 0 : (cy == 2) ? 1 : (cz == 2) ? 2 : -1;
+#pragma unroll
+          for (int N = 0; N <= LAB; ++N)
+#pragma unroll
+            for (int t = N; t >= 0; --t)
+#pragma unroll
+              for (int u = N - t; u >= 0; --u) {
+                const int v = N - t - u;
+                if (two == 0)
+                  W[tuv_idx(t, u, v)] = fma(g1, R[tuv_idx(t + 2, u, v)], R[tuv_idx(t, u, v)]);
+                else if (two == 1)
+                  W[tuv_idx(t, u, v)] = fma(g1, R[tuv_idx(t, u + 2, v)], R[tuv_idx(t, u, v)]);
+                else if (two == 2)
+                  W[tuv_idx(t, u, v)] = fma(g1, R[tuv_idx(t, u, v + 2)], R[tuv_idx(t, u, v)]);
+                else
+                  W[tuv_idx(t, u, v)] = R[tuv_idx(t + cx, u + cy, v + cz)];
+              }
+          if (two >= 0)
+            scale = g1;
+          else if (LC == 1)
+            scale = -g1;
+          else
+            scale = g1 * g1;
+        }
+        const double ps = pt * scale;
+        int k = 0;
+#pragma unroll
+        for (int ca = 0; ca < NCA; ++ca)
+#pragma unroll
+          for (int cb = 0; cb < NCB; ++cb) {
+            const int ax = cart_x(LA, ca), ay = cart_y(LA, ca), az = cart_z(LA, ca);
+            const int bx = cart_x(LB, cb), by = cart_y(LB, cb), bz = cart_z(LB, cb);
+            double sum = 0.0;
+#pragma unroll
+            for (int t = 0; t <= ax + bx; ++t)
+#pragma unroll
+              for (int u = 0; u <= ay + by; ++u)
+#pragma unroll
+                for (int v = 0; v <= az + bz; ++v) sum = fma(srec[REC_HDR + k++], W[tuv_idx(t, u, v)], sum);
+            acc[(ca * NCB + cb) * NCC + cc] = fma(ps, sum, acc[(ca * NCB + cb) * NCC + cc]);
+          }
+      }
+    }
+  }
+  if (!active) return;
+  const long long col0 = args.pair_col[pair] - args.col_begin;
+  const int P0 = aux.func_off[sc];
+#pragma unroll
+  for (int ca = 0; ca < NCA; ++ca)
+#pragma unroll
+    for (int cb = 0; cb < NCB; ++cb)
+#pragma unroll
+      for (int cc = 0; cc < NCC; ++cc)
+        args.T[(col0 + ca * NCB + cb) * args.ldT + P0 + cc] =
+            acc[(ca * NCB + cb) * NCC + cc] *
+            (comp_factor(LA, ca) * comp_factor(LB, cb) * comp_factor(LC, cc));
+}
+
+// ---- 2-centre metric and overlap ----------------------------------------------
+
+// Hermite expansion of a one-centre Cartesian power k with exponent a, one
+// direction: up to two terms (t, coefficient).
+__device__ __forceinline__ int one_centre_terms(int k, double inv2a, int *t, double *c) {
+  if (k == 0) {
+    t[0] = 0; c[0] = 1.0;
+    return 1;
+  }
+  if (k == 1) {
+    t[0] = 1; c[0] = inv2a;
+    return 1;
+  }
+  t[0] = 0; c[0] = inv2a;
+  t[1] = 2; c[1] = inv2a * inv2a;
+  return 2;
+}
+
+// One thread per aux shell pair (P >= Q in internal order, class (LP, LQ)).
+template <int LP, int LQ>
+__global__ void __launch_bounds__(128) metric_kernel(MetricArgs args, AuxArgs aux,
+                                                     const double *__restrict__ boys_tab) {
+  const int ip = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ip >= args.npair) return;
+  constexpr int L = LP + LQ;
+  constexpr int NP = ncart(LP), NQ = ncart(LQ);
+  const int sp = args.shell_p[ip], sq = args.shell_q[ip];
+  const double X = aux.center[3 * sp] - aux.center[3 * sq];
+  const double Y = aux.center[3 * sp + 1] - aux.center[3 * sq + 1];
+  const double Z = aux.center[3 * sp + 2] - aux.center[3 * sq + 2];
+  double out[NP * NQ];
+#pragma unroll
+  for (int i = 0; i < NP * NQ; ++i) out[i] = 0.0;
+  for (int kp = 0; kp < aux.nprim[sp]; ++kp)
+    for (int kq = 0; kq < aux.nprim[sq]; ++kq) {
+      const int ip0 = aux.prim_off[sp] + kp, iq0 = aux.prim_off[sq] + kq;
+      const double a = aux.exps[ip0], g = aux.exps[iq0];
+      const double s = rsqrt(a + g);
+      const double al = a * g * s * s;
+      double F[L + 1];
+      boys_eval<L>(al * (X * X + Y * Y + Z * Z), boys_tab, F);
+      double R[ntuv(L)];
+      hermite_R<L>(F, al, X, Y, Z, R);
+      // 2 pi^2.5/(a g sqrt(a+g)) c_a c_g = 2 pi^2.5 s cdiv_a cdiv_g
+      const double pref = 2.0 * 17.493418327624862846 * s * aux.cdiv[ip0] * aux.cdiv[iq0];
+#pragma unroll
+      for (int cp = 0; cp < NP; ++cp)
+#pragma unroll
+        for (int cq = 0; cq < NQ; ++cq) {
+          int tp[3][2], tq[3][2], np_[3], nq_[3];
+          double cpf[3][2], cqf[3][2];
+          np_[0] = one_centre_terms(cart_x(LP, cp), aux.g1[ip0], tp[0], cpf[0]);
+          np_[1] = one_centre_terms(cart_y(LP, cp), aux.g1[ip0], tp[1], cpf[1]);
+          np_[2] = one_centre_terms(cart_z(LP, cp), aux.g1[ip0], tp[2], cpf[2]);
+          nq_[0] = one_centre_terms(cart_x(LQ, cq), aux.g1[iq0], tq[0], cqf[0]);
+          nq_[1] = one_centre_terms(cart_y(LQ, cq), aux.g1[iq0], tq[1], cqf[1]);
+          nq_[2] = one_centre_terms(cart_z(LQ, cq), aux.g1[iq0], tq[2], cqf[2]);
+          double sum = 0.0;
+          for (int i0 = 0; i0 < np_[0]; ++i0)
+            for (int i1 = 0; i1 < np_[1]; ++i1)
+              for (int i2 = 0; i2 < np_[2]; ++i2)
+                for (int j0 = 0; j0 < nq_[0]; ++j0)
+                  for (int j1 = 0; j1 < nq_[1]; ++j1)
+                    for (int j2 = 0; j2 < nq_[2]; ++j2) {
+                      const int t = tp[0][i0] + tq[0][j0], u = tp[1][i1] + tq[1][j1],
+                                v = tp[2][i2] + tq[2][j2];
+                      const double sg = ((tq[0][j0] + tq[1][j1] + tq[2][j2]) & 1) ? -1.0 : 1.0;
+                      sum += sg * cpf[0][i0] * cpf[1][i1] * cpf[2][i2] * cqf[0][j0] * cqf[1][j1] *
+                             cqf[2][j2] * R[tuv_idx(t, u, v)];
+                    }
+          out[cp * NQ + cq] += pref * sum;
+        }
+    }
+  const int P0 = aux.func_off[sp], Q0 = aux.func_off[sq];
+  for (int cp = 0; cp < NP; ++cp)
+    for (int cq = 0; cq < NQ; ++cq) {
+      const double v = out[cp * NQ + cq] * comp_factor(LP, cp) * comp_factor(LQ, cq);
+      args.V[(long long)(P0 + cp) * args.ldV + Q0 + cq] = v;
+      args.V[(long long)(Q0 + cq) * args.ldV + P0 + cp] = v;
+    }
+}
+
+// Overlap <a|b> = sum c_a c_b K_ab (pi/p)^(3/2) E^x_0 E^y_0 E^z_0; one thread
+// per ordered orbital shell pair.
+template <int LA, int LB>
+__global__ void overlap_kernel(OverlapArgs args, OrbArgs orb) {
+  const int ip = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ip >= args.npair) return;
+  constexpr int NCA = ncart(LA), NCB = ncart(LB);
+  const int sa = args.shell_a[ip], sb = args.shell_b[ip];
+  const double Ax = orb.center[3 * sa], Ay = orb.center[3 * sa + 1], Az = orb.center[3 * sa + 2];
+  const double Bx = orb.center[3 * sb], By = orb.center[3 * sb + 1], Bz = orb.center[3 * sb + 2];
+  const double AB2 = (Ax - Bx) * (Ax - Bx) + (Ay - By) * (Ay - By) + (Az - Bz) * (Az - Bz);
+  double out[NCA * NCB];
+#pragma unroll
+  for (int i = 0; i < NCA * NCB; ++i) out[i] = 0.0;
+  for (int ka = 0; ka < orb.nprim[sa]; ++ka)
+    for (int kb = 0; kb < orb.nprim[sb]; ++kb) {
+      const double a = orb.exps[orb.prim_off[sa] + ka], b = orb.exps[orb.prim_off[sb] + kb];
+      const double p = a + b, ip_ = 1.0 / p;
+      const double Px = (a * Ax + b * Bx) * ip_, Py = (a * Ay + b * By) * ip_,
+                   Pz = (a * Az + b * Bz) * ip_;
+      double Ex[LA + 1][LB + 1][LA + LB + 1], Ey[LA + 1][LB + 1][LA + LB + 1],
+          Ez[LA + 1][LB + 1][LA + LB + 1];
+      hermite_E<LA, LB>(0.5 * ip_, Px - Ax, Px - Bx, Ex);
+      hermite_E<LA, LB>(0.5 * ip_, Py - Ay, Py - By, Ey);
+      hermite_E<LA, LB>(0.5 * ip_, Pz - Az, Pz - Bz, Ez);
+      const double pref = orb.coefs[orb.prim_off[sa] + ka] * orb.coefs[orb.prim_off[sb] + kb] *
+                          exp(-a * b * ip_ * AB2) * (5.5683279968317078453 * ip_ * sqrt(ip_));
+#pragma unroll
+      for (int ca = 0; ca < NCA; ++ca)
+#pragma unroll
+        for (int cb = 0; cb < NCB; ++cb)
+          out[ca * NCB + cb] += pref * Ex[cart_x(LA, ca)][cart_x(LB, cb)][0] *
+                                Ey[cart_y(LA, ca)][cart_y(LB, cb)][0] *
+                                Ez[cart_z(LA, ca)][cart_z(LB, cb)][0];
+    }
+  const int A0 = orb.func_off[sa], B0 = orb.func_off[sb];
+  for (int ca = 0; ca < NCA; ++ca)
+    for (int cb = 0; cb < NCB; ++cb) {
+      const double v = out[ca * NCB + cb] * comp_factor(LA, ca) * comp_factor(LB, cb);
+      args.S[(long long)(A0 + ca) * args.ldS + B0 + cb] = v;
+      args.S[(long long)(B0 + cb) * args.ldS + A0 + ca] = v;
+    }
+}
+
+// Boys table evaluation for tests.
+template <int M>
+__global__ void boys_kernel(int n, const double *__restrict__ T, double *__restrict__ F,
+                            const double *__restrict__ tab) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double f[M + 1];
+  boys_eval<M>(T[i], tab, f);
+  for (int m = 0; m <= M; ++m) F[(long long)i * (M + 1) + m] = f[m];
+}
+
+
+#define DISPATCH_LALB(LA, LB, CALL)                                   \
+  switch ((LA) * 3 + (LB)) {                                          \
+    case 0: { constexpr int A_ = 0, B_ = 0; CALL; } break;            \
+    case 3: { constexpr int A_ = 1, B_ = 0; CALL; } break;            \
+    case 4: { constexpr int A_ = 1, B_ = 1; CALL; } break;            \
+    case 6: { constexpr int A_ = 2, B_ = 0; CALL; } break;            \
+    case 7: { constexpr int A_ = 2, B_ = 1; CALL; } break;            \
+    case 8: { constexpr int A_ = 2, B_ = 2; CALL; } break;            \
+    default: throw Error{DFJK_ERR_UNSUPPORTED, "shell class"};        \
+  }
+
+}  // namespace dfjk

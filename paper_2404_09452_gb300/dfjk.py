@@ -1,0 +1,301 @@
+"""Thin Python binding of libdfjk.so (the C ABI in include/dfjk.h).
+
+Argument marshalling only: every step of the DF-J/K path runs in the CUDA
+library.  PyTorch supplies device memory and streams.  There is no fallback:
+if the library cannot be loaded or no CUDA device is present, calls raise.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libdfjk.so")
+
+DFJK_FP64 = 0
+DFJK_MIXED = 1
+
+STATUS = {
+    0: "DFJK_OK",
+    1: "DFJK_ERR_ARG",
+    2: "DFJK_ERR_UNSUPPORTED",
+    3: "DFJK_ERR_NOT_PD",
+    4: "DFJK_ERR_OOM",
+    5: "DFJK_ERR_BUDGET",
+    6: "DFJK_ERR_TIMEOUT",
+    7: "DFJK_ERR_CUDA",
+    8: "DFJK_ERR_STATE",
+}
+
+# Every symbol include/dfjk.h declares.
+EXPORTS = [
+    "dfjk_default_options",
+    "dfjk_setup",
+    "dfjk_query",
+    "dfjk_build",
+    "dfjk_overlap",
+    "dfjk_evict",
+    "dfjk_destroy",
+    "dfjk_status_string",
+    "dfjk_last_error",
+    "dfjk_launch_count",
+    "dfjk_boys",
+    "dfjk_get_metric",
+    "dfjk_get_cholesky",
+    "dfjk_get_B",
+    "dfjk_get_pair_mask",
+    "dfjk_get_three_center",
+]
+
+
+class DfjkError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Shell(ctypes.Structure):
+    _fields_ = [
+        ("atom", ctypes.c_int32),
+        ("l", ctypes.c_int32),
+        ("nprim", ctypes.c_int32),
+        ("exps", ctypes.POINTER(ctypes.c_double)),
+        ("coefs", ctypes.POINTER(ctypes.c_double)),
+    ]
+
+
+class BasisC(ctypes.Structure):
+    _fields_ = [("nshell", ctypes.c_int32), ("shells", ctypes.POINTER(Shell))]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [
+        ("precision", ctypes.c_int32),
+        ("schwarz_thresh", ctypes.c_double),
+        ("hbm_budget_bytes", ctypes.c_size_t),
+        ("timeout_iters", ctypes.c_int64),
+        ("energies_on_host", ctypes.c_int32),
+    ]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Loads libdfjk.so and declares the signatures.  Raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise OSError(
+            f"{path} is missing: build it with paper_2404_09452_gb300/build_lib.py "
+            "(there is no CPU fallback)"
+        )
+    lib = ctypes.CDLL(path)
+    vp, i32, f64p = ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)
+    lib.dfjk_default_options.argtypes = [ctypes.POINTER(Options)]
+    lib.dfjk_default_options.restype = None
+    lib.dfjk_setup.argtypes = [
+        ctypes.POINTER(BasisC), ctypes.POINTER(BasisC), i32, f64p, ctypes.POINTER(Options), vp,
+        ctypes.POINTER(vp),
+    ]
+    lib.dfjk_query.argtypes = [
+        vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_size_t)
+    ]
+    lib.dfjk_build.argtypes = [vp, i32, i32, vp, vp, vp, vp, vp, vp]
+    lib.dfjk_overlap.argtypes = [vp, vp, vp]
+    lib.dfjk_evict.argtypes = [vp]
+    lib.dfjk_destroy.argtypes = [vp]
+    lib.dfjk_status_string.argtypes = [ctypes.c_int]
+    lib.dfjk_status_string.restype = ctypes.c_char_p
+    lib.dfjk_last_error.argtypes = []
+    lib.dfjk_last_error.restype = ctypes.c_char_p
+    lib.dfjk_launch_count.argtypes = []
+    lib.dfjk_launch_count.restype = ctypes.c_uint64
+    lib.dfjk_boys.argtypes = [i32, i32, vp, vp, vp]
+    for fn in ("dfjk_get_metric", "dfjk_get_cholesky", "dfjk_get_B", "dfjk_get_pair_mask",
+               "dfjk_get_three_center"):
+        getattr(lib, fn).argtypes = [vp, vp, vp]
+    for fn in EXPORTS:
+        if fn not in ("dfjk_default_options", "dfjk_status_string", "dfjk_last_error",
+                      "dfjk_launch_count"):
+            getattr(lib, fn).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise DfjkError(rc, load_library().dfjk_last_error().decode())
+
+
+def _torch():
+    import torch
+
+    if not torch.cuda.is_available():
+        raise RuntimeError("the DF-J/K library needs a CUDA device (no CPU fallback)")
+    return torch
+
+
+def _stream(stream=None):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class _BasisHolder:
+    """Keeps the numpy arrays alive while C holds pointers into them."""
+
+    def __init__(self, basis):
+        shells = list(basis.shells)
+        self.arrays = []
+        arr = (Shell * max(1, len(shells)))()
+        for i, s in enumerate(shells):
+            e = np.ascontiguousarray(s.exps, dtype=np.float64)
+            c = np.ascontiguousarray(s.coefs, dtype=np.float64)
+            self.arrays += [e, c]
+            arr[i].atom = int(s.atom)
+            arr[i].l = int(s.l)
+            arr[i].nprim = len(e)
+            arr[i].exps = e.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+            arr[i].coefs = c.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        self.shells = arr
+        self.c = BasisC(len(shells), ctypes.cast(arr, ctypes.POINTER(Shell)))
+
+
+def default_options(precision: int = DFJK_FP64, schwarz_thresh: float = 1e-12,
+                    hbm_budget_bytes: int = 0, energies_on_host: bool = True) -> Options:
+    o = Options()
+    load_library().dfjk_default_options(ctypes.byref(o))
+    o.precision = precision
+    o.schwarz_thresh = schwarz_thresh
+    o.hbm_budget_bytes = hbm_budget_bytes
+    o.energies_on_host = 1 if energies_on_host else 0
+    return o
+
+
+class Handle:
+    """A molecule set up on the device (steps a0-a5); B stays resident."""
+
+    def __init__(self, mol, precision: int = DFJK_FP64, schwarz_thresh: float = 1e-12,
+                 hbm_budget_bytes: int = 0, stream=None):
+        lib = load_library()
+        _torch()
+        self.mol = mol
+        self._orb = _BasisHolder(mol.orb)
+        self._aux = _BasisHolder(mol.aux)
+        xyz = np.ascontiguousarray(mol.coords, dtype=np.float64)
+        opt = default_options(precision, schwarz_thresh, hbm_budget_bytes)
+        h = ctypes.c_void_p()
+        _check(
+            lib.dfjk_setup(
+                ctypes.byref(self._orb.c), ctypes.byref(self._aux.c), int(xyz.shape[0]),
+                xyz.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(opt),
+                _stream(stream), ctypes.byref(h),
+            )
+        )
+        self.h = h
+        self.precision = precision
+        nao, naux, npk = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        nbytes = ctypes.c_size_t()
+        _check(lib.dfjk_query(h, ctypes.byref(nao), ctypes.byref(naux), ctypes.byref(npk),
+                              ctypes.byref(nbytes)))
+        self.nao, self.naux, self.npair_kept, self.device_bytes = (
+            nao.value, naux.value, npk.value, nbytes.value)
+
+    def close(self):
+        if getattr(self, "h", None):
+            load_library().dfjk_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def build(self, C, J=None, K=None, E=None, stream=None, energies_on_device=False):
+        """J, K, E_J, E_K for C [nao x nocc] or [nset x nao x nocc] (device FP64).
+        Returns (J, K, E_J, E_K) with J, K device tensors."""
+        torch = _torch()
+        C = C.contiguous()
+        if C.dim() == 2:
+            C = C.unsqueeze(0)
+        nset, nao, nocc = C.shape
+        if nao != self.nao:
+            raise ValueError("C has the wrong number of rows")
+        if J is None:
+            J = torch.empty((nset, nao, nao), dtype=torch.float64, device=C.device)
+        if K is None:
+            K = torch.empty((nset, nao, nao), dtype=torch.float64, device=C.device)
+        if energies_on_device:
+            EJ = torch.empty(nset, dtype=torch.float64, device=C.device)
+            EK = torch.empty(nset, dtype=torch.float64, device=C.device)
+            pj, pk = ctypes.c_void_p(EJ.data_ptr()), ctypes.c_void_p(EK.data_ptr())
+        else:
+            EJ = np.zeros(nset)
+            EK = np.zeros(nset)
+            pj, pk = ctypes.c_void_p(EJ.ctypes.data), ctypes.c_void_p(EK.ctypes.data)
+        _check(load_library().dfjk_build(
+            self.h, nset, nocc, ctypes.c_void_p(C.data_ptr()), ctypes.c_void_p(J.data_ptr()),
+            ctypes.c_void_p(K.data_ptr()), pj, pk, _stream(stream)))
+        return J, K, EJ, EK
+
+    def overlap(self, stream=None):
+        torch = _torch()
+        S = torch.empty((self.nao, self.nao), dtype=torch.float64, device="cuda")
+        _check(load_library().dfjk_overlap(self.h, ctypes.c_void_p(S.data_ptr()), _stream(stream)))
+        return S
+
+    def evict(self):
+        _check(load_library().dfjk_evict(self.h))
+
+    def _get(self, fn, shape, dtype=None):
+        torch = _torch()
+        out = torch.empty(shape, dtype=dtype or torch.float64, device="cuda")
+        _check(getattr(load_library(), fn)(self.h, ctypes.c_void_p(out.data_ptr()), _stream()))
+        torch.cuda.current_stream().synchronize()
+        return out
+
+    def metric(self):
+        return self._get("dfjk_get_metric", (self.naux, self.naux))
+
+    def cholesky(self):
+        return self._get("dfjk_get_cholesky", (self.naux, self.naux))
+
+    def B(self):
+        return self._get("dfjk_get_B", (self.naux, self.nao, self.nao))
+
+    def three_center(self):
+        return self._get("dfjk_get_three_center", (self.naux, self.nao, self.nao))
+
+    def pair_mask(self):
+        torch = _torch()
+        n = len(self.mol.orb.shells)
+        return self._get("dfjk_get_pair_mask", (n, n), dtype=torch.int32)
+
+
+def boys(mmax: int, T, stream=None):
+    """F_0..F_mmax at the device points T (FP64), shape [n, mmax+1]."""
+    torch = _torch()
+    T = T.contiguous()
+    F = torch.empty((T.numel(), mmax + 1), dtype=torch.float64, device=T.device)
+    _check(load_library().dfjk_boys(mmax, T.numel(), ctypes.c_void_p(T.data_ptr()),
+                                    ctypes.c_void_p(F.data_ptr()), _stream(stream)))
+    return F
+
+
+def launch_count() -> int:
+    return int(load_library().dfjk_launch_count())
+
+
+def orthonormal_c_occ(handle: Handle, C0: np.ndarray):
+    """C_occ made orthonormal in the overlap metric that the library computes
+    on the device (input preparation, outside any timed region)."""
+    from .inputs import orthonormalize
+
+    S = handle.overlap().cpu().numpy()
+    return orthonormalize(C0, S)
