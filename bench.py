@@ -1,0 +1,359 @@
+#!/usr/bin/env python
+"""DF-J/K benchmark: one step = the whole hot path (shell pairs, metric,
+Cholesky, 3-centre integrals, whitening, X = B C, K, rho and J, energies) for
+one synthetic molecule, through the C ABI.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|mixed]
+                  [--workload mol60|mol120|water] [--impl ours|reference]
+
+Prints one JSON line on rank 0.  `value` is whole-job builds/s with inputs
+resident in HBM (device time, CUDA events, max over ranks); `e2e` is the same
+metric through the public API with pinned host buffers and the host<->device
+copies inside the timed region.  For N > 1 (torchrun) every rank runs its own
+molecule (independent units, no data-path collective): weak scaling.
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DF-J/K builds/s & TFLOP/s vs plain FP64 GPU at |ΔE|≤1e-6 Eh; p50/p99 latency"
+UNIT = "builds/s"
+WORKLOADS = {
+    "mol60": dict(natom=60, seed=1002, note="60 atoms uniform in a cube at 0.01 atoms/bohr^3, "
+                  "nao 900, naux 2160, nocc 180, Schwarz 1e-12"),
+    "mol120": dict(natom=120, seed=1003, note="120 atoms, nao 1800, naux 4320, nocc 360"),
+    "water": dict(natom=0, seed=1001, note="3-atom water, nao 18, naux 30, nocc 5"),
+}
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FP64_PEAK_GFLOPS = 1199.0  # measured FP64 DFMA throughput of this GB300 pool (FMA chains)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--workload", default="mol60", choices=list(WORKLOADS))
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def make_molecule(name):
+    from paper_2404_09452_gb300 import inputs as I
+
+    w = WORKLOADS[name]
+    if w["natom"] == 0:
+        return I.water(), 5
+    m = I.molecule(w["natom"], seed=w["seed"])
+    return m, I.default_nocc(m.nao)
+
+
+def algorithmic_flops(nao, naux, nocc, ncol):
+    """Flops of each dense phase as the method defines them (not as tiled):
+    whitening a triangular solve per kept AO pair, X = B_P C for every P,
+    K on one triangle, rho and J on the mu >= nu rows."""
+    return {
+        "whiten": float(ncol) * naux * (naux + 1),
+        "X=BC": 2.0 * naux * nao * nao * nocc,
+        "K": float(naux) * nocc * nao * (nao + 1),
+        "rho+J": 2.0 * 2.0 * naux * nao * (nao + 1) / 2 + 2.0 * nao * nao * nocc,
+    }
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=5)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ---- CPU baseline: the oracle on a bounded sample --------------------------------------
+
+def oracle_sample(m, nocc):
+    """Times the FP64 CPU oracle on a bounded sample of one build and scales it
+    to a whole build.  Returns (seconds per build, sample description, cores)."""
+    import numpy as np
+    import scipy.linalg
+
+    from oracle import oracle as O
+
+    natom = m.natom
+    nao, naux = m.nao, m.naux
+    t = {}
+    t0 = time.perf_counter()
+    V = O.metric(m.aux, m.coords)
+    L = scipy.linalg.cholesky(V, lower=True)
+    t["metric+cholesky"] = time.perf_counter() - t0
+    # 3-centre integrals for the aux shells of one atom (every l class), x natom
+    per_atom = len(m.aux.shells) // max(natom, 1)
+    t0 = time.perf_counter()
+    T = O.three_center(m.orb, m.aux, m.coords, sym=True, aux_shells=(0, per_atom))
+    t["three_center"] = (time.perf_counter() - t0) * natom
+    # whitening: triangular solve on a column sample of the full mu,nu layout
+    rng = np.random.default_rng(0)
+    ncs = min(nao * nao, 8192)
+    Tc = rng.standard_normal((naux, ncs))
+    t0 = time.perf_counter()
+    scipy.linalg.solve_triangular(L, Tc, lower=True)
+    t["whiten"] = (time.perf_counter() - t0) * (nao * nao / ncs)
+    # J and K contractions on a sample of P
+    nps = min(naux, 48)
+    Bs = rng.standard_normal((nps, nao, nao))
+    C = rng.standard_normal((nao, nocc))
+    t0 = time.perf_counter()
+    O.jk_from_B(Bs, C)
+    t["jk"] = (time.perf_counter() - t0) * (naux / nps)
+    total = sum(t.values())
+    desc = (f"oracle: full metric+Cholesky; 3-centre for the {per_atom} aux shells of one atom "
+            f"x{natom}; triangular solve on {ncs} of {nao * nao} columns; J/K on {nps} of "
+            f"{naux} aux functions; scaled to one build")
+    del T
+    return total, desc, O.num_threads(), t
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    m, nocc = make_molecule(args.workload)
+    secs = []
+    for i in range(args.warmup + args.steps):
+        s, desc, cores, _ = oracle_sample(m, nocc)
+        if i >= args.warmup:
+            secs.append(s)
+    value = 1.0 / statistics.mean(secs)
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(secs),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "note": WORKLOADS[args.workload]["note"]},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+# ---- our arm -------------------------------------------------------------------------------
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_2404_09452_gb300 import dfjk, inputs as I
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    prec = dfjk.DFJK_MIXED if args.precision == "mixed" else dfjk.DFJK_FP64
+    m, nocc = make_molecule(args.workload)
+
+    # input preparation (outside any timed region): C_occ orthonormal in the
+    # overlap metric the library computes; kept-pair columns for the flop count
+    h0 = dfjk.Handle(m, precision=prec)
+    S = h0.overlap().cpu().numpy()
+    Cnp = I.orthonormalize(I.c_occ_raw(m.nao, nocc, 3000 + rank), S)
+    mask = h0.pair_mask().cpu().numpy()
+    nc = [(s.l + 1) * (s.l + 2) // 2 for s in m.orb.shells]
+    ncol = sum(nc[a] * nc[b] for a in range(len(nc)) for b in range(a + 1) if mask[a, b])
+    ncol -= sum(nc[a] * (nc[a] - 1) // 2 for a in range(len(nc)) if mask[a, a])
+    h0.close()
+    C = torch.from_numpy(Cnp).cuda()
+    J = torch.empty((1, m.nao, m.nao), dtype=torch.float64, device="cuda")
+    K = torch.empty_like(J)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        h = dfjk.Handle(m, precision=prec)
+        _, _, EJ, EK = h.build(C, J=J, K=K)
+        h.close()
+        return EJ[0], EK[0]
+
+    for _ in range(args.warmup):
+        energies = step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    dfjk.phase_times()
+    dfjk.set_timing(True)
+    n0 = dfjk.launch_count()
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    evs[0].record(stream)
+    for i in range(args.steps):
+        energies = step()
+        evs[i + 1].record(stream)
+    torch.cuda.synchronize()
+    launches = dfjk.launch_count() - n0
+    dfjk.set_timing(False)
+    phases = dfjk.phase_times()
+    clocks = sampler.stop()
+    if dist:
+        dist.barrier()
+    total_ms = evs[0].elapsed_time(evs[-1])
+    step_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)]
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * args.steps / (total_ms / 1e3)
+
+    # e2e: public API, pinned host C in, J/K/energies out, copies timed
+    Ch = torch.from_numpy(Cnp).pin_memory()
+    Jh = torch.empty((1, m.nao, m.nao), dtype=torch.float64).pin_memory()
+    Kh = torch.empty_like(Jh).pin_memory()
+    h2d = Ch.numel() * 8 + 8 * (m.coords.size + sum(2 * len(s.exps) for s in m.orb.shells + m.aux.shells))
+    d2h = 2 * m.nao * m.nao * 8 + 16
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        Cd = Ch.to("cuda", non_blocking=True)
+        h = dfjk.Handle(m, precision=prec)
+        Jd, Kd, EJ, EK = h.build(Cd)
+        Jh.copy_(Jd, non_blocking=True)
+        Kh.copy_(Kd, non_blocking=True)
+        torch.cuda.synchronize()
+        h.close()
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = world * args.e2e_steps / e2e_s
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    flops = algorithmic_flops(m.nao, m.naux, nocc, ncol)
+    per_step = {k: v / args.steps for k, v in phases.items()}
+    step_flops = sum(flops.values())
+    # dominant dense phase
+    dom = max(flops, key=lambda k: per_step.get(k, 0.0))
+    dom_ms = per_step[dom]
+    achieved = flops[dom] / (dom_ms / 1e3) / 1e12
+    fp64 = prec == dfjk.DFJK_FP64
+    roof = {
+        "kernel": dom, "bound": "alu" if fp64 else "tensor",
+        "achieved": achieved, "unit": "TFLOP/s",
+        "peak": FP64_PEAK_GFLOPS / 1e3 if fp64 else None,
+        "peak_source": "measured FP64 DFMA rate of this GPU pool (FP64 FMA-chain probe)" if fp64 else None,
+        "traffic": None,
+        "algorithmic_flops_per_launch": flops[dom], "ms_per_launch": dom_ms,
+    }
+    if roof["peak"]:
+        roof["frac"] = achieved / roof["peak"]
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if fp64 else "f64+bf16-sliced",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "note": WORKLOADS[args.workload]["note"],
+                   "natom": m.natom, "nao": m.nao, "naux": m.naux, "nocc": nocc,
+                   "kept_ao_pairs": ncol, "precision": args.precision,
+                   "l2": "working set > L2 (B alone is GBs), no flush needed",
+                   "parallelism": f"replicas x{world}"},
+        "tflops": step_flops / (total_ms / args.steps / 1e3) / 1e12,
+        "p50_ms": statistics.median(step_ms), "p99_ms": max(step_ms) if len(step_ms) < 100 else
+        sorted(step_ms)[int(0.99 * len(step_ms))],
+        "phase_ms": per_step, "E_J": float(energies[0]), "E_K": float(energies[1]),
+        "roofline": roof,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        s, desc, cores, parts = oracle_sample(m, nocc)
+        out["cpu_baseline"] = {"value": 1.0 / s, "unit": UNIT, "cores": cores, "kind": "oracle",
+                               "sample": desc}
+    print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -137,6 +137,17 @@ const char *dfjk_last_error(void);
 /* Number of kernels this library has launched in this process.             */
 uint64_t dfjk_launch_count(void);
 
+/* Phase timing (process-wide).  dfjk_set_timing(1) makes every later call
+ * record a CUDA event pair around each phase, on the stream the phase is
+ * launched on; dfjk_phase_times waits for those events, writes the
+ * accumulated milliseconds of phases 0..n-1 to ms[] and clears them.
+ * Phases: 0 shell pairs + Schwarz + metric (a0-a2), 1 Cholesky + inverse
+ * (a3), 2 3-centre integrals (a4), 3 whitening (a5), 4 X = B C (a6),
+ * 5 K = sum X X^T (a7), 6 D, rho and J (a8), 7 energies (a9).             */
+#define DFJK_NPHASE 8
+int dfjk_set_timing(int32_t enable);
+int dfjk_phase_times(double *ms, int32_t n);
+
 /* ---- diagnostic accessors (tests and parity checks) ---------------------- */
 
 /* F_m(T) for m = 0..mmax at n points: T device [n], F device [n][mmax+1].

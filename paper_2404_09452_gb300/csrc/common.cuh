@@ -38,6 +38,15 @@ struct Error {
     DFJK_CUDA_CHECK(cudaGetLastError());                                        \
   } while (0)
 
+// Phase timer: a CUDA event pair per phase instance on the launching stream.
+struct PhaseScope {
+  int phase;
+  cudaStream_t st;
+  void *ev0 = nullptr;
+  PhaseScope(int phase, cudaStream_t st);
+  ~PhaseScope();
+};
+
 inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
 
 // Device status word bits (written by kernels, read by the host).

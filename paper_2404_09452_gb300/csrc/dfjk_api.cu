@@ -25,6 +25,50 @@ std::atomic<uint64_t> &launch_counter() {
   return c;
 }
 
+// ---- phase timing ----------------------------------------------------------------
+
+struct PhaseRec {
+  int phase;
+  cudaEvent_t a, b;
+};
+static std::mutex g_timing_mu;
+static bool g_timing = false;
+static std::vector<PhaseRec> g_phase_recs;
+static std::vector<cudaEvent_t> g_event_pool;
+
+static cudaEvent_t take_event() {
+  if (!g_event_pool.empty()) {
+    cudaEvent_t e = g_event_pool.back();
+    g_event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  DFJK_CUDA_CHECK(cudaEventCreate(&e));
+  return e;
+}
+
+PhaseScope::PhaseScope(int ph, cudaStream_t s) : phase(ph), st(s) {
+  std::lock_guard<std::mutex> lk(g_timing_mu);
+  if (!g_timing) return;
+  cudaEvent_t e = take_event();
+  DFJK_CUDA_CHECK(cudaEventRecord(e, st));
+  ev0 = (void *)e;
+}
+
+PhaseScope::~PhaseScope() {
+  if (!ev0) return;
+  std::lock_guard<std::mutex> lk(g_timing_mu);
+  cudaEvent_t e1;
+  if (!g_event_pool.empty()) {
+    e1 = g_event_pool.back();
+    g_event_pool.pop_back();
+  } else if (cudaEventCreate(&e1) != cudaSuccess) {
+    return;
+  }
+  if (cudaEventRecord(e1, st) != cudaSuccess) return;
+  g_phase_recs.push_back(PhaseRec{phase, (cudaEvent_t)ev0, e1});
+}
+
 // ---- device buffers -------------------------------------------------------------
 
 template <class T>
@@ -300,6 +344,7 @@ void make_resident(dfjk_ctx *h, cudaStream_t st) {
   h->status.alloc(1);
   DFJK_CUDA_CHECK(cudaMemsetAsync(h->status.p, 0, sizeof(int), st));
 
+  PhaseScope *ph0 = new PhaseScope(0, st);
   // a2: metric
   compute_metric(h, tab, st);
 
@@ -329,6 +374,7 @@ void make_resident(dfjk_ctx *h, cudaStream_t st) {
   max_sqrt_diag(h->V.p, h->naux, np, h->scal.p, st);
   h->pair_keep.alloc(std::max(npair, 1));
   screen_pairs(h->q.p, npair, h->scal.p, h->opt.schwarz_thresh, h->pair_keep.p, st);
+  delete ph0;
   std::vector<int> keep(npair);
   if (npair) DFJK_CUDA_CHECK(cudaMemcpyAsync(keep.data(), h->pair_keep.p, npair * sizeof(int), cudaMemcpyDeviceToHost, st));
   DFJK_CUDA_CHECK(cudaStreamSynchronize(st));
@@ -365,6 +411,7 @@ void make_resident(dfjk_ctx *h, cudaStream_t st) {
   h->colnu.upload(cnu, st);
 
   // a3: Cholesky and inverse of the metric
+  PhaseScope *ph1 = new PhaseScope(1, st);
   h->L.alloc((size_t)np * np);
   DFJK_CUDA_CHECK(cudaMemcpyAsync(h->L.p, h->V.p, h->V.bytes(), cudaMemcpyDeviceToDevice, st));
   h->Dinv.alloc((size_t)(np / 64) * 4096);
@@ -376,6 +423,7 @@ void make_resident(dfjk_ctx *h, cudaStream_t st) {
     DBuf<double> work;
     work.alloc((size_t)np * np);
     tri_inverse_f64(h->L.p, np, np, h->Dinv.p, h->Linv.p, work.p, st);
+    delete ph1;
     DFJK_CUDA_CHECK(cudaStreamSynchronize(st));
   }
 
@@ -406,6 +454,7 @@ void make_resident(dfjk_ctx *h, cudaStream_t st) {
       ++r1;
     }
     const long long c1 = (r1 < h->npair_kept) ? h->pair_col_h[h->kept_h[r1]] : h->ncol;
+    PhaseScope *ph2 = new PhaseScope(2, st);
     for (int c = 0; c < 6; ++c) {
       const int lo = std::max(r0, h->kept_cls_begin[c]), hi = std::min(r1, h->kept_cls_begin[c + 1]);
       if (hi <= lo) continue;
@@ -415,6 +464,8 @@ void make_resident(dfjk_ctx *h, cudaStream_t st) {
         launch_eri3c(cls[c][0], cls[c][1], lc, a, aux_args(h), tab, st);
       }
     }
+    delete ph2;
+    PhaseScope ph3(3, st);
     if (!mixed) {
       GemmArgs g;  // B[(mu,nu)][P] = sum_Q T[col][Q] Linv[P][Q]
       g.M = (int)(c1 - c0); g.N = np; g.K = np;
@@ -494,15 +545,21 @@ void build_fp64(dfjk_ctx *h, int nocc, const double *C, double *J, double *Kout,
   d.A = C; d.sAm = nocc; d.sAk = 1;
   d.B = C; d.sBn = nocc; d.sBk = 1;
   d.C = h->D.p; d.sCm = nao; d.sCn = 1;
-  gemm_f64(d, st);
-  rho_gemv_f64(h->B.p, h->ldb, nao, np, h->D.p, h->rho.p, h->rho_work.p, 128, st);
-  j_gemv_f64(h->B.p, h->ldb, nao, np, h->rho.p, J, st);
+  {
+    PhaseScope ph(6, st);
+    gemm_f64(d, st);
+    rho_gemv_f64(h->B.p, h->ldb, nao, np, h->D.p, h->rho.p, h->rho_work.p, 128, st);
+    j_gemv_f64(h->B.p, h->ldb, nao, np, h->rho.p, J, st);
+  }
   GemmArgs x;  // X[mu][P][i] = sum_nu B[(mu,nu)][P] C[nu][i]
   x.M = np; x.N = nocc; x.K = nao; x.batch = nao;
   x.A = h->B.p; x.sAm = 1; x.sAk = h->ldb; x.sAb = (long long)nao * h->ldb;
   x.B = C; x.sBn = 1; x.sBk = nocc; x.sBb = 0;
   x.C = h->X.p; x.sCm = nocc; x.sCn = 1; x.sCb = (long long)np * nocc;
-  gemm_f64(x, st);
+  {
+    PhaseScope ph(4, st);
+    gemm_f64(x, st);
+  }
   const long long kt = (long long)np * nocc;
   GemmArgs k;  // K[mu][nu] = sum_(P,i) X[mu][(P,i)] X[nu][(P,i)]
   k.M = nao; k.N = nao; k.K = (int)kt;
@@ -512,8 +569,12 @@ void build_fp64(dfjk_ctx *h, int nocc, const double *C, double *J, double *Kout,
   k.k_split = (int)((kt + h->ksplit - 1) / h->ksplit);
   k.k_split = ((k.k_split + 15) / 16) * 16;
   k.lower_only = 1;
-  gemm_f64(k, st);
-  reduce_sym_f64(h->Kpart.p, ceil_div(kt, k.k_split), nao, Kout, st);
+  {
+    PhaseScope ph(5, st);
+    gemm_f64(k, st);
+    reduce_sym_f64(h->Kpart.p, ceil_div(kt, k.k_split), nao, Kout, st);
+  }
+  PhaseScope ph(7, st);
   energies_f64(h->D.p, J, Kout, nao, e, h->en_work.p, st);
 }
 
@@ -548,6 +609,32 @@ const char *dfjk_status_string(int code) {
 const char *dfjk_last_error(void) { return g_last_error.c_str(); }
 
 uint64_t dfjk_launch_count(void) { return launch_counter().load(); }
+
+int dfjk_set_timing(int32_t enable) {
+  std::lock_guard<std::mutex> lk(g_timing_mu);
+  g_timing = enable != 0;
+  return DFJK_OK;
+}
+
+int dfjk_phase_times(double *ms, int32_t n) {
+  if (!ms || n < 0) return fail(Error{DFJK_ERR_ARG, "phase_times arguments"});
+  std::lock_guard<std::mutex> lk(g_timing_mu);
+  for (int i = 0; i < n; ++i) ms[i] = 0.0;
+  int rc = DFJK_OK;
+  for (auto &r : g_phase_recs) {
+    float t = 0.f;
+    if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) {
+      if (r.phase >= 0 && r.phase < n) ms[r.phase] += t;
+    } else {
+      rc = DFJK_ERR_CUDA;
+    }
+    g_event_pool.push_back(r.a);
+    g_event_pool.push_back(r.b);
+  }
+  g_phase_recs.clear();
+  if (rc) set_error("event timing failed");
+  return rc;
+}
 
 int dfjk_setup(const dfjk_basis *orb, const dfjk_basis *aux, int32_t natom, const double *coords,
                const dfjk_options *opt, void *stream, dfjk_handle *out) {

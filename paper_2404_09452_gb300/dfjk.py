@@ -48,7 +48,11 @@ EXPORTS = [
     "dfjk_get_B",
     "dfjk_get_pair_mask",
     "dfjk_get_three_center",
+    "dfjk_set_timing",
+    "dfjk_phase_times",
 ]
+
+PHASES = ["pairs+metric", "cholesky", "eri3c", "whiten", "X=BC", "K", "rho+J", "energies"]
 
 
 class DfjkError(RuntimeError):
@@ -119,6 +123,8 @@ def load_library(path: str = LIB_PATH):
     for fn in ("dfjk_get_metric", "dfjk_get_cholesky", "dfjk_get_B", "dfjk_get_pair_mask",
                "dfjk_get_three_center"):
         getattr(lib, fn).argtypes = [vp, vp, vp]
+    lib.dfjk_set_timing.argtypes = [i32]
+    lib.dfjk_phase_times.argtypes = [f64p, i32]
     for fn in EXPORTS:
         if fn not in ("dfjk_default_options", "dfjk_status_string", "dfjk_last_error",
                       "dfjk_launch_count"):
@@ -286,6 +292,17 @@ def boys(mmax: int, T, stream=None):
     _check(load_library().dfjk_boys(mmax, T.numel(), ctypes.c_void_p(T.data_ptr()),
                                     ctypes.c_void_p(F.data_ptr()), _stream(stream)))
     return F
+
+
+def set_timing(enable: bool):
+    _check(load_library().dfjk_set_timing(1 if enable else 0))
+
+
+def phase_times() -> dict:
+    """Accumulated device milliseconds per phase since the last call."""
+    ms = (ctypes.c_double * len(PHASES))()
+    _check(load_library().dfjk_phase_times(ms, len(PHASES)))
+    return {name: ms[i] for i, name in enumerate(PHASES)}
 
 
 def launch_count() -> int:
