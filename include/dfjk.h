@@ -168,6 +168,25 @@ int dfjk_get_pair_mask(dfjk_handle h, int32_t *keep, void *stream);
  * naux x nao x nao; recomputed on demand.                                    */
 int dfjk_get_three_center(dfjk_handle h, double *T, void *stream);
 
+/* ---- allocation-free variant ------------------------------------------------ */
+
+/* E[0] = Tr(D J)/2 and E[1] = Tr(D K)/2 for caller-owned device matrices
+ * D, J, K (n x n FP64, row-major) into E (device, 2 doubles), allocating
+ * nothing.  For callers that must not call cudaMalloc: an application whose
+ * memory pool already owns the device memory, or code that cannot take the
+ * device-wide synchronisation of cudaMalloc/cudaFree.  The paper has no
+ * counterpart.
+ *   Scratch: a 256 KB static device array inside this library (every GPU that
+ *   loads the library holds it until exit).  The first call on each device
+ *   looks up its address (cudaGetSymbolAddress) with that device current;
+ *   make that first call before any stream capture.  All calls share the
+ *   array and each call writes every slot it later reads; calls that overlap
+ *   on the GPU race on it.
+ *   Limit: n <= 8192; larger n returns DFJK_ERR_ARG without launching.
+ *   Enqueued on `stream`; E is valid once the stream reaches this point.     */
+int dfjk_energies_noalloc(int32_t n, const double *D, const double *J, const double *K,
+                          double *E, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

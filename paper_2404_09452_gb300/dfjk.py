@@ -50,6 +50,7 @@ EXPORTS = [
     "dfjk_get_three_center",
     "dfjk_set_timing",
     "dfjk_phase_times",
+    "dfjk_energies_noalloc",
 ]
 
 PHASES = ["pairs+metric", "cholesky", "eri3c", "whiten", "X=BC", "K", "rho+J", "energies"]
@@ -123,6 +124,7 @@ def load_library(path: str = LIB_PATH):
     for fn in ("dfjk_get_metric", "dfjk_get_cholesky", "dfjk_get_B", "dfjk_get_pair_mask",
                "dfjk_get_three_center"):
         getattr(lib, fn).argtypes = [vp, vp, vp]
+    lib.dfjk_energies_noalloc.argtypes = [i32, vp, vp, vp, vp, vp]
     lib.dfjk_set_timing.argtypes = [i32]
     lib.dfjk_phase_times.argtypes = [f64p, i32]
     for fn in EXPORTS:
@@ -303,6 +305,16 @@ def phase_times() -> dict:
     ms = (ctypes.c_double * len(PHASES))()
     _check(load_library().dfjk_phase_times(ms, len(PHASES)))
     return {name: ms[i] for i, name in enumerate(PHASES)}
+
+
+def energies_noalloc(D, J, K, E, stream=None):
+    """E[0] = Tr(D J)/2, E[1] = Tr(D K)/2 via the allocation-free entry point
+    (device tensors; n x n and 2 elements)."""
+    n = D.shape[-1]
+    _check(load_library().dfjk_energies_noalloc(
+        n, ctypes.c_void_p(D.data_ptr()), ctypes.c_void_p(J.data_ptr()),
+        ctypes.c_void_p(K.data_ptr()), ctypes.c_void_p(E.data_ptr()), _stream(stream)))
+    return E
 
 
 def launch_count() -> int:
