@@ -168,6 +168,15 @@ int dfjk_get_pair_mask(dfjk_handle h, int32_t *keep, void *stream);
  * naux x nao x nao; recomputed on demand.                                    */
 int dfjk_get_three_center(dfjk_handle h, double *T, void *stream);
 
+/* The exact sliced-product tensor-core GEMM used by DFJK_MIXED, on its own:
+ * C[z][m][n] = sum_k A[z][m][k] B[n][k] with A (batch x M x K), B (N x K),
+ * C (batch x M x N) device FP64 row-major; S = 6 or 8 slices of 6 bits per
+ * operand row and 1024-wide K block.  Allocates its slice buffers, synchronises
+ * `stream`.  *status (device int, may be NULL) receives STATUS bits.         */
+int dfjk_debug_sliced_gemm(int32_t batch, int32_t M, int32_t N, int32_t K, int32_t S,
+                           const double *A, const double *B, double *C, int32_t *status,
+                           void *stream);
+
 /* ---- allocation-free variant ------------------------------------------------ */
 
 /* E[0] = Tr(D J)/2 and E[1] = Tr(D K)/2 for caller-owned device matrices

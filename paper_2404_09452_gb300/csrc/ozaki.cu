@@ -1,0 +1,493 @@
+// Exact sliced-product GEMM on tcgen05 tensor cores, and the slicing kernels
+// that feed it.  See ozaki.cuh for the representation.  The scheme follows the
+// error-free splitting idea of Ozaki et al. (Numer. Algorithms 59, 2012):
+// split each operand into pieces whose products and partial sums are exact in
+// the accumulator, and recombine in higher precision.  Here the pieces are
+// 6-bit integers in BF16, the accumulator is FP32 in TMEM, the recombination
+// int64 + FP64 in registers.
+//
+// Kernel layout (one CTA per SM: 512 TMEM columns, ~200 KB shared memory):
+//   tile 128 (M, one TMEM lane per row) x 64 (N) ; K stages of 32 (64-byte
+//   swizzled rows) ; 2-3 stage TMA ring ; thread 0 issues TMA and MMA ; after
+//   each K-block of 1024 every thread drains its TMEM row: S level
+//   accumulators -> two int64 groups -> FP64 register accumulators.
+#include <cuda.h>
+
+#include <mutex>
+
+#include "common.cuh"
+#include "ozaki.cuh"
+#include "tc.cuh"
+
+namespace dfjk {
+
+// ---- slicing --------------------------------------------------------------------
+
+__device__ __forceinline__ int oz_expo_of(double mx) {
+  if (!(mx > 0.0)) return 0;
+  const long long u = __double_as_longlong(mx);
+  const int ex = (int)((u >> 52) & 0x7FF);
+  return ex == 0 ? -1021 : ex - 1022;  // |x| <= mx < 2^e
+}
+
+// round(x 2^(6S - e)) as an integer, |result| <= 2^(6S).
+template <int S>
+__device__ __forceinline__ long long oz_fixed(double x, int e) {
+  const long long u = __double_as_longlong(x);
+  const int ex = (int)((u >> 52) & 0x7FF);
+  if (ex == 0) return 0;  // zero (subnormals are far below any row maximum here)
+  const long long mant = (u & 0xFFFFFFFFFFFFFLL) | (1LL << 52);
+  const int sh = ex - 1075 + 6 * S - e;
+  long long n;
+  if (sh >= 0) n = mant << sh;
+  else if (sh < -60) n = 0;
+  else n = (mant + (1LL << (-sh - 1))) >> (-sh);
+  return u < 0 ? -n : n;
+}
+
+// Exponent of every (z, row, K-block); one warp per entry, lanes along K
+// (for K-contiguous sources).
+__global__ void oz_expo_warp_kernel(const double *__restrict__ src, long long sz, long long sr,
+                                    long long sk, int batch, int rows, int K, int rows_pad, int nkb,
+                                    int *__restrict__ expo) {
+  const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= (long long)batch * rows_pad * nkb) return;
+  const int kb = (int)(w % nkb);
+  const int r = (int)((w / nkb) % rows_pad);
+  const int z = (int)(w / ((long long)nkb * rows_pad));
+  double mx = 0.0;
+  if (r < rows) {
+    const int k1 = min(K, (kb + 1) * OZ_KB);
+    const double *p = src + z * sz + r * sr;
+    for (int k = kb * OZ_KB + lane; k < k1; k += 32) mx = fmax(mx, fabs(p[k * sk]));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (lane == 0) expo[w] = oz_expo_of(mx);
+}
+
+// Same, one thread per entry walking K (for row-contiguous sources).
+__global__ void oz_expo_thread_kernel(const double *__restrict__ src, long long sz, long long sr,
+                                      long long sk, int batch, int rows, int K, int rows_pad, int nkb,
+                                      int *__restrict__ expo) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)batch * rows_pad * nkb) return;
+  const int r = (int)(t % rows_pad);
+  const int kb = (int)((t / rows_pad) % nkb);
+  const int z = (int)(t / ((long long)rows_pad * nkb));
+  double mx = 0.0;
+  if (r < rows) {
+    const int k1 = min(K, (kb + 1) * OZ_KB);
+    const double *p = src + z * sz + r * sr;
+    for (int k = kb * OZ_KB; k < k1; ++k) mx = fmax(mx, fabs(p[k * sk]));
+  }
+  expo[((long long)z * rows_pad + r) * nkb + kb] = oz_expo_of(mx);
+}
+
+// Slices of 8 consecutive K elements of one row per thread.  `row_fast`
+// selects the thread order (consecutive rows for row-contiguous sources).
+template <int S>
+__global__ void oz_slice_kernel(const double *__restrict__ src, long long sz, long long sr, long long sk,
+                                int batch, int rows, int K, int rows_pad, int kpitch, int nkb,
+                                const int *__restrict__ expo, __nv_bfloat16 *__restrict__ out,
+                                int row_fast) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int nkc = kpitch / 8;
+  if (t >= (long long)batch * rows_pad * nkc) return;
+  int z, r, kc;
+  if (row_fast) {
+    r = (int)(t % rows_pad);
+    kc = (int)((t / rows_pad) % nkc);
+    z = (int)(t / ((long long)rows_pad * nkc));
+  } else {
+    kc = (int)(t % nkc);
+    r = (int)((t / nkc) % rows_pad);
+    z = (int)(t / ((long long)rows_pad * nkc));
+  }
+  const int k0 = kc * 8;
+  const int e = expo[((long long)z * rows_pad + r) * nkb + k0 / OZ_KB];
+  int dig[8][S];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int k = k0 + j;
+    const double x = (r < rows && k < K) ? src[z * sz + r * sr + (long long)k * sk] : 0.0;
+    long long n = oz_fixed<S>(x, e);
+#pragma unroll
+    for (int s = S - 1; s >= 1; --s) {
+      const int d = (int)(((n + 32) & 63) - 32);
+      dig[j][s] = d;
+      n = (n - d) >> 6;
+    }
+    dig[j][0] = (int)n;
+  }
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    __align__(16) __nv_bfloat16 v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = __float2bfloat16_rn((float)dig[j][s]);
+    *reinterpret_cast<uint4 *>(out + (((long long)z * S + s) * rows_pad + r) * kpitch + k0) =
+        *reinterpret_cast<const uint4 *>(v);
+  }
+}
+
+void oz_alloc(SlicedOp &op, int batch, int S, int rows, int K, int row_tile) {
+  oz_free(op);
+  op.batch = batch;
+  op.S = S;
+  op.rows = rows;
+  op.rows_pad = ((rows + row_tile - 1) / row_tile) * row_tile;
+  op.K = K;
+  op.kpitch = ((K + OZ_BK - 1) / OZ_BK) * OZ_BK;
+  op.nkb = (K + OZ_KB - 1) / OZ_KB;
+  const size_t nd = (size_t)batch * S * op.rows_pad * op.kpitch;
+  const size_t ne = (size_t)batch * op.rows_pad * op.nkb;
+  cudaError_t e1 = cudaMalloc(&op.data, nd * sizeof(__nv_bfloat16));
+  if (e1 != cudaSuccess) {
+    cudaGetLastError();
+    op.data = nullptr;
+    throw Error{DFJK_ERR_OOM, "slice planes: cudaMalloc failed"};
+  }
+  cudaError_t e2 = cudaMalloc(&op.expo, ne * sizeof(int));
+  if (e2 != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(op.data);
+    op.data = nullptr;
+    op.expo = nullptr;
+    throw Error{DFJK_ERR_OOM, "slice exponents: cudaMalloc failed"};
+  }
+}
+
+void oz_free(SlicedOp &op) {
+  if (op.data) cudaFree(op.data);
+  if (op.expo) cudaFree(op.expo);
+  op.data = nullptr;
+  op.expo = nullptr;
+}
+
+void oz_slice_f64(const double *src, long long sz, long long sr, long long sk, SlicedOp &op,
+                  cudaStream_t st) {
+  const long long nexp = (long long)op.batch * op.rows_pad * op.nkb;
+  if (sk == 1) {
+    oz_expo_warp_kernel<<<(unsigned)((nexp * 32 + 255) / 256), 256, 0, st>>>(
+        src, sz, sr, sk, op.batch, op.rows, op.K, op.rows_pad, op.nkb, op.expo);
+  } else {
+    oz_expo_thread_kernel<<<(unsigned)((nexp + 255) / 256), 256, 0, st>>>(
+        src, sz, sr, sk, op.batch, op.rows, op.K, op.rows_pad, op.nkb, op.expo);
+  }
+  DFJK_LAUNCHED();
+  const long long nt = (long long)op.batch * op.rows_pad * (op.kpitch / 8);
+  const int row_fast = sk != 1;
+  const unsigned grid = (unsigned)((nt + 255) / 256);
+  switch (op.S) {
+    case 6:
+      oz_slice_kernel<6><<<grid, 256, 0, st>>>(src, sz, sr, sk, op.batch, op.rows, op.K, op.rows_pad,
+                                               op.kpitch, op.nkb, op.expo, op.data, row_fast);
+      break;
+    case 8:
+      oz_slice_kernel<8><<<grid, 256, 0, st>>>(src, sz, sr, sk, op.batch, op.rows, op.K, op.rows_pad,
+                                               op.kpitch, op.nkb, op.expo, op.data, row_fast);
+      break;
+    default:
+      throw Error{DFJK_ERR_UNSUPPORTED, "slice count must be 6 or 8"};
+  }
+  DFJK_LAUNCHED();
+}
+
+// ---- GEMM -----------------------------------------------------------------------
+
+template <int S>
+struct OzCfg {
+  static constexpr int NST = (S <= 6) ? 3 : 2;
+  static constexpr int A_TILE = OZ_BM * OZ_BK * 2;
+  static constexpr int B_TILE = OZ_BN * OZ_BK * 2;
+  static constexpr int STAGE = S * (A_TILE + B_TILE);
+  static constexpr int SMEM = NST * STAGE + 1024 + 256;
+  static_assert(S * OZ_BN <= 512, "TMEM holds S level accumulators of 64 columns");
+};
+
+struct OzKernelArgs {
+  OzGemmArgs g;
+  const int *expoA, *expoB;
+  int rows_padA, rows_padB, nkbA, nkbB;
+};
+
+__device__ __forceinline__ double pow2(int e) { return __longlong_as_double((long long)(e + 1023) << 52); }
+
+template <int S>
+__global__ void __launch_bounds__(128, 1)
+    oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                   const OzKernelArgs ka) {
+  using Cfg = OzCfg<S>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t *full = (uint64_t *)(smem + Cfg::NST * Cfg::STAGE);
+  uint64_t *empty = full + Cfg::NST;
+  uint64_t *accf = empty + Cfg::NST;
+  uint32_t *tmem_holder = (uint32_t *)(accf + 1);
+
+  const OzGemmArgs &g = ka.g;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int m0 = blockIdx.x * OZ_BM, n0 = blockIdx.y * OZ_BN, z = blockIdx.z;
+  if (g.lower_only && n0 > m0 + OZ_BM - 1) return;
+  int kb0 = 0, kb1 = (g.K + OZ_KB - 1) / OZ_KB, kend = g.K;
+  if (g.kb_per_split > 0) {
+    kb0 = z * g.kb_per_split;
+    kb1 = min(kb1, kb0 + g.kb_per_split);
+  }
+  if (g.k_upto_n) {
+    kend = min(kend, n0 + OZ_BN);
+    kb1 = min(kb1, (kend + OZ_KB - 1) / OZ_KB);
+  }
+  const int zA = g.a_batched ? z : 0, zB = g.b_batched ? z : 0;
+
+  if (warp == 0) tc::tmem_alloc(tmem_holder, 512);
+  if (tid == 0) {
+    for (int i = 0; i < Cfg::NST; ++i) {
+      tc::mbar_init(&full[i], 1);
+      tc::mbar_init(&empty[i], 1);
+    }
+    tc::mbar_init(accf, 1);
+    tc::fence_mbar_init();
+    tc::prefetch_tensormap(&tmA);
+    tc::prefetch_tensormap(&tmB);
+  }
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tbase = *tmem_holder;
+
+  double acc[OZ_BN];
+#pragma unroll
+  for (int j = 0; j < OZ_BN; ++j) acc[j] = 0.0;
+  const int m = m0 + tid;
+  constexpr uint32_t IDESC = tc::idesc_bf16(OZ_BM, OZ_BN);
+  uint32_t gstage = 0;  // stages consumed so far (thread 0)
+  bool ok = true;
+  int kbi = 0;
+  for (int kb = kb0; kb < kb1; ++kb, ++kbi) {
+    const int kstart = kb * OZ_KB;
+    const int kstop = min(kend, kstart + OZ_KB);
+    const int nst = (kstop - kstart + OZ_BK - 1) / OZ_BK;
+    if (tid == 0) {
+      uint32_t lev_init = 0;
+      constexpr int dist = Cfg::NST - 1;
+      int issued = 0, consumed = 0;
+      for (int j = 0; j < nst + dist && ok; ++j) {
+        if (j < nst) {
+          const uint32_t gs = gstage + j, slot = gs % Cfg::NST;
+          if (gs >= (uint32_t)Cfg::NST &&
+              !tc::mbar_wait(&empty[slot], ((gs / Cfg::NST) - 1) & 1, g.timeout)) {
+            ok = false;
+            break;
+          }
+          uint8_t *stp = smem + slot * Cfg::STAGE;
+          tc::mbar_expect_tx(&full[slot], Cfg::STAGE);
+          const int kc = kstart + j * OZ_BK;
+#pragma unroll
+          for (int s = 0; s < S; ++s)
+            tc::tma_load_3d(stp + s * Cfg::A_TILE, &tmA, &full[slot], kc, m0, zA * S + s);
+#pragma unroll
+          for (int t = 0; t < S; ++t)
+            tc::tma_load_3d(stp + S * Cfg::A_TILE + t * Cfg::B_TILE, &tmB, &full[slot], kc, n0, zB * S + t);
+          ++issued;
+        }
+        if (j >= dist) {
+          const uint32_t gs = gstage + (j - dist), slot = gs % Cfg::NST;
+          if (!tc::mbar_wait(&full[slot], (gs / Cfg::NST) & 1, g.timeout)) {
+            ok = false;
+            break;
+          }
+          ++consumed;
+          tc::tc_fence_after();
+          const uint32_t sa = tc::smem_u32(smem + slot * Cfg::STAGE);
+          const uint32_t sb = sa + S * Cfg::A_TILE;
+#pragma unroll
+          for (int kk = 0; kk < OZ_BK / 16; ++kk)
+#pragma unroll
+            for (int s = 0; s < S; ++s)
+#pragma unroll
+              for (int t = 0; t < S - s; ++t) {
+                const int lev = s + t;
+                const uint64_t ad = tc::sdesc_k_sw64(sa + s * Cfg::A_TILE + kk * 32);
+                const uint64_t bd = tc::sdesc_k_sw64(sb + t * Cfg::B_TILE + kk * 32);
+                tc::mma_bf16(tbase + lev * OZ_BN, ad, bd, IDESC, (lev_init >> lev) & 1u);
+                lev_init |= 1u << lev;
+              }
+          tc::mma_commit(&empty[slot]);
+        }
+      }
+      if (ok) {
+        tc::mma_commit(accf);
+        gstage += nst;
+      } else {
+        if (g.status) atomicOr(g.status, STATUS_TIMEOUT);
+        // copies still in flight land before the CTA leaves
+        for (int c = consumed; c < issued; ++c) {
+          const uint32_t gs = gstage + c, slot = gs % Cfg::NST;
+          tc::mbar_wait(&full[slot], (gs / Cfg::NST) & 1, g.timeout);
+        }
+      }
+    }
+    // every thread: wait for this K-block's MMAs (bounded)
+    if (!tc::mbar_wait(accf, kbi & 1, g.timeout)) ok = false;
+    ok = __syncthreads_and(ok);
+    if (!ok) {
+      if (tid == 0 && g.status) atomicOr(g.status, STATUS_TIMEOUT);
+      break;
+    }
+    tc::tc_fence_after();
+    const int eA = ka.expoA[((long long)zA * ka.rows_padA + m) * ka.nkbA + kb];
+    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+#pragma unroll
+    for (int c = 0; c < OZ_BN / 16; ++c) {
+      long long T0[16], T1[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) T0[j] = T1[j] = 0;
+#pragma unroll
+      for (int lev = 0; lev < S; ++lev) {
+        float v[16];
+        tc::tmem_ld16(tbase + lane_base + lev * OZ_BN + c * 16, v);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const long long iv = (long long)__float2int_rn(v[j]);
+          if (lev < 4) T0[j] += iv << (6 * (3 - lev));
+          else T1[j] += iv << (6 * (7 - lev));
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int n = n0 + c * 16 + j;
+        const int eB = __ldg(ka.expoB + ((long long)zB * ka.rows_padB + n) * ka.nkbB + kb);
+        acc[c * 16 + j] = fma((double)T0[j], pow2(eA + eB - 30), acc[c * 16 + j]);
+        if (S > 4) acc[c * 16 + j] = fma((double)T1[j], pow2(eA + eB - 54), acc[c * 16 + j]);
+      }
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+  }
+
+  if (ok && m < g.M) {
+    if (g.mode == 0) {
+      double *o = g.out + (long long)z * g.out_bs + (long long)m * g.ldo;
+#pragma unroll
+      for (int j = 0; j < OZ_BN; ++j)
+        if (n0 + j < g.N) o[n0 + j] = acc[j];
+    } else {
+      const int mu = g.colmu[m], nu = g.colnu[m];
+      if (mu >= 0) {
+        double *o1 = g.out + ((long long)mu * g.nao + nu) * g.ldb;
+        double *o2 = g.out + ((long long)nu * g.nao + mu) * g.ldb;
+#pragma unroll
+        for (int j = 0; j < OZ_BN; ++j)
+          if (n0 + j < g.N) {
+            o1[n0 + j] = acc[j];
+            if (mu != nu) o2[n0 + j] = acc[j];
+          }
+      }
+    }
+  }
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tbase, 512);
+}
+
+// ---- host ---------------------------------------------------------------------------
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *,
+                                  CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                  CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+  static std::mutex mu;
+  static EncodeTiledFn fn = nullptr;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!fn) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    DFJK_CUDA_CHECK(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q));
+    if (!p || q != cudaDriverEntryPointSuccess)
+      throw Error{DFJK_ERR_CUDA, "cuTensorMapEncodeTiled is not available"};
+    fn = (EncodeTiledFn)p;
+  }
+  return fn;
+}
+
+static CUtensorMap make_map(const SlicedOp &op, int box_rows) {
+  CUtensorMap map;
+  cuuint64_t dims[3] = {(cuuint64_t)op.K, (cuuint64_t)op.rows_pad, (cuuint64_t)op.batch * op.S};
+  cuuint64_t strides[2] = {(cuuint64_t)op.kpitch * 2, (cuuint64_t)op.rows_pad * op.kpitch * 2};
+  cuuint32_t box[3] = {OZ_BK, (cuuint32_t)box_rows, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = encode_fn()(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, op.data, dims, strides, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) throw Error{DFJK_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")"};
+  return map;
+}
+
+template <int S>
+static void launch_oz(const SlicedOp &A, const SlicedOp &B, const OzGemmArgs &g, cudaStream_t st) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    DFJK_CUDA_CHECK(cudaFuncSetAttribute(oz_gemm_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         OzCfg<S>::SMEM));
+    attr_set = true;
+  }
+  const CUtensorMap ma = make_map(A, OZ_BM), mb = make_map(B, OZ_BN);
+  OzKernelArgs ka{g, A.expo, B.expo, A.rows_pad, B.rows_pad, A.nkb, B.nkb};
+  dim3 grid((unsigned)((g.M + OZ_BM - 1) / OZ_BM), (unsigned)((g.N + OZ_BN - 1) / OZ_BN), (unsigned)g.nz);
+  oz_gemm_kernel<S><<<grid, 128, OzCfg<S>::SMEM, st>>>(ma, mb, ka);
+  DFJK_LAUNCHED();
+}
+
+void oz_gemm(const SlicedOp &A, const SlicedOp &B, const OzGemmArgs &g, cudaStream_t st) {
+  if (g.M <= 0 || g.N <= 0 || g.nz <= 0) return;
+  if (A.S != B.S) throw Error{DFJK_ERR_ARG, "oz_gemm: slice counts differ"};
+  if (A.K != B.K || A.K < g.K) throw Error{DFJK_ERR_ARG, "oz_gemm: K mismatch"};
+  if (A.rows_pad % OZ_BM || B.rows_pad % OZ_BN) throw Error{DFJK_ERR_ARG, "oz_gemm: row padding"};
+  if ((long long)((g.M + OZ_BM - 1) / OZ_BM) * OZ_BM > A.rows_pad ||
+      (long long)((g.N + OZ_BN - 1) / OZ_BN) * OZ_BN > B.rows_pad)
+    throw Error{DFJK_ERR_ARG, "oz_gemm: tiles exceed the padded operands"};
+  if (g.a_batched && g.nz > A.batch) throw Error{DFJK_ERR_ARG, "oz_gemm: A batch"};
+  if (g.b_batched && g.nz > B.batch) throw Error{DFJK_ERR_ARG, "oz_gemm: B batch"};
+  if (g.mode == 1 && (!g.colmu || !g.colnu)) throw Error{DFJK_ERR_ARG, "oz_gemm: scatter map"};
+  if (g.nz > 65535 || (g.M + OZ_BM - 1) / OZ_BM > 2147483647) throw Error{DFJK_ERR_ARG, "oz_gemm: grid"};
+  switch (A.S) {
+    case 6: launch_oz<6>(A, B, g, st); break;
+    case 8: launch_oz<8>(A, B, g, st); break;
+    default: throw Error{DFJK_ERR_UNSUPPORTED, "slice count must be 6 or 8"};
+  }
+}
+
+}  // namespace dfjk
+
+// Debug entry point for tests: C[z][m][n] = sum_k A[z][m][k] B[n][k] through
+// slicing + the tensor-core GEMM (A, B, C device FP64 row-major).
+extern "C" int dfjk_debug_sliced_gemm(int32_t batch, int32_t M, int32_t N, int32_t K, int32_t S,
+                                      const double *A, const double *B, double *C, int32_t *status,
+                                      void *stream) {
+  using namespace dfjk;
+  SlicedOp a, b;
+  try {
+    if (batch < 1 || M < 1 || N < 1 || K < 1 || !A || !B || !C) throw Error{DFJK_ERR_ARG, "sliced gemm arguments"};
+    cudaStream_t st = (cudaStream_t)stream;
+    oz_alloc(a, batch, S, M, K, OZ_BM);
+    oz_alloc(b, 1, S, N, K, OZ_BN);
+    oz_slice_f64(A, (long long)M * K, K, 1, a, st);
+    oz_slice_f64(B, 0, K, 1, b, st);
+    OzGemmArgs g;
+    g.M = M; g.N = N; g.K = K; g.nz = batch; g.a_batched = 1;
+    g.mode = 0; g.out = C; g.ldo = N; g.out_bs = (long long)M * N;
+    g.status = (int *)status;
+    oz_gemm(a, b, g, st);
+    DFJK_CUDA_CHECK(cudaStreamSynchronize(st));
+    oz_free(a);
+    oz_free(b);
+    return DFJK_OK;
+  } catch (const Error &e) {
+    oz_free(a);
+    oz_free(b);
+    set_error(e.msg);
+    return e.code;
+  }
+}

@@ -1,0 +1,65 @@
+// Exact sliced-product GEMM on the tcgen05 tensor cores (ozaki.cu).
+//
+// An FP64 operand row is split, per block of OZ_KB consecutive K elements,
+// into S integer "slices" of 6 bits under a common power-of-two exponent e:
+//     x = 2^e * sum_{s<S} a_s 2^{-6(s+1)},  a_0 in [-64, 64], a_s in [-32, 31],
+// each a_s stored exactly as BF16.  A product of two slices is an integer
+// below 2^12 and a K-block sum of them stays below 2^24, so the FP32 tensor
+// core accumulation is exact whatever its internal rounding.  Products with
+// s + t = l share TMEM accumulator l; levels l < S are kept (error about
+// 2^-6S of |A||B| per term), combined exactly in int64 and added to FP64
+// accumulators once per K-block with scale 2^(eA + eB).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dfjk {
+
+constexpr int OZ_W = 6;      // bits per slice
+constexpr int OZ_KB = 1024;  // K elements per exponent block
+constexpr int OZ_BM = 128, OZ_BN = 64, OZ_BK = 32;
+
+// Slices of an operand: planes [batch][S][rows_pad][kpitch] (BF16, K
+// contiguous) and exponents [batch][rows_pad][nkb] (int32).
+struct SlicedOp {
+  __nv_bfloat16 *data = nullptr;
+  int *expo = nullptr;
+  int batch = 1, S = 0, rows = 0, rows_pad = 0, K = 0, kpitch = 0, nkb = 0;
+  size_t bytes() const {
+    return (size_t)batch * S * rows_pad * kpitch * 2 + (size_t)batch * rows_pad * nkb * 4;
+  }
+};
+
+// Sizes an operand (rows padded to `row_tile`, K pitch to OZ_BK) and allocates it.
+void oz_alloc(SlicedOp &op, int batch, int S, int rows, int K, int row_tile);
+void oz_free(SlicedOp &op);
+
+// Fills `op` from the FP64 view x(z, r, k) = src[z sz + r sr + k sk]
+// (rows >= op.rows and k >= op.K are zero).
+void oz_slice_f64(const double *src, long long sz, long long sr, long long sk, SlicedOp &op,
+                  cudaStream_t st);
+
+struct OzGemmArgs {
+  int M = 0, N = 0, K = 0;
+  int nz = 1;            // grid z: batches, or split-K parts
+  int a_batched = 0;     // A indexed by z
+  int b_batched = 0;     // B indexed by z
+  int kb_per_split = 0;  // >0: z selects K-blocks [z kb_per_split, (z+1) kb_per_split)
+  int k_upto_n = 0;      // K limited to < end of the N tile (B lower triangular)
+  int lower_only = 0;    // skip tiles strictly above the diagonal
+  int mode = 0;          // 0: out[z out_bs + m ldo + n] = C; 1: whitening scatter
+  double *out = nullptr;
+  long long ldo = 0, out_bs = 0;
+  const int *colmu = nullptr, *colnu = nullptr;  // mode 1: row m -> AO pair
+  int nao = 0;
+  long long ldb = 0;
+  int *status = nullptr;       // STATUS_TIMEOUT on an expired wait
+  long long timeout = 1 << 26; // polls per mbarrier wait
+};
+
+// out = A B^T with A (M x K) and B (N x K) in sliced form, both with S slices.
+void oz_gemm(const SlicedOp &A, const SlicedOp &B, const OzGemmArgs &g, cudaStream_t st);
+
+}  // namespace dfjk

@@ -48,6 +48,7 @@ EXPORTS = [
     "dfjk_get_B",
     "dfjk_get_pair_mask",
     "dfjk_get_three_center",
+    "dfjk_debug_sliced_gemm",
     "dfjk_set_timing",
     "dfjk_phase_times",
     "dfjk_energies_noalloc",
@@ -124,6 +125,7 @@ def load_library(path: str = LIB_PATH):
     for fn in ("dfjk_get_metric", "dfjk_get_cholesky", "dfjk_get_B", "dfjk_get_pair_mask",
                "dfjk_get_three_center"):
         getattr(lib, fn).argtypes = [vp, vp, vp]
+    lib.dfjk_debug_sliced_gemm.argtypes = [i32, i32, i32, i32, i32, vp, vp, vp, vp, vp]
     lib.dfjk_energies_noalloc.argtypes = [i32, vp, vp, vp, vp, vp]
     lib.dfjk_set_timing.argtypes = [i32]
     lib.dfjk_phase_times.argtypes = [f64p, i32]
@@ -305,6 +307,24 @@ def phase_times() -> dict:
     ms = (ctypes.c_double * len(PHASES))()
     _check(load_library().dfjk_phase_times(ms, len(PHASES)))
     return {name: ms[i] for i, name in enumerate(PHASES)}
+
+
+def sliced_gemm(A, B, S=6, stream=None):
+    """C[z] = A[z] B^T through the exact sliced tensor-core GEMM (FP64 device
+    tensors; A [batch, M, K] or [M, K], B [N, K])."""
+    torch = _torch()
+    A3 = A.contiguous().reshape(-1, A.shape[-2], A.shape[-1])
+    B = B.contiguous()
+    batch, M, K = A3.shape
+    N = B.shape[0]
+    C = torch.empty((batch, M, N), dtype=torch.float64, device=A.device)
+    status = torch.zeros(1, dtype=torch.int32, device=A.device)
+    _check(load_library().dfjk_debug_sliced_gemm(
+        batch, M, N, K, S, ctypes.c_void_p(A3.data_ptr()), ctypes.c_void_p(B.data_ptr()),
+        ctypes.c_void_p(C.data_ptr()), ctypes.c_void_p(status.data_ptr()), _stream(stream)))
+    if int(status.item()) != 0:
+        raise DfjkError(6, f"device status {int(status.item())}")
+    return C.reshape(A.shape[:-1] + (N,))
 
 
 def energies_noalloc(D, J, K, E, stream=None):
