@@ -14,7 +14,7 @@
 #include "common.cuh"
 #include "integrals.cuh"
 #include "linalg.cuh"
-#include "mixed.cuh"
+#include "ozaki.cuh"
 
 namespace dfjk {
 
@@ -204,15 +204,16 @@ struct dfjk_ctx {
   // metric
   DBuf<double> V, L, Linv, Dinv;
   DBuf<int> status;
-  // whitened tensor: FP64 B[(mu nao + nu) ldb + P] or the mixed representation
+  // whitened tensor: FP64 B[(mu nao + nu) ldb + P]; in DFJK_MIXED also its
+  // 6-slice form for the tensor-core X = B C (batch mu, rows P, K nu)
   DBuf<double> B;
   long long ldb = 0;
-  MixedB mixedB;
+  SlicedOp Bsl;
   // build workspace
   int ws_nocc = -1;
   DBuf<double> D, rho, rho_work, X, Kpart, en_work, e;
   int ksplit = 1;
-  MixedWork mixedW;
+  SlicedOp Csl, Xsl;  // DFJK_MIXED build operands
 };
 
 namespace {
@@ -249,8 +250,9 @@ void enumerate_pairs(dfjk_ctx *h) {
 
 size_t resident_estimate(const dfjk_ctx *h) {
   const size_t np2 = (size_t)h->naux_pad * h->naux_pad;
-  size_t b = (h->opt.precision == DFJK_MIXED) ? mixed_B_bytes(h->nao, h->naux_pad)
-                                              : (size_t)h->nao * h->nao * h->naux_pad * sizeof(double);
+  const size_t nao2p = (size_t)h->nao * h->nao * h->naux_pad;
+  size_t b = nao2p * sizeof(double);
+  if (h->opt.precision == DFJK_MIXED) b += nao2p * 6 * 2 + nao2p / 4;  // slices + padding slack
   return b + 3 * np2 * sizeof(double);
 }
 
@@ -429,12 +431,13 @@ void make_resident(dfjk_ctx *h, cudaStream_t st) {
 
   // a4 + a5: 3-centre integrals in column slabs, whitened into B
   const bool mixed = h->opt.precision == DFJK_MIXED;
-  if (!mixed) {
-    h->ldb = np;
-    h->B.alloc((size_t)h->nao * h->nao * np);
-    DFJK_CUDA_CHECK(cudaMemsetAsync(h->B.p, 0, h->B.bytes(), st));
-  } else {
-    mixed_alloc_B(h->mixedB, h->nao, np, st);
+  h->ldb = np;
+  h->B.alloc((size_t)h->nao * h->nao * np);
+  DFJK_CUDA_CHECK(cudaMemsetAsync(h->B.p, 0, h->B.bytes(), st));
+  SlicedOp Linv8, T8;
+  if (mixed) {  // L^-1 as the B operand of the whitening (rows P, K Q), 8 slices
+    oz_alloc(Linv8, 1, 8, np, np, OZ_BN);
+    oz_slice_f64(h->Linv.p, 0, np, 1, Linv8, st);
   }
   const long long slab_budget = 4LL << 30;  // bytes of one T slab
   long long slab_cols = std::max<long long>(36, slab_budget / ((long long)np * 8));
@@ -475,23 +478,40 @@ void make_resident(dfjk_ctx *h, cudaStream_t st) {
       g.colmu = h->colmu.p + c0; g.colnu = h->colnu.p + c0;
       g.nao = h->nao; g.ldo = h->ldb; g.out = h->B.p;
       gemm_f64(g, st);
-    } else {
-      mixed_whiten_slab(h->mixedB, T.p, (int)(c1 - c0), np, h->Linv.p, h->colmu.p + c0,
-                        h->colnu.p + c0, h->nao, st);
+    } else {  // the same product on the tensor cores, 8 slices per operand
+      const int ncols = (int)(c1 - c0);
+      if (!T8.data || T8.rows_pad < ncols) oz_alloc(T8, 1, 8, (int)slab_cols, np, OZ_BM);
+      T8.rows = ncols;
+      oz_slice_f64(T.p, 0, np, 1, T8, st);
+      OzGemmArgs g;
+      g.M = ncols; g.N = np; g.K = np; g.k_upto_n = 1;
+      g.mode = 1; g.out = h->B.p; g.colmu = h->colmu.p + c0; g.colnu = h->colnu.p + c0;
+      g.nao = h->nao; g.ldb = h->ldb; g.status = h->status.p; g.timeout = h->opt.timeout_iters;
+      oz_gemm(T8, Linv8, g, st);
     }
     r0 = r1;
+  }
+  if (mixed) {
+    DFJK_CUDA_CHECK(cudaStreamSynchronize(st));
+    oz_free(T8);
+    oz_free(Linv8);
+    // B as the A operand of X = B C: batch mu, rows P, K nu (6 slices)
+    PhaseScope ph(3, st);
+    oz_alloc(h->Bsl, h->nao, 6, np, h->nao, OZ_BM);
+    oz_slice_f64(h->B.p, (long long)h->nao * h->ldb, 1, h->ldb, h->Bsl, st);
   }
   int status = 0;
   DFJK_CUDA_CHECK(cudaMemcpyAsync(&status, h->status.p, sizeof(int), cudaMemcpyDeviceToHost, st));
   DFJK_CUDA_CHECK(cudaStreamSynchronize(st));
   if (status & STATUS_NOT_PD)
     throw Error{DFJK_ERR_NOT_PD, "(P|Q) metric is not positive definite (non-positive Cholesky pivot)"};
+  if (status & STATUS_TIMEOUT) throw Error{DFJK_ERR_TIMEOUT, "a bounded device wait expired during setup"};
   h->resident = true;
 }
 
 void release_device(dfjk_ctx *h) {
   h->B.release();
-  mixed_release_B(h->mixedB);
+  oz_free(h->Bsl);
   h->V.release();
   h->L.release();
   h->Linv.release();
@@ -507,7 +527,8 @@ void release_device(dfjk_ctx *h) {
   h->Kpart.release();
   h->en_work.release();
   h->e.release();
-  mixed_release_work(h->mixedW);
+  oz_free(h->Csl);
+  oz_free(h->Xsl);
   h->ws_nocc = -1;
   h->resident = false;
 }
@@ -518,7 +539,7 @@ void ensure_workspace(dfjk_ctx *h, int nocc, int nset) {
     h->D.alloc(nao2);
     h->rho.alloc(h->naux_pad);
     h->rho_work.alloc((size_t)128 * ceil_div(h->naux_pad, 256) * 256);
-    if (h->opt.precision != DFJK_MIXED) h->X.alloc((size_t)h->nao * h->naux_pad * nocc);
+    h->X.alloc((size_t)h->nao * h->naux_pad * nocc);
     const int t = ceil_div(h->nao, 64);
     const int tiles = t * (t + 1) / 2;
     h->ksplit = std::max(1, std::min(64, ceil_div(4 * 152, tiles)));
@@ -537,9 +558,13 @@ __global__ void split_energies_kernel(const double *e, int nset, double *EJ, dou
   }
 }
 
-void build_fp64(dfjk_ctx *h, int nocc, const double *C, double *J, double *Kout, double *e,
-                cudaStream_t st) {
+// Steps a6-a9 for one occupied set.  DFJK_FP64 runs X = B C and K on the
+// FP64 pipe; DFJK_MIXED runs both on the tensor cores as exact sliced
+// products (6 slices); D, rho, J and the energies are FP64 in both.
+void build_one(dfjk_ctx *h, int nocc, const double *C, double *J, double *Kout, double *e,
+               cudaStream_t st) {
   const int nao = h->nao, np = h->naux_pad;
+  const bool mixed = h->opt.precision == DFJK_MIXED;
   GemmArgs d;  // D = C C^T
   d.M = nao; d.N = nao; d.K = nocc;
   d.A = C; d.sAm = nocc; d.sAk = 1;
@@ -551,28 +576,58 @@ void build_fp64(dfjk_ctx *h, int nocc, const double *C, double *J, double *Kout,
     rho_gemv_f64(h->B.p, h->ldb, nao, np, h->D.p, h->rho.p, h->rho_work.p, 128, st);
     j_gemv_f64(h->B.p, h->ldb, nao, np, h->rho.p, J, st);
   }
-  GemmArgs x;  // X[mu][P][i] = sum_nu B[(mu,nu)][P] C[nu][i]
-  x.M = np; x.N = nocc; x.K = nao; x.batch = nao;
-  x.A = h->B.p; x.sAm = 1; x.sAk = h->ldb; x.sAb = (long long)nao * h->ldb;
-  x.B = C; x.sBn = 1; x.sBk = nocc; x.sBb = 0;
-  x.C = h->X.p; x.sCm = nocc; x.sCn = 1; x.sCb = (long long)np * nocc;
-  {
-    PhaseScope ph(4, st);
-    gemm_f64(x, st);
-  }
   const long long kt = (long long)np * nocc;
-  GemmArgs k;  // K[mu][nu] = sum_(P,i) X[mu][(P,i)] X[nu][(P,i)]
-  k.M = nao; k.N = nao; k.K = (int)kt;
-  k.A = h->X.p; k.sAm = kt; k.sAk = 1;
-  k.B = h->X.p; k.sBn = kt; k.sBk = 1;
-  k.C = h->Kpart.p; k.sCm = nao; k.sCn = 1; k.sCb = (long long)nao * nao;
-  k.k_split = (int)((kt + h->ksplit - 1) / h->ksplit);
-  k.k_split = ((k.k_split + 15) / 16) * 16;
-  k.lower_only = 1;
-  {
+  if (!mixed) {
+    GemmArgs x;  // X[mu][P][i] = sum_nu B[(mu,nu)][P] C[nu][i]
+    x.M = np; x.N = nocc; x.K = nao; x.batch = nao;
+    x.A = h->B.p; x.sAm = 1; x.sAk = h->ldb; x.sAb = (long long)nao * h->ldb;
+    x.B = C; x.sBn = 1; x.sBk = nocc; x.sBb = 0;
+    x.C = h->X.p; x.sCm = nocc; x.sCn = 1; x.sCb = (long long)np * nocc;
+    {
+      PhaseScope ph(4, st);
+      gemm_f64(x, st);
+    }
+    GemmArgs k;  // K[mu][nu] = sum_(P,i) X[mu][(P,i)] X[nu][(P,i)]
+    k.M = nao; k.N = nao; k.K = (int)kt;
+    k.A = h->X.p; k.sAm = kt; k.sAk = 1;
+    k.B = h->X.p; k.sBn = kt; k.sBk = 1;
+    k.C = h->Kpart.p; k.sCm = nao; k.sCn = 1; k.sCb = (long long)nao * nao;
+    k.k_split = (int)((kt + h->ksplit - 1) / h->ksplit);
+    k.k_split = ((k.k_split + 15) / 16) * 16;
+    k.lower_only = 1;
     PhaseScope ph(5, st);
     gemm_f64(k, st);
     reduce_sym_f64(h->Kpart.p, ceil_div(kt, k.k_split), nao, Kout, st);
+  } else {
+    {
+      PhaseScope ph(4, st);
+      if (!h->Csl.data || h->Csl.rows != nocc) oz_alloc(h->Csl, 1, 6, nocc, nao, OZ_BN);
+      oz_slice_f64(C, 0, 1, nocc, h->Csl, st);  // rows i, K nu
+      OzGemmArgs x;
+      x.M = np; x.N = nocc; x.K = nao; x.nz = nao; x.a_batched = 1;
+      x.mode = 0; x.out = h->X.p; x.ldo = nocc; x.out_bs = (long long)np * nocc;
+      x.status = h->status.p; x.timeout = h->opt.timeout_iters;
+      oz_gemm(h->Bsl, h->Csl, x, st);
+    }
+    PhaseScope ph(5, st);
+    if (!h->Xsl.data || h->Xsl.K != kt) oz_alloc(h->Xsl, 1, 6, nao, (int)kt, OZ_BM);
+    oz_slice_f64(h->X.p, 0, kt, 1, h->Xsl, st);
+    const int mt = ceil_div(nao, OZ_BM), nt = ceil_div(nao, OZ_BN);
+    int tiles = 0;
+    for (int i = 0; i < mt; ++i)
+      for (int j = 0; j < nt; ++j)
+        if (j * OZ_BN <= i * OZ_BM + OZ_BM - 1) ++tiles;
+    const int nkb = h->Xsl.nkb;
+    int nsplit = std::max(1, std::min(h->ksplit, (2 * 152 + tiles - 1) / tiles));
+    nsplit = std::min(nsplit, nkb);
+    const int per = ceil_div(nkb, nsplit);
+    nsplit = ceil_div(nkb, per);
+    OzGemmArgs k;
+    k.M = nao; k.N = nao; k.K = (int)kt; k.nz = nsplit; k.kb_per_split = per; k.lower_only = 1;
+    k.mode = 0; k.out = h->Kpart.p; k.ldo = nao; k.out_bs = (long long)nao * nao;
+    k.status = h->status.p; k.timeout = h->opt.timeout_iters;
+    oz_gemm(h->Xsl, h->Xsl, k, st);
+    reduce_sym_f64(h->Kpart.p, nsplit, nao, Kout, st);
   }
   PhaseScope ph(7, st);
   energies_f64(h->D.p, J, Kout, nao, e, h->en_work.p, st);
@@ -675,7 +730,7 @@ int dfjk_query(dfjk_handle h, int32_t *nao, int32_t *naux, int32_t *npair_kept, 
   if (nao) *nao = h->nao;
   if (naux) *naux = h->naux;
   if (npair_kept) *npair_kept = h->npair_kept;
-  if (bytes) *bytes = h->B.bytes() + mixed_B_resident_bytes(h->mixedB) + h->V.bytes() +
+  if (bytes) *bytes = h->B.bytes() + h->Bsl.bytes() + h->V.bytes() +
                       h->L.bytes() + h->Linv.bytes() + h->rec.bytes();
   return DFJK_OK;
 }
@@ -692,13 +747,7 @@ int dfjk_build(dfjk_handle h, int32_t nset, int32_t nocc, const double *C, doubl
     const size_t nao2 = (size_t)h->nao * h->nao;
     for (int s = 0; s < nset; ++s) {
       const double *Cs = C + (size_t)s * h->nao * nocc;
-      if (h->opt.precision == DFJK_MIXED)
-        mixed_build(h->mixedB, h->mixedW, h->nao, h->naux_pad, nocc, Cs, h->D.p, h->rho.p,
-                    h->rho_work.p, J + s * nao2, K + s * nao2, h->Kpart.p, h->ksplit, st);
-      else
-        build_fp64(h, nocc, Cs, J + s * nao2, K + s * nao2, h->e.p + 2 * s, st);
-      if (h->opt.precision == DFJK_MIXED)
-        energies_f64(h->D.p, J + s * nao2, K + s * nao2, h->nao, h->e.p + 2 * s, h->en_work.p, st);
+      build_one(h, nocc, Cs, J + s * nao2, K + s * nao2, h->e.p + 2 * s, st);
     }
     if (h->opt.energies_on_host) {
       std::vector<double> e(2 * nset);
@@ -809,16 +858,8 @@ int dfjk_get_B(dfjk_handle h, double *Bout, void *stream) {
     for (int i = 0; i < h->naux; ++i) ident[i] = i;
     DBuf<int> perm;
     perm.upload(ident, st);
-    if (h->opt.precision == DFJK_MIXED) {
-      DBuf<double> tmp;
-      tmp.alloc((size_t)h->nao * h->nao * h->naux_pad);
-      mixed_expand_B(h->mixedB, h->nao, h->naux_pad, tmp.p, st);
-      gather_B_f64(tmp.p, h->naux_pad, h->nao, perm.p, h->naux, Bout, st);
-      DFJK_CUDA_CHECK(cudaStreamSynchronize(st));
-    } else {
-      gather_B_f64(h->B.p, h->ldb, h->nao, perm.p, h->naux, Bout, st);
-      DFJK_CUDA_CHECK(cudaStreamSynchronize(st));
-    }
+    gather_B_f64(h->B.p, h->ldb, h->nao, perm.p, h->naux, Bout, st);
+    DFJK_CUDA_CHECK(cudaStreamSynchronize(st));
     return DFJK_OK;
   } catch (const Error &e) {
     return fail(e);
