@@ -214,6 +214,11 @@ struct dfjk_ctx {
   DBuf<double> D, rho, rho_work, X, Kpart, en_work, e;
   int ksplit = 1;
   SlicedOp Csl, Xsl;  // DFJK_MIXED build operands
+  ~dfjk_ctx() {
+    oz_free(Bsl);
+    oz_free(Csl);
+    oz_free(Xsl);
+  }
 };
 
 namespace {
@@ -434,7 +439,11 @@ void make_resident(dfjk_ctx *h, cudaStream_t st) {
   h->ldb = np;
   h->B.alloc((size_t)h->nao * h->nao * np);
   DFJK_CUDA_CHECK(cudaMemsetAsync(h->B.p, 0, h->B.bytes(), st));
-  SlicedOp Linv8, T8;
+  struct OzLocal {  // slice buffers that live only during setup
+    SlicedOp op;
+    ~OzLocal() { oz_free(op); }
+  } linv8_, t8_;
+  SlicedOp &Linv8 = linv8_.op, &T8 = t8_.op;
   if (mixed) {  // L^-1 as the B operand of the whitening (rows P, K Q), 8 slices
     oz_alloc(Linv8, 1, 8, np, np, OZ_BN);
     oz_slice_f64(h->Linv.p, 0, np, 1, Linv8, st);
