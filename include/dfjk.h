@@ -143,9 +143,16 @@ uint64_t dfjk_launch_count(void);
  * accumulated milliseconds of phases 0..n-1 to ms[] and clears them.
  * Phases: 0 shell pairs + Schwarz + metric (a0-a2), 1 Cholesky + inverse
  * (a3), 2 3-centre integrals (a4), 3 whitening (a5), 4 X = B C (a6),
- * 5 K = sum X X^T (a7), 6 D, rho and J (a8), 7 energies (a9).             */
-#define DFJK_NPHASE 8
+ * 5 K = sum X X^T (a7), 6 D, rho and J (a8), 7 energies (a9); in
+ * DFJK_MIXED also the tensor-core GEMM launches alone: 8 whitening, 9 X = B C,
+ * 10 K (each also counted inside phases 3, 4, 5).                          */
+#define DFJK_NPHASE 11
 int dfjk_set_timing(int32_t enable);
+
+/* Frees the device blocks the library keeps cached for reuse after handles
+ * release them (the cache holds at most DFJK_CACHE_BYTES per device,
+ * environment variable, default 96 GiB).                                     */
+int dfjk_trim_cache(void);
 int dfjk_phase_times(double *ms, int32_t n);
 
 /* ---- diagnostic accessors (tests and parity checks) ---------------------- */

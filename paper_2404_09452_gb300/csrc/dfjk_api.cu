@@ -15,6 +15,7 @@
 #include "integrals.cuh"
 #include "linalg.cuh"
 #include "ozaki.cuh"
+#include "pool.cuh"
 
 namespace dfjk {
 
@@ -78,12 +79,7 @@ struct DBuf {
   void alloc(size_t count) {
     release();
     if (count == 0) return;
-    cudaError_t e = cudaMalloc((void **)&p, count * sizeof(T));
-    if (e != cudaSuccess) {
-      p = nullptr;
-      cudaGetLastError();
-      throw Error{DFJK_ERR_OOM, "cudaMalloc of " + std::to_string(count * sizeof(T)) + " bytes failed"};
-    }
+    p = (T *)pool_alloc(count * sizeof(T));
     n = count;
   }
   void upload(const std::vector<T> &v, cudaStream_t st) {
@@ -91,7 +87,7 @@ struct DBuf {
     if (!v.empty()) DFJK_CUDA_CHECK(cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st));
   }
   void release() {
-    if (p) cudaFree(p);
+    if (p) pool_free(p, n * sizeof(T));
     p = nullptr;
     n = 0;
   }
@@ -496,6 +492,7 @@ void make_resident(dfjk_ctx *h, cudaStream_t st) {
       g.M = ncols; g.N = np; g.K = np; g.k_upto_n = 1;
       g.mode = 1; g.out = h->B.p; g.colmu = h->colmu.p + c0; g.colnu = h->colnu.p + c0;
       g.nao = h->nao; g.ldb = h->ldb; g.status = h->status.p; g.timeout = h->opt.timeout_iters;
+      g.phase = 8;
       oz_gemm(T8, Linv8, g, st);
     }
     r0 = r1;
@@ -616,6 +613,7 @@ void build_one(dfjk_ctx *h, int nocc, const double *C, double *J, double *Kout, 
       x.M = np; x.N = nocc; x.K = nao; x.nz = nao; x.a_batched = 1;
       x.mode = 0; x.out = h->X.p; x.ldo = nocc; x.out_bs = (long long)np * nocc;
       x.status = h->status.p; x.timeout = h->opt.timeout_iters;
+      x.phase = 9;
       oz_gemm(h->Bsl, h->Csl, x, st);
     }
     PhaseScope ph(5, st);
@@ -635,6 +633,7 @@ void build_one(dfjk_ctx *h, int nocc, const double *C, double *J, double *Kout, 
     k.M = nao; k.N = nao; k.K = (int)kt; k.nz = nsplit; k.kb_per_split = per; k.lower_only = 1;
     k.mode = 0; k.out = h->Kpart.p; k.ldo = nao; k.out_bs = (long long)nao * nao;
     k.status = h->status.p; k.timeout = h->opt.timeout_iters;
+    k.phase = 10;
     oz_gemm(h->Xsl, h->Xsl, k, st);
     reduce_sym_f64(h->Kpart.p, nsplit, nao, Kout, st);
   }

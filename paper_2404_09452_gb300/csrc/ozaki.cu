@@ -17,6 +17,7 @@
 
 #include "common.cuh"
 #include "ozaki.cuh"
+#include "pool.cuh"
 #include "tc.cuh"
 
 namespace dfjk {
@@ -142,25 +143,19 @@ void oz_alloc(SlicedOp &op, int batch, int S, int rows, int K, int row_tile) {
   op.nkb = (K + OZ_KB - 1) / OZ_KB;
   const size_t nd = (size_t)batch * S * op.rows_pad * op.kpitch;
   const size_t ne = (size_t)batch * op.rows_pad * op.nkb;
-  cudaError_t e1 = cudaMalloc(&op.data, nd * sizeof(__nv_bfloat16));
-  if (e1 != cudaSuccess) {
-    cudaGetLastError();
+  op.data = (__nv_bfloat16 *)pool_alloc(nd * sizeof(__nv_bfloat16));
+  try {
+    op.expo = (int *)pool_alloc(ne * sizeof(int));
+  } catch (...) {
+    pool_free(op.data, nd * sizeof(__nv_bfloat16));
     op.data = nullptr;
-    throw Error{DFJK_ERR_OOM, "slice planes: cudaMalloc failed"};
-  }
-  cudaError_t e2 = cudaMalloc(&op.expo, ne * sizeof(int));
-  if (e2 != cudaSuccess) {
-    cudaGetLastError();
-    cudaFree(op.data);
-    op.data = nullptr;
-    op.expo = nullptr;
-    throw Error{DFJK_ERR_OOM, "slice exponents: cudaMalloc failed"};
+    throw;
   }
 }
 
 void oz_free(SlicedOp &op) {
-  if (op.data) cudaFree(op.data);
-  if (op.expo) cudaFree(op.expo);
+  if (op.data) pool_free(op.data, (size_t)op.batch * op.S * op.rows_pad * op.kpitch * sizeof(__nv_bfloat16));
+  if (op.expo) pool_free(op.expo, (size_t)op.batch * op.rows_pad * op.nkb * sizeof(int));
   op.data = nullptr;
   op.expo = nullptr;
 }
@@ -427,6 +422,7 @@ static CUtensorMap make_map(const SlicedOp &op, int box_rows) {
 
 template <int S>
 static void launch_oz(const SlicedOp &A, const SlicedOp &B, const OzGemmArgs &g, cudaStream_t st) {
+  PhaseScope ph(g.phase, st);
   static bool attr_set = false;
   if (!attr_set) {
     DFJK_CUDA_CHECK(cudaFuncSetAttribute(oz_gemm_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,

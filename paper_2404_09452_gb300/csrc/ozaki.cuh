@@ -57,6 +57,7 @@ struct OzGemmArgs {
   long long ldb = 0;
   int *status = nullptr;       // STATUS_TIMEOUT on an expired wait
   long long timeout = 1 << 26; // polls per mbarrier wait
+  int phase = -1;              // phase timer id of this launch (-1: none)
 };
 
 // out = A B^T with A (M x K) and B (N x K) in sliced form, both with S slices.

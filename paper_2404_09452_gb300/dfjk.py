@@ -52,9 +52,11 @@ EXPORTS = [
     "dfjk_set_timing",
     "dfjk_phase_times",
     "dfjk_energies_noalloc",
+    "dfjk_trim_cache",
 ]
 
-PHASES = ["pairs+metric", "cholesky", "eri3c", "whiten", "X=BC", "K", "rho+J", "energies"]
+PHASES = ["pairs+metric", "cholesky", "eri3c", "whiten", "X=BC", "K", "rho+J", "energies",
+          "tc:whiten", "tc:X=BC", "tc:K"]
 
 
 class DfjkError(RuntimeError):
@@ -128,6 +130,7 @@ def load_library(path: str = LIB_PATH):
     lib.dfjk_debug_sliced_gemm.argtypes = [i32, i32, i32, i32, i32, vp, vp, vp, vp, vp]
     lib.dfjk_energies_noalloc.argtypes = [i32, vp, vp, vp, vp, vp]
     lib.dfjk_set_timing.argtypes = [i32]
+    lib.dfjk_trim_cache.argtypes = []
     lib.dfjk_phase_times.argtypes = [f64p, i32]
     for fn in EXPORTS:
         if fn not in ("dfjk_default_options", "dfjk_status_string", "dfjk_last_error",
