@@ -44,6 +44,12 @@ void launch_pair_kernel(int la, int lb, const PairClassArgs &a, const OrbArgs &o
   DFJK_LAUNCHED();
 }
 
+void launch_schwarz(int la, int lb, const PairClassArgs &a, const double *tab, cudaStream_t st) {
+  if (a.npair == 0) return;
+  DISPATCH_LALB(la, lb, (schwarz_kernel<A_, B_><<<a.npair, 64, 0, st>>>(a, tab)));
+  DFJK_LAUNCHED();
+}
+
 void launch_eri3c(int la, int lb, int lc, const Eri3cArgs &a, const AuxArgs &x, const double *tab,
                   cudaStream_t st) {
   if (a.npairs == 0 || a.naux_shells == 0) return;

@@ -30,6 +30,7 @@ struct PairClassArgs {
   const long long *rec_off;      // record offset (doubles) of the pair
   double *rec;                   // all records
   double *q;                     // Schwarz factor per pair (class-local)
+  const int *npp_of;             // primitive pairs per pair (class-local)
 };
 
 struct Eri3cArgs {
@@ -62,6 +63,7 @@ struct OverlapArgs {
 
 void launch_pair_kernel(int la, int lb, const PairClassArgs &a, const OrbArgs &o, const double *tab,
                         cudaStream_t st);
+void launch_schwarz(int la, int lb, const PairClassArgs &a, const double *tab, cudaStream_t st);
 void launch_eri3c_l0(int la, int lb, const Eri3cArgs &a, const AuxArgs &x, const double *tab,
                      cudaStream_t st);
 void launch_eri3c_l1(int la, int lb, const Eri3cArgs &a, const AuxArgs &x, const double *tab,

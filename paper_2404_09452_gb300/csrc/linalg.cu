@@ -38,6 +38,13 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(GemmArgs g) {
     C += z * g.sCb;
   }
   if (g.k_upto_n) kend = min(kend, (long long)(n0 + GBN));
+  int Mz = g.M;
+  if (g.rag_step > 0) {
+    const int valid = g.rag_n - (z * g.rag_step + g.rag_off);
+    if (valid <= 0 || m0 >= valid) return;
+    Mz = min(Mz, valid);
+    if (g.rag_clip_k) kend = min(kend, (long long)valid);
+  }
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   double acc[4][4];
 #pragma unroll
@@ -52,7 +59,7 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(GemmArgs g) {
       const int mm = A_KC ? (e >> 4) : (e & 63);
       const int kk = A_KC ? (e & 15) : (e >> 6);
       const long long gm = m0 + mm, gk = k0 + kk;
-      As[kk][mm] = (gm < g.M && gk < kend) ? A[gm * g.sAm + gk * g.sAk] : 0.0;
+      As[kk][mm] = (gm < Mz && gk < kend) ? A[gm * g.sAm + gk * g.sAk] : 0.0;
     }
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -81,7 +88,7 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(GemmArgs g) {
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     const int m = m0 + ty * 4 + i;
-    if (m >= g.M) continue;
+    if (m >= Mz) continue;
     if (SCATTER) {
       const int mu = g.colmu[m], nu = g.colnu[m];
       if (mu < 0) continue;
@@ -134,13 +141,18 @@ void gemm_f64(const GemmArgs &g, cudaStream_t st) {
 // Factors the 64x64 lower block at A in place (upper part zeroed) and writes
 // its inverse (lower triangular) to Dinv.  A non-positive or non-finite pivot
 // sets STATUS_NOT_PD and continues with pivot 1 so no NaN spreads.
+// Dynamic shared memory: two 64 x 65 FP64 arrays.
 __global__ void __launch_bounds__(256) potrf_diag_kernel(double *A, int lda, double *Dinv,
                                                          int *status) {
-  __shared__ double a[64][65];
-  const int tid = threadIdx.x;
+  extern __shared__ double psm[];
+  double(*a)[65] = reinterpret_cast<double(*)[65]>(psm);
+  double(*x)[65] = reinterpret_cast<double(*)[65]>(psm + 64 * 65);
+  __shared__ double rdiag[64];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   for (int e = tid; e < 64 * 64; e += 256) {
     const int i = e >> 6, j = e & 63;
     a[i][j] = (j <= i) ? A[(long long)i * lda + j] : 0.0;
+    x[i][j] = 0.0;
   }
   __syncthreads();
   for (int j = 0; j < 64; ++j) {
@@ -150,44 +162,52 @@ __global__ void __launch_bounds__(256) potrf_diag_kernel(double *A, int lda, dou
         atomicOr(status, STATUS_NOT_PD);
         d = 1.0;
       }
-      a[j][j] = sqrt(d);
+      const double l = sqrt(d);
+      a[j][j] = l;
+      rdiag[j] = 1.0 / l;
     }
     __syncthreads();
-    const double ljj = a[j][j];
-    for (int i = j + 1 + tid; i < 64; i += 256) a[i][j] /= ljj;
+    const double r = rdiag[j];
+    if (tid > j && tid < 64) a[tid][j] *= r;
     __syncthreads();
-    const int m = 63 - j;  // trailing size
-    for (int e = tid; e < m * m; e += 256) {
-      const int i = j + 1 + e / m, c = j + 1 + e % m;
-      if (c <= i) a[i][c] = fma(-a[i][j], a[c][j], a[i][c]);
+    for (int i = j + 1 + ty; i < 64; i += 16) {
+      const double lij = a[i][j];
+      for (int c = j + 1 + tx; c <= i; c += 16) a[i][c] = fma(-lij, a[c][j], a[i][c]);
     }
     __syncthreads();
   }
-  if (tid < 64) {  // column tid of the inverse by forward substitution
-    const int c = tid;
-    double x[64];
-    for (int i = 0; i < 64; ++i) x[i] = 0.0;
-    x[c] = 1.0 / a[c][c];
-    for (int i = c + 1; i < 64; ++i) {
-      double s = 0.0;
-      for (int k = c; k < i; ++k) s = fma(a[i][k], x[k], s);
-      x[i] = -s / a[i][i];
-    }
-    for (int i = 0; i < 64; ++i) Dinv[i * 64 + c] = x[i];
+  // X = L^-1 row by row: x[k][c] = -(sum_{c<=j<k} l[k][j] x[j][c]) / l[k][k];
+  // four lanes share each dot product.
+  const int c = tid >> 2, part = tid & 3;
+  for (int k = 0; k < 64; ++k) {
+    double sum = 0.0;
+    if (c < k)
+      for (int j = c + part; j < k; j += 4) sum = fma(a[k][j], x[j][c], sum);
+    sum += __shfl_xor_sync(0xffffffffu, sum, 1);
+    sum += __shfl_xor_sync(0xffffffffu, sum, 2);
+    if (part == 0 && c <= k) x[k][c] = (c == k) ? rdiag[k] : -sum * rdiag[k];
+    __syncthreads();
   }
   for (int e = tid; e < 64 * 64; e += 256) {
     const int i = e >> 6, j = e & 63;
     A[(long long)i * lda + j] = a[i][j];
+    Dinv[e] = x[i][j];
   }
 }
 
 void cholesky_f64(double *A, int n, int lda, double *Dinv, int *status, double *work,
                   cudaStream_t st) {
   (void)work;
+  static bool attr = false;
+  if (!attr) {
+    DFJK_CUDA_CHECK(cudaFuncSetAttribute(potrf_diag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         2 * 64 * 65 * (int)sizeof(double)));
+    attr = true;
+  }
   const int nb = n / 64;
   for (int k = 0; k < nb; ++k) {
     double *Akk = A + (long long)k * 64 * lda + k * 64;
-    potrf_diag_kernel<<<1, 256, 0, st>>>(Akk, lda, Dinv + (long long)k * 4096, status);
+    potrf_diag_kernel<<<1, 256, 2 * 64 * 65 * sizeof(double), st>>>(Akk, lda, Dinv + (long long)k * 4096, status);
     DFJK_LAUNCHED();
     const int rows = n - (k + 1) * 64;
     if (rows <= 0) continue;
@@ -216,36 +236,36 @@ __global__ void place_diag_blocks(double *Linv, int ld, const double *Dinv, int 
   }
 }
 
-static void tri_inv_rec(const double *L, int ld, double *Linv, double *work, int lo, int hi,
-                        cudaStream_t st) {
-  if (hi - lo <= 64) return;
-  const int half = (hi - lo) / 2;
-  const int mid = lo + ((half + 63) / 64) * 64;
-  tri_inv_rec(L, ld, Linv, work, lo, mid, st);
-  tri_inv_rec(L, ld, Linv, work, mid, hi, st);
-  const int n1 = mid - lo, n2 = hi - mid;
-  GemmArgs a;  // work = L21 Linv11   (n2 x n1)
-  a.M = n2; a.N = n1; a.K = n1;
-  a.A = L + (long long)mid * ld + lo; a.sAm = ld; a.sAk = 1;
-  a.B = Linv + (long long)lo * ld + lo; a.sBn = 1; a.sBk = ld;
-  a.C = work; a.sCm = n1; a.sCn = 1;
-  gemm_f64(a, st);
-  GemmArgs b;  // Linv21 = -Linv22 work
-  b.M = n2; b.N = n1; b.K = n2;
-  b.A = Linv + (long long)mid * ld + mid; b.sAm = ld; b.sAk = 1;
-  b.B = work; b.sBn = 1; b.sBk = n1;
-  b.C = Linv + (long long)mid * ld + lo; b.sCm = ld; b.sCn = 1;
-  b.alpha = -1.0;
-  gemm_f64(b, st);
-}
-
+// L^-1 bottom-up: at level s the already inverted diagonal blocks of size s
+// are merged in pairs (rows [j 2s, j 2s + s) and [j 2s + s, min(n, j 2s + 2s)));
+// the lower-left block of the merged inverse is -Linv22 (L21 Linv11).  All
+// pairs of a level run in one batched launch; the ragged last pair is clipped
+// in the kernel.
 void tri_inverse_f64(const double *L, int n, int ld, const double *Dinv, double *Linv,
                      double *work, cudaStream_t st) {
   DFJK_CUDA_CHECK(cudaMemsetAsync(Linv, 0, sizeof(double) * (size_t)n * ld, st));
   const int nb = n / 64;
   place_diag_blocks<<<nb, 256, 0, st>>>(Linv, ld, Dinv, nb);
   DFJK_LAUNCHED();
-  tri_inv_rec(L, ld, Linv, work, 0, n, st);
+  for (int s = 64; s < n; s *= 2) {
+    const int pairs = (n + 2 * s - 1) / (2 * s);
+    const long long dstep = 2LL * s * (ld + 1);
+    GemmArgs a;  // work_j = L21_j Linv11_j   (rows clipped to the valid part of block 2)
+    a.M = s; a.N = s; a.K = s; a.batch = pairs;
+    a.A = L + (long long)s * ld; a.sAm = ld; a.sAk = 1; a.sAb = dstep;
+    a.B = Linv; a.sBn = 1; a.sBk = ld; a.sBb = dstep;
+    a.C = work; a.sCm = s; a.sCn = 1; a.sCb = (long long)s * s;
+    a.rag_n = n; a.rag_step = 2 * s; a.rag_off = s;
+    gemm_f64(a, st);
+    GemmArgs b;  // Linv21_j = -Linv22_j work_j
+    b.M = s; b.N = s; b.K = s; b.batch = pairs;
+    b.A = Linv + (long long)s * ld + s; b.sAm = ld; b.sAk = 1; b.sAb = dstep;
+    b.B = work; b.sBn = 1; b.sBk = s; b.sBb = (long long)s * s;
+    b.C = Linv + (long long)s * ld; b.sCm = ld; b.sCn = 1; b.sCb = dstep;
+    b.alpha = -1.0;
+    b.rag_n = n; b.rag_step = 2 * s; b.rag_off = s; b.rag_clip_k = 1;
+    gemm_f64(b, st);
+  }
 }
 
 // ---- J: rho = B vec(D), J = B^T rho ------------------------------------------------

@@ -20,6 +20,9 @@ struct GemmArgs {
   int k_upto_n = 0;    // K range of an output tile limited to k < n_tile_end
                        // (B lower triangular in (n, k))
   int k_split = 0;     // >0: blockIdx.z selects K range [z k_split, ...) and C += z sCb
+  // ragged diagonal-block batches: batch z has rag_n - (z rag_step + rag_off)
+  // valid rows (and, with rag_clip_k, as many K); z with none returns
+  int rag_n = 0, rag_step = 0, rag_off = 0, rag_clip_k = 0;
   // whitening epilogue: row m is column `m` of a T slab; writes
   // out[(mu nao + nu) ldo + n] and out[(nu nao + mu) ldo + n]
   const int *colmu = nullptr, *colnu = nullptr;

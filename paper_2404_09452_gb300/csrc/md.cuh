@@ -200,70 +200,85 @@ __global__ void __launch_bounds__(128) pair_kernel(PairClassArgs args, OrbArgs o
         }
     }
 
-  // Schwarz: diagonal (ab|ab) per component from all primitive quadruples
-  // (runtime loops: a negligible share of the work).
+}
+
+
+// Schwarz factor q = sqrt(max over components of (ab|ab)) for every shell pair
+// of class (LA, LB): one block per pair, one thread per primitive quadruple
+// (kl, k'l') of the pair's records, then a block reduction.  Runtime loops:
+// this is a small share of the work and unrolling it costs minutes of compile.
+template <int LA, int LB>
+__global__ void __launch_bounds__(64) schwarz_kernel(PairClassArgs args, const double *__restrict__ boys_tab) {
+  constexpr int NT = nterms(LA, LB);
+  constexpr int REC = REC_HDR + NT;
+  constexpr int NCA = ncart(LA), NCB = ncart(LB);
   constexpr int L4 = 2 * (LA + LB);
+  __shared__ double red[64][NCA * NCB + 1];
+  const int ip = blockIdx.x;
+  const double *rec0 = args.rec + args.rec_off[ip];
+  const int npp = args.npp_of[ip];
   double diag[NCA * NCB];
   for (int c = 0; c < NCA * NCB; ++c) diag[c] = 0.0;
 #pragma unroll 1
-  for (int i = 0; i < npp; ++i) {
-    const double *ri = rec0 + (long long)i * REC;
+  for (int q = threadIdx.x; q < npp * npp; q += blockDim.x) {
+    const double *ri = rec0 + (long long)(q / npp) * REC;
+    const double *rj = rec0 + (long long)(q % npp) * REC;
+    const double p = ri[0], qq = rj[0];
+    const double s = rsqrt(p + qq);
+    const double al = p * qq * s * s;
+    const double X = ri[1] - rj[1], Y = ri[2] - rj[2], Z = ri[3] - rj[3];
+    double F[L4 + 1];
+    boys_eval<L4>(al * (X * X + Y * Y + Z * Z), boys_tab, F);
+    double R[ntuv(8)];
+    hermite_R_rt(L4, F, al, X, Y, Z, R);
+    // ri[4] rj[4] = c c K c c K (2 pi^2.5)^2 / (p q); wanted 2 pi^2.5 / (p q sqrt(p+q))
+    const double fac = ri[4] * rj[4] * s * (1.0 / (2.0 * 17.493418327624862846));
+    int k = 0;
 #pragma unroll 1
-    for (int j = 0; j < npp; ++j) {
-      const double *rj = rec0 + (long long)j * REC;
-      const double p = ri[0], q = rj[0];
-      const double s = rsqrt(p + q);
-      const double al = p * q * s * s;
-      const double X = ri[1] - rj[1], Y = ri[2] - rj[2], Z = ri[3] - rj[3];
-      double F[L4 + 1];
-      boys_eval<L4>(al * (X * X + Y * Y + Z * Z), boys_tab, F);
-      double R[ntuv(8)];
-      hermite_R_rt(L4, F, al, X, Y, Z, R);
-      // ri[4] rj[4] = c c K c c K (2 pi^2.5)^2 / (p q); we need 2 pi^2.5 /(p q sqrt(p+q))
-      const double fac = ri[4] * rj[4] * s * (1.0 / (2.0 * 17.493418327624862846));
-      int k = 0;
+    for (int ca = 0; ca < NCA; ++ca)
 #pragma unroll 1
-      for (int ca = 0; ca < NCA; ++ca)
+      for (int cb = 0; cb < NCB; ++cb) {
+        const int ax = cart_x(LA, ca), ay = cart_y(LA, ca), az = cart_z(LA, ca);
+        const int bx = cart_x(LB, cb), by = cart_y(LB, cb), bz = cart_z(LB, cb);
+        const int k0 = k;
+        double sum = 0.0;
 #pragma unroll 1
-        for (int cb = 0; cb < NCB; ++cb) {
-          const int ax = cart_x(LA, ca), ay = cart_y(LA, ca), az = cart_z(LA, ca);
-          const int bx = cart_x(LB, cb), by = cart_y(LB, cb), bz = cart_z(LB, cb);
-          const int k0 = k;
-          double sum = 0.0;
+        for (int t = 0; t <= ax + bx; ++t)
 #pragma unroll 1
-          for (int t = 0; t <= ax + bx; ++t)
+          for (int u = 0; u <= ay + by; ++u)
 #pragma unroll 1
-            for (int u = 0; u <= ay + by; ++u)
+            for (int v = 0; v <= az + bz; ++v) {
+              double inner = 0.0;
+              int k2 = k0;
 #pragma unroll 1
-              for (int v = 0; v <= az + bz; ++v) {
-                double inner = 0.0;
-                int k2 = k0;
+              for (int t2 = 0; t2 <= ax + bx; ++t2)
 #pragma unroll 1
-                for (int t2 = 0; t2 <= ax + bx; ++t2)
+                for (int u2 = 0; u2 <= ay + by; ++u2)
 #pragma unroll 1
-                  for (int u2 = 0; u2 <= ay + by; ++u2)
-#pragma unroll 1
-                    for (int v2 = 0; v2 <= az + bz; ++v2) {
-                      const double e2 = ((t2 + u2 + v2) & 1) ? -rj[REC_HDR + k2] : rj[REC_HDR + k2];
-                      inner = fma(e2, R[tuv_idx(t + t2, u + u2, v + v2)], inner);
-                      ++k2;
-                    }
-                sum = fma(ri[REC_HDR + k], inner, sum);
-                ++k;
-              }
-          diag[ca * NCB + cb] = fma(fac, sum, diag[ca * NCB + cb]);
-        }
-    }
+                  for (int v2 = 0; v2 <= az + bz; ++v2) {
+                    const double e2 = ((t2 + u2 + v2) & 1) ? -rj[REC_HDR + k2] : rj[REC_HDR + k2];
+                    inner = fma(e2, R[tuv_idx(t + t2, u + u2, v + v2)], inner);
+                    ++k2;
+                  }
+              sum = fma(ri[REC_HDR + k], inner, sum);
+              ++k;
+            }
+        diag[ca * NCB + cb] = fma(fac, sum, diag[ca * NCB + cb]);
+      }
   }
-  double qmax = 0.0;
-#pragma unroll
-  for (int ca = 0; ca < NCA; ++ca)
-#pragma unroll
-    for (int cb = 0; cb < NCB; ++cb) {
-      const double f = comp_factor(LA, ca) * comp_factor(LB, cb);
-      qmax = fmax(qmax, diag[ca * NCB + cb] * f * f);
-    }
-  args.q[ip] = sqrt(fmax(qmax, 0.0));
+  for (int c = 0; c < NCA * NCB; ++c) red[threadIdx.x][c] = diag[c];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double qmax = 0.0;
+    for (int ca = 0; ca < NCA; ++ca)
+      for (int cb = 0; cb < NCB; ++cb) {
+        double d = 0.0;
+        for (int t = 0; t < 64; ++t) d += red[t][ca * NCB + cb];
+        const double f = comp_factor(LA, ca) * comp_factor(LB, cb);
+        qmax = fmax(qmax, d * f * f);
+      }
+    args.q[ip] = sqrt(fmax(qmax, 0.0));
+  }
 }
 
 // ---- 3-centre kernel ---------------------------------------------------------

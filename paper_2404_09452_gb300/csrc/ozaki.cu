@@ -132,6 +132,45 @@ __global__ void oz_slice_kernel(const double *__restrict__ src, long long sz, lo
   }
 }
 
+// Slices of a 64 (rows) x 64 (K) tile per block for row-contiguous sources:
+// reads coalesced along rows, digits staged in shared memory as [s][row][k],
+// written as 128-byte row segments along K.
+template <int S>
+__global__ void __launch_bounds__(256) oz_slice_tr_kernel(const double *__restrict__ src, long long sz,
+                                                          long long sk, int rows, int K, int rows_pad,
+                                                          int kpitch, int nkb, const int *__restrict__ expo,
+                                                          __nv_bfloat16 *__restrict__ out) {
+  extern __shared__ __nv_bfloat16 tile[];  // [S][64][64 + 8]
+  constexpr int LD = 72;
+  const int z = blockIdx.z, r0 = blockIdx.y * 64, k0 = blockIdx.x * 64;
+  const int rr = threadIdx.x & 63, kq = threadIdx.x >> 6;
+  const int r = r0 + rr;
+  const int e = expo[((long long)z * rows_pad + r) * nkb + k0 / OZ_KB];
+  for (int kk = kq; kk < 64; kk += 4) {
+    const int k = k0 + kk;
+    const double x = (r < rows && k < K) ? src[z * sz + r + (long long)k * sk] : 0.0;
+    long long n = oz_fixed<S>(x, e);
+#pragma unroll
+    for (int s = S - 1; s >= 1; --s) {
+      const int d = (int)(((n + 32) & 63) - 32);
+      tile[(s * 64 + rr) * LD + kk] = __float2bfloat16_rn((float)d);
+      n = (n - d) >> 6;
+    }
+    tile[rr * LD + kk] = __float2bfloat16_rn((float)n);
+  }
+  __syncthreads();
+  const int c8 = threadIdx.x & 7, rw = threadIdx.x >> 3;  // 8 x 16-byte chunks per row
+#pragma unroll
+  for (int s = 0; s < S; ++s)
+    for (int rb = rw; rb < 64; rb += 32) {
+      const int kc = k0 + c8 * 8;
+      if (kc < kpitch) {
+        const uint4 v = *reinterpret_cast<const uint4 *>(&tile[(s * 64 + rb) * LD + c8 * 8]);
+        *reinterpret_cast<uint4 *>(out + (((long long)z * S + s) * rows_pad + r0 + rb) * kpitch + kc) = v;
+      }
+    }
+}
+
 void oz_alloc(SlicedOp &op, int batch, int S, int rows, int K, int row_tile) {
   oz_free(op);
   op.batch = batch;
@@ -171,6 +210,34 @@ void oz_slice_f64(const double *src, long long sz, long long sr, long long sk, S
         src, sz, sr, sk, op.batch, op.rows, op.K, op.rows_pad, op.nkb, op.expo);
   }
   DFJK_LAUNCHED();
+  if (sr == 1 && op.rows_pad % 64 == 0) {
+    // row-contiguous source: transpose through shared memory
+    const size_t smem = (size_t)op.S * 64 * 72 * sizeof(__nv_bfloat16);
+    dim3 grid((unsigned)((op.kpitch + 63) / 64), (unsigned)(op.rows_pad / 64), (unsigned)op.batch);
+    static bool attr6 = false, attr8 = false;
+    switch (op.S) {
+      case 6:
+        if (!attr6) {
+          DFJK_CUDA_CHECK(cudaFuncSetAttribute(oz_slice_tr_kernel<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+          attr6 = true;
+        }
+        oz_slice_tr_kernel<6><<<grid, 256, smem, st>>>(src, sz, sk, op.rows, op.K, op.rows_pad, op.kpitch,
+                                                       op.nkb, op.expo, op.data);
+        break;
+      case 8:
+        if (!attr8) {
+          DFJK_CUDA_CHECK(cudaFuncSetAttribute(oz_slice_tr_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+          attr8 = true;
+        }
+        oz_slice_tr_kernel<8><<<grid, 256, smem, st>>>(src, sz, sk, op.rows, op.K, op.rows_pad, op.kpitch,
+                                                       op.nkb, op.expo, op.data);
+        break;
+      default:
+        throw Error{DFJK_ERR_UNSUPPORTED, "slice count must be 6 or 8"};
+    }
+    DFJK_LAUNCHED();
+    return;
+  }
   const long long nt = (long long)op.batch * op.rows_pad * (op.kpitch / 8);
   const int row_fast = sk != 1;
   const unsigned grid = (unsigned)((nt + 255) / 256);
