@@ -120,6 +120,18 @@ int dfjk_query(dfjk_handle h, int32_t *nao, int32_t *naux, int32_t *npair_kept,
 int dfjk_build(dfjk_handle h, int32_t nset, int32_t nocc, const double *C_occ,
                double *J, double *K, double *E_J, double *E_K, void *stream);
 
+/* Steps a6-a9 for nmol resident handles at once (row a10, batching): the builds
+ * are spread over `nstreams` internal streams forked from and joined back to
+ * `stream`, so small molecules run concurrently.  Handle i uses nocc[i],
+ * C_occ[i] (device nao_i x nocc_i), J[i], K[i] (device nao_i x nao_i), and
+ * writes E_J[i], E_K[i] (device arrays of nmol doubles).  No host
+ * synchronisation: once each handle has been built at its nocc before (so
+ * its work buffers exist), the call can be captured in a CUDA graph.  Each
+ * handle may appear once per call.  Errors: DFJK_ERR_ARG, _STATE (evicted).  */
+int dfjk_build_batch(int32_t nmol, const dfjk_handle *hs, const int32_t *nocc,
+                     const double *const *C_occ, double *const *J, double *const *K,
+                     double *E_J, double *E_K, int32_t nstreams, void *stream);
+
 /* Overlap matrix S (device, nao x nao), computed by a device kernel; used to
  * orthonormalise occupied orbitals.                                           */
 int dfjk_overlap(dfjk_handle h, double *S, void *stream);

@@ -777,6 +777,62 @@ int dfjk_build(dfjk_handle h, int32_t nset, int32_t nocc, const double *C, doubl
   }
 }
 
+int dfjk_build_batch(int32_t nmol, const dfjk_handle *hs, const int32_t *nocc, const double *const *C,
+                     double *const *J, double *const *K, double *EJ, double *EK, int32_t nstreams,
+                     void *stream) {
+  try {
+    if (nmol < 0 || (nmol > 0 && (!hs || !nocc || !C || !J || !K || !EJ || !EK)))
+      throw Error{DFJK_ERR_ARG, "build_batch arguments"};
+    if (nmol == 0) return DFJK_OK;
+    nstreams = std::max(1, std::min(nstreams, 32));
+    cudaStream_t st = S(stream);
+    for (int i = 0; i < nmol; ++i) {
+      if (!hs[i] || nocc[i] < 1 || !C[i] || !J[i] || !K[i]) throw Error{DFJK_ERR_ARG, "build_batch entry"};
+      if (!hs[i]->resident) throw Error{DFJK_ERR_STATE, "build_batch: handle evicted"};
+      for (int j = 0; j < i; ++j)
+        if (hs[j] == hs[i]) throw Error{DFJK_ERR_ARG, "build_batch: a handle appears twice"};
+    }
+    // internal streams and events, created once per device
+    struct Fork {
+      std::vector<cudaStream_t> streams;
+      std::vector<cudaEvent_t> done;
+      cudaEvent_t start;
+    };
+    static std::mutex mu;
+    static std::map<int, Fork> forks;
+    int dev = 0;
+    DFJK_CUDA_CHECK(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(mu);
+    Fork &f = forks[dev];
+    if (f.streams.empty()) DFJK_CUDA_CHECK(cudaEventCreateWithFlags(&f.start, cudaEventDisableTiming));
+    while ((int)f.streams.size() < nstreams) {
+      cudaStream_t s2;
+      cudaEvent_t e2;
+      DFJK_CUDA_CHECK(cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking));
+      DFJK_CUDA_CHECK(cudaEventCreateWithFlags(&e2, cudaEventDisableTiming));
+      f.streams.push_back(s2);
+      f.done.push_back(e2);
+    }
+    DFJK_CUDA_CHECK(cudaEventRecord(f.start, st));
+    for (int k = 0; k < nstreams; ++k) DFJK_CUDA_CHECK(cudaStreamWaitEvent(f.streams[k], f.start, 0));
+    for (int i = 0; i < nmol; ++i) {
+      dfjk_ctx *h = hs[i];
+      cudaStream_t s2 = f.streams[i % nstreams];
+      ensure_workspace(h, nocc[i], 1);
+      build_one(h, nocc[i], C[i], J[i], K[i], h->e.p, s2);
+      split_energies_kernel<<<1, 64, 0, s2>>>(h->e.p, 1, EJ + i, EK + i);
+      DFJK_LAUNCHED();
+    }
+    for (int k = 0; k < nstreams; ++k) {
+      DFJK_CUDA_CHECK(cudaEventRecord(f.done[k], f.streams[k]));
+      DFJK_CUDA_CHECK(cudaStreamWaitEvent(st, f.done[k], 0));
+    }
+    return DFJK_OK;
+  } catch (const Error &e) {
+    return fail(e);
+  }
+}
+
 int dfjk_overlap(dfjk_handle h, double *Sout, void *stream) {
   try {
     if (!h || !Sout) throw Error{DFJK_ERR_ARG, "overlap arguments"};

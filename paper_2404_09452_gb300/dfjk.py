@@ -36,6 +36,7 @@ EXPORTS = [
     "dfjk_setup",
     "dfjk_query",
     "dfjk_build",
+    "dfjk_build_batch",
     "dfjk_overlap",
     "dfjk_evict",
     "dfjk_destroy",
@@ -115,6 +116,7 @@ def load_library(path: str = LIB_PATH):
     ]
     lib.dfjk_build.argtypes = [vp, i32, i32, vp, vp, vp, vp, vp, vp]
     lib.dfjk_overlap.argtypes = [vp, vp, vp]
+    lib.dfjk_build_batch.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, i32, vp]
     lib.dfjk_evict.argtypes = [vp]
     lib.dfjk_destroy.argtypes = [vp]
     lib.dfjk_status_string.argtypes = [ctypes.c_int]
@@ -289,6 +291,30 @@ class Handle:
         torch = _torch()
         n = len(self.mol.orb.shells)
         return self._get("dfjk_get_pair_mask", (n, n), dtype=torch.int32)
+
+
+def build_batch(handles, Cs, Js=None, Ks=None, E=None, nstreams=8, stream=None):
+    """Builds every resident handle with its C (device [nao_i, nocc_i]) in one
+    call (row a10).  Returns (Js, Ks, E) with E a device tensor [2, nmol]
+    (E_J, E_K); nothing is synchronised."""
+    torch = _torch()
+    n = len(handles)
+    Cs = [c.contiguous() for c in Cs]
+    if Js is None:
+        Js = [torch.empty((h.nao, h.nao), dtype=torch.float64, device="cuda") for h in handles]
+    if Ks is None:
+        Ks = [torch.empty((h.nao, h.nao), dtype=torch.float64, device="cuda") for h in handles]
+    if E is None:
+        E = torch.empty((2, n), dtype=torch.float64, device="cuda")
+    vp = ctypes.c_void_p
+    hs = (vp * n)(*[h.h for h in handles])
+    nocc = (ctypes.c_int32 * n)(*[int(c.shape[1]) for c in Cs])
+    cp = (vp * n)(*[c.data_ptr() for c in Cs])
+    jp = (vp * n)(*[j.data_ptr() for j in Js])
+    kp = (vp * n)(*[k.data_ptr() for k in Ks])
+    _check(load_library().dfjk_build_batch(n, hs, nocc, cp, jp, kp, vp(E[0].data_ptr()),
+                                           vp(E[1].data_ptr()), int(nstreams), _stream(stream)))
+    return Js, Ks, E
 
 
 def boys(mmax: int, T, stream=None):
