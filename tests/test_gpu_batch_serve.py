@@ -41,7 +41,7 @@ def test_batch_equals_alone(precision):
     mols = _mols([2, 7, 3, 5, 1, 4])
     Cs = [_c(m, i) for i, m in enumerate(mols)]
     # a budget that forces several waves
-    budget = 2 * max(batch.resident_bytes(m.nao, m.naux, C.shape[1], precision) for m, C in zip(mols, Cs))
+    budget = int(1.2 * max(batch.resident_bytes(m.nao, m.naux, C.shape[1], precision) for m, C in zip(mols, Cs)))
     E, res, st = batch.run_batch(mols, Cs, precision=precision, budget_bytes=budget, workers=3,
                                  nstreams=4, keep_results=True)
     assert st["waves"] > 1
@@ -81,7 +81,7 @@ def test_serving_same_alone_and_in_mix():
 
     reqs = serve.make_stream(mols, 40, rate=2000.0, repeat=0.7, seed=5001, c_of=c_of)
     # budget for about two molecules at a time: forces evictions and recompute
-    budget = 2 * max(batch.resident_bytes(m.nao, m.naux, I.default_nocc(m.nao), prec) for m in mols)
+    budget = int(1.5 * max(batch.resident_bytes(m.nao, m.naux, I.default_nocc(m.nao), prec) for m in mols))
     srv = serve.Server(mols, precision=prec, budget_bytes=budget, slots=4, keep_outputs=True)
     srv.run(reqs)
     srv.close()
