@@ -84,9 +84,9 @@ typedef struct {
   size_t hbm_budget_bytes; /* 0 = no limit; else setup fails with
                               DFJK_ERR_BUDGET if resident data would exceed it */
   int64_t timeout_iters;   /* iteration limit of bounded device waits        */
-  int32_t energies_on_host;/* 1: E_J/E_K pointers of dfjk_build are host
-                              memory (the call then synchronises the stream);
-                              0: device memory                               */
+  int32_t energies_on_host;/* informational: dfjk_build detects whether its
+                              E_J/E_K pointers are host memory (the call then
+                              synchronises the stream) or device memory      */
 } dfjk_options;
 
 typedef struct dfjk_ctx *dfjk_handle;
@@ -114,7 +114,8 @@ int dfjk_query(dfjk_handle h, int32_t *nao, int32_t *naux, int32_t *npair_kept,
 /* Steps a6-a9 for nset occupied-orbital sets.
  *   C_occ : device, nset x nao x nocc, row-major FP64 (caller-owned).
  *   J, K  : device, nset x nao x nao FP64, written in full (symmetric).
- *   E_J, E_K : nset doubles each, host or device per opt.energies_on_host.
+ *   E_J, E_K : nset doubles each, both host or both device memory (detected;
+ *              host memory makes the call synchronise the stream).
  * Work buffers are owned by the handle and reused across calls; calls on one
  * handle must therefore be ordered on a stream.                              */
 int dfjk_build(dfjk_handle h, int32_t nset, int32_t nocc, const double *C_occ,

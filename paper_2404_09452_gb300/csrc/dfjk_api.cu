@@ -759,7 +759,14 @@ int dfjk_build(dfjk_handle h, int32_t nset, int32_t nocc, const double *C, doubl
       const double *Cs = C + (size_t)s * h->nao * nocc;
       build_one(h, nocc, Cs, J + s * nao2, K + s * nao2, h->e.p + 2 * s, st);
     }
-    if (h->opt.energies_on_host) {
+    // energies go to host or device memory as the pointers are (detected per call)
+    cudaPointerAttributes pa{}, pb{};
+    DFJK_CUDA_CHECK(cudaPointerGetAttributes(&pa, EJ));
+    DFJK_CUDA_CHECK(cudaPointerGetAttributes(&pb, EK));
+    const bool dev_j = pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged;
+    const bool dev_k = pb.type == cudaMemoryTypeDevice || pb.type == cudaMemoryTypeManaged;
+    if (dev_j != dev_k) throw Error{DFJK_ERR_ARG, "E_J and E_K must both be host or both device memory"};
+    if (!dev_j) {
       std::vector<double> e(2 * nset);
       DFJK_CUDA_CHECK(cudaMemcpyAsync(e.data(), h->e.p, e.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
       DFJK_CUDA_CHECK(cudaStreamSynchronize(st));
