@@ -48,7 +48,14 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
-    ap.add_argument("--workload", default="mol60", choices=list(WORKLOADS))
+    ap.add_argument("--workload", default="mol60", choices=list(WORKLOADS) + ["batch", "serve"])
+    ap.add_argument("--batch-n", type=int, default=256)
+    ap.add_argument("--compare-fp64", action="store_true",
+                    help="batch/serve: also time the plain FP64 per-molecule path")
+    ap.add_argument("--serve-rates", default="10,50,200,500")
+    ap.add_argument("--serve-requests", type=int, default=300)
+    ap.add_argument("--serve-pool", type=int, default=24)
+    ap.add_argument("--serve-max-atoms", type=int, default=60)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -364,10 +371,119 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def _orthonormal_cs(mols, seed0):
+    import torch
+
+    from paper_2404_09452_gb300 import dfjk, inputs as I
+
+    out = []
+    for i, m in enumerate(mols):
+        S = dfjk.overlap_matrix(m).cpu().numpy()
+        C = I.orthonormalize(I.c_occ_raw(m.nao, I.default_nocc(m.nao), seed0 + i), S)
+        out.append(torch.from_numpy(C).cuda())
+    return out
+
+
+def run_batch_mode(args):
+    """Row a10: a batch of uneven molecules (atom counts uniform in [5, 80],
+    seed 4000), each set up and built once per step; waves under a 150 GB
+    budget, concurrent setups, one multi-stream build call per wave."""
+    import torch
+
+    from paper_2404_09452_gb300 import batch, dfjk, inputs as I
+
+    counts = I.batch_atom_counts(n=args.batch_n)
+    mols = [I.molecule(int(n), seed=4100 + i) for i, n in enumerate(counts)]
+    Cs = _orthonormal_cs(mols, 3000)
+    prec = dfjk.DFJK_MIXED if args.precision == "mixed" else dfjk.DFJK_FP64
+    for _ in range(args.warmup):
+        batch.run_batch(mols, Cs, precision=prec)
+    torch.cuda.synchronize()
+    n0 = dfjk.launch_count()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        E, _, st = batch.run_batch(mols, Cs, precision=prec)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    out = {"metric": "DF-J/K builds/s, batch of uneven molecules (setup + build each)",
+           "value": len(mols) * args.steps / dt, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
+           "scaling": "weak", "dtype": "f64" if prec == dfjk.DFJK_FP64 else "f64+bf16-sliced",
+           "data": "synthetic",
+           "config": {"workload": f"batch of {len(mols)} molecules, atoms uniform in [5, 80] (seed 4000)",
+                      "atoms_total": int(sum(counts)), "waves": st["waves"], "precision": args.precision,
+                      "budget_bytes": 150 << 30},
+           "gpu_launches": int(dfjk.launch_count() - n0)}
+    if args.compare_fp64:
+        t0 = time.perf_counter()
+        for m, C in zip(mols, Cs):
+            h = dfjk.Handle(m, precision=dfjk.DFJK_FP64)
+            h.build(C)
+            h.close()
+        torch.cuda.synchronize()
+        out["fp64_sequential_builds_per_s"] = len(mols) / (time.perf_counter() - t0)
+        out["vs_fp64_sequential"] = out["value"] / out["fp64_sequential_builds_per_s"]
+    print(json.dumps(out), flush=True)
+
+
+def run_serve_mode(args):
+    """Row a11: Poisson requests over a pool of molecules (atom counts
+    log-uniform in [5, serve-max-atoms]), 70 % repeats of resident molecules,
+    150 GB residency budget; p50/p99 latency and builds/s per arrival rate."""
+    import torch
+
+    from paper_2404_09452_gb300 import dfjk, inputs as I, serve
+
+    counts = I.serve_atom_counts(args.serve_pool, hi=args.serve_max_atoms)
+    pool = [I.molecule(int(n), seed=6100 + i) for i, n in enumerate(counts)]
+    Cbase = _orthonormal_cs(pool, 3100)
+    # four orbital sets per molecule (an SCF-like sequence of new C_occ)
+    rng_sets = {}
+
+    def c_of(mid, k):
+        key = (mid, k % 4)
+        if key not in rng_sets:
+            C = Cbase[mid]
+            Q, _ = torch.linalg.qr(torch.randn(C.shape[1], C.shape[1], dtype=torch.float64,
+                                               generator=torch.Generator().manual_seed(97 * mid + key[1])))
+            rng_sets[key] = (C @ Q.cuda()).contiguous()
+        return rng_sets[key]
+
+    rates = [float(r) for r in args.serve_rates.split(",")]
+    precs = [("mixed", dfjk.DFJK_MIXED, 8)] + ([("fp64", dfjk.DFJK_FP64, 1)] if args.compare_fp64 else [])
+    rows = []
+    for rate in rates:
+        for name, prec, slots in precs:
+            reqs = serve.make_stream(pool, args.serve_requests, rate, repeat=0.7, seed=5000 + int(rate), c_of=c_of)
+            srv = serve.Server(pool, precision=prec, budget_bytes=150 << 30, slots=slots)
+            srv.run(reqs[: max(1, args.serve_requests // 10)])  # warm-up: first tenth of the stream
+            srv.stats = serve.Stats()
+            off = reqs[0].arrival
+            for r in reqs:
+                r.arrival -= off
+            srv.run(reqs)
+            s = srv.stats.summary()
+            srv.close()
+            s.update(rate=rate, precision=name, slots=slots)
+            rows.append(s)
+    best = max(r["builds_per_s"] for r in rows if r["precision"] == "mixed")
+    out = {"metric": "DF-J/K serving: builds/s and p50/p99 latency under Poisson arrivals",
+           "value": best, "unit": UNIT, "n_gpus": 1, "higher_is_better": True, "scaling": "weak",
+           "dtype": "f64+bf16-sliced", "data": "synthetic",
+           "config": {"workload": f"pool of {len(pool)} molecules, atoms log-uniform in [5, {args.serve_max_atoms}], "
+                                  f"70% repeats, {args.serve_requests} requests per rate, 150 GB budget"},
+           "rates": rows}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch":
+        run_batch_mode(args)
+    elif args.workload == "serve":
+        run_serve_mode(args)
     else:
         run_ours(args)
 

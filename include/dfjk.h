@@ -137,6 +137,11 @@ int dfjk_build_batch(int32_t nmol, const dfjk_handle *hs, const int32_t *nocc,
  * orthonormalise occupied orbitals.                                           */
 int dfjk_overlap(dfjk_handle h, double *S, void *stream);
 
+/* Overlap matrix of a basis without a handle (no setup): S device nao x nao.
+ * Used to prepare orthonormal occupied orbitals for many molecules.         */
+int dfjk_overlap_matrix(const dfjk_basis *orb, int32_t natom, const double *coords, double *S,
+                        void *stream);
+
 /* Frees B and the work buffers but keeps the host copy of the inputs, so a
  * later dfjk_build recomputes steps a0-a5 first (resident-set eviction).     */
 int dfjk_evict(dfjk_handle h);

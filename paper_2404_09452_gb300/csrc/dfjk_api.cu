@@ -868,6 +868,25 @@ int dfjk_overlap(dfjk_handle h, double *Sout, void *stream) {
   }
 }
 
+int dfjk_overlap_matrix(const dfjk_basis *orb, int32_t natom, const double *coords, double *Sout,
+                        void *stream) {
+  dfjk_ctx *h = nullptr;
+  try {
+    if (natom <= 0 || !coords || !Sout) throw Error{DFJK_ERR_ARG, "overlap_matrix arguments"};
+    h = new dfjk_ctx();
+    DFJK_CUDA_CHECK(cudaGetDevice(&h->device));
+    h->natom = natom;
+    read_basis(orb, natom, coords, h->orb, "orbital basis");
+    h->nao = h->orb.nfunc;
+    const int rc = dfjk_overlap(h, Sout, stream);
+    delete h;
+    return rc;
+  } catch (const Error &e) {
+    delete h;
+    return fail(e);
+  }
+}
+
 int dfjk_evict(dfjk_handle h) {
   if (!h) return fail(Error{DFJK_ERR_ARG, "null handle"});
   try {

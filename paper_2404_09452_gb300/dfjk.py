@@ -38,6 +38,7 @@ EXPORTS = [
     "dfjk_build",
     "dfjk_build_batch",
     "dfjk_overlap",
+    "dfjk_overlap_matrix",
     "dfjk_evict",
     "dfjk_destroy",
     "dfjk_status_string",
@@ -116,6 +117,7 @@ def load_library(path: str = LIB_PATH):
     ]
     lib.dfjk_build.argtypes = [vp, i32, i32, vp, vp, vp, vp, vp, vp]
     lib.dfjk_overlap.argtypes = [vp, vp, vp]
+    lib.dfjk_overlap_matrix.argtypes = [ctypes.POINTER(BasisC), i32, f64p, vp, vp]
     lib.dfjk_build_batch.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, i32, vp]
     lib.dfjk_evict.argtypes = [vp]
     lib.dfjk_destroy.argtypes = [vp]
@@ -368,6 +370,19 @@ def energies_noalloc(D, J, K, E, stream=None):
 
 def launch_count() -> int:
     return int(load_library().dfjk_launch_count())
+
+
+def overlap_matrix(mol, stream=None):
+    """S of the orbital basis of `mol` (device), without a setup."""
+    torch = _torch()
+    b = _BasisHolder(mol.orb)
+    xyz = np.ascontiguousarray(mol.coords, dtype=np.float64)
+    S = torch.empty((mol.nao, mol.nao), dtype=torch.float64, device="cuda")
+    _check(load_library().dfjk_overlap_matrix(
+        ctypes.byref(b.c), int(xyz.shape[0]), xyz.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+        ctypes.c_void_p(S.data_ptr()), _stream(stream)))
+    torch.cuda.current_stream().synchronize()
+    return S
 
 
 def orthonormal_c_occ(handle: Handle, C0: np.ndarray):
