@@ -47,7 +47,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--fp64-steps", type=int, default=2,
+                    help="mixed runs: steps of the plain FP64 path timed alongside (0: skip)")
     ap.add_argument("--workload", default="mol60", choices=list(WORKLOADS) + ["batch", "serve"])
     ap.add_argument("--batch-n", type=int, default=256)
     ap.add_argument("--compare-fp64", action="store_true",
@@ -212,7 +214,7 @@ def run_ours(args):
     import numpy as np
     import torch
 
-    from paper_2404_09452_gb300 import dfjk, inputs as I
+    from paper_2404_09452_gb300 import dfjk, dist as D, inputs as I
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -272,10 +274,7 @@ def run_ours(args):
         dist.barrier()
     total_ms = evs[0].elapsed_time(evs[-1])
     step_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)]
-    if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = D.max_over_ranks(total_ms, device="cuda")
     value = world * args.steps / (total_ms / 1e3)
 
     # e2e: public API, pinned host C in, J/K/energies out, copies timed
@@ -296,12 +295,36 @@ def run_ours(args):
         Kh.copy_(Kd, non_blocking=True)
         torch.cuda.synchronize()
         h.close()
-    e2e_s = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = D.max_over_ranks(time.perf_counter() - t0, device="cuda")
     e2e_value = world * args.e2e_steps / e2e_s if args.e2e_steps > 0 else None
+
+    # the plain FP64 GPU path on the same input, same clocks: builds/s and the
+    # energy deviation of the timed path from it
+    fp64_cmp = None
+    if prec != dfjk.DFJK_FP64 and args.fp64_steps > 0:
+        def step64():
+            h = dfjk.Handle(m, precision=dfjk.DFJK_FP64)
+            J64, K64, EJ, EK = h.build(C)
+            h.close()
+            return J64, K64, EJ[0], EK[0]
+
+        J64, K64, ej64, ek64 = step64()
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(args.fp64_steps):
+            step64()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = ev0.elapsed_time(ev1) / args.fp64_steps
+        hm = dfjk.Handle(m, precision=prec)
+        Jm, Km, ejm, ekm = hm.build(C)
+        fp64_cmp = {"fp64_builds_per_s": 1e3 / ms64, "fp64_ms_per_step": ms64,
+                    "dE_J_vs_fp64": abs(float(ejm[0]) - float(ej64)),
+                    "dE_K_vs_fp64": abs(float(ekm[0]) - float(ek64)),
+                    "max_dJ_vs_fp64": float((Jm[0] - J64[0]).abs().max()),
+                    "max_dK_vs_fp64": float((Km[0] - K64[0]).abs().max())}
+        hm.close()
 
     if rank != 0:
         if dist:
@@ -345,7 +368,8 @@ def run_ours(args):
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if fp64 else "f64+bf16-sliced",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if fp64 else "bf16 (exact 6-bit slices, fp32 accumulate) + f64",
         "data": "synthetic",
         "config": {"workload": args.workload, "note": WORKLOADS[args.workload]["note"],
                    "natom": m.natom, "nao": m.nao, "naux": m.naux, "nocc": nocc,
@@ -362,6 +386,9 @@ def run_ours(args):
         "gpu_launches": int(launches),
         "clocks": clocks,
     }
+    if fp64_cmp:
+        out.update(fp64_cmp)
+        out["vs_fp64"] = value / fp64_cmp["fp64_builds_per_s"]
     if world == 1 and not args.no_cpu_baseline:
         s, desc, cores, parts = oracle_sample(m, nocc)
         out["cpu_baseline"] = {"value": 1.0 / s, "unit": UNIT, "cores": cores, "kind": "oracle",

@@ -774,6 +774,12 @@ int dfjk_build(dfjk_handle h, int32_t nset, int32_t nocc, const double *C, doubl
         EJ[s] = e[2 * s];
         EK[s] = e[2 * s + 1];
       }
+      int status = 0;  // the stream is synchronised here: surface device status
+      DFJK_CUDA_CHECK(cudaMemcpy(&status, h->status.p, sizeof(int), cudaMemcpyDeviceToHost));
+      if (status & STATUS_TIMEOUT) {
+        DFJK_CUDA_CHECK(cudaMemset(h->status.p, 0, sizeof(int)));
+        throw Error{DFJK_ERR_TIMEOUT, "a bounded device wait expired during the build"};
+      }
     } else {
       split_energies_kernel<<<ceil_div(nset, 64), 64, 0, st>>>(h->e.p, nset, EJ, EK);
       DFJK_LAUNCHED();

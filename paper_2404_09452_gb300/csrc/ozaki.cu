@@ -13,6 +13,8 @@
 //   accumulators -> two int64 groups -> FP64 register accumulators.
 #include <cuda.h>
 
+#include <algorithm>
+#include <cstdlib>
 #include <mutex>
 
 #include "common.cuh"
@@ -258,6 +260,11 @@ void oz_slice_f64(const double *src, long long sz, long long sr, long long sk, S
 
 // ---- GEMM -----------------------------------------------------------------------
 
+// Poll limit for the waits that wind a CTA down after an abort (copies and
+// MMAs already issued must land before shared memory and TMEM are released);
+// independent of the caller's timeout, which may be tiny in tests.
+constexpr long long OZ_CLEANUP_POLLS = 1LL << 24;
+
 template <int S>
 struct OzCfg {
   static constexpr int NST = (S <= 6) ? 3 : 2;
@@ -274,7 +281,11 @@ struct OzKernelArgs {
   int rows_padA, rows_padB, nkbA, nkbB;
 };
 
-__device__ __forceinline__ double pow2(int e) { return __longlong_as_double((long long)(e + 1023) << 52); }
+// 2^e for normal exponents; 0 below the normal range (row maxima that small
+// do not occur for these operands except as exact zeros).
+__device__ __forceinline__ double pow2(int e) {
+  return e < -1022 ? 0.0 : __longlong_as_double((long long)(e + 1023) << 52);
+}
 
 template <int S>
 __global__ void __launch_bounds__(128, 1)
@@ -383,10 +394,14 @@ __global__ void __launch_bounds__(128, 1)
         gstage += nst;
       } else {
         if (g.status) atomicOr(g.status, STATUS_TIMEOUT);
-        // copies still in flight land before the CTA leaves
+        // copies still in flight land, and issued MMAs finish, before the CTA leaves
         for (int c = consumed; c < issued; ++c) {
           const uint32_t gs = gstage + c, slot = gs % Cfg::NST;
-          tc::mbar_wait(&full[slot], (gs / Cfg::NST) & 1, g.timeout);
+          tc::mbar_wait(&full[slot], (gs / Cfg::NST) & 1, OZ_CLEANUP_POLLS);
+        }
+        if (consumed > 0) {
+          tc::mma_commit(accf);
+          tc::mbar_wait(accf, kbi & 1, OZ_CLEANUP_POLLS);
         }
       }
     }
@@ -452,6 +467,255 @@ __global__ void __launch_bounds__(128, 1)
   if (warp == 0) tc::tmem_dealloc(tbase, 512);
 }
 
+// ---- persistent warp-specialised GEMM -----------------------------------------------
+//
+// 192 threads: warp 0 = TMA producer, warp 1 = MMA issuer (and TMEM owner),
+// warps 2-5 = epilogue (warp w reads TMEM lanes 32 (w % 4) .. +31).  A CTA
+// walks tiles blockIdx.x, += gridDim.x (n fastest, so consecutive tiles share
+// their A rows in L2).  Per K-block: the producer fills the stage ring, the
+// MMA warp accumulates S levels in TMEM and commits `accf`; the epilogue
+// drains into FP64 registers and releases TMEM through `acce` (128 arrivals).
+// The producer runs ahead into the next K-block / tile during the drain.
+
+struct OzTiles {
+  int ntm, ntn, nz, total;
+};
+
+__device__ __forceinline__ bool oz_tile(const OzGemmArgs &g, const OzTiles &T, int t, int &m0, int &n0, int &z,
+                                        int &kb0, int &kb1, int &kend) {
+  const int tn = t % T.ntn, tm = (t / T.ntn) % T.ntm;
+  z = t / (T.ntn * T.ntm);
+  m0 = tm * OZ_BM;
+  n0 = tn * OZ_BN;
+  if (g.lower_only && n0 > m0 + OZ_BM - 1) return false;
+  kb0 = 0;
+  kb1 = (g.K + OZ_KB - 1) / OZ_KB;
+  kend = g.K;
+  if (g.kb_per_split > 0) {
+    kb0 = z * g.kb_per_split;
+    kb1 = min(kb1, kb0 + g.kb_per_split);
+  }
+  if (g.k_upto_n) {
+    kend = min(kend, n0 + OZ_BN);
+    kb1 = min(kb1, (kend + OZ_KB - 1) / OZ_KB);
+  }
+  return kb0 < kb1;
+}
+
+template <int S>
+__global__ void __launch_bounds__(192, 1)
+    oz_gemm_ws_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                      const OzKernelArgs ka, const OzTiles T) {
+  using Cfg = OzCfg<S>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t *full = (uint64_t *)(smem + Cfg::NST * Cfg::STAGE);
+  uint64_t *empty = full + Cfg::NST;
+  uint64_t *accf = empty + Cfg::NST;
+  uint64_t *acce = accf + 1;
+  uint64_t *fin = acce + 1;
+  uint32_t *tmem_holder = (uint32_t *)(fin + 1);
+  volatile int *abort_flag = (volatile int *)(tmem_holder + 1);
+
+  const OzGemmArgs &g = ka.g;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (warp == 1) tc::tmem_alloc(tmem_holder, 512);
+  if (tid == 0) {
+    for (int i = 0; i < Cfg::NST; ++i) {
+      tc::mbar_init(&full[i], 1);
+      tc::mbar_init(&empty[i], 1);
+    }
+    tc::mbar_init(accf, 1);
+    tc::mbar_init(acce, 128);
+    tc::mbar_init(fin, 1);
+    *abort_flag = 0;
+    tc::fence_mbar_init();
+    tc::prefetch_tensormap(&tmA);
+    tc::prefetch_tensormap(&tmB);
+  }
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tbase = *tmem_holder;
+  const long long lim = g.timeout;
+
+  if (warp == 0) {
+    if (lane == 0) {  // ---- producer
+      uint32_t gs = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < T.total && ok; t += gridDim.x) {
+        int m0, n0, z, kb0, kb1, kend;
+        if (!oz_tile(g, T, t, m0, n0, z, kb0, kb1, kend)) continue;
+        const int zA = g.a_batched ? z : 0, zB = g.b_batched ? z : 0;
+        for (int kb = kb0; kb < kb1 && ok; ++kb) {
+          const int kstart = kb * OZ_KB, kstop = min(kend, kstart + OZ_KB);
+          for (int kc = kstart; kc < kstop; kc += OZ_BK, ++gs) {
+            const uint32_t slot = gs % Cfg::NST;
+            if (gs >= (uint32_t)Cfg::NST && !tc::mbar_wait(&empty[slot], ((gs / Cfg::NST) - 1) & 1, lim)) {
+              ok = false;
+              break;
+            }
+            if (*abort_flag) {
+              ok = false;
+              break;
+            }
+            uint8_t *stp = smem + slot * Cfg::STAGE;
+            tc::mbar_expect_tx(&full[slot], Cfg::STAGE);
+#pragma unroll
+            for (int s = 0; s < S; ++s)
+              tc::tma_load_3d(stp + s * Cfg::A_TILE, &tmA, &full[slot], kc, m0, zA * S + s);
+#pragma unroll
+            for (int q = 0; q < S; ++q)
+              tc::tma_load_3d(stp + S * Cfg::A_TILE + q * Cfg::B_TILE, &tmB, &full[slot], kc, n0, zB * S + q);
+          }
+        }
+      }
+      if (!ok) {
+        *abort_flag = 1;
+        if (g.status) atomicOr(g.status, STATUS_TIMEOUT);
+      }
+      // copies in flight (the last NST stages issued) land before the CTA leaves
+      for (uint32_t k = (gs > (uint32_t)Cfg::NST ? gs - Cfg::NST : 0); k < gs; ++k)
+        tc::mbar_wait(&full[k % Cfg::NST], (k / Cfg::NST) & 1, OZ_CLEANUP_POLLS);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {  // ---- MMA issuer
+      constexpr uint32_t IDESC = tc::idesc_bf16(OZ_BM, OZ_BN);
+      uint32_t gs = 0, kbi = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < T.total && ok; t += gridDim.x) {
+        int m0, n0, z, kb0, kb1, kend;
+        if (!oz_tile(g, T, t, m0, n0, z, kb0, kb1, kend)) continue;
+        for (int kb = kb0; kb < kb1 && ok; ++kb, ++kbi) {
+          if (kbi > 0 && !tc::mbar_wait(acce, (kbi - 1) & 1, lim)) {  // TMEM drained
+            ok = false;
+            break;
+          }
+          tc::tc_fence_after();
+          const int kstart = kb * OZ_KB, kstop = min(kend, kstart + OZ_KB);
+          uint32_t lev_init = 0;
+          for (int kc = kstart; kc < kstop; kc += OZ_BK, ++gs) {
+            const uint32_t slot = gs % Cfg::NST;
+            if (!tc::mbar_wait(&full[slot], (gs / Cfg::NST) & 1, lim) || *abort_flag) {
+              ok = false;
+              break;
+            }
+            tc::tc_fence_after();
+            const uint32_t sa = tc::smem_u32(smem + slot * Cfg::STAGE);
+            const uint32_t sb = sa + S * Cfg::A_TILE;
+#pragma unroll
+            for (int kk = 0; kk < OZ_BK / 16; ++kk)
+#pragma unroll
+              for (int s = 0; s < S; ++s)
+#pragma unroll
+                for (int q = 0; q < S - s; ++q) {
+                  const int lev = s + q;
+                  const uint64_t ad = tc::sdesc_k_sw64(sa + s * Cfg::A_TILE + kk * 32);
+                  const uint64_t bd = tc::sdesc_k_sw64(sb + q * Cfg::B_TILE + kk * 32);
+                  tc::mma_bf16(tbase + lev * OZ_BN, ad, bd, IDESC, (lev_init >> lev) & 1u);
+                  lev_init |= 1u << lev;
+                }
+            tc::mma_commit(&empty[slot]);
+          }
+          if (ok) tc::mma_commit(accf);
+        }
+      }
+      if (!ok) {
+        *abort_flag = 1;
+        if (g.status) atomicOr(g.status, STATUS_TIMEOUT);
+      }
+      // every MMA issued has finished before TMEM is released
+      tc::mma_commit(fin);
+      tc::mbar_wait(fin, 0, OZ_CLEANUP_POLLS);
+    }
+  } else {  // ---- epilogue, 128 threads
+    const int lgrp = warp & 3;  // TMEM lane group of this warp
+    const int row = lgrp * 32 + lane;
+    const uint32_t lane_base = (uint32_t)(lgrp * 32) << 16;
+    uint32_t kbi = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < T.total && ok; t += gridDim.x) {
+      int m0, n0, z, kb0, kb1, kend;
+      if (!oz_tile(g, T, t, m0, n0, z, kb0, kb1, kend)) continue;
+      const int zA = g.a_batched ? z : 0, zB = g.b_batched ? z : 0;
+      const int m = m0 + row;
+      double acc[OZ_BN];
+#pragma unroll
+      for (int j = 0; j < OZ_BN; ++j) acc[j] = 0.0;
+      for (int kb = kb0; kb < kb1; ++kb, ++kbi) {
+        // warp-uniform decision: tcgen05.ld below needs the whole warp
+        const bool waited = tc::mbar_wait(accf, kbi & 1, lim);
+        if (!__all_sync(0xffffffffu, waited && !*abort_flag)) {
+          ok = false;
+          break;
+        }
+        tc::tc_fence_after();
+        const double sa = pow2(ka.expoA[((long long)zA * ka.rows_padA + m) * ka.nkbA + kb]);
+#pragma unroll
+        for (int c = 0; c < OZ_BN / 16; ++c) {
+          long long T0[16], T1[16];
+#pragma unroll
+          for (int j = 0; j < 16; ++j) T0[j] = T1[j] = 0;
+#pragma unroll
+          for (int lev = 0; lev < S; ++lev) {
+            float v[16];
+            tc::tmem_ld16(tbase + lane_base + lev * OZ_BN + c * 16, v);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              const long long iv = (long long)__float2int_rn(v[j]);
+              // S <= 6: one group, |sum| < 2^54 (rounded once when converted);
+              // S = 8: levels 0-3 and 4-7 in separate groups
+              if (S <= 6) T0[j] += iv << (6 * (S - 1 - lev));
+              else if (lev < 4) T0[j] += iv << (6 * (3 - lev));
+              else T1[j] += iv << (6 * (7 - lev));
+            }
+          }
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int eB = __ldg(ka.expoB + ((long long)zB * ka.rows_padB + n0 + c * 16 + j) * ka.nkbB + kb);
+            const double cscale = pow2(eB - 6 * (S + 1)) * sa;
+            if (S <= 6) {
+              acc[c * 16 + j] = fma((double)T0[j], cscale, acc[c * 16 + j]);
+            } else {
+              // group 0 carries 2^24 relative to group 1's unit: T0 2^(6(S-1)-18)
+              acc[c * 16 + j] = fma((double)T0[j], cscale * 16777216.0, acc[c * 16 + j]);
+              acc[c * 16 + j] = fma((double)T1[j], cscale, acc[c * 16 + j]);
+            }
+          }
+        }
+        tc::tc_fence_before();
+        tc::mbar_arrive(acce);
+      }
+      if (!ok) break;
+      if (m < g.M) {
+        if (g.mode == 0) {
+          double *o = g.out + (long long)z * g.out_bs + (long long)m * g.ldo;
+#pragma unroll
+          for (int j = 0; j < OZ_BN; ++j)
+            if (n0 + j < g.N) o[n0 + j] = acc[j];
+        } else {
+          const int mu = g.colmu[m], nu = g.colnu[m];
+          if (mu >= 0) {
+            double *o1 = g.out + ((long long)mu * g.nao + nu) * g.ldb;
+            double *o2 = g.out + ((long long)nu * g.nao + mu) * g.ldb;
+#pragma unroll
+            for (int j = 0; j < OZ_BN; ++j)
+              if (n0 + j < g.N) {
+                o1[n0 + j] = acc[j];
+                if (mu != nu) o2[n0 + j] = acc[j];
+              }
+          }
+        }
+      }
+    }
+    if (!ok) {
+      *abort_flag = 1;
+      if (g.status) atomicOr(g.status, STATUS_TIMEOUT);
+    }
+  }
+  __syncthreads();
+  if (warp == 1) tc::tmem_dealloc(tbase, 512);
+}
+
 // ---- host ---------------------------------------------------------------------------
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
@@ -487,6 +751,40 @@ static CUtensorMap make_map(const SlicedOp &op, int box_rows) {
   return map;
 }
 
+static int num_sms() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    DFJK_CUDA_CHECK(cudaGetDevice(&dev));
+    DFJK_CUDA_CHECK(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev));
+  }
+  return n;
+}
+
+// Persistent warp-specialised launch (the default).
+template <int S>
+static void launch_oz_ws(const SlicedOp &A, const SlicedOp &B, const OzGemmArgs &g, cudaStream_t st) {
+  PhaseScope ph(g.phase, st);
+  constexpr int SMEM = OzCfg<S>::SMEM;
+  static bool attr_set = false;
+  if (!attr_set) {
+    DFJK_CUDA_CHECK(cudaFuncSetAttribute(oz_gemm_ws_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM));
+    attr_set = true;
+  }
+  const CUtensorMap ma = make_map(A, OZ_BM), mb = make_map(B, OZ_BN);
+  OzKernelArgs ka{g, A.expo, B.expo, A.rows_pad, B.rows_pad, A.nkb, B.nkb};
+  OzTiles T;
+  T.ntm = (g.M + OZ_BM - 1) / OZ_BM;
+  T.ntn = (g.N + OZ_BN - 1) / OZ_BN;
+  T.nz = g.nz;
+  const long long total = (long long)T.ntm * T.ntn * T.nz;
+  if (total > 2147483647LL) throw Error{DFJK_ERR_ARG, "oz_gemm: too many tiles"};
+  T.total = (int)total;
+  const int grid = (int)std::min<long long>(total, num_sms());
+  oz_gemm_ws_kernel<S><<<grid, 192, SMEM, st>>>(ma, mb, ka, T);
+  DFJK_LAUNCHED();
+}
+
 template <int S>
 static void launch_oz(const SlicedOp &A, const SlicedOp &B, const OzGemmArgs &g, cudaStream_t st) {
   PhaseScope ph(g.phase, st);
@@ -515,9 +813,13 @@ void oz_gemm(const SlicedOp &A, const SlicedOp &B, const OzGemmArgs &g, cudaStre
   if (g.b_batched && g.nz > B.batch) throw Error{DFJK_ERR_ARG, "oz_gemm: B batch"};
   if (g.mode == 1 && (!g.colmu || !g.colnu)) throw Error{DFJK_ERR_ARG, "oz_gemm: scatter map"};
   if (g.nz > 65535 || (g.M + OZ_BM - 1) / OZ_BM > 2147483647) throw Error{DFJK_ERR_ARG, "oz_gemm: grid"};
+  static const bool simple = [] {
+    const char *e = std::getenv("DFJK_OZ_SIMPLE");
+    return e && e[0] == '1';
+  }();
   switch (A.S) {
-    case 6: launch_oz<6>(A, B, g, st); break;
-    case 8: launch_oz<8>(A, B, g, st); break;
+    case 6: simple ? launch_oz<6>(A, B, g, st) : launch_oz_ws<6>(A, B, g, st); break;
+    case 8: simple ? launch_oz<8>(A, B, g, st) : launch_oz_ws<8>(A, B, g, st); break;
     default: throw Error{DFJK_ERR_UNSUPPORTED, "slice count must be 6 or 8"};
   }
 }

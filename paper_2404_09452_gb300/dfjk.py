@@ -184,13 +184,16 @@ class _BasisHolder:
 
 
 def default_options(precision: int = DFJK_FP64, schwarz_thresh: float = 1e-12,
-                    hbm_budget_bytes: int = 0, energies_on_host: bool = True) -> Options:
+                    hbm_budget_bytes: int = 0, energies_on_host: bool = True,
+                    timeout_iters: int = 0) -> Options:
     o = Options()
     load_library().dfjk_default_options(ctypes.byref(o))
     o.precision = precision
     o.schwarz_thresh = schwarz_thresh
     o.hbm_budget_bytes = hbm_budget_bytes
     o.energies_on_host = 1 if energies_on_host else 0
+    if timeout_iters > 0:
+        o.timeout_iters = timeout_iters
     return o
 
 
@@ -198,14 +201,14 @@ class Handle:
     """A molecule set up on the device (steps a0-a5); B stays resident."""
 
     def __init__(self, mol, precision: int = DFJK_FP64, schwarz_thresh: float = 1e-12,
-                 hbm_budget_bytes: int = 0, stream=None):
+                 hbm_budget_bytes: int = 0, stream=None, timeout_iters: int = 0):
         lib = load_library()
         _torch()
         self.mol = mol
         self._orb = _BasisHolder(mol.orb)
         self._aux = _BasisHolder(mol.aux)
         xyz = np.ascontiguousarray(mol.coords, dtype=np.float64)
-        opt = default_options(precision, schwarz_thresh, hbm_budget_bytes)
+        opt = default_options(precision, schwarz_thresh, hbm_budget_bytes, timeout_iters=timeout_iters)
         h = ctypes.c_void_p()
         _check(
             lib.dfjk_setup(

@@ -98,3 +98,19 @@ def test_full_size_sampled_integrals():
         got = T[oa[c]:oa[c + 1], oo[a]:oo[a + 1], oo[b]:oo[b + 1]].permute(1, 2, 0).cpu().numpy()
         assert np.abs(got - blk).max() < 1e-11, (a, b, c)
     h.close()
+
+
+def test_expired_device_wait_is_reported_and_context_survives():
+    """Failure detection without a GPU fault: the tensor-core kernels poll
+    their mbarriers a bounded number of times.  With a limit of 1 poll the
+    waits run out, the kernel records DFJK_ERR_TIMEOUT, lets its copies and
+    MMAs land, frees TMEM and returns; the context stays usable."""
+    m = I.molecule(4, seed=1004)
+    with pytest.raises(dfjk.DfjkError) as e:
+        dfjk.Handle(m, precision=dfjk.DFJK_MIXED, timeout_iters=1)
+    assert e.value.code == 6  # DFJK_ERR_TIMEOUT
+    h = dfjk.Handle(m, precision=dfjk.DFJK_MIXED)
+    C = torch.from_numpy(dfjk.orthonormal_c_occ(h, I.c_occ_raw(m.nao, 12, 3000))).cuda()
+    J, K, EJ, EK = h.build(C)
+    assert np.isfinite(EJ[0]) and np.isfinite(EK[0])
+    h.close()

@@ -51,3 +51,31 @@ def test_exact_for_small_integers():
     B = rng.integers(-30, 31, (70, 1024)).astype(float)
     C = dfjk.sliced_gemm(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), S=6).cpu().numpy()
     assert np.array_equal(C, A @ B.T)
+
+
+def test_persistent_and_simple_kernels_agree(tmp_path):
+    """The persistent warp-specialised kernel (default) and the one-tile-per-CTA
+    kernel (DFJK_OZ_SIMPLE=1, read once per process) give identical results."""
+    import os
+    import subprocess
+    import sys
+
+    A, B = _case(2, 200, 130, 2100, 4)
+    np.save(tmp_path / "A.npy", A)
+    np.save(tmp_path / "B.npy", B)
+    code = (
+        "import sys, numpy as np, torch; sys.path.insert(0, %r);"
+        "from paper_2404_09452_gb300 import dfjk;"
+        "A = torch.from_numpy(np.load(%r)).cuda(); B = torch.from_numpy(np.load(%r)).cuda();"
+        "np.save(%r, dfjk.sliced_gemm(A, B, S=int(sys.argv[1])).cpu().numpy())"
+    )
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    for S in (6, 8):
+        outs = []
+        for simple in ("0", "1"):
+            out = str(tmp_path / f"C{S}{simple}.npy")
+            env = dict(os.environ, DFJK_OZ_SIMPLE=simple)
+            subprocess.run([sys.executable, "-c", code % (root, str(tmp_path / "A.npy"), str(tmp_path / "B.npy"), out),
+                            str(S)], check=True, env=env, timeout=300)
+            outs.append(np.load(out))
+        assert np.array_equal(outs[0], outs[1])
