@@ -546,7 +546,7 @@ void ensure_workspace(dfjk_ctx *h, int nocc, int nset) {
   if (h->ws_nocc < nocc || !h->D.p) {
     h->D.alloc(nao2);
     h->rho.alloc(h->naux_pad);
-    h->rho_work.alloc((size_t)128 * ceil_div(h->naux_pad, 256) * 256);
+    h->rho_work.alloc(std::max((size_t)128 * ceil_div(h->naux_pad, 256) * 256, (size_t)h->nao * h->naux_pad));
     h->X.alloc((size_t)h->nao * h->naux_pad * nocc);
     const int t = ceil_div(h->nao, 64);
     const int tiles = t * (t + 1) / 2;
@@ -581,8 +581,6 @@ void build_one(dfjk_ctx *h, int nocc, const double *C, double *J, double *Kout, 
   {
     PhaseScope ph(6, st);
     gemm_f64(d, st);
-    rho_gemv_f64(h->B.p, h->ldb, nao, np, h->D.p, h->rho.p, h->rho_work.p, 128, st);
-    j_gemv_f64(h->B.p, h->ldb, nao, np, h->rho.p, J, st);
   }
   const long long kt = (long long)np * nocc;
   if (!mixed) {
@@ -594,6 +592,11 @@ void build_one(dfjk_ctx *h, int nocc, const double *C, double *J, double *Kout, 
     {
       PhaseScope ph(4, st);
       gemm_f64(x, st);
+    }
+    {  // rho from X (5x smaller than B), then J over B
+      PhaseScope ph(6, st);
+      rho_from_x_f64(h->X.p, C, nao, np, nocc, h->rho.p, h->rho_work.p, st);
+      j_gemv_f64(h->B.p, h->ldb, nao, np, h->rho.p, J, st);
     }
     GemmArgs k;  // K[mu][nu] = sum_(P,i) X[mu][(P,i)] X[nu][(P,i)]
     k.M = nao; k.N = nao; k.K = (int)kt;
@@ -617,6 +620,11 @@ void build_one(dfjk_ctx *h, int nocc, const double *C, double *J, double *Kout, 
       x.status = h->status.p; x.timeout = h->opt.timeout_iters;
       x.phase = 9;
       oz_gemm(h->Bsl, h->Csl, x, st);
+    }
+    {  // rho from X (5x smaller than B), then J over B
+      PhaseScope ph(6, st);
+      rho_from_x_f64(h->X.p, C, nao, np, nocc, h->rho.p, h->rho_work.p, st);
+      j_gemv_f64(h->B.p, h->ldb, nao, np, h->rho.p, J, st);
     }
     PhaseScope ph(5, st);
     if (!h->Xsl.data || h->Xsl.K != kt) oz_alloc(h->Xsl, 1, 6, nao, (int)kt, OZ_BM);

@@ -38,6 +38,8 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(GemmArgs g) {
     C += z * g.sCb;
   }
   if (g.k_upto_n) kend = min(kend, (long long)(n0 + GBN));
+  if (g.k_upto_m) kend = min(kend, (long long)(m0 + GBM));
+  if (g.k_from_n) kbeg = max(kbeg, (long long)n0);
   int Mz = g.M;
   if (g.rag_step > 0) {
     const int valid = g.rag_n - (z * g.rag_step + g.rag_off);
@@ -256,6 +258,7 @@ void tri_inverse_f64(const double *L, int n, int ld, const double *Dinv, double 
     a.B = Linv; a.sBn = 1; a.sBk = ld; a.sBb = dstep;
     a.C = work; a.sCm = s; a.sCn = 1; a.sCb = (long long)s * s;
     a.rag_n = n; a.rag_step = 2 * s; a.rag_off = s;
+    a.k_from_n = 1;  // Linv11 lower triangular: B(n, k) = Linv11[k][n] = 0 for k < n
     gemm_f64(a, st);
     GemmArgs b;  // Linv21_j = -Linv22_j work_j
     b.M = s; b.N = s; b.K = s; b.batch = pairs;
@@ -264,6 +267,7 @@ void tri_inverse_f64(const double *L, int n, int ld, const double *Dinv, double 
     b.C = Linv + (long long)s * ld; b.sCm = ld; b.sCn = 1; b.sCb = dstep;
     b.alpha = -1.0;
     b.rag_n = n; b.rag_step = 2 * s; b.rag_off = s; b.rag_clip_k = 1;
+    b.k_upto_m = 1;  // Linv22 lower triangular: A(m, k) = 0 for k > m
     gemm_f64(b, st);
   }
 }
@@ -320,6 +324,32 @@ void rho_gemv_f64(const double *B, long long ldb, int nao, int naux, const doubl
   rho_partial_kernel<<<dim3(gx, nchunk), 256, 0, st>>>(B, ldb, nao, naux, D, work, ldw, rows_per);
   DFJK_LAUNCHED();
   column_sum_kernel<<<ceil_div(naux, 256), 256, 0, st>>>(work, ldw, nchunk, naux, rho);
+  DFJK_LAUNCHED();
+}
+
+// part[mu][P] = sum_i C[mu][i] X[mu][P][i]: one warp per (mu, P), lanes along i.
+__global__ void __launch_bounds__(256) rho_from_x_kernel(const double *__restrict__ X,
+                                                         const double *__restrict__ C, int nao, int np,
+                                                         int nocc, double *__restrict__ part) {
+  const long long w = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (w >= (long long)nao * np) return;
+  const int mu = (int)(w / np);
+  const double *x = X + w * nocc;
+  const double *c = C + (long long)mu * nocc;
+  double s = 0.0;
+  for (int i = lane; i < nocc; i += 32) s = fma(__ldg(c + i), x[i], s);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) part[w] = s;
+}
+
+void rho_from_x_f64(const double *X, const double *C, int nao, int np, int nocc, double *rho,
+                    double *part, cudaStream_t st) {
+  const long long n = (long long)nao * np;
+  rho_from_x_kernel<<<(unsigned)((n + 7) / 8), 256, 0, st>>>(X, C, nao, np, nocc, part);
+  DFJK_LAUNCHED();
+  column_sum_kernel<<<ceil_div(np, 256), 256, 0, st>>>(part, np, nao, np, rho);
   DFJK_LAUNCHED();
 }
 

@@ -19,6 +19,8 @@ struct GemmArgs {
   int lower_only = 0;  // skip output tiles strictly above the diagonal
   int k_upto_n = 0;    // K range of an output tile limited to k < n_tile_end
                        // (B lower triangular in (n, k))
+  int k_from_n = 0;    // K range starts at the tile's first n (B(n, k) = 0 for k < n)
+  int k_upto_m = 0;    // K range ends at the tile's last m (A(m, k) = 0 for k > m)
   int k_split = 0;     // >0: blockIdx.z selects K range [z k_split, ...) and C += z sCb
   // ragged diagonal-block batches: batch z has rag_n - (z rag_step + rag_off)
   // valid rows (and, with rag_clip_k, as many K); z with none returns
@@ -48,6 +50,10 @@ void tri_inverse_f64(const double *L, int n, int ld, const double *Dinv, double 
 // reduction.
 void rho_gemv_f64(const double *B, long long ldb, int nao, int naux, const double *D,
                   double *rho, double *work, int nchunk, cudaStream_t st);
+// rho[P] = sum_{mu,i} C[mu][i] X[mu][P][i]  (= sum_{mu nu} B[mu][nu][P] D[mu][nu]
+// since X_P = B_P C and D = C C^T); per-mu partials in `part` (nao x np).
+void rho_from_x_f64(const double *X, const double *C, int nao, int np, int nocc, double *rho,
+                    double *part, cudaStream_t st);
 // J[mu][nu] = J[nu][mu] = sum_P B[(mu nao + nu) ldb + P] rho[P].
 void j_gemv_f64(const double *B, long long ldb, int nao, int naux, const double *rho, double *J,
                 cudaStream_t st);

@@ -295,7 +295,8 @@ __global__ void __launch_bounds__(128) eri3c_kernel(Eri3cArgs args, AuxArgs aux,
   constexpr int REC = REC_HDR + NT;
   constexpr int NCA = ncart(LA), NCB = ncart(LB), NCC = ncart(LC);
   constexpr int LAB = LA + LB, L = LA + LB + LC;
-  __shared__ double srec[REC];
+  constexpr int PPCH = 8;  // primitive-pair records staged per barrier
+  __shared__ double srec_all[PPCH * REC];
   const int pair = args.pairs[blockIdx.x];
   const int as = blockIdx.y * blockDim.x + threadIdx.x;
   const bool active = as < args.naux_shells;
@@ -307,10 +308,13 @@ __global__ void __launch_bounds__(128) eri3c_kernel(Eri3cArgs args, AuxArgs aux,
   for (int i = 0; i < NCA * NCB * NCC; ++i) acc[i] = 0.0;
   const double *rec0 = args.rec + args.rec_off[pair];
   const int npp = args.npp[pair];
-  for (int ipp = 0; ipp < npp; ++ipp) {
+  for (int ip0 = 0; ip0 < npp; ip0 += PPCH) {
+    const int nch = min(PPCH, npp - ip0);
     __syncthreads();
-    for (int i = threadIdx.x; i < REC; i += blockDim.x) srec[i] = rec0[(long long)ipp * REC + i];
+    for (int i = threadIdx.x; i < nch * REC; i += blockDim.x) srec_all[i] = rec0[(long long)ip0 * REC + i];
     __syncthreads();
+  for (int ipc = 0; ipc < nch; ++ipc) {
+    const double *srec = srec_all + ipc * REC;
     for (int kc = 0; kc < nc; ++kc) {
       const double g = aux.exps[pc0 + kc];
       const double g1 = aux.g1[pc0 + kc];  // 1/(2g)
@@ -376,6 +380,7 @@ __global__ void __launch_bounds__(128) eri3c_kernel(Eri3cArgs args, AuxArgs aux,
           }
       }
     }
+  }
   }
   if (!active) return;
   const long long col0 = args.pair_col[pair] - args.col_begin;
