@@ -4,6 +4,7 @@
 // then tensor contractions) and Sec. "Dataset and Performance" (intermediates
 // of small and medium molecules kept resident in GPU memory).
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -205,6 +206,10 @@ struct dfjk_ctx {
   DBuf<double> B;
   long long ldb = 0;
   SlicedOp Bsl;
+  // memory-lean mixed mode: B's slices are not kept; each build slices B in
+  // chunks of mu (Bchunk) just before X = B C of that chunk
+  bool lean = false;
+  SlicedOp Bchunk;
   // build workspace
   int ws_nocc = -1;
   DBuf<double> D, rho, rho_work, X, Kpart, en_work, e;
@@ -212,6 +217,7 @@ struct dfjk_ctx {
   SlicedOp Csl, Xsl;  // DFJK_MIXED build operands
   ~dfjk_ctx() {
     oz_free(Bsl);
+    oz_free(Bchunk);
     oz_free(Csl);
     oz_free(Xsl);
   }
@@ -249,11 +255,26 @@ void enumerate_pairs(dfjk_ctx *h) {
   h->cls_begin[6] = (int)h->pa_h.size();
 }
 
+// Bytes of B's resident 6-slice form; above the limit (DFJK_BSLICE_MAX_BYTES,
+// default 64 GiB) the mixed path runs memory-lean and slices B per build.
+size_t bslice_bytes(int nao, int np) {
+  const size_t rows = ((size_t)np + 127) / 128 * 128, kp = ((size_t)nao + 31) / 32 * 32;
+  return (size_t)nao * 6 * rows * kp * 2;
+}
+bool choose_lean(int nao, int np) {
+  static const size_t lim = [] {
+    const char *e = std::getenv("DFJK_BSLICE_MAX_BYTES");
+    return e ? (size_t)std::strtoull(e, nullptr, 10) : ((size_t)64 << 30);
+  }();
+  return bslice_bytes(nao, np) > lim;
+}
+
 size_t resident_estimate(const dfjk_ctx *h) {
   const size_t np2 = (size_t)h->naux_pad * h->naux_pad;
   const size_t nao2p = (size_t)h->nao * h->nao * h->naux_pad;
   size_t b = nao2p * sizeof(double);
-  if (h->opt.precision == DFJK_MIXED) b += nao2p * 6 * 2 + nao2p / 4;  // slices + padding slack
+  if (h->opt.precision == DFJK_MIXED && !choose_lean(h->nao, h->naux_pad))
+    b += bslice_bytes(h->nao, h->naux_pad);
   return b + 3 * np2 * sizeof(double);
 }
 
@@ -503,10 +524,14 @@ void make_resident(dfjk_ctx *h, cudaStream_t st) {
     DFJK_CUDA_CHECK(cudaStreamSynchronize(st));
     oz_free(T8);
     oz_free(Linv8);
-    // B as the A operand of X = B C: batch mu, rows P, K nu (6 slices)
-    PhaseScope ph(3, st);
-    oz_alloc(h->Bsl, h->nao, 6, np, h->nao, OZ_BM);
-    oz_slice_f64(h->B.p, (long long)h->nao * h->ldb, 1, h->ldb, h->Bsl, st);
+    // B as the A operand of X = B C: batch mu, rows P, K nu (6 slices),
+    // resident unless that would exceed the slice-memory limit
+    h->lean = choose_lean(h->nao, np);
+    if (!h->lean) {
+      PhaseScope ph(3, st);
+      oz_alloc(h->Bsl, h->nao, 6, np, h->nao, OZ_BM);
+      oz_slice_f64(h->B.p, (long long)h->nao * h->ldb, 1, h->ldb, h->Bsl, st);
+    }
   }
   int status = 0;
   DFJK_CUDA_CHECK(cudaMemcpyAsync(&status, h->status.p, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -619,7 +644,23 @@ void build_one(dfjk_ctx *h, int nocc, const double *C, double *J, double *Kout, 
       x.mode = 0; x.out = h->X.p; x.ldo = nocc; x.out_bs = (long long)np * nocc;
       x.status = h->status.p; x.timeout = h->opt.timeout_iters;
       x.phase = 9;
-      oz_gemm(h->Bsl, h->Csl, x, st);
+      if (!h->lean) {
+        oz_gemm(h->Bsl, h->Csl, x, st);
+      } else {  // slice B per chunk of mu (about 4 GiB of slices), then X for it
+        const size_t per_mu = (size_t)6 * ((np + 127) / 128 * 128) * ((nao + 31) / 32 * 32) * 2;
+        const int mc = (int)std::max<size_t>(1, std::min<size_t>(nao, ((size_t)4 << 30) / per_mu));
+        if (!h->Bchunk.data || h->Bchunk.batch != mc) oz_alloc(h->Bchunk, mc, 6, np, nao, OZ_BM);
+        for (int mu0 = 0; mu0 < nao; mu0 += mc) {
+          const int n = std::min(mc, nao - mu0);
+          SlicedOp ck = h->Bchunk;  // view of the first n batches (the last chunk is short)
+          ck.batch = n;
+          oz_slice_f64(h->B.p + (size_t)mu0 * nao * h->ldb, (long long)nao * h->ldb, 1, h->ldb, ck, st);
+          OzGemmArgs xc = x;
+          xc.nz = n;
+          xc.out = h->X.p + (size_t)mu0 * np * nocc;
+          oz_gemm(ck, h->Csl, xc, st);
+        }
+      }
     }
     {  // rho from X (5x smaller than B), then J over B
       PhaseScope ph(6, st);

@@ -114,3 +114,47 @@ def test_expired_device_wait_is_reported_and_context_survives():
     J, K, EJ, EK = h.build(C)
     assert np.isfinite(EJ[0]) and np.isfinite(EK[0])
     h.close()
+
+
+def test_memory_lean_mode_matches_resident_slices(tmp_path):
+    """With the resident slice limit set to 0 the mixed path slices B per build
+    in chunks of mu; results are identical to the resident-slice mode."""
+    import os
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = (
+        "import sys, numpy as np, torch; sys.path.insert(0, %r);"
+        "from paper_2404_09452_gb300 import dfjk, inputs as I;"
+        "m = I.molecule(12, seed=1012); h = dfjk.Handle(m, precision=dfjk.DFJK_MIXED);"
+        "C = torch.from_numpy(dfjk.orthonormal_c_occ(h, I.c_occ_raw(m.nao, 36, 3000))).cuda();"
+        "J, K, EJ, EK = h.build(C); np.save(sys.argv[1], np.concatenate([J[0].cpu().numpy().ravel(), "
+        "K[0].cpu().numpy().ravel(), [EJ[0], EK[0]]]))"
+    ) % root
+    outs = []
+    for lim in ("0", str(1 << 40)):
+        out = str(tmp_path / f"r{lim}.npy")
+        env = dict(os.environ, DFJK_BSLICE_MAX_BYTES=lim)
+        subprocess.run([sys.executable, "-c", code, out], check=True, env=env, timeout=300)
+        outs.append(np.load(out))
+    assert np.array_equal(outs[0], outs[1])
+
+
+def test_config_120_atoms_mixed_vs_fp64_gpu():
+    """The 120-atom mixed configuration (nao 1800, naux 4320, nocc 360; B
+    sliced per build, memory-lean) against the FP64 GPU path at the same size."""
+    m = I.molecule(120, seed=1003)
+    nocc = I.default_nocc(m.nao)
+    h64 = dfjk.Handle(m, precision=dfjk.DFJK_FP64)
+    C = torch.from_numpy(dfjk.orthonormal_c_occ(h64, I.c_occ_raw(m.nao, nocc, 3000))).cuda()
+    J64, K64, EJ64, EK64 = h64.build(C)
+    J64, K64 = J64.clone(), K64.clone()
+    h64.close()
+    hm = dfjk.Handle(m, precision=dfjk.DFJK_MIXED)
+    Jm, Km, EJm, EKm = hm.build(C)
+    dJ, dK = (Jm - J64).abs().max().item(), (Km - K64).abs().max().item()
+    dEJ, dEK = abs(EJm[0] - EJ64[0]), abs(EKm[0] - EK64[0])
+    print(f"mol120 mixed vs fp64: dJ {dJ:.2e} dK {dK:.2e} dEJ {dEJ:.2e} dEK {dEK:.2e}")
+    assert dJ <= JK_TOL and dK <= JK_TOL and dEJ <= E_TOL and dEK <= E_TOL
+    hm.close()
