@@ -675,11 +675,18 @@ void build_one(dfjk_ctx *h, int nocc, const double *C, double *J, double *Kout, 
     for (int i = 0; i < mt; ++i)
       for (int j = 0; j < nt; ++j)
         if (j * OZ_BN <= i * OZ_BM + OZ_BM - 1) ++tiles;
+    // K ranges of about 96 MB of operand slices (all rows) so that the tiles
+    // working on one range at a time (the persistent kernel orders work
+    // split-major) reuse it from L2; partial K buffers capped at 2 GiB
     const int nkb = h->Xsl.nkb;
-    int nsplit = std::max(1, std::min(h->ksplit, (2 * 152 + tiles - 1) / tiles));
-    nsplit = std::min(nsplit, nkb);
-    const int per = ceil_div(nkb, nsplit);
+    const size_t chunk_kb_bytes = (size_t)h->Xsl.rows_pad * 6 * 2 * OZ_KB;
+    int per = (int)std::max<size_t>(1, ((size_t)96 << 20) / chunk_kb_bytes);
+    const int max_split = (int)std::max<size_t>(1, ((size_t)2 << 30) / ((size_t)nao * nao * 8));
+    int nsplit = std::min(ceil_div(nkb, per), max_split);
+    nsplit = std::max(nsplit, std::min(nkb, (2 * 152 + tiles - 1) / tiles));
+    per = ceil_div(nkb, nsplit);
     nsplit = ceil_div(nkb, per);
+    if (h->Kpart.n < (size_t)nsplit * nao * nao) h->Kpart.alloc((size_t)nsplit * nao * nao);
     OzGemmArgs k;
     k.M = nao; k.N = nao; k.K = (int)kt; k.nz = nsplit; k.kb_per_split = per; k.lower_only = 1;
     k.mode = 0; k.out = h->Kpart.p; k.ldo = nao; k.out_bs = (long long)nao * nao;

@@ -289,7 +289,7 @@ __global__ void __launch_bounds__(64) schwarz_kernel(PairClassArgs args, const d
 // the aux primitives, accumulating the ncart(LA) ncart(LB) ncart(LC) block,
 // then writes T[col - col_begin][P] (P contiguous).
 template <int LA, int LB, int LC>
-__global__ void __launch_bounds__(128) eri3c_kernel(Eri3cArgs args, AuxArgs aux,
+__global__ void __launch_bounds__(128, 3) eri3c_kernel(Eri3cArgs args, AuxArgs aux,
                                                     const double *__restrict__ boys_tab) {
   constexpr int NT = nterms(LA, LB);
   constexpr int REC = REC_HDR + NT;
