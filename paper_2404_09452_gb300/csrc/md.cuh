@@ -289,14 +289,13 @@ __global__ void __launch_bounds__(64) schwarz_kernel(PairClassArgs args, const d
 // the aux primitives, accumulating the ncart(LA) ncart(LB) ncart(LC) block,
 // then writes T[col - col_begin][P] (P contiguous).
 template <int LA, int LB, int LC>
-__global__ void __launch_bounds__(128, 3) eri3c_kernel(Eri3cArgs args, AuxArgs aux,
+__global__ void __launch_bounds__(128) eri3c_kernel(Eri3cArgs args, AuxArgs aux,
                                                     const double *__restrict__ boys_tab) {
   constexpr int NT = nterms(LA, LB);
   constexpr int REC = REC_HDR + NT;
   constexpr int NCA = ncart(LA), NCB = ncart(LB), NCC = ncart(LC);
   constexpr int LAB = LA + LB, L = LA + LB + LC;
-  constexpr int PPCH = 8;  // primitive-pair records staged per barrier
-  __shared__ double srec_all[PPCH * REC];
+  __shared__ double srec[REC];
   const int pair = args.pairs[blockIdx.x];
   const int as = blockIdx.y * blockDim.x + threadIdx.x;
   const bool active = as < args.naux_shells;
@@ -308,13 +307,10 @@ __global__ void __launch_bounds__(128, 3) eri3c_kernel(Eri3cArgs args, AuxArgs a
   for (int i = 0; i < NCA * NCB * NCC; ++i) acc[i] = 0.0;
   const double *rec0 = args.rec + args.rec_off[pair];
   const int npp = args.npp[pair];
-  for (int ip0 = 0; ip0 < npp; ip0 += PPCH) {
-    const int nch = min(PPCH, npp - ip0);
+  for (int ipp = 0; ipp < npp; ++ipp) {
     __syncthreads();
-    for (int i = threadIdx.x; i < nch * REC; i += blockDim.x) srec_all[i] = rec0[(long long)ip0 * REC + i];
+    for (int i = threadIdx.x; i < REC; i += blockDim.x) srec[i] = rec0[(long long)ipp * REC + i];
     __syncthreads();
-  for (int ipc = 0; ipc < nch; ++ipc) {
-    const double *srec = srec_all + ipc * REC;
     for (int kc = 0; kc < nc; ++kc) {
       const double g = aux.exps[pc0 + kc];
       const double g1 = aux.g1[pc0 + kc];  // 1/(2g)
@@ -380,7 +376,6 @@ __global__ void __launch_bounds__(128, 3) eri3c_kernel(Eri3cArgs args, AuxArgs a
           }
       }
     }
-  }
   }
   if (!active) return;
   const long long col0 = args.pair_col[pair] - args.col_begin;
