@@ -16,10 +16,14 @@
 
 namespace dfjk {
 
-constexpr int GBM = 64, GBN = 64, GBK = 16;
+constexpr int GBK = 16;
 
-template <bool A_KC, bool B_KC, bool SCATTER>
+// TILE x TILE output tile per 256-thread CTA, (TILE/16)^2 outputs per thread;
+// TILE = 32 gives four times more CTAs for the small, latency-bound GEMMs of
+// the Cholesky factorisation and the triangular inverse.
+template <int TILE, bool A_KC, bool B_KC, bool SCATTER>
 __global__ void __launch_bounds__(256) gemm_f64_kernel(GemmArgs g) {
+  constexpr int GBM = TILE, GBN = TILE, TT = TILE / 16;
   __shared__ double As[GBK][GBM + 1];
   __shared__ double Bs[GBK][GBN + 1];
   const int m0 = blockIdx.y * GBM, n0 = blockIdx.x * GBN;
@@ -48,48 +52,48 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(GemmArgs g) {
     if (g.rag_clip_k) kend = min(kend, (long long)valid);
   }
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  double acc[4][4];
+  double acc[TT][TT];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < TT; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+    for (int j = 0; j < TT; ++j) acc[i][j] = 0.0;
 
   for (long long k0 = kbeg; k0 < kend; k0 += GBK) {
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < TT; ++i) {
       const int e = tid + i * 256;
-      const int mm = A_KC ? (e >> 4) : (e & 63);
-      const int kk = A_KC ? (e & 15) : (e >> 6);
+      const int mm = A_KC ? (e >> 4) : (e % GBM);
+      const int kk = A_KC ? (e & 15) : (e / GBM);
       const long long gm = m0 + mm, gk = k0 + kk;
       As[kk][mm] = (gm < Mz && gk < kend) ? A[gm * g.sAm + gk * g.sAk] : 0.0;
     }
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < TT; ++i) {
       const int e = tid + i * 256;
-      const int nn = B_KC ? (e >> 4) : (e & 63);
-      const int kk = B_KC ? (e & 15) : (e >> 6);
+      const int nn = B_KC ? (e >> 4) : (e % GBN);
+      const int kk = B_KC ? (e & 15) : (e / GBN);
       const long long gn = n0 + nn, gk = k0 + kk;
       Bs[kk][nn] = (gn < g.N && gk < kend) ? B[gn * g.sBn + gk * g.sBk] : 0.0;
     }
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < GBK; ++kk) {
-      double a[4], b[4];
+      double a[TT], b[TT];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+      for (int i = 0; i < TT; ++i) a[i] = As[kk][ty * TT + i];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
+      for (int j = 0; j < TT; ++j) b[j] = Bs[kk][tx * TT + j];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < TT; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        for (int j = 0; j < TT; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
     }
     __syncthreads();
   }
 
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int m = m0 + ty * 4 + i;
+  for (int i = 0; i < TT; ++i) {
+    const int m = m0 + ty * TT + i;
     if (m >= Mz) continue;
     if (SCATTER) {
       const int mu = g.colmu[m], nu = g.colnu[m];
@@ -97,8 +101,8 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(GemmArgs g) {
       double *o1 = g.out + ((long long)mu * g.nao + nu) * g.ldo;
       double *o2 = g.out + ((long long)nu * g.nao + mu) * g.ldo;
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int n = n0 + tx * 4 + j;
+      for (int j = 0; j < TT; ++j) {
+        const int n = n0 + tx * TT + j;
         if (n < g.N) {
           o1[n] = acc[i][j];
           if (mu != nu) o2[n] = acc[i][j];
@@ -106,8 +110,8 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(GemmArgs g) {
       }
     } else {
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int n = n0 + tx * 4 + j;
+      for (int j = 0; j < TT; ++j) {
+        const int n = n0 + tx * TT + j;
         if (n >= g.N) continue;
         double *c = C + m * g.sCm + n * g.sCn;
         *c = (g.beta != 0.0) ? fma(g.alpha, acc[i][j], g.beta * *c) : g.alpha * acc[i][j];
@@ -116,26 +120,32 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(GemmArgs g) {
   }
 }
 
-void gemm_f64(const GemmArgs &g, cudaStream_t st) {
-  if (g.M <= 0 || g.N <= 0) return;
+template <int TILE>
+static void gemm_f64_launch(const GemmArgs &g, cudaStream_t st) {
   const int nz = g.k_split > 0 ? ceil_div(g.K, g.k_split) : g.batch;
   if (nz <= 0) return;
-  dim3 grid(ceil_div(g.N, GBN), ceil_div(g.M, GBM), nz);
+  dim3 grid(ceil_div(g.N, TILE), ceil_div(g.M, TILE), nz);
   if (grid.y > 65535 || grid.z > 65535) throw Error{DFJK_ERR_ARG, "gemm grid too large"};
   const bool akc = g.sAk == 1, bkc = g.sBk == 1, sc = g.out != nullptr;
   if (sc) {
-    if (akc && bkc) gemm_f64_kernel<true, true, true><<<grid, 256, 0, st>>>(g);
+    if (akc && bkc) gemm_f64_kernel<TILE, true, true, true><<<grid, 256, 0, st>>>(g);
     else throw Error{DFJK_ERR_ARG, "scatter gemm needs K-contiguous operands"};
   } else if (akc && bkc) {
-    gemm_f64_kernel<true, true, false><<<grid, 256, 0, st>>>(g);
+    gemm_f64_kernel<TILE, true, true, false><<<grid, 256, 0, st>>>(g);
   } else if (akc && !bkc) {
-    gemm_f64_kernel<true, false, false><<<grid, 256, 0, st>>>(g);
+    gemm_f64_kernel<TILE, true, false, false><<<grid, 256, 0, st>>>(g);
   } else if (!akc && bkc) {
-    gemm_f64_kernel<false, true, false><<<grid, 256, 0, st>>>(g);
+    gemm_f64_kernel<TILE, false, true, false><<<grid, 256, 0, st>>>(g);
   } else {
-    gemm_f64_kernel<false, false, false><<<grid, 256, 0, st>>>(g);
+    gemm_f64_kernel<TILE, false, false, false><<<grid, 256, 0, st>>>(g);
   }
   DFJK_LAUNCHED();
+}
+
+void gemm_f64(const GemmArgs &g, cudaStream_t st) {
+  if (g.M <= 0 || g.N <= 0) return;
+  if (g.tile == 32) gemm_f64_launch<32>(g, st);
+  else gemm_f64_launch<64>(g, st);
 }
 
 // ---- Cholesky -------------------------------------------------------------------
@@ -219,6 +229,9 @@ void cholesky_f64(double *A, int n, int lda, double *Dinv, int *status, double *
     p.A = panel; p.sAm = lda; p.sAk = 1;
     p.B = Dinv + (long long)k * 4096; p.sBn = 64; p.sBk = 1;
     p.C = panel; p.sCm = lda; p.sCn = 1;
+    // tile 64 = the whole panel width: the update is in place, so one CTA must
+    // own complete rows (with 32-wide tiles two CTAs would share them)
+    p.tile = 64;
     gemm_f64(p, st);
     GemmArgs t;  // A_ij -= L_ik L_jk^T on the trailing lower triangle
     t.M = rows; t.N = rows; t.K = 64;
@@ -226,6 +239,7 @@ void cholesky_f64(double *A, int n, int lda, double *Dinv, int *status, double *
     t.B = panel; t.sBn = lda; t.sBk = 1;
     t.C = A + (long long)(k + 1) * 64 * (lda + 1); t.sCm = lda; t.sCn = 1;
     t.alpha = -1.0; t.beta = 1.0; t.lower_only = 1;
+    t.tile = 32;
     gemm_f64(t, st);
   }
 }
@@ -259,6 +273,7 @@ void tri_inverse_f64(const double *L, int n, int ld, const double *Dinv, double 
     a.C = work; a.sCm = s; a.sCn = 1; a.sCb = (long long)s * s;
     a.rag_n = n; a.rag_step = 2 * s; a.rag_off = s;
     a.k_from_n = 1;  // Linv11 lower triangular: B(n, k) = Linv11[k][n] = 0 for k < n
+    a.tile = 32;
     gemm_f64(a, st);
     GemmArgs b;  // Linv21_j = -Linv22_j work_j
     b.M = s; b.N = s; b.K = s; b.batch = pairs;
@@ -268,6 +283,7 @@ void tri_inverse_f64(const double *L, int n, int ld, const double *Dinv, double 
     b.alpha = -1.0;
     b.rag_n = n; b.rag_step = 2 * s; b.rag_off = s; b.rag_clip_k = 1;
     b.k_upto_m = 1;  // Linv22 lower triangular: A(m, k) = 0 for k > m
+    b.tile = 32;
     gemm_f64(b, st);
   }
 }

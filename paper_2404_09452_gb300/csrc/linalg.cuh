@@ -16,6 +16,7 @@ struct GemmArgs {
   double *C = nullptr;
   long long sCm = 0, sCn = 0, sCb = 0;
   double alpha = 1.0, beta = 0.0;
+  int tile = 64;       // output tile edge: 64 (default) or 32 (4x more CTAs)
   int lower_only = 0;  // skip output tiles strictly above the diagonal
   int k_upto_n = 0;    // K range of an output tile limited to k < n_tile_end
                        // (B lower triangular in (n, k))
