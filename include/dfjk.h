@@ -121,6 +121,22 @@ int dfjk_query(dfjk_handle h, int32_t *nao, int32_t *naux, int32_t *npair_kept,
 int dfjk_build(dfjk_handle h, int32_t nset, int32_t nocc, const double *C_occ,
                double *J, double *K, double *E_J, double *E_K, void *stream);
 
+/* Spin-unrestricted build: two occupied sets, alpha and beta, with their own
+ * counts (the unrestricted case the paper's code supports alongside the
+ * restricted one).  D_a = C_a C_a^T, D_b = C_b C_b^T.
+ *   C_a : device nao x nocc_a, C_b : device nao x nocc_b (row-major FP64);
+ *         1 <= nocc_a, 0 <= nocc_b <= nocc_a (nocc_b = 0: C_b may be NULL).
+ *   J   : device nao x nao, Coulomb matrix of the total density D_a + D_b.
+ *   K_a, K_b : device nao x nao, exchange matrices of each spin (K_b = 0 when
+ *         nocc_b = 0).
+ *   E   : 3 doubles, host or device (detected): E[0] = Tr((D_a + D_b) J)/2,
+ *         E[1] = Tr(D_a K_a)/2, E[2] = Tr(D_b K_b)/2; the two-electron energy
+ *         of the determinant is E[0] - E[1] - E[2].
+ * Same buffers, ordering and errors as dfjk_build.                          */
+int dfjk_build_uks(dfjk_handle h, int32_t nocc_a, const double *C_a, int32_t nocc_b,
+                   const double *C_b, double *J, double *K_a, double *K_b, double *E,
+                   void *stream);
+
 /* Steps a6-a9 for nmol resident handles at once (row a10, batching): the builds
  * are spread over `nstreams` internal streams forked from and joined back to
  * `stream`, so small molecules run concurrently.  Handle i uses nocc[i],

@@ -248,3 +248,25 @@ def energies_second_way(T, V, B, C):
     M = np.einsum("mi,Pmn,nj->Pij", C, B, C, optimize=True)
     return 0.5 * float(u @ d), 0.5 * float(np.sum(M * M))
 
+
+
+def dfjk_uks(B: np.ndarray, C_a: np.ndarray, C_b: np.ndarray):
+    """Spin-unrestricted J/K from the whitened tensor B (the unrestricted row of
+    the paper's functionality table): D_a = C_a C_a^T, D_b = C_b C_b^T, J from
+    the total density D_a + D_b (J is linear in D), K per spin, and
+    E_J = Tr((D_a + D_b) J)/2, E_K,s = Tr(D_s K_s)/2.  C_b may have no columns."""
+    naux, nao, _ = B.shape
+    B2 = B.reshape(naux, nao * nao)
+    D_a = C_a @ C_a.T
+    D_b = C_b @ C_b.T
+    D = D_a + D_b
+    rho = B2 @ D.ravel()
+    J = (rho @ B2).reshape(nao, nao)
+
+    def exchange(C):
+        X = np.matmul(B, C).transpose(1, 0, 2).reshape(nao, -1)
+        return X @ X.T
+
+    K_a, K_b = exchange(C_a), exchange(C_b)
+    return dict(D=D, J=J, K_a=K_a, K_b=K_b, E_J=0.5 * np.sum(D * J),
+                E_K_a=0.5 * np.sum(D_a * K_a), E_K_b=0.5 * np.sum(D_b * K_b))

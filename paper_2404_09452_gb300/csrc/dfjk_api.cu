@@ -215,6 +215,7 @@ struct dfjk_ctx {
   DBuf<double> D, rho, rho_work, X, Kpart, en_work, e;
   int ksplit = 1;
   SlicedOp Csl, Xsl;  // DFJK_MIXED build operands
+  DBuf<double> uks_D, uks_J;  // spin-unrestricted build: D_a + D_b and J[D_b]
   ~dfjk_ctx() {
     oz_free(Bsl);
     oz_free(Bchunk);
@@ -562,6 +563,8 @@ void release_device(dfjk_ctx *h) {
   h->e.release();
   oz_free(h->Csl);
   oz_free(h->Xsl);
+  h->uks_D.release();
+  h->uks_J.release();
   h->ws_nocc = -1;
   h->resident = false;
 }
@@ -589,6 +592,17 @@ __global__ void split_energies_kernel(const double *e, int nset, double *EJ, dou
     EJ[s] = e[2 * s];
     EK[s] = e[2 * s + 1];
   }
+}
+
+// y += x over n doubles (the sum of the two spin densities and of their J).
+__global__ void add_inplace_kernel(double *__restrict__ y, const double *__restrict__ x, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] += x[i];
+}
+
+void add_inplace(double *y, const double *x, long long n, cudaStream_t st) {
+  add_inplace_kernel<<<(unsigned)std::min<long long>(ceil_div(n, 256), 152 * 8), 256, 0, st>>>(y, x, n);
+  DFJK_LAUNCHED();
 }
 
 // Steps a6-a9 for one occupied set.  DFJK_FP64 runs X = B C and K on the
@@ -839,6 +853,62 @@ int dfjk_build(dfjk_handle h, int32_t nset, int32_t nocc, const double *C, doubl
     } else {
       split_energies_kernel<<<ceil_div(nset, 64), 64, 0, st>>>(h->e.p, nset, EJ, EK);
       DFJK_LAUNCHED();
+    }
+    return DFJK_OK;
+  } catch (const Error &e) {
+    return fail(e);
+  }
+}
+
+int dfjk_build_uks(dfjk_handle h, int32_t nocc_a, const double *C_a, int32_t nocc_b, const double *C_b,
+                   double *J, double *K_a, double *K_b, double *E, void *stream) {
+  try {
+    if (!h) throw Error{DFJK_ERR_ARG, "null handle"};
+    if (nocc_a < 1 || nocc_b < 0 || nocc_b > nocc_a || !C_a || (nocc_b > 0 && !C_b) || !J || !K_a || !K_b || !E)
+      throw Error{DFJK_ERR_ARG, "build_uks arguments"};
+    cudaStream_t st = S(stream);
+    DFJK_CUDA_CHECK(cudaSetDevice(h->device));
+    if (!h->resident) make_resident(h, st);
+    ensure_workspace(h, nocc_a, 3);
+    const size_t nao2 = (size_t)h->nao * h->nao;
+    if (!h->uks_D.p) h->uks_D.alloc(nao2);
+    if (!h->uks_J.p) h->uks_J.alloc(nao2);
+    double *e = h->e.p;  // [E_J a, E_K a, E_J b, E_K b, E_J total, -]
+    build_one(h, nocc_a, C_a, J, K_a, e, st);
+    DFJK_CUDA_CHECK(cudaMemcpyAsync(h->uks_D.p, h->D.p, nao2 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    if (nocc_b > 0) {
+      build_one(h, nocc_b, C_b, h->uks_J.p, K_b, e + 2, st);
+      add_inplace(h->uks_D.p, h->D.p, (long long)nao2, st);
+      add_inplace(J, h->uks_J.p, (long long)nao2, st);
+    } else {
+      DFJK_CUDA_CHECK(cudaMemsetAsync(K_b, 0, nao2 * sizeof(double), st));
+      DFJK_CUDA_CHECK(cudaMemsetAsync(e + 2, 0, 2 * sizeof(double), st));
+    }
+    {
+      PhaseScope ph(7, st);
+      energies_f64(h->uks_D.p, J, K_a, h->nao, e + 4, h->en_work.p, st);
+    }
+    // E = {E_J of the total density, E_K alpha, E_K beta}
+    cudaPointerAttributes pa{};
+    DFJK_CUDA_CHECK(cudaPointerGetAttributes(&pa, E));
+    const bool dev = pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged;
+    if (dev) {  // E[0] = e[4], E[1] = e[1], E[2] = e[3], stream-ordered
+      DFJK_CUDA_CHECK(cudaMemcpyAsync(E, e + 4, sizeof(double), cudaMemcpyDeviceToDevice, st));
+      DFJK_CUDA_CHECK(cudaMemcpyAsync(E + 1, e + 1, sizeof(double), cudaMemcpyDeviceToDevice, st));
+      DFJK_CUDA_CHECK(cudaMemcpyAsync(E + 2, e + 3, sizeof(double), cudaMemcpyDeviceToDevice, st));
+    } else {
+      double host[6];
+      DFJK_CUDA_CHECK(cudaMemcpyAsync(host, e, sizeof(host), cudaMemcpyDeviceToHost, st));
+      DFJK_CUDA_CHECK(cudaStreamSynchronize(st));
+      E[0] = host[4];
+      E[1] = host[1];
+      E[2] = host[3];
+      int status = 0;
+      DFJK_CUDA_CHECK(cudaMemcpy(&status, h->status.p, sizeof(int), cudaMemcpyDeviceToHost));
+      if (status & STATUS_TIMEOUT) {
+        DFJK_CUDA_CHECK(cudaMemset(h->status.p, 0, sizeof(int)));
+        throw Error{DFJK_ERR_TIMEOUT, "a bounded device wait expired during the build"};
+      }
     }
     return DFJK_OK;
   } catch (const Error &e) {

@@ -36,6 +36,7 @@ EXPORTS = [
     "dfjk_setup",
     "dfjk_query",
     "dfjk_build",
+    "dfjk_build_uks",
     "dfjk_build_batch",
     "dfjk_overlap",
     "dfjk_overlap_matrix",
@@ -263,6 +264,32 @@ class Handle:
             self.h, nset, nocc, ctypes.c_void_p(C.data_ptr()), ctypes.c_void_p(J.data_ptr()),
             ctypes.c_void_p(K.data_ptr()), pj, pk, _stream(stream)))
         return J, K, EJ, EK
+
+    def build_uks(self, C_a, C_b, stream=None, energies_on_device=False):
+        """Spin-unrestricted build: C_a [nao x nocc_a], C_b [nao x nocc_b] (device
+        FP64, nocc_b <= nocc_a, nocc_b may be 0).  Returns (J of the total
+        density, K_a, K_b, E) with E = [E_J total, E_K alpha, E_K beta]."""
+        torch = _torch()
+        C_a = C_a.contiguous()
+        C_b = C_b.contiguous()
+        nao = self.nao
+        if C_a.shape[0] != nao or C_b.shape[0] != nao:
+            raise ValueError("C has the wrong number of rows")
+        J = torch.empty((nao, nao), dtype=torch.float64, device=C_a.device)
+        Ka = torch.empty_like(J)
+        Kb = torch.empty_like(J)
+        if energies_on_device:
+            E = torch.empty(3, dtype=torch.float64, device=C_a.device)
+            pe = ctypes.c_void_p(E.data_ptr())
+        else:
+            E = np.zeros(3)
+            pe = ctypes.c_void_p(E.ctypes.data)
+        nb = int(C_b.shape[1])
+        _check(load_library().dfjk_build_uks(
+            self.h, int(C_a.shape[1]), ctypes.c_void_p(C_a.data_ptr()), nb,
+            ctypes.c_void_p(C_b.data_ptr() if nb else None), ctypes.c_void_p(J.data_ptr()),
+            ctypes.c_void_p(Ka.data_ptr()), ctypes.c_void_p(Kb.data_ptr()), pe, _stream(stream)))
+        return J, Ka, Kb, E
 
     def overlap(self, stream=None):
         torch = _torch()

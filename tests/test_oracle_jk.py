@@ -118,3 +118,42 @@ def test_water_golden():
     assert r["E_K"] == pytest.approx(g["E_K"], rel=1e-13)
     assert np.allclose(r["J"], np.array(g["J"]), rtol=0, atol=1e-13)
     assert np.allclose(r["K"], np.array(g["K"]), rtol=0, atol=1e-13)
+
+
+# ---- spin-unrestricted densities (two occupied sets) -------------------------------
+
+
+def test_uks_one_electron_has_no_two_electron_energy(sys_):
+    """A single occupied spin orbital: the Coulomb self-energy equals its
+    exchange self-energy (both are sum_P (c^T B_P c)^2 / 2), so the
+    two-electron energy vanishes — also within density fitting."""
+    _, _, C, _, _, r = sys_
+    u = O.dfjk_uks(r["B"], C[:, :1], C[:, :0])
+    assert abs(u["E_J"] - u["E_K_a"]) < 1e-13 * abs(u["E_J"]) and u["E_K_b"] == 0.0
+    assert np.max(np.abs(u["K_b"])) == 0.0
+
+
+def test_uks_closed_shell_limit(sys_):
+    """C_a = C_b = C: J doubles, each K is the restricted one, E_J is 4x."""
+    _, _, C, _, _, r = sys_
+    u = O.dfjk_uks(r["B"], C, C)
+    assert np.max(np.abs(u["J"] - 2 * r["J"])) < 1e-12 * np.abs(r["J"]).max()
+    assert np.max(np.abs(u["K_a"] - r["K"])) < 1e-13 * np.abs(r["K"]).max()
+    assert np.array_equal(u["K_a"], u["K_b"])
+    assert abs(u["E_J"] - 4 * r["E_J"]) < 1e-12 * abs(r["E_J"])
+
+
+def test_uks_coulomb_from_fitted_coefficients(sys_):
+    """E_J of the total density through the fitted coefficients d = V^-1 u of
+    u_P = sum (P|mu nu)(D_a + D_b)_mu nu (LU solve, no Cholesky, no B), and the
+    exchange energies as sum_P ||C_s^T B_P C_s||^2 / 2."""
+    _, _, C, T, V, r = sys_
+    nb = max(1, C.shape[1] - 2)
+    Ca, Cb = C, C[:, ::-1][:, :nb].copy()
+    u = O.dfjk_uks(r["B"], Ca, Cb)
+    naux = V.shape[0]
+    ut = T.reshape(naux, -1) @ (Ca @ Ca.T + Cb @ Cb.T).ravel()
+    assert abs(u["E_J"] - 0.5 * ut @ np.linalg.solve(V, ut)) < 1e-10 * abs(u["E_J"])
+    for Cs, key in ((Ca, "E_K_a"), (Cb, "E_K_b")):
+        M = np.einsum("mi,Pmn,nj->Pij", Cs, r["B"], Cs, optimize=True)
+        assert abs(u[key] - 0.5 * np.sum(M * M)) < 1e-12 * abs(u[key])
