@@ -39,6 +39,26 @@ WORKLOADS = {
 }
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FP64_PEAK_GFLOPS = 1199.0  # measured FP64 DFMA throughput of this GB300 pool (FMA chains)
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_mol60.md")
+
+
+def recorded_traffic(key: str, workload: str):
+    """DRAM bytes (read + write) per launch of the tensor-core GEMM `key`, from the
+    ncu capture summarised in profiles/traffic_mol60.md, or None when there is
+    no capture for this workload or the kernel source changed since (the
+    summary records the sha256 of csrc/ozaki.cu it was taken with)."""
+    import hashlib
+
+    src = os.path.join(ROOT, "paper_2404_09452_gb300", "csrc", "ozaki.cu")
+    if not os.path.exists(TRAFFIC_FILE) or not os.path.exists(src):
+        return None
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    for line in open(TRAFFIC_FILE):
+        f = line.split()
+        # traffic-per-launch <kernel> <workload> <bytes> <sha256 of ozaki.cu>
+        if len(f) == 5 and f[0] == "traffic-per-launch" and f[1] == key and f[2] == workload and f[4] == sha:
+            return int(f[3])
+    return None
 
 
 def parse():
@@ -82,6 +102,19 @@ def algorithmic_flops(nao, naux, nocc, ncol):
         "X=BC": 2.0 * naux * nao * nao * nocc,
         "K": float(naux) * nocc * nao * (nao + 1),
         "rho+J": 2.0 * 2.0 * naux * nao * (nao + 1) / 2 + 2.0 * nao * nao * nocc,
+    }
+
+
+def algorithmic_bytes(nao, naux, nocc, ncol):
+    """Bytes each tensor-core GEMM must move once per step (operand slices read
+    once, outputs written once): whitening reads the 8 BF16 slices of T and of
+    L^-1 and writes B in both triangles; X reads the 6 slices of B and C and
+    writes X; K reads the 6 slices of X and writes one FP64 triangle."""
+    npad = (naux + 63) // 64 * 64
+    return {
+        "whiten": 16.0 * ncol * npad + 16.0 * npad * npad + 16.0 * ncol * npad,
+        "X=BC": 12.0 * nao * nao * npad + 12.0 * nao * nocc + 8.0 * nao * npad * nocc,
+        "K": 12.0 * nao * npad * nocc + 8.0 * nao * (nao + 1) / 2,
     }
 
 
@@ -361,8 +394,9 @@ def run_ours(args):
                 "unit": "TFLOP/s", "peak": bf16_sust / prods,
                 "peak_source": f"measured sustained BF16 dense {bf16_sust} TFLOP/s of measured "
                                f"(MEASURED_PEAKS.json) / {prods} exact slice products",
-                "tensor_pipe_tflops": achieved * prods, "traffic": None,
+                "tensor_pipe_tflops": achieved * prods, "traffic": recorded_traffic(dom, args.workload),
                 "algorithmic_flops_per_launch": flops[dom] / nl, "ms_per_launch": dom_ms,
+                "algorithmic_bytes_per_launch": algorithmic_bytes(m.nao, m.naux, nocc, ncol)[dom] / nl,
                 "launches_per_step": nl}
     roof["frac"] = roof["achieved"] / roof["peak"]
     out = {

@@ -368,6 +368,23 @@ __device__ __forceinline__ double pow2(int e) {
   return e < -1022 ? 0.0 : __longlong_as_double((long long)(e + 1023) << 52);
 }
 
+// Recombination of the S level sums of one output (exact integers in FP32,
+// |sum| < 2^23) into one int64: levels 0..TOP exactly, shifted by 6 bits per
+// level; for S = 8 the last level is rounded to the unit of level 6, so that
+// |T| < 2^60 (S <= 6: every level exact, |T| < 2^54).  The output value is
+// T 2^(eA + eB - UNIT), one FP64 multiply-add per output and K block.
+template <int S>
+struct OzLev {
+  static constexpr int TOP = (S <= 6) ? S - 1 : S - 2;
+  static constexpr int UNIT = 12 + 6 * TOP;
+};
+template <int S>
+__device__ __forceinline__ void oz_add_level(long long &T, int lev, float v) {
+  const long long iv = (long long)__float2int_rn(v);
+  if (lev <= OzLev<S>::TOP) T += iv << (6 * (OzLev<S>::TOP - lev));
+  else T += (iv + (1LL << (6 * (lev - OzLev<S>::TOP) - 1))) >> (6 * (lev - OzLev<S>::TOP));
+}
+
 template <int S>
 __global__ void __launch_bounds__(128, 1)
     oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
@@ -494,30 +511,25 @@ __global__ void __launch_bounds__(128, 1)
       break;
     }
     tc::tc_fence_after();
-    const int eA = ka.expoA[((long long)zA * ka.rows_padA + m) * ka.nkbA + kb];
+    const int eA = ka.expoA[((long long)zA * ka.rows_padA + m) * ka.nkbA + kb] - OzLev<S>::UNIT;
     const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
 #pragma unroll
     for (int c = 0; c < OZ_BN / 16; ++c) {
-      long long T0[16], T1[16];
+      long long T[16];
 #pragma unroll
-      for (int j = 0; j < 16; ++j) T0[j] = T1[j] = 0;
+      for (int j = 0; j < 16; ++j) T[j] = 0;
 #pragma unroll
       for (int lev = 0; lev < S; ++lev) {
         float v[16];
         tc::tmem_ld16(tbase + lane_base + lev * OZ_BN + c * 16, v);
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const long long iv = (long long)__float2int_rn(v[j]);
-          if (lev < 4) T0[j] += iv << (6 * (3 - lev));
-          else T1[j] += iv << (6 * (7 - lev));
-        }
+        for (int j = 0; j < 16; ++j) oz_add_level<S>(T[j], lev, v[j]);
       }
 #pragma unroll
       for (int j = 0; j < 16; ++j) {
         const int n = n0 + c * 16 + j;
         const int eB = __ldg(ka.expoB + ((long long)zB * ka.rows_padB + n) * ka.nkbB + kb);
-        acc[c * 16 + j] = fma((double)T0[j], pow2(eA + eB - 30), acc[c * 16 + j]);
-        if (S > 4) acc[c * 16 + j] = fma((double)T1[j], pow2(eA + eB - 54), acc[c * 16 + j]);
+        acc[c * 16 + j] = fma((double)T[j], pow2(eA + eB), acc[c * 16 + j]);
       }
     }
     tc::tc_fence_before();
@@ -550,13 +562,15 @@ __global__ void __launch_bounds__(128, 1)
 
 // ---- persistent warp-specialised GEMM -----------------------------------------------
 //
-// 192 threads: warp 0 = TMA producer, warp 1 = MMA issuer (and TMEM owner),
-// warps 2-5 = epilogue (warp w reads TMEM lanes 32 (w % 4) .. +31).  A CTA
-// walks tiles blockIdx.x, += gridDim.x (n fastest, so consecutive tiles share
-// their A rows in L2).  Per K-block: the producer fills the stage ring, the
-// MMA warp accumulates S levels in TMEM and commits `accf`; the epilogue
-// drains into FP64 registers and releases TMEM through `acce` (128 arrivals).
-// The producer runs ahead into the next K-block / tile during the drain.
+// 320 threads: warp 0 = TMA producer, warp 1 = MMA issuer (and TMEM owner),
+// warps 2-9 = epilogue (warp w reads TMEM lanes 32 (w % 4) .. +31, columns
+// 32 ((w - 2) / 4) .. +31 of the tile).  A CTA walks tiles blockIdx.x,
+// += gridDim.x (n fastest, so consecutive tiles share their A rows in L2).
+// Per K-block: the producer fills the stage ring, the MMA warp accumulates S
+// levels in TMEM and commits `accf`; the epilogue drains into FP64 registers
+// and releases TMEM through `acce` (256 arrivals).  The producer runs ahead
+// into the next K-block / tile during the drain.
+constexpr int OZ_WS_THREADS = 320;
 
 struct OzTiles {
   int ntm, ntn, nz, total;
@@ -584,7 +598,7 @@ __device__ __forceinline__ bool oz_tile(const OzGemmArgs &g, const OzTiles &T, i
 }
 
 template <int S>
-__global__ void __launch_bounds__(192, 1)
+__global__ void __launch_bounds__(OZ_WS_THREADS, 1)
     oz_gemm_ws_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                       const OzKernelArgs ka, const OzTiles T) {
   using Cfg = OzCfg<S>;
@@ -607,7 +621,7 @@ __global__ void __launch_bounds__(192, 1)
       tc::mbar_init(&empty[i], 1);
     }
     tc::mbar_init(accf, 1);
-    tc::mbar_init(acce, 128);
+    tc::mbar_init(acce, OZ_WS_THREADS - 64);
     tc::mbar_init(fin, 1);
     *abort_flag = 0;
     tc::fence_mbar_init();
@@ -708,10 +722,12 @@ __global__ void __launch_bounds__(192, 1)
       tc::mma_commit(fin);
       tc::mbar_wait(fin, 0, OZ_CLEANUP_POLLS);
     }
-  } else {  // ---- epilogue, 128 threads
-    const int lgrp = warp & 3;  // TMEM lane group of this warp
+  } else {  // ---- epilogue, 8 warps: TMEM lane group (warp % 4), column half
+    const int lgrp = warp & 3;
+    const int half = (warp - 2) >> 2;  // columns 32 half .. 32 half + 31 of the tile
     const int row = lgrp * 32 + lane;
     const uint32_t lane_base = (uint32_t)(lgrp * 32) << 16;
+    constexpr int NH = OZ_BN / 2;
     uint32_t kbi = 0;
     bool ok = true;
     for (int t = blockIdx.x; t < T.total && ok; t += gridDim.x) {
@@ -719,9 +735,10 @@ __global__ void __launch_bounds__(192, 1)
       if (!oz_tile(g, T, t, m0, n0, z, kb0, kb1, kend)) continue;
       const int zA = g.a_batched ? z : 0, zB = g.b_batched ? z : 0;
       const int m = m0 + row;
-      double acc[OZ_BN];
+      const int nh = n0 + half * NH;
+      double acc[NH];
 #pragma unroll
-      for (int j = 0; j < OZ_BN; ++j) acc[j] = 0.0;
+      for (int j = 0; j < NH; ++j) acc[j] = 0.0;
       for (int kb = kb0; kb < kb1; ++kb, ++kbi) {
         // warp-uniform decision: tcgen05.ld below needs the whole warp
         const bool waited = tc::mbar_wait(accf, kbi & 1, lim);
@@ -730,37 +747,25 @@ __global__ void __launch_bounds__(192, 1)
           break;
         }
         tc::tc_fence_after();
-        const double sa = pow2(ka.expoA[((long long)zA * ka.rows_padA + m) * ka.nkbA + kb]);
+        const int eA = ka.expoA[((long long)zA * ka.rows_padA + m) * ka.nkbA + kb] - OzLev<S>::UNIT;
+        // this warp's 32 column exponents, one per lane, broadcast by shuffles
+        const int eBl = __ldg(ka.expoB + ((long long)zB * ka.rows_padB + nh + lane) * ka.nkbB + kb);
 #pragma unroll
-        for (int c = 0; c < OZ_BN / 16; ++c) {
-          long long T0[16], T1[16];
+        for (int c = 0; c < NH / 16; ++c) {
+          long long T[16];
 #pragma unroll
-          for (int j = 0; j < 16; ++j) T0[j] = T1[j] = 0;
+          for (int j = 0; j < 16; ++j) T[j] = 0;
 #pragma unroll
           for (int lev = 0; lev < S; ++lev) {
             float v[16];
-            tc::tmem_ld16(tbase + lane_base + lev * OZ_BN + c * 16, v);
+            tc::tmem_ld16(tbase + lane_base + lev * OZ_BN + half * NH + c * 16, v);
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-              const long long iv = (long long)__float2int_rn(v[j]);
-              // S <= 6: one group, |sum| < 2^54 (rounded once when converted);
-              // S = 8: levels 0-3 and 4-7 in separate groups
-              if (S <= 6) T0[j] += iv << (6 * (S - 1 - lev));
-              else if (lev < 4) T0[j] += iv << (6 * (3 - lev));
-              else T1[j] += iv << (6 * (7 - lev));
-            }
+            for (int j = 0; j < 16; ++j) oz_add_level<S>(T[j], lev, v[j]);
           }
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
-            const int eB = __ldg(ka.expoB + ((long long)zB * ka.rows_padB + n0 + c * 16 + j) * ka.nkbB + kb);
-            const double cscale = pow2(eB - 6 * (S + 1)) * sa;
-            if (S <= 6) {
-              acc[c * 16 + j] = fma((double)T0[j], cscale, acc[c * 16 + j]);
-            } else {
-              // group 0 carries 2^24 relative to group 1's unit: T0 2^(6(S-1)-18)
-              acc[c * 16 + j] = fma((double)T0[j], cscale * 16777216.0, acc[c * 16 + j]);
-              acc[c * 16 + j] = fma((double)T1[j], cscale, acc[c * 16 + j]);
-            }
+            const int eB = __shfl_sync(0xffffffffu, eBl, c * 16 + j);
+            acc[c * 16 + j] = fma((double)T[j], pow2(eA + eB), acc[c * 16 + j]);
           }
         }
         tc::tc_fence_before();
@@ -768,22 +773,37 @@ __global__ void __launch_bounds__(192, 1)
       }
       if (!ok) break;
       if (m < g.M) {
+        const bool full = nh + NH <= g.N;
         if (g.mode == 0) {
-          double *o = g.out + (long long)z * g.out_bs + (long long)m * g.ldo;
+          double *o = g.out + (long long)z * g.out_bs + (long long)m * g.ldo + nh;
+          if (full && ((uintptr_t)o & 15) == 0) {
 #pragma unroll
-          for (int j = 0; j < OZ_BN; ++j)
-            if (n0 + j < g.N) o[n0 + j] = acc[j];
+            for (int j = 0; j < NH; j += 2) *reinterpret_cast<double2 *>(o + j) = make_double2(acc[j], acc[j + 1]);
+          } else {
+#pragma unroll
+            for (int j = 0; j < NH; ++j)
+              if (nh + j < g.N) o[j] = acc[j];
+          }
         } else {
           const int mu = g.colmu[m], nu = g.colnu[m];
           if (mu >= 0) {
-            double *o1 = g.out + ((long long)mu * g.nao + nu) * g.ldb;
-            double *o2 = g.out + ((long long)nu * g.nao + mu) * g.ldb;
+            double *o1 = g.out + ((long long)mu * g.nao + nu) * g.ldb + nh;
+            double *o2 = g.out + ((long long)nu * g.nao + mu) * g.ldb + nh;
+            if (full && (((uintptr_t)o1 | (uintptr_t)o2) & 15) == 0) {
 #pragma unroll
-            for (int j = 0; j < OZ_BN; ++j)
-              if (n0 + j < g.N) {
-                o1[n0 + j] = acc[j];
-                if (mu != nu) o2[n0 + j] = acc[j];
+              for (int j = 0; j < NH; j += 2) {
+                const double2 v = make_double2(acc[j], acc[j + 1]);
+                *reinterpret_cast<double2 *>(o1 + j) = v;
+                if (mu != nu) *reinterpret_cast<double2 *>(o2 + j) = v;
               }
+            } else {
+#pragma unroll
+              for (int j = 0; j < NH; ++j)
+                if (nh + j < g.N) {
+                  o1[j] = acc[j];
+                  if (mu != nu) o2[j] = acc[j];
+                }
+            }
           }
         }
       }
@@ -862,7 +882,7 @@ static void launch_oz_ws(const SlicedOp &A, const SlicedOp &B, const OzGemmArgs 
   if (total > 2147483647LL) throw Error{DFJK_ERR_ARG, "oz_gemm: too many tiles"};
   T.total = (int)total;
   const int grid = (int)std::min<long long>(total, num_sms());
-  oz_gemm_ws_kernel<S><<<grid, 192, SMEM, st>>>(ma, mb, ka, T);
+  oz_gemm_ws_kernel<S><<<grid, OZ_WS_THREADS, SMEM, st>>>(ma, mb, ka, T);
   DFJK_LAUNCHED();
 }
 
