@@ -201,6 +201,7 @@ struct dfjk_ctx {
   // metric
   DBuf<double> V, L, Linv, Dinv;
   DBuf<int> status;
+  DBuf<int> tctr;  // tile counter of the tensor-core GEMM launches (stream-ordered)
   // whitened tensor: FP64 B[(mu nao + nu) ldb + P]; in DFJK_MIXED also its
   // 6-slice form for the tensor-core X = B C (batch mu, rows P, K nu)
   DBuf<double> B;
@@ -367,6 +368,7 @@ void make_resident(dfjk_ctx *h, cudaStream_t st) {
                                      " bytes) exceeds hbm_budget_bytes"};
   upload_bases(h, st);
   h->status.alloc(1);
+  if (!h->tctr.p) h->tctr.alloc(1);
   DFJK_CUDA_CHECK(cudaMemsetAsync(h->status.p, 0, sizeof(int), st));
 
   PhaseScope *ph0 = new PhaseScope(0, st);
@@ -516,6 +518,7 @@ void make_resident(dfjk_ctx *h, cudaStream_t st) {
       g.M = ncols; g.N = np; g.K = np; g.k_upto_n = 1;
       g.mode = 1; g.out = h->B.p; g.colmu = h->colmu.p + c0; g.colnu = h->colnu.p + c0;
       g.nao = h->nao; g.ldb = h->ldb; g.status = h->status.p; g.timeout = h->opt.timeout_iters;
+      g.tile_ctr = h->tctr.p;
       g.phase = 8;
       oz_gemm(T8, Linv8, g, st);
     }
@@ -657,6 +660,7 @@ void build_one(dfjk_ctx *h, int nocc, const double *C, double *J, double *Kout, 
       x.M = np; x.N = nocc; x.K = nao; x.nz = nao; x.a_batched = 1;
       x.mode = 0; x.out = h->X.p; x.ldo = nocc; x.out_bs = (long long)np * nocc;
       x.status = h->status.p; x.timeout = h->opt.timeout_iters;
+      x.tile_ctr = h->tctr.p;
       x.phase = 9;
       if (!h->lean) {
         oz_gemm(h->Bsl, h->Csl, x, st);
@@ -689,13 +693,18 @@ void build_one(dfjk_ctx *h, int nocc, const double *C, double *J, double *Kout, 
     for (int i = 0; i < mt; ++i)
       for (int j = 0; j < nt; ++j)
         if (j * OZ_BN <= i * OZ_BM + OZ_BM - 1) ++tiles;
-    // K ranges of about 96 MB of operand slices (all rows) so that the tiles
-    // working on one range at a time (the persistent kernel orders work
-    // split-major) reuse it from L2; partial K buffers capped at 2 GiB
+    // K ranges of about 64 MB of operand slices (all rows): the tiles in
+    // flight (work is handed out split-major, a few ranges at a time) then
+    // reuse their operands from L2; partial K buffers capped at 4 GiB
+    static const size_t range_bytes = [] {
+      const char *e = std::getenv("DFJK_K_RANGE_MB");
+      const long v = e ? std::atol(e) : 0;
+      return (size_t)(v > 0 ? v : 64) << 20;
+    }();
     const int nkb = h->Xsl.nkb;
     const size_t chunk_kb_bytes = (size_t)h->Xsl.rows_pad * 6 * 2 * OZ_KB;
-    int per = (int)std::max<size_t>(1, ((size_t)96 << 20) / chunk_kb_bytes);
-    const int max_split = (int)std::max<size_t>(1, ((size_t)2 << 30) / ((size_t)nao * nao * 8));
+    int per = (int)std::max<size_t>(1, range_bytes / chunk_kb_bytes);
+    const int max_split = (int)std::max<size_t>(1, ((size_t)4 << 30) / ((size_t)nao * nao * 8));
     int nsplit = std::min(ceil_div(nkb, per), max_split);
     nsplit = std::max(nsplit, std::min(nkb, (2 * 152 + tiles - 1) / tiles));
     per = ceil_div(nkb, nsplit);
@@ -705,6 +714,7 @@ void build_one(dfjk_ctx *h, int nocc, const double *C, double *J, double *Kout, 
     k.M = nao; k.N = nao; k.K = (int)kt; k.nz = nsplit; k.kb_per_split = per; k.lower_only = 1;
     k.mode = 0; k.out = h->Kpart.p; k.ldo = nao; k.out_bs = (long long)nao * nao;
     k.status = h->status.p; k.timeout = h->opt.timeout_iters;
+    k.tile_ctr = h->tctr.p;
     k.phase = 10;
     oz_gemm(h->Xsl, h->Xsl, k, st);
     reduce_sym_f64(h->Kpart.p, nsplit, nao, Kout, st);

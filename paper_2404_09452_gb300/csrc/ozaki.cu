@@ -564,13 +564,19 @@ __global__ void __launch_bounds__(128, 1)
 //
 // 320 threads: warp 0 = TMA producer, warp 1 = MMA issuer (and TMEM owner),
 // warps 2-9 = epilogue (warp w reads TMEM lanes 32 (w % 4) .. +31, columns
-// 32 ((w - 2) / 4) .. +31 of the tile).  A CTA walks tiles blockIdx.x,
-// += gridDim.x (n fastest, so consecutive tiles share their A rows in L2).
-// Per K-block: the producer fills the stage ring, the MMA warp accumulates S
+// 32 ((w - 2) / 4) .. +31 of the tile).  Tile order: n fastest, so tiles in
+// flight at the same time share their A rows.
+// Tiles are handed out dynamically: the producer takes the next tile index
+// from a global counter and passes it to the MMA and epilogue warps through a
+// small queue in shared memory, so the CTAs advance through the tile order
+// together and the operands of the tiles in flight stay in L2 (a static
+// round-robin lets CTAs drift apart when tiles differ in length).  Per
+// K-block: the producer fills the stage ring, the MMA warp accumulates S
 // levels in TMEM and commits `accf`; the epilogue drains into FP64 registers
 // and releases TMEM through `acce` (256 arrivals).  The producer runs ahead
 // into the next K-block / tile during the drain.
 constexpr int OZ_WS_THREADS = 320;
+constexpr int OZ_QD = 4;  // depth of the tile queue
 
 struct OzTiles {
   int ntm, ntn, nz, total;
@@ -609,16 +615,24 @@ __global__ void __launch_bounds__(OZ_WS_THREADS, 1)
   uint64_t *accf = empty + Cfg::NST;
   uint64_t *acce = accf + 1;
   uint64_t *fin = acce + 1;
-  uint32_t *tmem_holder = (uint32_t *)(fin + 1);
+  uint64_t *tqf = fin + 1;     // tile queue: slot filled (producer arrives)
+  uint64_t *tqe = tqf + OZ_QD; // slot read (MMA warp + 8 epilogue warps arrive)
+  uint32_t *tmem_holder = (uint32_t *)(tqe + OZ_QD);
   volatile int *abort_flag = (volatile int *)(tmem_holder + 1);
+  volatile int *tq = (volatile int *)(tmem_holder + 2);  // OZ_QD tile indices (-1: no more)
 
   const OzGemmArgs &g = ka.g;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  constexpr int NEPI = (OZ_WS_THREADS - 64) / 32;
   if (warp == 1) tc::tmem_alloc(tmem_holder, 512);
   if (tid == 0) {
     for (int i = 0; i < Cfg::NST; ++i) {
       tc::mbar_init(&full[i], 1);
       tc::mbar_init(&empty[i], 1);
+    }
+    for (int i = 0; i < OZ_QD; ++i) {
+      tc::mbar_init(&tqf[i], 1);
+      tc::mbar_init(&tqe[i], 1 + NEPI);
     }
     tc::mbar_init(accf, 1);
     tc::mbar_init(acce, OZ_WS_THREADS - 64);
@@ -635,11 +649,22 @@ __global__ void __launch_bounds__(OZ_WS_THREADS, 1)
 
   if (warp == 0) {
     if (lane == 0) {  // ---- producer
-      uint32_t gs = 0;
+      uint32_t gs = 0, qi = 0;
       bool ok = true;
-      for (int t = blockIdx.x; t < T.total && ok; t += gridDim.x) {
-        int m0, n0, z, kb0, kb1, kend;
-        if (!oz_tile(g, T, t, m0, n0, z, kb0, kb1, kend)) continue;
+      while (ok) {
+        int t, m0 = 0, n0 = 0, z = 0, kb0 = 0, kb1 = 0, kend = 0;
+        do {
+          t = atomicAdd(g.tile_ctr, 1);
+        } while (t < T.total && !oz_tile(g, T, t, m0, n0, z, kb0, kb1, kend));
+        const uint32_t qs = qi % OZ_QD;
+        if (qi >= (uint32_t)OZ_QD && !tc::mbar_wait(&tqe[qs], ((qi / OZ_QD) - 1) & 1, lim)) {
+          ok = false;
+          break;
+        }
+        tq[qs] = t < T.total ? t : -1;
+        tc::mbar_arrive(&tqf[qs]);
+        ++qi;
+        if (t >= T.total) break;
         const int zA = g.a_batched ? z : 0, zB = g.b_batched ? z : 0;
         for (int kb = kb0; kb < kb1 && ok; ++kb) {
           const int kstart = kb * OZ_KB, kstop = min(kend, kstart + OZ_KB);
@@ -675,11 +700,20 @@ __global__ void __launch_bounds__(OZ_WS_THREADS, 1)
   } else if (warp == 1) {
     if (lane == 0) {  // ---- MMA issuer
       constexpr uint32_t IDESC = tc::idesc_bf16(OZ_BM, OZ_BN);
-      uint32_t gs = 0, kbi = 0;
+      uint32_t gs = 0, kbi = 0, qi = 0;
       bool ok = true;
-      for (int t = blockIdx.x; t < T.total && ok; t += gridDim.x) {
+      while (ok) {
+        const uint32_t qs = qi % OZ_QD;
+        if (!tc::mbar_wait(&tqf[qs], (qi / OZ_QD) & 1, lim) || *abort_flag) {
+          ok = false;
+          break;
+        }
+        const int t = tq[qs];
+        tc::mbar_arrive(&tqe[qs]);
+        ++qi;
+        if (t < 0) break;
         int m0, n0, z, kb0, kb1, kend;
-        if (!oz_tile(g, T, t, m0, n0, z, kb0, kb1, kend)) continue;
+        oz_tile(g, T, t, m0, n0, z, kb0, kb1, kend);
         for (int kb = kb0; kb < kb1 && ok; ++kb, ++kbi) {
           if (kbi > 0 && !tc::mbar_wait(acce, (kbi - 1) & 1, lim)) {  // TMEM drained
             ok = false;
@@ -728,11 +762,22 @@ __global__ void __launch_bounds__(OZ_WS_THREADS, 1)
     const int row = lgrp * 32 + lane;
     const uint32_t lane_base = (uint32_t)(lgrp * 32) << 16;
     constexpr int NH = OZ_BN / 2;
-    uint32_t kbi = 0;
+    uint32_t kbi = 0, qi = 0;
     bool ok = true;
-    for (int t = blockIdx.x; t < T.total && ok; t += gridDim.x) {
+    while (ok) {
+      const uint32_t qs = qi % OZ_QD;
+      const bool got = tc::mbar_wait(&tqf[qs], (qi / OZ_QD) & 1, lim);
+      if (!__all_sync(0xffffffffu, got && !*abort_flag)) {
+        ok = false;
+        break;
+      }
+      const int t = tq[qs];
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&tqe[qs]);
+      ++qi;
+      if (t < 0) break;
       int m0, n0, z, kb0, kb1, kend;
-      if (!oz_tile(g, T, t, m0, n0, z, kb0, kb1, kend)) continue;
+      oz_tile(g, T, t, m0, n0, z, kb0, kb1, kend);
       const int zA = g.a_batched ? z : 0, zB = g.b_batched ? z : 0;
       const int m = m0 + row;
       const int nh = n0 + half * NH;
@@ -882,6 +927,8 @@ static void launch_oz_ws(const SlicedOp &A, const SlicedOp &B, const OzGemmArgs 
   if (total > 2147483647LL) throw Error{DFJK_ERR_ARG, "oz_gemm: too many tiles"};
   T.total = (int)total;
   const int grid = (int)std::min<long long>(total, num_sms());
+  if (!g.tile_ctr) throw Error{DFJK_ERR_ARG, "oz_gemm: tile counter"};
+  DFJK_CUDA_CHECK(cudaMemsetAsync(g.tile_ctr, 0, sizeof(int), st));
   oz_gemm_ws_kernel<S><<<grid, OZ_WS_THREADS, SMEM, st>>>(ma, mb, ka, T);
   DFJK_LAUNCHED();
 }
@@ -934,9 +981,11 @@ extern "C" int dfjk_debug_sliced_gemm(int32_t batch, int32_t M, int32_t N, int32
                                       void *stream) {
   using namespace dfjk;
   SlicedOp a, b;
+  int *ctr = nullptr;
   try {
     if (batch < 1 || M < 1 || N < 1 || K < 1 || !A || !B || !C) throw Error{DFJK_ERR_ARG, "sliced gemm arguments"};
     cudaStream_t st = (cudaStream_t)stream;
+    ctr = (int *)pool_alloc(sizeof(int));
     oz_alloc(a, batch, S, M, K, OZ_BM);
     oz_alloc(b, 1, S, N, K, OZ_BN);
     oz_slice_f64(A, (long long)M * K, K, 1, a, st);
@@ -945,14 +994,18 @@ extern "C" int dfjk_debug_sliced_gemm(int32_t batch, int32_t M, int32_t N, int32
     g.M = M; g.N = N; g.K = K; g.nz = batch; g.a_batched = 1;
     g.mode = 0; g.out = C; g.ldo = N; g.out_bs = (long long)M * N;
     g.status = (int *)status;
+    g.tile_ctr = ctr;
     oz_gemm(a, b, g, st);
     DFJK_CUDA_CHECK(cudaStreamSynchronize(st));
     oz_free(a);
     oz_free(b);
+    pool_free(ctr, sizeof(int));
     return DFJK_OK;
   } catch (const Error &e) {
+    cudaStreamSynchronize((cudaStream_t)stream);
     oz_free(a);
     oz_free(b);
+    if (ctr) pool_free(ctr, sizeof(int));
     set_error(e.msg);
     return e.code;
   }

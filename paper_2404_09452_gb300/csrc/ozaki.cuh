@@ -58,6 +58,9 @@ struct OzGemmArgs {
   int *status = nullptr;       // STATUS_TIMEOUT on an expired wait
   long long timeout = 1 << 26; // polls per mbarrier wait
   int phase = -1;              // phase timer id of this launch (-1: none)
+  int *tile_ctr = nullptr;     // device int for the dynamic tile queue; oz_gemm
+                               // zeroes it on the stream, so launches that can
+                               // run concurrently need distinct counters
 };
 
 // out = A B^T with A (M x K) and B (N x K) in sliced form, both with S slices.
