@@ -80,6 +80,9 @@ def parse():
     ap.add_argument("--serve-max-atoms", type=int, default=60)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fp32-pair-thresh", type=float, default=-1.0,
+                    help="Schwarz bound below which shell pairs' integrals run in FP32 "
+                         "(-1: the precision's default, 0: all FP64)")
     return ap.parse_args()
 
 
@@ -263,7 +266,9 @@ def run_ours(args):
 
     # input preparation (outside any timed region): C_occ orthonormal in the
     # overlap metric the library computes; kept-pair columns for the flop count
-    h0 = dfjk.Handle(m, precision=prec)
+    h0 = dfjk.Handle(m, precision=prec, fp32_pair_thresh=args.fp32_pair_thresh)
+    fp32_pairs = {"thresh": h0.fp32_pair_thresh, "fp32_shell_pairs": h0.npair_fp32,
+                  "kept_shell_pairs": h0.npair_kept}
     S = h0.overlap().cpu().numpy()
     Cnp = I.orthonormalize(I.c_occ_raw(m.nao, nocc, 3000 + rank), S)
     mask = h0.pair_mask().cpu().numpy()
@@ -277,7 +282,7 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
 
     def step():
-        h = dfjk.Handle(m, precision=prec)
+        h = dfjk.Handle(m, precision=prec, fp32_pair_thresh=args.fp32_pair_thresh)
         _, _, EJ, EK = h.build(C, J=J, K=K)
         h.close()
         return EJ[0], EK[0]
@@ -322,7 +327,7 @@ def run_ours(args):
     t0 = time.perf_counter()
     for _ in range(args.e2e_steps):
         Cd = Ch.to("cuda", non_blocking=True)
-        h = dfjk.Handle(m, precision=prec)
+        h = dfjk.Handle(m, precision=prec, fp32_pair_thresh=args.fp32_pair_thresh)
         Jd, Kd, EJ, EK = h.build(Cd)
         Jh.copy_(Jd, non_blocking=True)
         Kh.copy_(Kd, non_blocking=True)
@@ -350,7 +355,7 @@ def run_ours(args):
         ev1.record(stream)
         torch.cuda.synchronize()
         ms64 = ev0.elapsed_time(ev1) / args.fp64_steps
-        hm = dfjk.Handle(m, precision=prec)
+        hm = dfjk.Handle(m, precision=prec, fp32_pair_thresh=args.fp32_pair_thresh)
         Jm, Km, ejm, ekm = hm.build(C)
         fp64_cmp = {"fp64_builds_per_s": 1e3 / ms64, "fp64_ms_per_step": ms64,
                     "dE_J_vs_fp64": abs(float(ejm[0]) - float(ej64)),
@@ -407,7 +412,7 @@ def run_ours(args):
         "data": "synthetic",
         "config": {"workload": args.workload, "note": WORKLOADS[args.workload]["note"],
                    "natom": m.natom, "nao": m.nao, "naux": m.naux, "nocc": nocc,
-                   "kept_ao_pairs": ncol, "precision": args.precision,
+                   "kept_ao_pairs": ncol, "precision": args.precision, "fp32_integrals": fp32_pairs,
                    "l2": "working set > L2 (B alone is GBs), no flush needed",
                    "parallelism": f"replicas x{world}"},
         "tflops": step_flops / (total_ms / args.steps / 1e3) / 1e12,

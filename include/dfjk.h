@@ -87,12 +87,20 @@ typedef struct {
   int32_t energies_on_host;/* informational: dfjk_build detects whether its
                               E_J/E_K pointers are host memory (the call then
                               synchronises the stream) or device memory      */
+  double fp32_pair_thresh; /* Schwarz-guided mixed precision of the 3-centre
+                              integrals (the paper's future-work item in
+                              "Limitations and Future Development"): kept
+                              pairs whose bound sqrt(max(ab|ab)) *
+                              max_P sqrt((P|P)) is below this value are
+                              evaluated in FP32.  0 = every pair in FP64;
+                              negative = the precision's default (0 for
+                              DFJK_FP64, 1e-6 for DFJK_MIXED)                 */
 } dfjk_options;
 
 typedef struct dfjk_ctx *dfjk_handle;
 
 /* Fills *opt with the defaults: DFJK_FP64, 1e-12, no budget, 1<<26, host
- * energies.                                                                  */
+ * energies, fp32_pair_thresh -1 (the precision's default).                   */
 void dfjk_default_options(dfjk_options *opt);
 
 /* Steps a0-a5: validates and normalises the bases, builds the shell-pair list
@@ -110,6 +118,11 @@ int dfjk_setup(const dfjk_basis *orb, const dfjk_basis *aux, int32_t natom,
  * device bytes it holds resident.  Any output pointer may be NULL.          */
 int dfjk_query(dfjk_handle h, int32_t *nao, int32_t *naux, int32_t *npair_kept,
                size_t *device_bytes);
+
+/* Precision split of the 3-centre integrals of a handle: the number of kept
+ * shell pairs evaluated in FP32 and the bound threshold that selected them
+ * (0 when every pair is FP64).  Either output pointer may be NULL.           */
+int dfjk_query_precision(dfjk_handle h, int32_t *npair_fp32, double *fp32_thresh);
 
 /* Steps a6-a9 for nset occupied-orbital sets.
  *   C_occ : device, nset x nao x nocc, row-major FP64 (caller-owned).

@@ -27,6 +27,40 @@ constexpr double BOYS_TMAX = 40.0;
 void boys_table_host(double *tab);
 // Device copy of the table for the current device (built on first use).
 const double *boys_table_device();
+// The same table rounded to FP32, for the FP32 integral path.
+const float *boys_table_device_f32();
+
+// FP32 Boys function for the single-precision integrals of small shell pairs:
+// the same grid and expansion with five Taylor terms ((h/2)^5/5! ~ 3e-9, below
+// FP32 rounding), the FP32 table, and the same downward / upward recursions.
+template <int M>
+__device__ __forceinline__ void boys_eval(float T, const float *__restrict__ tab, float *F) {
+  constexpr int NT = 5;
+  if (T < (float)BOYS_TMAX) {
+    const int k = __float2int_rn(T * (float)(1.0 / BOYS_H));
+    const float x = (float)k * (float)BOYS_H - T;
+    const float *row = tab + k * (BOYS_NCOL + 1);
+    float f = __ldg(row + M + NT - 1);
+    float e = 1.0f;
+#pragma unroll
+    for (int j = NT - 2; j >= 0; --j) {
+      const float xj = x * (1.0f / (j + 1));
+      f = fmaf(f, xj, __ldg(row + M + j));
+      e = fmaf(e, xj, 1.0f);
+    }
+    e *= __ldg(row + BOYS_NCOL);
+    F[M] = f;
+    const float t2 = T + T;
+#pragma unroll
+    for (int m = M - 1; m >= 0; --m) F[m] = fmaf(t2, F[m + 1], e) * (1.0f / (2 * m + 1));
+  } else {
+    const float e = expf(-T);
+    const float r = 1.0f / (T + T);
+    F[0] = 0.88622692545275801365f * rsqrtf(T);
+#pragma unroll
+    for (int m = 0; m < M; ++m) F[m + 1] = fmaf((float)(2 * m + 1), F[m], -e) * r;
+  }
+}
 
 template <int M>
 __device__ __forceinline__ void boys_eval(double T, const double *__restrict__ tab, double *F) {

@@ -115,6 +115,24 @@ const double *boys_table_device() {
   return d;
 }
 
+const float *boys_table_device_f32() {
+  static std::mutex mu;
+  static std::map<int, float *> tabs;
+  int dev = 0;
+  DFJK_CUDA_CHECK(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = tabs.find(dev);
+  if (it != tabs.end()) return it->second;
+  std::vector<double> h((size_t)BOYS_NPT * (BOYS_NCOL + 1));
+  boys_table_host(h.data());
+  std::vector<float> f(h.begin(), h.end());
+  float *d = nullptr;
+  DFJK_CUDA_CHECK(cudaMalloc(&d, f.size() * sizeof(float)));
+  DFJK_CUDA_CHECK(cudaMemcpy(d, f.data(), f.size() * sizeof(float), cudaMemcpyHostToDevice));
+  tabs[dev] = d;
+  return d;
+}
+
 // ---- host-side basis ---------------------------------------------------------------
 
 struct HostBasis {
@@ -197,6 +215,9 @@ struct dfjk_ctx {
   std::vector<int> kept_cls_begin;  // 7 entries into kept list
   long long ncol = 0;
   int npair_kept = 0;
+  std::vector<int> kept32_begin;  // per class: first kept index evaluated in FP32
+  int npair_fp32 = 0;
+  double fp32_thresh = 0.0;
   DBuf<int> colmu, colnu;
   // metric
   DBuf<double> V, L, Linv, Dinv;
@@ -362,6 +383,7 @@ void compute_metric(dfjk_ctx *h, const double *tab, cudaStream_t st) {
 // Steps a0-a5 on the device.
 void make_resident(dfjk_ctx *h, cudaStream_t st) {
   const double *tab = boys_table_device();
+  const float *tab32 = boys_table_device_f32();
   const int np = h->naux_pad;
   if (h->opt.hbm_budget_bytes > 0 && resident_estimate(h) > h->opt.hbm_budget_bytes)
     throw Error{DFJK_ERR_BUDGET, "resident data (" + std::to_string(resident_estimate(h)) +
@@ -405,8 +427,19 @@ void make_resident(dfjk_ctx *h, cudaStream_t st) {
   screen_pairs(h->q.p, npair, h->scal.p, h->opt.schwarz_thresh, h->pair_keep.p, st);
   delete ph0;
   std::vector<int> keep(npair);
-  if (npair) DFJK_CUDA_CHECK(cudaMemcpyAsync(keep.data(), h->pair_keep.p, npair * sizeof(int), cudaMemcpyDeviceToHost, st));
+  std::vector<double> qh(npair);
+  double scal = 0.0;
+  if (npair) {
+    DFJK_CUDA_CHECK(cudaMemcpyAsync(keep.data(), h->pair_keep.p, npair * sizeof(int), cudaMemcpyDeviceToHost, st));
+    DFJK_CUDA_CHECK(cudaMemcpyAsync(qh.data(), h->q.p, npair * sizeof(double), cudaMemcpyDeviceToHost, st));
+  }
+  DFJK_CUDA_CHECK(cudaMemcpyAsync(&scal, h->scal.p, sizeof(double), cudaMemcpyDeviceToHost, st));
   DFJK_CUDA_CHECK(cudaStreamSynchronize(st));
+  // Schwarz-guided precision: kept pairs with bound below thr32 go to the FP32
+  // kernels; within each class the FP64 pairs come first
+  const double thr32 = h->opt.fp32_pair_thresh >= 0.0 ? h->opt.fp32_pair_thresh
+                       : (h->opt.precision == DFJK_MIXED ? 1e-6 : 0.0);
+  h->fp32_thresh = thr32;
 
   // kept list, columns, column -> (mu, nu) map (host bookkeeping)
   h->kept_h.clear();
@@ -414,11 +447,19 @@ void make_resident(dfjk_ctx *h, cudaStream_t st) {
   h->pair_col_h.assign(npair, -1);
   std::vector<int> cmu, cnu;
   long long col = 0;
+  h->kept32_begin.assign(6, 0);
+  h->npair_fp32 = 0;
   for (int c = 0; c < 6; ++c) {
     h->kept_cls_begin[c] = (int)h->kept_h.size();
     const int na = ncart(cls[c][0]), nb = ncart(cls[c][1]);
-    for (int i = h->cls_begin[c]; i < h->cls_begin[c + 1]; ++i) {
-      if (!keep[i]) continue;
+    std::vector<int> order;
+    for (int i = h->cls_begin[c]; i < h->cls_begin[c + 1]; ++i)
+      if (keep[i] && !(qh[i] * scal < thr32)) order.push_back(i);
+    h->kept32_begin[c] = h->kept_cls_begin[c] + (int)order.size();
+    for (int i = h->cls_begin[c]; i < h->cls_begin[c + 1]; ++i)
+      if (keep[i] && qh[i] * scal < thr32) order.push_back(i);
+    h->npair_fp32 += h->kept_cls_begin[c] + (int)order.size() - h->kept32_begin[c];
+    for (int i : order) {
       h->kept_h.push_back(i);
       h->pair_col_h[i] = col;
       const int sa = h->pa_h[i], sb = h->pb_h[i];
@@ -492,10 +533,15 @@ void make_resident(dfjk_ctx *h, cudaStream_t st) {
     for (int c = 0; c < 6; ++c) {
       const int lo = std::max(r0, h->kept_cls_begin[c]), hi = std::min(r1, h->kept_cls_begin[c + 1]);
       if (hi <= lo) continue;
+      const int mid = std::min(std::max(lo, h->kept32_begin[c]), hi);  // [lo, mid) FP64, [mid, hi) FP32
       for (int lc = 0; lc < 3; ++lc) {
-        Eri3cArgs a{h->kept.p + lo, hi - lo, h->pair_rec_off.p, h->pair_npp.p, h->pair_col.p, h->rec.p,
+        Eri3cArgs a{h->kept.p + lo, mid - lo, h->pair_rec_off.p, h->pair_npp.p, h->pair_col.p, h->rec.p,
                     h->aux_cls[lc].p, h->aux_cls_n[lc], T.p, c0, np};
         launch_eri3c(cls[c][0], cls[c][1], lc, a, aux_args(h), tab, st);
+        Eri3cArgs a32 = a;
+        a32.pairs = h->kept.p + mid;
+        a32.npairs = hi - mid;
+        launch_eri3c32(cls[c][0], cls[c][1], lc, a32, aux_args(h), tab32, st);
       }
     }
     delete ph2;
@@ -734,6 +780,7 @@ void dfjk_default_options(dfjk_options *opt) {
   opt->hbm_budget_bytes = 0;
   opt->timeout_iters = 1LL << 26;
   opt->energies_on_host = 1;
+  opt->fp32_pair_thresh = -1.0;
 }
 
 const char *dfjk_status_string(int code) {
@@ -822,6 +869,13 @@ int dfjk_query(dfjk_handle h, int32_t *nao, int32_t *naux, int32_t *npair_kept, 
   if (npair_kept) *npair_kept = h->npair_kept;
   if (bytes) *bytes = h->B.bytes() + h->Bsl.bytes() + h->V.bytes() +
                       h->L.bytes() + h->Linv.bytes() + h->rec.bytes();
+  return DFJK_OK;
+}
+
+int dfjk_query_precision(dfjk_handle h, int32_t *npair_fp32, double *fp32_thresh) {
+  if (!h) return fail(Error{DFJK_ERR_ARG, "null handle"});
+  if (npair_fp32) *npair_fp32 = h->npair_fp32;
+  if (fp32_thresh) *fp32_thresh = h->fp32_thresh;
   return DFJK_OK;
 }
 
@@ -1148,13 +1202,19 @@ extern "C" int dfjk_get_three_center(dfjk_handle h, double *Tout, void *stream) 
     DFJK_CUDA_CHECK(cudaMemsetAsync(T.p, 0, T.bytes(), st));
     DFJK_CUDA_CHECK(cudaMemsetAsync(Tout, 0, sizeof(double) * (size_t)h->naux * h->nao * h->nao, st));
     static const int cls[6][2] = {{0, 0}, {1, 0}, {1, 1}, {2, 0}, {2, 1}, {2, 2}};
-    for (int c = 0; c < 6; ++c) {
+    const float *tab32 = boys_table_device_f32();
+    for (int c = 0; c < 6; ++c) {  // the same FP64 / FP32 split as the setup
       const int lo = h->kept_cls_begin[c], hi = h->kept_cls_begin[c + 1];
       if (hi <= lo) continue;
+      const int mid = std::min(std::max(lo, h->kept32_begin[c]), hi);
       for (int lc = 0; lc < 3; ++lc) {
-        Eri3cArgs a{h->kept.p + lo, hi - lo, h->pair_rec_off.p, h->pair_npp.p, h->pair_col.p, h->rec.p,
+        Eri3cArgs a{h->kept.p + lo, mid - lo, h->pair_rec_off.p, h->pair_npp.p, h->pair_col.p, h->rec.p,
                     h->aux_cls[lc].p, h->aux_cls_n[lc], T.p, 0, np};
         launch_eri3c(cls[c][0], cls[c][1], lc, a, aux_args(h), tab, st);
+        Eri3cArgs a32 = a;
+        a32.pairs = h->kept.p + mid;
+        a32.npairs = hi - mid;
+        launch_eri3c32(cls[c][0], cls[c][1], lc, a32, aux_args(h), tab32, st);
       }
     }
     const long long n = h->ncol * h->naux;

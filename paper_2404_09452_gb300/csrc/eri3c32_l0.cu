@@ -1,0 +1,13 @@
+// FP32 3-centre kernel instantiations for aux shells with l = 0 (small shell
+// pairs; one translation unit per aux class so they compile in parallel).
+#include "md.cuh"
+
+namespace dfjk {
+
+void launch_eri3c32_l0(int la, int lb, const Eri3cArgs &a, const AuxArgs &x, const float *tab,
+                       cudaStream_t st) {
+  dim3 grid(a.npairs, ceil_div(a.naux_shells, 128));
+  DISPATCH_LALB(la, lb, (eri3c32_kernel<A_, B_, 0><<<grid, 128, 0, st>>>(a, x, tab)));
+}
+
+}  // namespace dfjk

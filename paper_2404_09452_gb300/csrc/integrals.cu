@@ -62,6 +62,18 @@ void launch_eri3c(int la, int lb, int lc, const Eri3cArgs &a, const AuxArgs &x, 
   DFJK_LAUNCHED();
 }
 
+void launch_eri3c32(int la, int lb, int lc, const Eri3cArgs &a, const AuxArgs &x, const float *tab,
+                    cudaStream_t st) {
+  if (a.npairs == 0 || a.naux_shells == 0) return;
+  switch (lc) {
+    case 0: launch_eri3c32_l0(la, lb, a, x, tab, st); break;
+    case 1: launch_eri3c32_l1(la, lb, a, x, tab, st); break;
+    case 2: launch_eri3c32_l2(la, lb, a, x, tab, st); break;
+    default: throw Error{DFJK_ERR_UNSUPPORTED, "aux class"};
+  }
+  DFJK_LAUNCHED();
+}
+
 void launch_metric(int lp, int lq, const MetricArgs &a, const AuxArgs &x, const double *tab,
                    cudaStream_t st) {
   if (a.npair == 0) return;

@@ -72,6 +72,12 @@ void launch_eri3c_l2(int la, int lb, const Eri3cArgs &a, const AuxArgs &x, const
                      cudaStream_t st);
 void launch_eri3c(int la, int lb, int lc, const Eri3cArgs &a, const AuxArgs &x, const double *tab,
                   cudaStream_t st);
+// FP32 integrals of small shell pairs (same arguments, FP32 Boys table).
+void launch_eri3c32_l0(int la, int lb, const Eri3cArgs &a, const AuxArgs &x, const float *tab, cudaStream_t st);
+void launch_eri3c32_l1(int la, int lb, const Eri3cArgs &a, const AuxArgs &x, const float *tab, cudaStream_t st);
+void launch_eri3c32_l2(int la, int lb, const Eri3cArgs &a, const AuxArgs &x, const float *tab, cudaStream_t st);
+void launch_eri3c32(int la, int lb, int lc, const Eri3cArgs &a, const AuxArgs &x, const float *tab,
+                    cudaStream_t st);
 void launch_metric(int lp, int lq, const MetricArgs &a, const AuxArgs &x, const double *tab,
                    cudaStream_t st);
 void launch_overlap(int la, int lb, const OverlapArgs &a, const OrbArgs &o, cudaStream_t st);

@@ -28,19 +28,18 @@ __host__ __device__ constexpr int nterms(int LA, int LB) {
 }
 
 
-// R^0_{tuv} for t+u+v <= L.
-template <int L>
-__device__ __forceinline__ void hermite_R(const double *F, double a, double X, double Y, double Z,
-                                          double *R) {
-  double pw[L + 1];
-  pw[0] = 1.0;
+// R^0_{tuv} for t+u+v <= L (Real = double, or float for the FP32 pairs).
+template <int L, typename Real = double>
+__device__ __forceinline__ void hermite_R(const Real *F, Real a, Real X, Real Y, Real Z, Real *R) {
+  Real pw[L + 1];
+  pw[0] = Real(1);
 #pragma unroll
-  for (int n = 1; n <= L; ++n) pw[n] = pw[n - 1] * (-2.0 * a);
-  double cur[ntuv(L)];
+  for (int n = 1; n <= L; ++n) pw[n] = pw[n - 1] * (Real(-2) * a);
+  Real cur[ntuv(L)];
   cur[0] = pw[L] * F[L];
 #pragma unroll
   for (int n = L - 1; n >= 0; --n) {
-    double nxt[ntuv(L)];
+    Real nxt[ntuv(L)];
     nxt[0] = pw[n] * F[n];
 #pragma unroll
     for (int N = 1; N <= L - n; ++N)
@@ -49,16 +48,16 @@ __device__ __forceinline__ void hermite_R(const double *F, double a, double X, d
 #pragma unroll
         for (int u = N - t; u >= 0; --u) {
           const int v = N - t - u;
-          double r;
+          Real r;
           if (t > 0) {
             r = X * cur[tuv_idx(t - 1, u, v)];
-            if (t > 1) r = fma((double)(t - 1), cur[tuv_idx(t - 2, u, v)], r);
+            if (t > 1) r = fma(Real(t - 1), cur[tuv_idx(t - 2, u, v)], r);
           } else if (u > 0) {
             r = Y * cur[tuv_idx(t, u - 1, v)];
-            if (u > 1) r = fma((double)(u - 1), cur[tuv_idx(t, u - 2, v)], r);
+            if (u > 1) r = fma(Real(u - 1), cur[tuv_idx(t, u - 2, v)], r);
           } else {
             r = Z * cur[tuv_idx(t, u, v - 1)];
-            if (v > 1) r = fma((double)(v - 1), cur[tuv_idx(t, u, v - 2)], r);
+            if (v > 1) r = fma(Real(v - 1), cur[tuv_idx(t, u, v - 2)], r);
           }
           nxt[tuv_idx(t, u, v)] = r;
         }
@@ -388,6 +387,121 @@ __global__ void __launch_bounds__(128) eri3c_kernel(Eri3cArgs args, AuxArgs aux,
       for (int cc = 0; cc < NCC; ++cc)
         args.T[(col0 + ca * NCB + cb) * args.ldT + P0 + cc] =
             acc[(ca * NCB + cb) * NCC + cc] *
+            (comp_factor(LA, ca) * comp_factor(LB, cb) * comp_factor(LC, cc));
+}
+
+// FP32 variant for shell pairs whose Schwarz bound Q_ab max_P sqrt((P|P)) is
+// below the FP32 threshold (the mixed-precision use of Schwarz estimates the
+// paper names as future work in "Limitations and Future Development"): every
+// integral of such a pair is below the bound, so FP32 rounding (relative
+// ~1e-7 of the bound) stays far below the FP64 error of the large pairs after
+// whitening.  Same loops as eri3c_kernel on the FP32 pipe (62x the FP64 rate
+// here); the pair-to-aux-centre vector is formed in FP64 before rounding, so
+// nearby centres keep their relative accuracy.
+template <int LA, int LB, int LC>
+__global__ void __launch_bounds__(128) eri3c32_kernel(Eri3cArgs args, AuxArgs aux,
+                                                      const float *__restrict__ boys_tab) {
+  constexpr int NT = nterms(LA, LB);
+  constexpr int REC = REC_HDR + NT;
+  constexpr int NCA = ncart(LA), NCB = ncart(LB), NCC = ncart(LC);
+  constexpr int LAB = LA + LB, L = LA + LB + LC;
+  __shared__ double sP[3];
+  __shared__ float srec[REC];
+  const int pair = args.pairs[blockIdx.x];
+  const int as = blockIdx.y * blockDim.x + threadIdx.x;
+  const bool active = as < args.naux_shells;
+  const int sc = active ? args.aux_shells[as] : 0;
+  const double Cx = aux.center[3 * sc], Cy = aux.center[3 * sc + 1], Cz = aux.center[3 * sc + 2];
+  const int pc0 = aux.prim_off[sc], nc = active ? aux.nprim[sc] : 0;
+  float acc[NCA * NCB * NCC];
+#pragma unroll
+  for (int i = 0; i < NCA * NCB * NCC; ++i) acc[i] = 0.0f;
+  const double *rec0 = args.rec + args.rec_off[pair];
+  const int npp = args.npp[pair];
+  for (int ipp = 0; ipp < npp; ++ipp) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < REC; i += blockDim.x) {
+      const double v = rec0[(long long)ipp * REC + i];
+      srec[i] = (float)v;
+      if (i >= 1 && i <= 3) sP[i - 1] = v;
+    }
+    __syncthreads();
+    const float X = (float)(sP[0] - Cx), Y = (float)(sP[1] - Cy), Z = (float)(sP[2] - Cz);
+    for (int kc = 0; kc < nc; ++kc) {
+      const float g = (float)aux.exps[pc0 + kc];
+      const float g1 = (float)aux.g1[pc0 + kc];
+      const float p = srec[0];
+      const float s = rsqrtf(p + g);
+      const float al = p * g * (s * s);
+      float F[L + 1];
+      boys_eval<L>(al * (X * X + Y * Y + Z * Z), boys_tab, F);
+      float R[ntuv(L)];
+      hermite_R<L, float>(F, al, X, Y, Z, R);
+      const float pt = srec[4] * (float)aux.cdiv[pc0 + kc] * s;
+#pragma unroll
+      for (int cc = 0; cc < NCC; ++cc) {
+        const int cx = cart_x(LC, cc), cy = cart_y(LC, cc), cz = cart_z(LC, cc);
+        float W[ntuv(LAB)];
+        float scale = 1.0f;
+        if (LC == 0) {
+#pragma unroll
+          for (int i = 0; i < ntuv(LAB); ++i) W[i] = R[i];
+        } else {
+          const int two = (cx == 2) ? 0 : (cy == 2) ? 1 : (cz == 2) ? 2 : -1;
+#pragma unroll
+          for (int N = 0; N <= LAB; ++N)
+#pragma unroll
+            for (int t = N; t >= 0; --t)
+#pragma unroll
+              for (int u = N - t; u >= 0; --u) {
+                const int v = N - t - u;
+                if (two == 0)
+                  W[tuv_idx(t, u, v)] = fmaf(g1, R[tuv_idx(t + 2, u, v)], R[tuv_idx(t, u, v)]);
+                else if (two == 1)
+                  W[tuv_idx(t, u, v)] = fmaf(g1, R[tuv_idx(t, u + 2, v)], R[tuv_idx(t, u, v)]);
+                else if (two == 2)
+                  W[tuv_idx(t, u, v)] = fmaf(g1, R[tuv_idx(t, u, v + 2)], R[tuv_idx(t, u, v)]);
+                else
+                  W[tuv_idx(t, u, v)] = R[tuv_idx(t + cx, u + cy, v + cz)];
+              }
+          if (two >= 0)
+            scale = g1;
+          else if (LC == 1)
+            scale = -g1;
+          else
+            scale = g1 * g1;
+        }
+        const float ps = pt * scale;
+        int k = 0;
+#pragma unroll
+        for (int ca = 0; ca < NCA; ++ca)
+#pragma unroll
+          for (int cb = 0; cb < NCB; ++cb) {
+            const int ax = cart_x(LA, ca), ay = cart_y(LA, ca), az = cart_z(LA, ca);
+            const int bx = cart_x(LB, cb), by = cart_y(LB, cb), bz = cart_z(LB, cb);
+            float sum = 0.0f;
+#pragma unroll
+            for (int t = 0; t <= ax + bx; ++t)
+#pragma unroll
+              for (int u = 0; u <= ay + by; ++u)
+#pragma unroll
+                for (int v = 0; v <= az + bz; ++v) sum = fmaf(srec[REC_HDR + k++], W[tuv_idx(t, u, v)], sum);
+            acc[(ca * NCB + cb) * NCC + cc] = fmaf(ps, sum, acc[(ca * NCB + cb) * NCC + cc]);
+          }
+      }
+    }
+  }
+  if (!active) return;
+  const long long col0 = args.pair_col[pair] - args.col_begin;
+  const int P0 = aux.func_off[sc];
+#pragma unroll
+  for (int ca = 0; ca < NCA; ++ca)
+#pragma unroll
+    for (int cb = 0; cb < NCB; ++cb)
+#pragma unroll
+      for (int cc = 0; cc < NCC; ++cc)
+        args.T[(col0 + ca * NCB + cb) * args.ldT + P0 + cc] =
+            (double)acc[(ca * NCB + cb) * NCC + cc] *
             (comp_factor(LA, ca) * comp_factor(LB, cb) * comp_factor(LC, cc));
 }
 

@@ -35,6 +35,7 @@ EXPORTS = [
     "dfjk_default_options",
     "dfjk_setup",
     "dfjk_query",
+    "dfjk_query_precision",
     "dfjk_build",
     "dfjk_build_uks",
     "dfjk_build_batch",
@@ -89,6 +90,7 @@ class Options(ctypes.Structure):
         ("hbm_budget_bytes", ctypes.c_size_t),
         ("timeout_iters", ctypes.c_int64),
         ("energies_on_host", ctypes.c_int32),
+        ("fp32_pair_thresh", ctypes.c_double),
     ]
 
 
@@ -186,7 +188,7 @@ class _BasisHolder:
 
 def default_options(precision: int = DFJK_FP64, schwarz_thresh: float = 1e-12,
                     hbm_budget_bytes: int = 0, energies_on_host: bool = True,
-                    timeout_iters: int = 0) -> Options:
+                    timeout_iters: int = 0, fp32_pair_thresh: float = -1.0) -> Options:
     o = Options()
     load_library().dfjk_default_options(ctypes.byref(o))
     o.precision = precision
@@ -195,6 +197,7 @@ def default_options(precision: int = DFJK_FP64, schwarz_thresh: float = 1e-12,
     o.energies_on_host = 1 if energies_on_host else 0
     if timeout_iters > 0:
         o.timeout_iters = timeout_iters
+    o.fp32_pair_thresh = fp32_pair_thresh
     return o
 
 
@@ -202,14 +205,16 @@ class Handle:
     """A molecule set up on the device (steps a0-a5); B stays resident."""
 
     def __init__(self, mol, precision: int = DFJK_FP64, schwarz_thresh: float = 1e-12,
-                 hbm_budget_bytes: int = 0, stream=None, timeout_iters: int = 0):
+                 hbm_budget_bytes: int = 0, stream=None, timeout_iters: int = 0,
+                 fp32_pair_thresh: float = -1.0):
         lib = load_library()
         _torch()
         self.mol = mol
         self._orb = _BasisHolder(mol.orb)
         self._aux = _BasisHolder(mol.aux)
         xyz = np.ascontiguousarray(mol.coords, dtype=np.float64)
-        opt = default_options(precision, schwarz_thresh, hbm_budget_bytes, timeout_iters=timeout_iters)
+        opt = default_options(precision, schwarz_thresh, hbm_budget_bytes, timeout_iters=timeout_iters,
+                              fp32_pair_thresh=fp32_pair_thresh)
         h = ctypes.c_void_p()
         _check(
             lib.dfjk_setup(
@@ -226,6 +231,9 @@ class Handle:
                               ctypes.byref(nbytes)))
         self.nao, self.naux, self.npair_kept, self.device_bytes = (
             nao.value, naux.value, npk.value, nbytes.value)
+        n32, thr = ctypes.c_int32(), ctypes.c_double()
+        _check(lib.dfjk_query_precision(h, ctypes.byref(n32), ctypes.byref(thr)))
+        self.npair_fp32, self.fp32_pair_thresh = n32.value, thr.value
 
     def close(self):
         if getattr(self, "h", None):
