@@ -238,11 +238,28 @@ struct dfjk_ctx {
   int ksplit = 1;
   SlicedOp Csl, Xsl;  // DFJK_MIXED build operands
   DBuf<double> uks_D, uks_J;  // spin-unrestricted build: D_a + D_b and J[D_b]
+  cudaStream_t side = nullptr;  // setup: Cholesky + inverse beside the integrals
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   ~dfjk_ctx() {
     oz_free(Bsl);
     oz_free(Bchunk);
     oz_free(Csl);
     oz_free(Xsl);
+    if (side) {
+      cudaStreamSynchronize(side);
+      cudaStreamDestroy(side);
+    }
+    if (ev_fork) cudaEventDestroy(ev_fork);
+    if (ev_join) cudaEventDestroy(ev_join);
+  }
+};
+
+// Waits for a stream on scope exit (error paths included), so that buffers the
+// stream still uses are not returned to the cache under it.
+struct StreamDrain {
+  cudaStream_t s;
+  ~StreamDrain() {
+    if (s) cudaStreamSynchronize(s);
   }
 };
 
@@ -480,37 +497,49 @@ void make_resident(dfjk_ctx *h, cudaStream_t st) {
   h->colmu.upload(cmu, st);
   h->colnu.upload(cnu, st);
 
-  // a3: Cholesky and inverse of the metric
-  PhaseScope *ph1 = new PhaseScope(1, st);
-  h->L.alloc((size_t)np * np);
-  DFJK_CUDA_CHECK(cudaMemcpyAsync(h->L.p, h->V.p, h->V.bytes(), cudaMemcpyDeviceToDevice, st));
-  h->Dinv.alloc((size_t)(np / 64) * 4096);
-  cholesky_f64(h->L.p, np, np, h->Dinv.p, h->status.p, nullptr, st);
-  zero_upper_kernel<<<(unsigned)(((long long)np * np + 255) / 256), 256, 0, st>>>(h->L.p, np, np);
-  DFJK_LAUNCHED();
-  h->Linv.alloc((size_t)np * np);
-  {
-    DBuf<double> work;
-    work.alloc((size_t)np * np);
-    tri_inverse_f64(h->L.p, np, np, h->Dinv.p, h->Linv.p, work.p, st);
-    delete ph1;
-    DFJK_CUDA_CHECK(cudaStreamSynchronize(st));
-  }
-
-  // a4 + a5: 3-centre integrals in column slabs, whitened into B
+  // a3: Cholesky and inverse of the metric, on a side stream: they do not
+  // depend on the 3-centre integrals, so they run while the first slab's
+  // integrals are computed; the first whitening waits for them
   const bool mixed = h->opt.precision == DFJK_MIXED;
-  h->ldb = np;
-  h->B.alloc((size_t)h->nao * h->nao * np);
-  DFJK_CUDA_CHECK(cudaMemsetAsync(h->B.p, 0, h->B.bytes(), st));
+  if (!h->side) {
+    DFJK_CUDA_CHECK(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
+    DFJK_CUDA_CHECK(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+    DFJK_CUDA_CHECK(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+  }
+  const cudaStream_t s2 = h->side;
+  DFJK_CUDA_CHECK(cudaEventRecord(h->ev_fork, st));
+  DFJK_CUDA_CHECK(cudaStreamWaitEvent(s2, h->ev_fork, 0));
   struct OzLocal {  // slice buffers that live only during setup
     SlicedOp op;
     ~OzLocal() { oz_free(op); }
   } linv8_, t8_;
   SlicedOp &Linv8 = linv8_.op, &T8 = t8_.op;
-  if (mixed) {  // L^-1 as the B operand of the whitening (rows P, K Q), 8 slices
-    oz_alloc(Linv8, 1, 8, np, np, OZ_BN);
-    oz_slice_f64(h->Linv.p, 0, np, 1, Linv8, st);
+  DBuf<double> inv_work;
+  StreamDrain drain_side{s2};  // destroyed before the buffers above
+  {
+    PhaseScope ph1(1, s2);
+    h->L.alloc((size_t)np * np);
+    DFJK_CUDA_CHECK(cudaMemcpyAsync(h->L.p, h->V.p, h->V.bytes(), cudaMemcpyDeviceToDevice, s2));
+    h->Dinv.alloc((size_t)(np / CHOL_NB) * CHOL_NB * CHOL_NB);
+    cholesky_f64(h->L.p, np, np, h->Dinv.p, h->status.p, nullptr, s2);
+    zero_upper_kernel<<<(unsigned)(((long long)np * np + 255) / 256), 256, 0, s2>>>(h->L.p, np, np);
+    DFJK_LAUNCHED();
+    h->Linv.alloc((size_t)np * np);
+    inv_work.alloc((size_t)np * np);
+    tri_inverse_f64(h->L.p, np, np, h->Dinv.p, h->Linv.p, inv_work.p, s2);
   }
+  if (mixed) {  // L^-1 as the B operand of the whitening (rows P, K Q), 8 slices
+    PhaseScope ph3(3, s2);
+    oz_alloc(Linv8, 1, 8, np, np, OZ_BN);
+    oz_slice_f64(h->Linv.p, 0, np, 1, Linv8, s2);
+  }
+  DFJK_CUDA_CHECK(cudaEventRecord(h->ev_join, s2));
+  bool joined = false;
+
+  // a4 + a5: 3-centre integrals in column slabs, whitened into B
+  h->ldb = np;
+  h->B.alloc((size_t)h->nao * h->nao * np);
+  DFJK_CUDA_CHECK(cudaMemsetAsync(h->B.p, 0, h->B.bytes(), st));
   const long long slab_budget = 4LL << 30;  // bytes of one T slab
   long long slab_cols = std::max<long long>(36, slab_budget / ((long long)np * 8));
   slab_cols = std::min<long long>(slab_cols, std::max<long long>(h->ncol, 1));
@@ -545,6 +574,10 @@ void make_resident(dfjk_ctx *h, cudaStream_t st) {
       }
     }
     delete ph2;
+    if (!joined) {  // L^-1 (and its slices) ready
+      DFJK_CUDA_CHECK(cudaStreamWaitEvent(st, h->ev_join, 0));
+      joined = true;
+    }
     PhaseScope ph3(3, st);
     if (!mixed) {
       GemmArgs g;  // B[(mu,nu)][P] = sum_Q T[col][Q] Linv[P][Q]
@@ -570,6 +603,7 @@ void make_resident(dfjk_ctx *h, cudaStream_t st) {
     }
     r0 = r1;
   }
+  if (!joined) DFJK_CUDA_CHECK(cudaStreamWaitEvent(st, h->ev_join, 0));
   if (mixed) {
     DFJK_CUDA_CHECK(cudaStreamSynchronize(st));
     oz_free(T8);

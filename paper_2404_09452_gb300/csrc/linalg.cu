@@ -150,24 +150,27 @@ void gemm_f64(const GemmArgs &g, cudaStream_t st) {
 
 // ---- Cholesky -------------------------------------------------------------------
 
-// Factors the 64x64 lower block at A in place (upper part zeroed) and writes
+// Factors the NB x NB lower block at A in place (upper part zeroed) and writes
 // its inverse (lower triangular) to Dinv.  A non-positive or non-finite pivot
-// sets STATUS_NOT_PD and continues with pivot 1 so no NaN spreads.
-// Dynamic shared memory: two 64 x 65 FP64 arrays.
+// sets STATUS_NOT_PD and continues with pivot 1 so no NaN spreads.  The block
+// runs on one SM, whose FP64 rate is 1/152 of the GPU's, so NB is kept small
+// (32): the panel and trailing updates, spread over all SMs, do the bulk.
+// Dynamic shared memory: two NB x (NB + 1) FP64 arrays.
+template <int NB>
 __global__ void __launch_bounds__(256) potrf_diag_kernel(double *A, int lda, double *Dinv,
                                                          int *status) {
   extern __shared__ double psm[];
-  double(*a)[65] = reinterpret_cast<double(*)[65]>(psm);
-  double(*x)[65] = reinterpret_cast<double(*)[65]>(psm + 64 * 65);
-  __shared__ double rdiag[64];
+  double(*a)[NB + 1] = reinterpret_cast<double(*)[NB + 1]>(psm);
+  double(*x)[NB + 1] = reinterpret_cast<double(*)[NB + 1]>(psm + NB * (NB + 1));
+  __shared__ double rdiag[NB];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  for (int e = tid; e < 64 * 64; e += 256) {
-    const int i = e >> 6, j = e & 63;
+  for (int e = tid; e < NB * NB; e += 256) {
+    const int i = e / NB, j = e % NB;
     a[i][j] = (j <= i) ? A[(long long)i * lda + j] : 0.0;
     x[i][j] = 0.0;
   }
   __syncthreads();
-  for (int j = 0; j < 64; ++j) {
+  for (int j = 0; j < NB; ++j) {
     if (tid == 0) {
       double d = a[j][j];
       if (!(d > 0.0) || !isfinite(d)) {
@@ -180,9 +183,9 @@ __global__ void __launch_bounds__(256) potrf_diag_kernel(double *A, int lda, dou
     }
     __syncthreads();
     const double r = rdiag[j];
-    if (tid > j && tid < 64) a[tid][j] *= r;
+    if (tid > j && tid < NB) a[tid][j] *= r;
     __syncthreads();
-    for (int i = j + 1 + ty; i < 64; i += 16) {
+    for (int i = j + 1 + ty; i < NB; i += 16) {
       const double lij = a[i][j];
       for (int c = j + 1 + tx; c <= i; c += 16) a[i][c] = fma(-lij, a[c][j], a[i][c]);
     }
@@ -191,7 +194,7 @@ __global__ void __launch_bounds__(256) potrf_diag_kernel(double *A, int lda, dou
   // X = L^-1 row by row: x[k][c] = -(sum_{c<=j<k} l[k][j] x[j][c]) / l[k][k];
   // four lanes share each dot product.
   const int c = tid >> 2, part = tid & 3;
-  for (int k = 0; k < 64; ++k) {
+  for (int k = 0; k < NB; ++k) {
     double sum = 0.0;
     if (c < k)
       for (int j = c + part; j < k; j += 4) sum = fma(a[k][j], x[j][c], sum);
@@ -200,8 +203,8 @@ __global__ void __launch_bounds__(256) potrf_diag_kernel(double *A, int lda, dou
     if (part == 0 && c <= k) x[k][c] = (c == k) ? rdiag[k] : -sum * rdiag[k];
     __syncthreads();
   }
-  for (int e = tid; e < 64 * 64; e += 256) {
-    const int i = e >> 6, j = e & 63;
+  for (int e = tid; e < NB * NB; e += 256) {
+    const int i = e / NB, j = e % NB;
     A[(long long)i * lda + j] = a[i][j];
     Dinv[e] = x[i][j];
   }
@@ -210,34 +213,35 @@ __global__ void __launch_bounds__(256) potrf_diag_kernel(double *A, int lda, dou
 void cholesky_f64(double *A, int n, int lda, double *Dinv, int *status, double *work,
                   cudaStream_t st) {
   (void)work;
+  constexpr int NB = CHOL_NB;
+  constexpr int SMEM = 2 * NB * (NB + 1) * (int)sizeof(double);
   static bool attr = false;
   if (!attr) {
-    DFJK_CUDA_CHECK(cudaFuncSetAttribute(potrf_diag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         2 * 64 * 65 * (int)sizeof(double)));
+    DFJK_CUDA_CHECK(cudaFuncSetAttribute(potrf_diag_kernel<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM));
     attr = true;
   }
-  const int nb = n / 64;
+  const int nb = n / NB;
   for (int k = 0; k < nb; ++k) {
-    double *Akk = A + (long long)k * 64 * lda + k * 64;
-    potrf_diag_kernel<<<1, 256, 2 * 64 * 65 * sizeof(double), st>>>(Akk, lda, Dinv + (long long)k * 4096, status);
+    double *Akk = A + (long long)k * NB * lda + k * NB;
+    potrf_diag_kernel<NB><<<1, 256, SMEM, st>>>(Akk, lda, Dinv + (long long)k * NB * NB, status);
     DFJK_LAUNCHED();
-    const int rows = n - (k + 1) * 64;
+    const int rows = n - (k + 1) * NB;
     if (rows <= 0) continue;
-    double *panel = A + (long long)(k + 1) * 64 * lda + k * 64;
-    GemmArgs p;  // L_ik = A_ik Dinv_k^T, in place (one 64-wide tile owns its rows)
-    p.M = rows; p.N = 64; p.K = 64;
+    double *panel = A + (long long)(k + 1) * NB * lda + k * NB;
+    GemmArgs p;  // L_ik = A_ik Dinv_k^T, in place (one tile owns complete rows)
+    p.M = rows; p.N = NB; p.K = NB;
     p.A = panel; p.sAm = lda; p.sAk = 1;
-    p.B = Dinv + (long long)k * 4096; p.sBn = 64; p.sBk = 1;
+    p.B = Dinv + (long long)k * NB * NB; p.sBn = NB; p.sBk = 1;
     p.C = panel; p.sCm = lda; p.sCn = 1;
-    // tile 64 = the whole panel width: the update is in place, so one CTA must
-    // own complete rows (with 32-wide tiles two CTAs would share them)
-    p.tile = 64;
+    // tile = the whole panel width: the update is in place, so one CTA must
+    // own complete rows (with narrower tiles two CTAs would share them)
+    p.tile = NB;
     gemm_f64(p, st);
     GemmArgs t;  // A_ij -= L_ik L_jk^T on the trailing lower triangle
-    t.M = rows; t.N = rows; t.K = 64;
+    t.M = rows; t.N = rows; t.K = NB;
     t.A = panel; t.sAm = lda; t.sAk = 1;
     t.B = panel; t.sBn = lda; t.sBk = 1;
-    t.C = A + (long long)(k + 1) * 64 * (lda + 1); t.sCm = lda; t.sCn = 1;
+    t.C = A + (long long)(k + 1) * NB * (lda + 1); t.sCm = lda; t.sCn = 1;
     t.alpha = -1.0; t.beta = 1.0; t.lower_only = 1;
     t.tile = 32;
     gemm_f64(t, st);
@@ -245,10 +249,11 @@ void cholesky_f64(double *A, int n, int lda, double *Dinv, int *status, double *
 }
 
 __global__ void place_diag_blocks(double *Linv, int ld, const double *Dinv, int nb) {
+  constexpr int NB = CHOL_NB;
   const int b = blockIdx.x;
-  for (int e = threadIdx.x; e < 4096; e += blockDim.x) {
-    const int i = e >> 6, j = e & 63;
-    Linv[((long long)b * 64 + i) * ld + b * 64 + j] = Dinv[(long long)b * 4096 + e];
+  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+    const int i = e / NB, j = e % NB;
+    Linv[((long long)b * NB + i) * ld + b * NB + j] = Dinv[(long long)b * NB * NB + e];
   }
 }
 
@@ -260,10 +265,10 @@ __global__ void place_diag_blocks(double *Linv, int ld, const double *Dinv, int 
 void tri_inverse_f64(const double *L, int n, int ld, const double *Dinv, double *Linv,
                      double *work, cudaStream_t st) {
   DFJK_CUDA_CHECK(cudaMemsetAsync(Linv, 0, sizeof(double) * (size_t)n * ld, st));
-  const int nb = n / 64;
+  const int nb = n / CHOL_NB;
   place_diag_blocks<<<nb, 256, 0, st>>>(Linv, ld, Dinv, nb);
   DFJK_LAUNCHED();
-  for (int s = 64; s < n; s *= 2) {
+  for (int s = CHOL_NB; s < n; s *= 2) {
     const int pairs = (n + 2 * s - 1) / (2 * s);
     const long long dstep = 2LL * s * (ld + 1);
     GemmArgs a;  // work_j = L21_j Linv11_j   (rows clipped to the valid part of block 2)

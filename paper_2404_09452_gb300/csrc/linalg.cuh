@@ -36,12 +36,16 @@ struct GemmArgs {
 
 void gemm_f64(const GemmArgs &g, cudaStream_t st);
 
-// Cholesky of the lower triangle of A (n x n, n a multiple of 64, lda), in
-// place; Dinv receives the inverse of every 64x64 diagonal block of L.
-// A non-positive pivot sets STATUS_NOT_PD in *status.
+// Diagonal block size of the blocked Cholesky and of the inverse's first level.
+constexpr int CHOL_NB = 32;
+
+// Cholesky of the lower triangle of A (n x n, n a multiple of CHOL_NB, lda),
+// in place; Dinv (n / CHOL_NB blocks of CHOL_NB^2 doubles) receives the
+// inverse of every diagonal block of L.  A non-positive pivot sets
+// STATUS_NOT_PD in *status.
 void cholesky_f64(double *A, int n, int lda, double *Dinv, int *status, double *work,
                   cudaStream_t st);
-// Linv = L^-1 (lower triangular), n a multiple of 64; uses Dinv from
+// Linv = L^-1 (lower triangular), n a multiple of CHOL_NB; uses Dinv from
 // cholesky_f64 and `work` (n x n doubles).
 void tri_inverse_f64(const double *L, int n, int ld, const double *Dinv, double *Linv,
                      double *work, cudaStream_t st);
