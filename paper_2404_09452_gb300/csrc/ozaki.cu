@@ -173,62 +173,70 @@ __global__ void __launch_bounds__(256) oz_slice_tr_kernel(const double *__restri
     }
 }
 
-// Row-contiguous sources, exponents and slices in one kernel: a block owns 32
+// Row-contiguous sources, exponents and slices in one kernel: a block owns 8
 // rows of one batch and walks all of K twice, first for the per-(row, K-block)
-// maxima, then for the slices (the second read is served from L2).
+// maxima, then for the slices.  8 rows x K doubles per block (58 KB for
+// K = 900) keeps the second read in L2 with every SM's blocks in flight; lanes
+// run along the rows (64 contiguous bytes per K index, four K indices per
+// warp load).
 template <int S>
 __global__ void __launch_bounds__(256) oz_slice_tr_fused_kernel(const double *__restrict__ src, long long sz,
                                                                 long long sk, int rows, int K, int rows_pad,
                                                                 int kpitch, int nkb, int *__restrict__ expo,
                                                                 __nv_bfloat16 *__restrict__ out) {
-  constexpr int LD = 72, MAXKB = 8;
-  __shared__ __nv_bfloat16 tile[S * 32 * LD];
-  __shared__ unsigned long long rmax[32][MAXKB];
-  __shared__ int rexp[32][MAXKB];
-  const int z = blockIdx.y, r0 = blockIdx.x * 32;
-  const int rr = threadIdx.x & 31, kq = threadIdx.x >> 5;  // 8 groups along K
+  constexpr int R = 8, KG = 256 / R, LD = 72, MAXKB = 8;
+  __shared__ __nv_bfloat16 tile[S * R * LD];
+  __shared__ unsigned long long rmax[R][MAXKB];
+  __shared__ int rexp[R][MAXKB];
+  const int z = blockIdx.y, r0 = blockIdx.x * R;
+  const int rr = threadIdx.x % R, kq = threadIdx.x / R;  // KG groups along K
   const int r = r0 + rr;
   const bool live = r < rows;
   const double *row = src + z * sz + r;
-  for (int i = threadIdx.x; i < 32 * MAXKB; i += 256) rmax[i / MAXKB][i % MAXKB] = 0ull;
+  if (threadIdx.x < R * MAXKB) rmax[threadIdx.x / MAXKB][threadIdx.x % MAXKB] = 0ull;
   __syncthreads();
   // pass 1: |x| maxima per K block (non-negative doubles order like their bits)
   for (int kb = 0; kb < nkb; ++kb) {
     double mx = 0.0;
-    if (live)
-      for (int k = kb * OZ_KB + kq; k < min(K, (kb + 1) * OZ_KB); k += 8) mx = fmax(mx, fabs(row[(long long)k * sk]));
-    atomicMax(&rmax[rr][kb], (unsigned long long)__double_as_longlong(mx));
+    if (live) {
+      const int k1 = min(K, (kb + 1) * OZ_KB);
+#pragma unroll 4
+      for (int k = kb * OZ_KB + kq; k < k1; k += KG) mx = fmax(mx, fabs(row[(long long)k * sk]));
+    }
+    // lanes with the same row in a warp: 4 of them (32 lanes / 8 rows)
+    mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, 8));
+    mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, 16));
+    if ((threadIdx.x & 31) < R) atomicMax(&rmax[rr][kb], (unsigned long long)__double_as_longlong(mx));
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < 32 * nkb; i += 256) {
-    const int q = i / nkb, kb = i % nkb;
+  if (threadIdx.x < R * nkb) {
+    const int q = threadIdx.x / nkb, kb = threadIdx.x % nkb;
     const int e = oz_expo_of(__longlong_as_double((long long)rmax[q][kb]));
     rexp[q][kb] = e;
     expo[((long long)z * rows_pad + r0 + q) * nkb + kb] = e;
   }
   __syncthreads();
   // pass 2: slices, 64 K at a time, staged [s][row][k] and written along K
-  const int c8 = threadIdx.x & 7, rw = threadIdx.x >> 3;  // 32 rows x 8 chunks of 8 K
   for (int k0 = 0; k0 < kpitch; k0 += 64) {
     const int e = rexp[rr][k0 / OZ_KB];
-    for (int kk = kq; kk < 64; kk += 8) {
+    for (int kk = kq; kk < 64; kk += KG) {
       const int k = k0 + kk;
       const double x = (live && k < K) ? row[(long long)k * sk] : 0.0;
       long long n = oz_fixed<S>(x, e);
 #pragma unroll
       for (int s = S - 1; s >= 1; --s) {
         const int d = (int)(((n + 32) & 63) - 32);
-        tile[(s * 32 + rr) * LD + kk] = __float2bfloat16_rn((float)d);
+        tile[(s * R + rr) * LD + kk] = __float2bfloat16_rn((float)d);
         n = (n - d) >> 6;
       }
       tile[rr * LD + kk] = __float2bfloat16_rn((float)n);
     }
     __syncthreads();
-    const int kc = k0 + c8 * 8;
-    if (kc < kpitch) {
-#pragma unroll
-      for (int s = 0; s < S; ++s) {
-        const uint4 v = *reinterpret_cast<const uint4 *>(&tile[(s * 32 + rw) * LD + c8 * 8]);
+    for (int i = threadIdx.x; i < S * R * 8; i += 256) {  // (slice, row, chunk of 8 K)
+      const int s = i / (R * 8), rw = (i / 8) % R, c8 = i % 8;
+      const int kc = k0 + c8 * 8;
+      if (kc < kpitch) {
+        const uint4 v = *reinterpret_cast<const uint4 *>(&tile[(s * R + rw) * LD + c8 * 8]);
         *reinterpret_cast<uint4 *>(out + (((long long)z * S + s) * rows_pad + r0 + rw) * kpitch + kc) = v;
       }
     }
@@ -266,9 +274,9 @@ void oz_free(SlicedOp &op) {
 
 void oz_slice_f64(const double *src, long long sz, long long sr, long long sk, SlicedOp &op,
                   cudaStream_t st) {
-  if (sr == 1 && op.rows_pad % 32 == 0 && op.nkb <= 8) {
+  if (sr == 1 && op.rows_pad % 8 == 0 && op.nkb <= 8) {
     // row-contiguous source: exponents and slices fused, one read from HBM
-    dim3 grid((unsigned)(op.rows_pad / 32), (unsigned)op.batch);
+    dim3 grid((unsigned)(op.rows_pad / 8), (unsigned)op.batch);
     switch (op.S) {
       case 6:
         oz_slice_tr_fused_kernel<6><<<grid, 256, 0, st>>>(src, sz, sk, op.rows, op.K, op.rows_pad, op.kpitch,
