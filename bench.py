@@ -269,6 +269,7 @@ def run_ours(args):
     h0 = dfjk.Handle(m, precision=prec, fp32_pair_thresh=args.fp32_pair_thresh)
     fp32_pairs = {"thresh": h0.fp32_pair_thresh, "fp32_shell_pairs": h0.npair_fp32,
                   "kept_shell_pairs": h0.npair_kept}
+    nslab, lean = h0.nslab, h0.lean
     S = h0.overlap().cpu().numpy()
     Cnp = I.orthonormalize(I.c_occ_raw(m.nao, nocc, 3000 + rank), S)
     mask = h0.pair_mask().cpu().numpy()
@@ -392,7 +393,7 @@ def run_ours(args):
         tc = {"whiten": ("tc:whiten", 36), "X=BC": ("tc:X=BC", 21), "K": ("tc:K", 21)}
         dom = max(tc, key=lambda k: per_step.get(tc[k][0], 0.0))
         key, prods = tc[dom]
-        nl = 2 if dom == "whiten" else 1  # launches per step (whitening: one per T slab)
+        nl = nslab if dom == "whiten" else 1  # launches per step (whitening: one per T slab)
         dom_ms = per_step[key] / nl
         achieved = flops[dom] / nl / (dom_ms / 1e3) / 1e12
         roof = {"kernel": "oz_gemm_kernel (" + dom + ")", "bound": "tensor", "achieved": achieved,
@@ -413,6 +414,7 @@ def run_ours(args):
         "config": {"workload": args.workload, "note": WORKLOADS[args.workload]["note"],
                    "natom": m.natom, "nao": m.nao, "naux": m.naux, "nocc": nocc,
                    "kept_ao_pairs": ncol, "precision": args.precision, "fp32_integrals": fp32_pairs,
+                   "t_slabs": nslab, "memory_lean": lean,
                    "l2": "working set > L2 (B alone is GBs), no flush needed",
                    "parallelism": f"replicas x{world}"},
         "tflops": step_flops / (total_ms / args.steps / 1e3) / 1e12,

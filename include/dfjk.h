@@ -124,6 +124,12 @@ int dfjk_query(dfjk_handle h, int32_t *nao, int32_t *naux, int32_t *npair_kept,
  * (0 when every pair is FP64).  Either output pointer may be NULL.           */
 int dfjk_query_precision(dfjk_handle h, int32_t *npair_fp32, double *fp32_thresh);
 
+/* Layout of a handle's setup: the number of 3-centre column slabs (T is
+ * built and whitened slab by slab, at most 4 GB each) and whether the mixed
+ * path runs memory-lean (B kept as the packed mu >= nu triangle, sliced per
+ * build).  Either output pointer may be NULL.                                 */
+int dfjk_query_setup(dfjk_handle h, int32_t *nslab, int32_t *lean);
+
 /* Steps a6-a9 for nset occupied-orbital sets.
  *   C_occ : device, nset x nao x nocc, row-major FP64 (caller-owned).
  *   J, K  : device, nset x nao x nao FP64, written in full (symmetric).

@@ -218,11 +218,13 @@ struct dfjk_ctx {
   std::vector<int> kept32_begin;  // per class: first kept index evaluated in FP32
   int npair_fp32 = 0;
   double fp32_thresh = 0.0;
+  int nslab = 0;  // T column slabs of the last setup (one whitening launch each)
   DBuf<int> colmu, colnu;
   // metric
   DBuf<double> V, L, Linv, Dinv;
   DBuf<int> status;
   DBuf<int> tctr;  // tile counter of the tensor-core GEMM launches (stream-ordered)
+  DBuf<int> kseq;  // split counters of the ordered split-K GEMM
   // whitened tensor: FP64 B[(mu nao + nu) ldb + P]; in DFJK_MIXED also its
   // 6-slice form for the tensor-core X = B C (batch mu, rows P, K nu)
   DBuf<double> B;
@@ -230,7 +232,7 @@ struct dfjk_ctx {
   SlicedOp Bsl;
   // memory-lean mixed mode: B's slices are not kept; each build slices B in
   // chunks of mu (Bchunk) just before X = B C of that chunk
-  bool lean = false;
+  bool lean = false;    // mixed path: B packed (mu >= nu rows), sliced per build
   SlicedOp Bchunk;
   // build workspace
   int ws_nocc = -1;
@@ -249,8 +251,8 @@ struct dfjk_ctx {
       cudaStreamSynchronize(side);
       cudaStreamDestroy(side);
     }
-    if (ev_fork) cudaEventDestroy(ev_fork);
-    if (ev_join) cudaEventDestroy(ev_join);
+    for (cudaEvent_t e : {ev_fork, ev_join})
+      if (e) cudaEventDestroy(e);
   }
 };
 
@@ -296,7 +298,9 @@ void enumerate_pairs(dfjk_ctx *h) {
 }
 
 // Bytes of B's resident 6-slice form; above the limit (DFJK_BSLICE_MAX_BYTES,
-// default 64 GiB) the mixed path runs memory-lean and slices B per build.
+// default 64 GiB) the mixed path runs memory-lean: B is kept as the packed
+// mu >= nu triangle in FP64 (half the bytes of the full square) and sliced per
+// build in chunks of mu.
 size_t bslice_bytes(int nao, int np) {
   const size_t rows = ((size_t)np + 127) / 128 * 128, kp = ((size_t)nao + 31) / 32 * 32;
   return (size_t)nao * 6 * rows * kp * 2;
@@ -311,10 +315,11 @@ bool choose_lean(int nao, int np) {
 
 size_t resident_estimate(const dfjk_ctx *h) {
   const size_t np2 = (size_t)h->naux_pad * h->naux_pad;
-  const size_t nao2p = (size_t)h->nao * h->nao * h->naux_pad;
-  size_t b = nao2p * sizeof(double);
-  if (h->opt.precision == DFJK_MIXED && !choose_lean(h->nao, h->naux_pad))
-    b += bslice_bytes(h->nao, h->naux_pad);
+  const bool mixed = h->opt.precision == DFJK_MIXED;
+  const bool lean = mixed && choose_lean(h->nao, h->naux_pad);
+  const size_t rows = lean ? (size_t)h->nao * (h->nao + 1) / 2 : (size_t)h->nao * h->nao;
+  size_t b = rows * h->naux_pad * sizeof(double);
+  if (mixed && !lean) b += bslice_bytes(h->nao, h->naux_pad);
   return b + 3 * np2 * sizeof(double);
 }
 
@@ -502,7 +507,11 @@ void make_resident(dfjk_ctx *h, cudaStream_t st) {
   // integrals are computed; the first whitening waits for them
   const bool mixed = h->opt.precision == DFJK_MIXED;
   if (!h->side) {
-    DFJK_CUDA_CHECK(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
+    // highest priority: the Cholesky chain is a sequence of small launches on
+    // the critical path, its blocks go first whenever the integrals free an SM
+    int lo = 0, hi = 0;
+    DFJK_CUDA_CHECK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    DFJK_CUDA_CHECK(cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, hi));
     DFJK_CUDA_CHECK(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
     DFJK_CUDA_CHECK(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
   }
@@ -538,7 +547,8 @@ void make_resident(dfjk_ctx *h, cudaStream_t st) {
 
   // a4 + a5: 3-centre integrals in column slabs, whitened into B
   h->ldb = np;
-  h->B.alloc((size_t)h->nao * h->nao * np);
+  h->lean = mixed && choose_lean(h->nao, np);
+  h->B.alloc((h->lean ? (size_t)h->nao * (h->nao + 1) / 2 : (size_t)h->nao * h->nao) * np);
   DFJK_CUDA_CHECK(cudaMemsetAsync(h->B.p, 0, h->B.bytes(), st));
   const long long slab_budget = 4LL << 30;  // bytes of one T slab
   long long slab_cols = std::max<long long>(36, slab_budget / ((long long)np * 8));
@@ -547,7 +557,9 @@ void make_resident(dfjk_ctx *h, cudaStream_t st) {
   T.alloc((size_t)slab_cols * np);
   DFJK_CUDA_CHECK(cudaMemsetAsync(T.p, 0, T.bytes(), st));
   int r0 = 0;
+  h->nslab = 0;
   while (r0 < h->npair_kept) {
+    ++h->nslab;
     const long long c0 = h->pair_col_h[h->kept_h[r0]];
     int r1 = r0;
     while (r1 < h->npair_kept) {
@@ -574,11 +586,17 @@ void make_resident(dfjk_ctx *h, cudaStream_t st) {
       }
     }
     delete ph2;
+    PhaseScope ph3(3, st);
+    const int ncols = (int)(c1 - c0);
+    if (mixed) {  // slices of T need only T: taken before waiting for L^-1
+      if (!T8.data || T8.rows_pad < ncols) oz_alloc(T8, 1, 8, (int)slab_cols, np, OZ_BM);
+      T8.rows = ncols;
+      oz_slice_f64(T.p, 0, np, 1, T8, st);
+    }
     if (!joined) {  // L^-1 (and its slices) ready
       DFJK_CUDA_CHECK(cudaStreamWaitEvent(st, h->ev_join, 0));
       joined = true;
     }
-    PhaseScope ph3(3, st);
     if (!mixed) {
       GemmArgs g;  // B[(mu,nu)][P] = sum_Q T[col][Q] Linv[P][Q]
       g.M = (int)(c1 - c0); g.N = np; g.K = np;
@@ -589,13 +607,10 @@ void make_resident(dfjk_ctx *h, cudaStream_t st) {
       g.nao = h->nao; g.ldo = h->ldb; g.out = h->B.p;
       gemm_f64(g, st);
     } else {  // the same product on the tensor cores, 8 slices per operand
-      const int ncols = (int)(c1 - c0);
-      if (!T8.data || T8.rows_pad < ncols) oz_alloc(T8, 1, 8, (int)slab_cols, np, OZ_BM);
-      T8.rows = ncols;
-      oz_slice_f64(T.p, 0, np, 1, T8, st);
       OzGemmArgs g;
       g.M = ncols; g.N = np; g.K = np; g.k_upto_n = 1;
       g.mode = 1; g.out = h->B.p; g.colmu = h->colmu.p + c0; g.colnu = h->colnu.p + c0;
+      g.packed = h->lean ? 1 : 0;
       g.nao = h->nao; g.ldb = h->ldb; g.status = h->status.p; g.timeout = h->opt.timeout_iters;
       g.tile_ctr = h->tctr.p;
       g.phase = 8;
@@ -610,7 +625,6 @@ void make_resident(dfjk_ctx *h, cudaStream_t st) {
     oz_free(Linv8);
     // B as the A operand of X = B C: batch mu, rows P, K nu (6 slices),
     // resident unless that would exceed the slice-memory limit
-    h->lean = choose_lean(h->nao, np);
     if (!h->lean) {
       PhaseScope ph(3, st);
       oz_alloc(h->Bsl, h->nao, 6, np, h->nao, OZ_BM);
@@ -718,7 +732,7 @@ void build_one(dfjk_ctx *h, int nocc, const double *C, double *J, double *Kout, 
     {  // rho from X (5x smaller than B), then J over B
       PhaseScope ph(6, st);
       rho_from_x_f64(h->X.p, C, nao, np, nocc, h->rho.p, h->rho_work.p, st);
-      j_gemv_f64(h->B.p, h->ldb, nao, np, h->rho.p, J, st);
+      j_gemv_f64(h->B.p, h->ldb, nao, np, h->rho.p, J, h->lean ? 1 : 0, st);
     }
     GemmArgs k;  // K[mu][nu] = sum_(P,i) X[mu][(P,i)] X[nu][(P,i)]
     k.M = nao; k.N = nao; k.K = (int)kt;
@@ -752,7 +766,7 @@ void build_one(dfjk_ctx *h, int nocc, const double *C, double *J, double *Kout, 
           const int n = std::min(mc, nao - mu0);
           SlicedOp ck = h->Bchunk;  // view of the first n batches (the last chunk is short)
           ck.batch = n;
-          oz_slice_f64(h->B.p + (size_t)mu0 * nao * h->ldb, (long long)nao * h->ldb, 1, h->ldb, ck, st);
+          oz_slice_f64_packed(h->B.p, h->ldb, mu0, ck, st);
           OzGemmArgs xc = x;
           xc.nz = n;
           xc.out = h->X.p + (size_t)mu0 * np * nocc;
@@ -763,7 +777,7 @@ void build_one(dfjk_ctx *h, int nocc, const double *C, double *J, double *Kout, 
     {  // rho from X (5x smaller than B), then J over B
       PhaseScope ph(6, st);
       rho_from_x_f64(h->X.p, C, nao, np, nocc, h->rho.p, h->rho_work.p, st);
-      j_gemv_f64(h->B.p, h->ldb, nao, np, h->rho.p, J, st);
+      j_gemv_f64(h->B.p, h->ldb, nao, np, h->rho.p, J, h->lean ? 1 : 0, st);
     }
     PhaseScope ph(5, st);
     if (!h->Xsl.data || h->Xsl.K != kt) oz_alloc(h->Xsl, 1, 6, nao, (int)kt, OZ_BM);
@@ -775,7 +789,9 @@ void build_one(dfjk_ctx *h, int nocc, const double *C, double *J, double *Kout, 
         if (j * OZ_BN <= i * OZ_BM + OZ_BM - 1) ++tiles;
     // K ranges of about 64 MB of operand slices (all rows): the tiles in
     // flight (work is handed out split-major, a few ranges at a time) then
-    // reuse their operands from L2; partial K buffers capped at 4 GiB
+    // reuse their operands from L2.  The persistent kernel adds the splits of
+    // a tile into K in split order (deterministic, no partial buffers); the
+    // one-tile-per-CTA kernel writes partials (capped at 4 GiB) and reduces.
     static const size_t range_bytes = [] {
       const char *e = std::getenv("DFJK_K_RANGE_MB");
       const long v = e ? std::atol(e) : 0;
@@ -784,20 +800,29 @@ void build_one(dfjk_ctx *h, int nocc, const double *C, double *J, double *Kout, 
     const int nkb = h->Xsl.nkb;
     const size_t chunk_kb_bytes = (size_t)h->Xsl.rows_pad * 6 * 2 * OZ_KB;
     int per = (int)std::max<size_t>(1, range_bytes / chunk_kb_bytes);
-    const int max_split = (int)std::max<size_t>(1, ((size_t)4 << 30) / ((size_t)nao * nao * 8));
+    const bool ordered = !oz_simple_mode();
+    const int max_split = ordered ? nkb : (int)std::max<size_t>(1, ((size_t)4 << 30) / ((size_t)nao * nao * 8));
     int nsplit = std::min(ceil_div(nkb, per), max_split);
     nsplit = std::max(nsplit, std::min(nkb, (2 * 152 + tiles - 1) / tiles));
     per = ceil_div(nkb, nsplit);
     nsplit = ceil_div(nkb, per);
-    if (h->Kpart.n < (size_t)nsplit * nao * nao) h->Kpart.alloc((size_t)nsplit * nao * nao);
     OzGemmArgs k;
     k.M = nao; k.N = nao; k.K = (int)kt; k.nz = nsplit; k.kb_per_split = per; k.lower_only = 1;
-    k.mode = 0; k.out = h->Kpart.p; k.ldo = nao; k.out_bs = (long long)nao * nao;
     k.status = h->status.p; k.timeout = h->opt.timeout_iters;
     k.tile_ctr = h->tctr.p;
     k.phase = 10;
-    oz_gemm(h->Xsl, h->Xsl, k, st);
-    reduce_sym_f64(h->Kpart.p, nsplit, nao, Kout, st);
+    if (ordered) {
+      const size_t nseq = oz_tile_seq_count(nao, nao);
+      if (h->kseq.n < nseq) h->kseq.alloc(nseq);
+      k.mode = 2; k.out = Kout; k.ldo = nao; k.tile_seq = h->kseq.p;
+      oz_gemm(h->Xsl, h->Xsl, k, st);
+      mirror_lower_f64(Kout, nao, st);
+    } else {
+      if (h->Kpart.n < (size_t)nsplit * nao * nao) h->Kpart.alloc((size_t)nsplit * nao * nao);
+      k.mode = 0; k.out = h->Kpart.p; k.ldo = nao; k.out_bs = (long long)nao * nao;
+      oz_gemm(h->Xsl, h->Xsl, k, st);
+      reduce_sym_f64(h->Kpart.p, nsplit, nao, Kout, st);
+    }
   }
   PhaseScope ph(7, st);
   energies_f64(h->D.p, J, Kout, nao, e, h->en_work.p, st);
@@ -910,6 +935,13 @@ int dfjk_query_precision(dfjk_handle h, int32_t *npair_fp32, double *fp32_thresh
   if (!h) return fail(Error{DFJK_ERR_ARG, "null handle"});
   if (npair_fp32) *npair_fp32 = h->npair_fp32;
   if (fp32_thresh) *fp32_thresh = h->fp32_thresh;
+  return DFJK_OK;
+}
+
+int dfjk_query_setup(dfjk_handle h, int32_t *nslab, int32_t *lean) {
+  if (!h) return fail(Error{DFJK_ERR_ARG, "null handle"});
+  if (nslab) *nslab = h->nslab;
+  if (lean) *lean = h->lean ? 1 : 0;
   return DFJK_OK;
 }
 
@@ -1180,7 +1212,7 @@ int dfjk_get_B(dfjk_handle h, double *Bout, void *stream) {
     for (int i = 0; i < h->naux; ++i) ident[i] = i;
     DBuf<int> perm;
     perm.upload(ident, st);
-    gather_B_f64(h->B.p, h->ldb, h->nao, perm.p, h->naux, Bout, st);
+    gather_B_f64(h->B.p, h->ldb, h->nao, perm.p, h->naux, Bout, h->lean ? 1 : 0, st);
     DFJK_CUDA_CHECK(cudaStreamSynchronize(st));
     return DFJK_OK;
   } catch (const Error &e) {

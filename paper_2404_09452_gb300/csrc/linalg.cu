@@ -377,14 +377,14 @@ void rho_from_x_f64(const double *X, const double *C, int nao, int np, int nocc,
 __global__ void __launch_bounds__(256) j_gemv_kernel(const double *__restrict__ B, long long ldb,
                                                      int nao, int naux,
                                                      const double *__restrict__ rho,
-                                                     double *__restrict__ J) {
+                                                     double *__restrict__ J, int packed) {
   const long long r = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   const long long nrows = (long long)nao * (nao + 1) / 2;
   if (r >= nrows) return;
   int mu, nu;
   tri_row(r, mu, nu);
-  const double *row = B + ((long long)mu * nao + nu) * ldb;
+  const double *row = B + (packed ? r : (long long)mu * nao + nu) * ldb;
   double s = 0.0;
   for (int P = lane; P < naux; P += 32) s = fma(row[P], __ldg(rho + P), s);
 #pragma unroll
@@ -396,9 +396,9 @@ __global__ void __launch_bounds__(256) j_gemv_kernel(const double *__restrict__ 
 }
 
 void j_gemv_f64(const double *B, long long ldb, int nao, int naux, const double *rho, double *J,
-                cudaStream_t st) {
+                int packed, cudaStream_t st) {
   const long long nrows = (long long)nao * (nao + 1) / 2;
-  j_gemv_kernel<<<(unsigned)((nrows + 7) / 8), 256, 0, st>>>(B, ldb, nao, naux, rho, J);
+  j_gemv_kernel<<<(unsigned)((nrows + 7) / 8), 256, 0, st>>>(B, ldb, nao, naux, rho, J, packed);
   DFJK_LAUNCHED();
 }
 
@@ -419,6 +419,19 @@ __global__ void reduce_sym_kernel(const double *__restrict__ part, int nsplit, i
 void reduce_sym_f64(const double *part, int nsplit, int n, double *out, cudaStream_t st) {
   const long long n2 = (long long)n * n;
   reduce_sym_kernel<<<(unsigned)((n2 + 255) / 256), 256, 0, st>>>(part, nsplit, n, out);
+  DFJK_LAUNCHED();
+}
+
+__global__ void mirror_lower_kernel(double *__restrict__ K, int n) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)n * n) return;
+  const int mu = (int)(e / n), nu = (int)(e % n);
+  if (nu > mu) K[e] = K[(long long)nu * n + mu];
+}
+
+void mirror_lower_f64(double *K, int n, cudaStream_t st) {
+  const long long n2 = (long long)n * n;
+  mirror_lower_kernel<<<(unsigned)((n2 + 255) / 256), 256, 0, st>>>(K, n);
   DFJK_LAUNCHED();
 }
 
@@ -536,20 +549,26 @@ void gather2d_f64(const double *in, long long ldi, const int *perm_r, const int 
 }
 
 __global__ void gather_B_kernel(const double *Bint, long long ldb, int nao, const int *perm,
-                                int naux, double *out) {
+                                int naux, double *out, int packed) {
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long n2 = (long long)nao * nao;
   if (e >= n2 * naux) return;
   const int P = (int)(e / n2);
   const long long mn = e % n2;
-  out[e] = Bint[mn * ldb + perm[P]];
+  long long row = mn;
+  if (packed) {
+    const long long mu = mn / nao, nu = mn % nao;
+    const long long hi = mu > nu ? mu : nu, lo = mu > nu ? nu : mu;
+    row = hi * (hi + 1) / 2 + lo;
+  }
+  out[e] = Bint[row * ldb + perm[P]];
 }
 
 void gather_B_f64(const double *Bint, long long ldb, int nao, const int *perm, int naux,
-                  double *out, cudaStream_t st) {
+                  double *out, int packed, cudaStream_t st) {
   const long long n = (long long)nao * nao * naux;
   if (n == 0) return;
-  gather_B_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(Bint, ldb, nao, perm, naux, out);
+  gather_B_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(Bint, ldb, nao, perm, naux, out, packed);
   DFJK_LAUNCHED();
 }
 

@@ -59,11 +59,14 @@ void rho_gemv_f64(const double *B, long long ldb, int nao, int naux, const doubl
 // since X_P = B_P C and D = C C^T); per-mu partials in `part` (nao x np).
 void rho_from_x_f64(const double *X, const double *C, int nao, int np, int nocc, double *rho,
                     double *part, cudaStream_t st);
-// J[mu][nu] = J[nu][mu] = sum_P B[(mu nao + nu) ldb + P] rho[P].
+// J[mu][nu] = J[nu][mu] = sum_P B[row(mu, nu) ldb + P] rho[P] for mu >= nu, with
+// row = mu nao + nu (full storage) or mu (mu + 1) / 2 + nu (packed triangle).
 void j_gemv_f64(const double *B, long long ldb, int nao, int naux, const double *rho, double *J,
-                cudaStream_t st);
+                int packed, cudaStream_t st);
 // out[mu][nu] = out[nu][mu] = sum_s part[s][mu][nu] (mu >= nu).
 void reduce_sym_f64(const double *part, int nsplit, int n, double *out, cudaStream_t st);
+// K[mu][nu] = K[nu][mu] for nu > mu (the lower triangle is the result).
+void mirror_lower_f64(double *K, int n, cudaStream_t st);
 // e[0] = Tr(D J)/2, e[1] = Tr(D K)/2 (fixed-order two-level reduction).
 void energies_f64(const double *D, const double *J, const double *K, int n, double *e,
                   double *work, cudaStream_t st);
@@ -76,8 +79,9 @@ void fill_f64(double *p, long long n, double v, cudaStream_t st);
 // out[i][j] = in[perm_r[i] * ldi + perm_c[j]] for an n_r x n_c gather.
 void gather2d_f64(const double *in, long long ldi, const int *perm_r, const int *perm_c, int nr,
                   int nc, double *out, long long ldo, cudaStream_t st);
-// B user-order copy: out[P][mu][nu] = Bint[(mu nao + nu) ldb + perm[P]].
+// B user-order copy: out[P][mu][nu] = Bint[row(mu, nu) ldb + perm[P]] (row as
+// for j_gemv_f64; packed storage holds the mu >= nu triangle).
 void gather_B_f64(const double *Bint, long long ldb, int nao, const int *perm, int naux,
-                  double *out, cudaStream_t st);
+                  double *out, int packed, cudaStream_t st);
 
 }  // namespace dfjk

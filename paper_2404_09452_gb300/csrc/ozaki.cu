@@ -179,11 +179,11 @@ __global__ void __launch_bounds__(256) oz_slice_tr_kernel(const double *__restri
 // K = 900) keeps the second read in L2 with every SM's blocks in flight; lanes
 // run along the rows (64 contiguous bytes per K index, four K indices per
 // warp load).
-template <int S>
+template <int S, bool PACKED>
 __global__ void __launch_bounds__(256) oz_slice_tr_fused_kernel(const double *__restrict__ src, long long sz,
                                                                 long long sk, int rows, int K, int rows_pad,
                                                                 int kpitch, int nkb, int *__restrict__ expo,
-                                                                __nv_bfloat16 *__restrict__ out) {
+                                                                __nv_bfloat16 *__restrict__ out, int mu0) {
   constexpr int R = 8, KG = 256 / R, LD = 72, MAXKB = 8;
   __shared__ __nv_bfloat16 tile[S * R * LD];
   __shared__ unsigned long long rmax[R][MAXKB];
@@ -192,7 +192,16 @@ __global__ void __launch_bounds__(256) oz_slice_tr_fused_kernel(const double *__
   const int rr = threadIdx.x % R, kq = threadIdx.x / R;  // KG groups along K
   const int r = r0 + rr;
   const bool live = r < rows;
-  const double *row = src + z * sz + r;
+  // element (z, r, k): src[z sz + k sk + r], or for a packed mu >= nu triangle
+  // (mu = mu0 + z, nu = k) src[row(max, min) sk + r]
+  const long long mu = (long long)mu0 + z;
+  auto at = [&](int k) -> double {
+    if (PACKED) {
+      const long long hi = mu > k ? mu : k, lo = mu > k ? k : mu;
+      return src[(hi * (hi + 1) / 2 + lo) * sk + r];
+    }
+    return src[z * sz + (long long)k * sk + r];
+  };
   if (threadIdx.x < R * MAXKB) rmax[threadIdx.x / MAXKB][threadIdx.x % MAXKB] = 0ull;
   __syncthreads();
   // pass 1: |x| maxima per K block (non-negative doubles order like their bits)
@@ -201,7 +210,7 @@ __global__ void __launch_bounds__(256) oz_slice_tr_fused_kernel(const double *__
     if (live) {
       const int k1 = min(K, (kb + 1) * OZ_KB);
 #pragma unroll 4
-      for (int k = kb * OZ_KB + kq; k < k1; k += KG) mx = fmax(mx, fabs(row[(long long)k * sk]));
+      for (int k = kb * OZ_KB + kq; k < k1; k += KG) mx = fmax(mx, fabs(at(k)));
     }
     // lanes with the same row in a warp: 4 of them (32 lanes / 8 rows)
     mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, 8));
@@ -221,7 +230,7 @@ __global__ void __launch_bounds__(256) oz_slice_tr_fused_kernel(const double *__
     const int e = rexp[rr][k0 / OZ_KB];
     for (int kk = kq; kk < 64; kk += KG) {
       const int k = k0 + kk;
-      const double x = (live && k < K) ? row[(long long)k * sk] : 0.0;
+      const double x = (live && k < K) ? at(k) : 0.0;
       long long n = oz_fixed<S>(x, e);
 #pragma unroll
       for (int s = S - 1; s >= 1; --s) {
@@ -272,6 +281,15 @@ void oz_free(SlicedOp &op) {
   op.expo = nullptr;
 }
 
+void oz_slice_f64_packed(const double *B, long long ldb, int mu0, SlicedOp &op, cudaStream_t st) {
+  if (op.S != 6 || op.rows_pad % 8 != 0 || op.nkb > 8)
+    throw Error{DFJK_ERR_UNSUPPORTED, "packed slicing: 6 slices, K <= 8192"};
+  dim3 grid((unsigned)(op.rows_pad / 8), (unsigned)op.batch);
+  oz_slice_tr_fused_kernel<6, true><<<grid, 256, 0, st>>>(B, 0, ldb, op.rows, op.K, op.rows_pad, op.kpitch,
+                                                          op.nkb, op.expo, op.data, mu0);
+  DFJK_LAUNCHED();
+}
+
 void oz_slice_f64(const double *src, long long sz, long long sr, long long sk, SlicedOp &op,
                   cudaStream_t st) {
   if (sr == 1 && op.rows_pad % 8 == 0 && op.nkb <= 8) {
@@ -279,12 +297,12 @@ void oz_slice_f64(const double *src, long long sz, long long sr, long long sk, S
     dim3 grid((unsigned)(op.rows_pad / 8), (unsigned)op.batch);
     switch (op.S) {
       case 6:
-        oz_slice_tr_fused_kernel<6><<<grid, 256, 0, st>>>(src, sz, sk, op.rows, op.K, op.rows_pad, op.kpitch,
-                                                          op.nkb, op.expo, op.data);
+        oz_slice_tr_fused_kernel<6, false><<<grid, 256, 0, st>>>(src, sz, sk, op.rows, op.K, op.rows_pad,
+                                                                 op.kpitch, op.nkb, op.expo, op.data, 0);
         break;
       case 8:
-        oz_slice_tr_fused_kernel<8><<<grid, 256, 0, st>>>(src, sz, sk, op.rows, op.K, op.rows_pad, op.kpitch,
-                                                          op.nkb, op.expo, op.data);
+        oz_slice_tr_fused_kernel<8, false><<<grid, 256, 0, st>>>(src, sz, sk, op.rows, op.K, op.rows_pad,
+                                                                 op.kpitch, op.nkb, op.expo, op.data, 0);
         break;
       default:
         throw Error{DFJK_ERR_UNSUPPORTED, "slice count must be 6 or 8"};
@@ -372,6 +390,12 @@ struct OzKernelArgs {
 
 // 2^e for normal exponents; 0 below the normal range (row maxima that small
 // do not occur for these operands except as exact zeros).
+// Row of (mu, nu) in a packed symmetric triangle: max (max + 1) / 2 + min.
+__device__ __forceinline__ long long tri_row_of(int mu, int nu) {
+  const long long hi = mu > nu ? mu : nu, lo = mu > nu ? nu : mu;
+  return hi * (hi + 1) / 2 + lo;
+}
+
 __device__ __forceinline__ double pow2(int e) {
   return e < -1022 ? 0.0 : __longlong_as_double((long long)(e + 1023) << 52);
 }
@@ -553,13 +577,14 @@ __global__ void __launch_bounds__(128, 1)
     } else {
       const int mu = g.colmu[m], nu = g.colnu[m];
       if (mu >= 0) {
-        double *o1 = g.out + ((long long)mu * g.nao + nu) * g.ldb;
+        const bool two = mu != nu && !g.packed;
+        double *o1 = g.out + (g.packed ? tri_row_of(mu, nu) : (long long)mu * g.nao + nu) * g.ldb;
         double *o2 = g.out + ((long long)nu * g.nao + mu) * g.ldb;
 #pragma unroll
         for (int j = 0; j < OZ_BN; ++j)
           if (n0 + j < g.N) {
             o1[n0 + j] = acc[j];
-            if (mu != nu) o2[n0 + j] = acc[j];
+            if (two) o2[n0 + j] = acc[j];
           }
       }
     }
@@ -825,7 +850,36 @@ __global__ void __launch_bounds__(OZ_WS_THREADS, 1)
         tc::mbar_arrive(acce);
       }
       if (!ok) break;
-      if (m < g.M) {
+      if (g.mode == 2) {
+        // split z of this tile adds onto splits 0..z-1 in order: wait until the
+        // same drain warp of split z-1 has stored (bounded), then read-add-store
+        int *seq = g.tile_seq + ((long long)(m0 / OZ_BM) * T.ntn + n0 / OZ_BN) * NEPI + (warp - 2);
+        bool ready = true;
+        if (lane == 0 && z > 0) {
+          long long i = 0;
+          while (*(volatile int *)seq != z) {
+            if (++i > lim) {
+              ready = false;
+              break;
+            }
+            __nanosleep(64);
+          }
+        }
+        if (!__shfl_sync(0xffffffffu, ready ? 1 : 0, 0)) {
+          ok = false;
+          break;
+        }
+        __threadfence();
+        if (m < g.M) {
+          double *o = g.out + (long long)m * g.ldo + nh;
+#pragma unroll
+          for (int j = 0; j < NH; ++j)
+            if (nh + j < g.N) o[j] = (z == 0) ? acc[j] : __ldcg(o + j) + acc[j];  // L2, not a stale L1 line
+        }
+        __threadfence();
+        __syncwarp();
+        if (lane == 0) *(volatile int *)seq = z + 1;
+      } else if (m < g.M) {
         const bool full = nh + NH <= g.N;
         if (g.mode == 0) {
           double *o = g.out + (long long)z * g.out_bs + (long long)m * g.ldo + nh;
@@ -840,21 +894,22 @@ __global__ void __launch_bounds__(OZ_WS_THREADS, 1)
         } else {
           const int mu = g.colmu[m], nu = g.colnu[m];
           if (mu >= 0) {
-            double *o1 = g.out + ((long long)mu * g.nao + nu) * g.ldb + nh;
+            const bool two = mu != nu && !g.packed;
+            double *o1 = g.out + (g.packed ? tri_row_of(mu, nu) : (long long)mu * g.nao + nu) * g.ldb + nh;
             double *o2 = g.out + ((long long)nu * g.nao + mu) * g.ldb + nh;
             if (full && (((uintptr_t)o1 | (uintptr_t)o2) & 15) == 0) {
 #pragma unroll
               for (int j = 0; j < NH; j += 2) {
                 const double2 v = make_double2(acc[j], acc[j + 1]);
                 *reinterpret_cast<double2 *>(o1 + j) = v;
-                if (mu != nu) *reinterpret_cast<double2 *>(o2 + j) = v;
+                if (two) *reinterpret_cast<double2 *>(o2 + j) = v;
               }
             } else {
 #pragma unroll
               for (int j = 0; j < NH; ++j)
                 if (nh + j < g.N) {
                   o1[j] = acc[j];
-                  if (mu != nu) o2[j] = acc[j];
+                  if (two) o2[j] = acc[j];
                 }
             }
           }
@@ -937,6 +992,11 @@ static void launch_oz_ws(const SlicedOp &A, const SlicedOp &B, const OzGemmArgs 
   const int grid = (int)std::min<long long>(total, num_sms());
   if (!g.tile_ctr) throw Error{DFJK_ERR_ARG, "oz_gemm: tile counter"};
   DFJK_CUDA_CHECK(cudaMemsetAsync(g.tile_ctr, 0, sizeof(int), st));
+  if (g.mode == 2) {
+    if (!g.tile_seq || g.kb_per_split <= 0 || g.a_batched || g.b_batched)
+      throw Error{DFJK_ERR_ARG, "oz_gemm: ordered split-K arguments"};
+    DFJK_CUDA_CHECK(cudaMemsetAsync(g.tile_seq, 0, oz_tile_seq_count(g.M, g.N) * sizeof(int), st));
+  }
   oz_gemm_ws_kernel<S><<<grid, OZ_WS_THREADS, SMEM, st>>>(ma, mb, ka, T);
   DFJK_LAUNCHED();
 }
@@ -957,6 +1017,18 @@ static void launch_oz(const SlicedOp &A, const SlicedOp &B, const OzGemmArgs &g,
   DFJK_LAUNCHED();
 }
 
+bool oz_simple_mode() {
+  static const bool simple = [] {
+    const char *e = std::getenv("DFJK_OZ_SIMPLE");
+    return e && e[0] == '1';
+  }();
+  return simple;
+}
+
+size_t oz_tile_seq_count(int M, int N) {
+  return (size_t)((M + OZ_BM - 1) / OZ_BM) * ((N + OZ_BN - 1) / OZ_BN) * ((OZ_WS_THREADS - 64) / 32);
+}
+
 void oz_gemm(const SlicedOp &A, const SlicedOp &B, const OzGemmArgs &g, cudaStream_t st) {
   if (g.M <= 0 || g.N <= 0 || g.nz <= 0) return;
   if (A.S != B.S) throw Error{DFJK_ERR_ARG, "oz_gemm: slice counts differ"};
@@ -969,10 +1041,8 @@ void oz_gemm(const SlicedOp &A, const SlicedOp &B, const OzGemmArgs &g, cudaStre
   if (g.b_batched && g.nz > B.batch) throw Error{DFJK_ERR_ARG, "oz_gemm: B batch"};
   if (g.mode == 1 && (!g.colmu || !g.colnu)) throw Error{DFJK_ERR_ARG, "oz_gemm: scatter map"};
   if (g.nz > 65535 || (g.M + OZ_BM - 1) / OZ_BM > 2147483647) throw Error{DFJK_ERR_ARG, "oz_gemm: grid"};
-  static const bool simple = [] {
-    const char *e = std::getenv("DFJK_OZ_SIMPLE");
-    return e && e[0] == '1';
-  }();
+  const bool simple = oz_simple_mode();
+  if (simple && g.mode == 2) throw Error{DFJK_ERR_UNSUPPORTED, "oz_gemm: mode 2 needs the persistent kernel"};
   switch (A.S) {
     case 6: simple ? launch_oz<6>(A, B, g, st) : launch_oz_ws<6>(A, B, g, st); break;
     case 8: simple ? launch_oz<8>(A, B, g, st) : launch_oz_ws<8>(A, B, g, st); break;

@@ -49,7 +49,11 @@ struct OzGemmArgs {
   int kb_per_split = 0;  // >0: z selects K-blocks [z kb_per_split, (z+1) kb_per_split)
   int k_upto_n = 0;      // K limited to < end of the N tile (B lower triangular)
   int lower_only = 0;    // skip tiles strictly above the diagonal
-  int mode = 0;          // 0: out[z out_bs + m ldo + n] = C; 1: whitening scatter
+  int mode = 0;          // 0: out[z out_bs + m ldo + n] = C; 1: whitening scatter;
+                         // 2: split-K in order, out[m ldo + n] (+)= C of split z
+                         //    after splits 0..z-1 (persistent kernel only)
+  int *tile_seq = nullptr;  // mode 2: per (tile, drain warp) split counters
+  int packed = 0;        // mode 1: out holds the mu >= nu triangle, row mu (mu + 1) / 2 + nu
   double *out = nullptr;
   long long ldo = 0, out_bs = 0;
   const int *colmu = nullptr, *colnu = nullptr;  // mode 1: row m -> AO pair
@@ -62,6 +66,15 @@ struct OzGemmArgs {
                                // zeroes it on the stream, so launches that can
                                // run concurrently need distinct counters
 };
+
+// Slices of B stored as the packed mu >= nu triangle (row mu (mu + 1) / 2 + nu,
+// ldb doubles per row, P contiguous): batch z is mu = mu0 + z, rows P, K nu.
+void oz_slice_f64_packed(const double *B, long long ldb, int mu0, SlicedOp &op, cudaStream_t st);
+
+// True when DFJK_OZ_SIMPLE=1 selects the one-tile-per-CTA kernel (no mode 2).
+bool oz_simple_mode();
+// Counters mode 2 needs for a launch of M x N (ints).
+size_t oz_tile_seq_count(int M, int N);
 
 // out = A B^T with A (M x K) and B (N x K) in sliced form, both with S slices.
 void oz_gemm(const SlicedOp &A, const SlicedOp &B, const OzGemmArgs &g, cudaStream_t st);

@@ -36,6 +36,7 @@ EXPORTS = [
     "dfjk_setup",
     "dfjk_query",
     "dfjk_query_precision",
+    "dfjk_query_setup",
     "dfjk_build",
     "dfjk_build_uks",
     "dfjk_build_batch",
@@ -234,6 +235,9 @@ class Handle:
         n32, thr = ctypes.c_int32(), ctypes.c_double()
         _check(lib.dfjk_query_precision(h, ctypes.byref(n32), ctypes.byref(thr)))
         self.npair_fp32, self.fp32_pair_thresh = n32.value, thr.value
+        ns, lean = ctypes.c_int32(), ctypes.c_int32()
+        _check(lib.dfjk_query_setup(h, ctypes.byref(ns), ctypes.byref(lean)))
+        self.nslab, self.lean = ns.value, bool(lean.value)
 
     def close(self):
         if getattr(self, "h", None):

@@ -158,3 +158,29 @@ def test_config_120_atoms_mixed_vs_fp64_gpu():
     print(f"mol120 mixed vs fp64: dJ {dJ:.2e} dK {dK:.2e} dEJ {dEJ:.2e} dEK {dEK:.2e}")
     assert dJ <= JK_TOL and dK <= JK_TOL and dEJ <= E_TOL and dEK <= E_TOL
     hm.close()
+
+
+def test_ordered_split_k_matches_partial_reduction(tmp_path):
+    """The persistent kernel adds the K splits of a tile into K in split order;
+    the one-tile-per-CTA kernel (DFJK_OZ_SIMPLE=1) writes one partial per split
+    and reduces them in the same order: identical K."""
+    import os
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = (
+        "import sys, numpy as np, torch; sys.path.insert(0, %r);"
+        "from paper_2404_09452_gb300 import dfjk, inputs as I;"
+        "m = I.molecule(12, seed=1012); h = dfjk.Handle(m, precision=dfjk.DFJK_MIXED);"
+        "C = torch.from_numpy(dfjk.orthonormal_c_occ(h, I.c_occ_raw(m.nao, 36, 3000))).cuda();"
+        "J, K, EJ, EK = h.build(C); np.save(sys.argv[1], K[0].cpu().numpy())"
+    ) % root
+    outs = []
+    for simple in ("0", "1"):
+        out = str(tmp_path / f"k{simple}.npy")
+        env = dict(os.environ, DFJK_OZ_SIMPLE=simple, DFJK_K_RANGE_MB="1")
+        subprocess.run([sys.executable, "-c", code, out], check=True, env=env, timeout=300)
+        outs.append(np.load(out))
+    assert np.array_equal(outs[0], outs[1])
+    assert np.array_equal(outs[0], outs[0].T)
