@@ -48,6 +48,14 @@ __device__ __forceinline__ long long oz_fixed(double x, int e) {
   return u < 0 ? -n : n;
 }
 
+// Element offset of slice s of (z, r, k) in a SlicedOp's data (k % 8 == 0 for
+// the 16-byte stores below, which then stay inside one 1024-wide K block).
+__device__ __forceinline__ long long oz_off(int z, int s, int r, int k, int S, int rows_pad, int kpitch,
+                                            int nkb, int kblk) {
+  if (kblk) return ((((long long)z * S + s) * nkb + (k >> 10)) * rows_pad + r) * OZ_KB + (k & (OZ_KB - 1));
+  return (((long long)z * S + s) * rows_pad + r) * kpitch + k;
+}
+
 // Exponent of every (z, row, K-block); one warp per entry, lanes along K
 // (for K-contiguous sources).
 __global__ void oz_expo_warp_kernel(const double *__restrict__ src, long long sz, long long sr,
@@ -94,7 +102,7 @@ template <int S>
 __global__ void oz_slice_kernel(const double *__restrict__ src, long long sz, long long sr, long long sk,
                                 int batch, int rows, int K, int rows_pad, int kpitch, int nkb,
                                 const int *__restrict__ expo, __nv_bfloat16 *__restrict__ out,
-                                int row_fast) {
+                                int row_fast, int kblk) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const int nkc = kpitch / 8;
   if (t >= (long long)batch * rows_pad * nkc) return;
@@ -129,7 +137,7 @@ __global__ void oz_slice_kernel(const double *__restrict__ src, long long sz, lo
     __align__(16) __nv_bfloat16 v[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) v[j] = __float2bfloat16_rn((float)dig[j][s]);
-    *reinterpret_cast<uint4 *>(out + (((long long)z * S + s) * rows_pad + r) * kpitch + k0) =
+    *reinterpret_cast<uint4 *>(out + oz_off(z, s, r, k0, S, rows_pad, kpitch, nkb, kblk)) =
         *reinterpret_cast<const uint4 *>(v);
   }
 }
@@ -141,7 +149,7 @@ template <int S>
 __global__ void __launch_bounds__(256) oz_slice_tr_kernel(const double *__restrict__ src, long long sz,
                                                           long long sk, int rows, int K, int rows_pad,
                                                           int kpitch, int nkb, const int *__restrict__ expo,
-                                                          __nv_bfloat16 *__restrict__ out) {
+                                                          __nv_bfloat16 *__restrict__ out, int kblk) {
   extern __shared__ __nv_bfloat16 tile[];  // [S][64][64 + 8]
   constexpr int LD = 72;
   const int z = blockIdx.z, r0 = blockIdx.y * 64, k0 = blockIdx.x * 64;
@@ -168,7 +176,7 @@ __global__ void __launch_bounds__(256) oz_slice_tr_kernel(const double *__restri
       const int kc = k0 + c8 * 8;
       if (kc < kpitch) {
         const uint4 v = *reinterpret_cast<const uint4 *>(&tile[(s * 64 + rb) * LD + c8 * 8]);
-        *reinterpret_cast<uint4 *>(out + (((long long)z * S + s) * rows_pad + r0 + rb) * kpitch + kc) = v;
+        *reinterpret_cast<uint4 *>(out + oz_off(z, s, r0 + rb, kc, S, rows_pad, kpitch, nkb, kblk)) = v;
       }
     }
 }
@@ -183,7 +191,8 @@ template <int S, bool PACKED>
 __global__ void __launch_bounds__(256) oz_slice_tr_fused_kernel(const double *__restrict__ src, long long sz,
                                                                 long long sk, int rows, int K, int rows_pad,
                                                                 int kpitch, int nkb, int *__restrict__ expo,
-                                                                __nv_bfloat16 *__restrict__ out, int mu0) {
+                                                                __nv_bfloat16 *__restrict__ out, int mu0,
+                                                                int kblk) {
   constexpr int R = 8, KG = 256 / R, LD = 72, MAXKB = 8;
   __shared__ __nv_bfloat16 tile[S * R * LD];
   __shared__ unsigned long long rmax[R][MAXKB];
@@ -246,7 +255,7 @@ __global__ void __launch_bounds__(256) oz_slice_tr_fused_kernel(const double *__
       const int kc = k0 + c8 * 8;
       if (kc < kpitch) {
         const uint4 v = *reinterpret_cast<const uint4 *>(&tile[(s * R + rw) * LD + c8 * 8]);
-        *reinterpret_cast<uint4 *>(out + (((long long)z * S + s) * rows_pad + r0 + rw) * kpitch + kc) = v;
+        *reinterpret_cast<uint4 *>(out + oz_off(z, s, r0 + rw, kc, S, rows_pad, kpitch, nkb, kblk)) = v;
       }
     }
     __syncthreads();
@@ -260,8 +269,9 @@ void oz_alloc(SlicedOp &op, int batch, int S, int rows, int K, int row_tile) {
   op.rows = rows;
   op.rows_pad = ((rows + row_tile - 1) / row_tile) * row_tile;
   op.K = K;
-  op.kpitch = ((K + OZ_BK - 1) / OZ_BK) * OZ_BK;
   op.nkb = (K + OZ_KB - 1) / OZ_KB;
+  op.kblk = op.nkb > 4 ? 1 : 0;
+  op.kpitch = op.kblk ? op.nkb * OZ_KB : ((K + OZ_BK - 1) / OZ_BK) * OZ_BK;
   const size_t nd = (size_t)batch * S * op.rows_pad * op.kpitch;
   const size_t ne = (size_t)batch * op.rows_pad * op.nkb;
   op.data = (__nv_bfloat16 *)pool_alloc(nd * sizeof(__nv_bfloat16));
@@ -286,7 +296,7 @@ void oz_slice_f64_packed(const double *B, long long ldb, int mu0, SlicedOp &op, 
     throw Error{DFJK_ERR_UNSUPPORTED, "packed slicing: 6 slices, K <= 8192"};
   dim3 grid((unsigned)(op.rows_pad / 8), (unsigned)op.batch);
   oz_slice_tr_fused_kernel<6, true><<<grid, 256, 0, st>>>(B, 0, ldb, op.rows, op.K, op.rows_pad, op.kpitch,
-                                                          op.nkb, op.expo, op.data, mu0);
+                                                          op.nkb, op.expo, op.data, mu0, op.kblk);
   DFJK_LAUNCHED();
 }
 
@@ -298,11 +308,13 @@ void oz_slice_f64(const double *src, long long sz, long long sr, long long sk, S
     switch (op.S) {
       case 6:
         oz_slice_tr_fused_kernel<6, false><<<grid, 256, 0, st>>>(src, sz, sk, op.rows, op.K, op.rows_pad,
-                                                                 op.kpitch, op.nkb, op.expo, op.data, 0);
+                                                                 op.kpitch, op.nkb, op.expo, op.data, 0,
+                                                                 op.kblk);
         break;
       case 8:
         oz_slice_tr_fused_kernel<8, false><<<grid, 256, 0, st>>>(src, sz, sk, op.rows, op.K, op.rows_pad,
-                                                                 op.kpitch, op.nkb, op.expo, op.data, 0);
+                                                                 op.kpitch, op.nkb, op.expo, op.data, 0,
+                                                                 op.kblk);
         break;
       default:
         throw Error{DFJK_ERR_UNSUPPORTED, "slice count must be 6 or 8"};
@@ -331,7 +343,7 @@ void oz_slice_f64(const double *src, long long sz, long long sr, long long sk, S
           attr6 = true;
         }
         oz_slice_tr_kernel<6><<<grid, 256, smem, st>>>(src, sz, sk, op.rows, op.K, op.rows_pad, op.kpitch,
-                                                       op.nkb, op.expo, op.data);
+                                                       op.nkb, op.expo, op.data, op.kblk);
         break;
       case 8:
         if (!attr8) {
@@ -339,7 +351,7 @@ void oz_slice_f64(const double *src, long long sz, long long sr, long long sk, S
           attr8 = true;
         }
         oz_slice_tr_kernel<8><<<grid, 256, smem, st>>>(src, sz, sk, op.rows, op.K, op.rows_pad, op.kpitch,
-                                                       op.nkb, op.expo, op.data);
+                                                       op.nkb, op.expo, op.data, op.kblk);
         break;
       default:
         throw Error{DFJK_ERR_UNSUPPORTED, "slice count must be 6 or 8"};
@@ -353,11 +365,11 @@ void oz_slice_f64(const double *src, long long sz, long long sr, long long sk, S
   switch (op.S) {
     case 6:
       oz_slice_kernel<6><<<grid, 256, 0, st>>>(src, sz, sr, sk, op.batch, op.rows, op.K, op.rows_pad,
-                                               op.kpitch, op.nkb, op.expo, op.data, row_fast);
+                                               op.kpitch, op.nkb, op.expo, op.data, row_fast, op.kblk);
       break;
     case 8:
       oz_slice_kernel<8><<<grid, 256, 0, st>>>(src, sz, sr, sk, op.batch, op.rows, op.K, op.rows_pad,
-                                               op.kpitch, op.nkb, op.expo, op.data, row_fast);
+                                               op.kpitch, op.nkb, op.expo, op.data, row_fast, op.kblk);
       break;
     default:
       throw Error{DFJK_ERR_UNSUPPORTED, "slice count must be 6 or 8"};
@@ -386,10 +398,18 @@ struct OzKernelArgs {
   OzGemmArgs g;
   const int *expoA, *expoB;
   int rows_padA, rows_padB, nkbA, nkbB;
+  int kblkA, kblkB;  // K-blocked slice layouts (4-D tensor maps)
 };
 
 // 2^e for normal exponents; 0 below the normal range (row maxima that small
 // do not occur for these operands except as exact zeros).
+// TMA load of one slice tile: rows row0.. of slice plane `plane` at K offset kc.
+__device__ __forceinline__ void oz_tma(void *dst, const CUtensorMap *map, uint64_t *bar, int kc, int row0,
+                                       int plane, int kblk) {
+  if (kblk) tc::tma_load_4d(dst, map, bar, kc & (OZ_KB - 1), row0, kc >> 10, plane);
+  else tc::tma_load_3d(dst, map, bar, kc, row0, plane);
+}
+
 // Row of (mu, nu) in a packed symmetric triangle: max (max + 1) / 2 + min.
 __device__ __forceinline__ long long tri_row_of(int mu, int nu) {
   const long long hi = mu > nu ? mu : nu, lo = mu > nu ? nu : mu;
@@ -488,10 +508,10 @@ __global__ void __launch_bounds__(128, 1)
           const int kc = kstart + j * OZ_BK;
 #pragma unroll
           for (int s = 0; s < S; ++s)
-            tc::tma_load_3d(stp + s * Cfg::A_TILE, &tmA, &full[slot], kc, m0, zA * S + s);
+            oz_tma(stp + s * Cfg::A_TILE, &tmA, &full[slot], kc, m0, zA * S + s, ka.kblkA);
 #pragma unroll
           for (int t = 0; t < S; ++t)
-            tc::tma_load_3d(stp + S * Cfg::A_TILE + t * Cfg::B_TILE, &tmB, &full[slot], kc, n0, zB * S + t);
+            oz_tma(stp + S * Cfg::A_TILE + t * Cfg::B_TILE, &tmB, &full[slot], kc, n0, zB * S + t, ka.kblkB);
           ++issued;
         }
         if (j >= dist) {
@@ -715,10 +735,10 @@ __global__ void __launch_bounds__(OZ_WS_THREADS, 1)
             tc::mbar_expect_tx(&full[slot], Cfg::STAGE);
 #pragma unroll
             for (int s = 0; s < S; ++s)
-              tc::tma_load_3d(stp + s * Cfg::A_TILE, &tmA, &full[slot], kc, m0, zA * S + s);
+              oz_tma(stp + s * Cfg::A_TILE, &tmA, &full[slot], kc, m0, zA * S + s, ka.kblkA);
 #pragma unroll
             for (int q = 0; q < S; ++q)
-              tc::tma_load_3d(stp + S * Cfg::A_TILE + q * Cfg::B_TILE, &tmB, &full[slot], kc, n0, zB * S + q);
+              oz_tma(stp + S * Cfg::A_TILE + q * Cfg::B_TILE, &tmB, &full[slot], kc, n0, zB * S + q, ka.kblkB);
           }
         }
       }
@@ -949,13 +969,26 @@ static EncodeTiledFn encode_fn() {
 
 static CUtensorMap make_map(const SlicedOp &op, int box_rows) {
   CUtensorMap map;
-  cuuint64_t dims[3] = {(cuuint64_t)op.K, (cuuint64_t)op.rows_pad, (cuuint64_t)op.batch * op.S};
-  cuuint64_t strides[2] = {(cuuint64_t)op.kpitch * 2, (cuuint64_t)op.rows_pad * op.kpitch * 2};
-  cuuint32_t box[3] = {OZ_BK, (cuuint32_t)box_rows, 1};
-  cuuint32_t estr[3] = {1, 1, 1};
-  CUresult r = encode_fn()(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, op.data, dims, strides, box, estr,
-                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
-                           CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  CUresult r;
+  if (!op.kblk) {  // (k, row, batch x slice)
+    cuuint64_t dims[3] = {(cuuint64_t)op.K, (cuuint64_t)op.rows_pad, (cuuint64_t)op.batch * op.S};
+    cuuint64_t strides[2] = {(cuuint64_t)op.kpitch * 2, (cuuint64_t)op.rows_pad * op.kpitch * 2};
+    cuuint32_t box[3] = {OZ_BK, (cuuint32_t)box_rows, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    r = encode_fn()(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, op.data, dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  } else {  // (k within block, row, K block, batch x slice); padding of the last block is zero
+    cuuint64_t dims[4] = {(cuuint64_t)OZ_KB, (cuuint64_t)op.rows_pad, (cuuint64_t)op.nkb,
+                          (cuuint64_t)op.batch * op.S};
+    cuuint64_t strides[3] = {(cuuint64_t)OZ_KB * 2, (cuuint64_t)op.rows_pad * OZ_KB * 2,
+                             (cuuint64_t)op.nkb * op.rows_pad * OZ_KB * 2};
+    cuuint32_t box[4] = {OZ_BK, (cuuint32_t)box_rows, 1, 1};
+    cuuint32_t estr[4] = {1, 1, 1, 1};
+    r = encode_fn()(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, op.data, dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  }
   if (r != CUDA_SUCCESS) throw Error{DFJK_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")"};
   return map;
 }
@@ -981,7 +1014,7 @@ static void launch_oz_ws(const SlicedOp &A, const SlicedOp &B, const OzGemmArgs 
     attr_set = true;
   }
   const CUtensorMap ma = make_map(A, OZ_BM), mb = make_map(B, OZ_BN);
-  OzKernelArgs ka{g, A.expo, B.expo, A.rows_pad, B.rows_pad, A.nkb, B.nkb};
+  OzKernelArgs ka{g, A.expo, B.expo, A.rows_pad, B.rows_pad, A.nkb, B.nkb, A.kblk, B.kblk};
   OzTiles T;
   T.ntm = (g.M + OZ_BM - 1) / OZ_BM;
   T.ntn = (g.N + OZ_BN - 1) / OZ_BN;
@@ -1011,7 +1044,7 @@ static void launch_oz(const SlicedOp &A, const SlicedOp &B, const OzGemmArgs &g,
     attr_set = true;
   }
   const CUtensorMap ma = make_map(A, OZ_BM), mb = make_map(B, OZ_BN);
-  OzKernelArgs ka{g, A.expo, B.expo, A.rows_pad, B.rows_pad, A.nkb, B.nkb};
+  OzKernelArgs ka{g, A.expo, B.expo, A.rows_pad, B.rows_pad, A.nkb, B.nkb, A.kblk, B.kblk};
   dim3 grid((unsigned)((g.M + OZ_BM - 1) / OZ_BM), (unsigned)((g.N + OZ_BN - 1) / OZ_BN), (unsigned)g.nz);
   oz_gemm_kernel<S><<<grid, 128, OzCfg<S>::SMEM, st>>>(ma, mb, ka);
   DFJK_LAUNCHED();

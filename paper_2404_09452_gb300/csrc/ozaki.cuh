@@ -23,10 +23,14 @@ constexpr int OZ_BM = 128, OZ_BN = 64, OZ_BK = 32;
 
 // Slices of an operand: planes [batch][S][rows_pad][kpitch] (BF16, K
 // contiguous) and exponents [batch][rows_pad][nkb] (int32).
+// Layout of data: [batch][S][rows_pad][kpitch], or, for long K (kblk = 1,
+// more than 4 exponent blocks), K-blocked [batch][S][nkb][rows_pad][1024] so
+// that the rows of one TMA box lie 2 KB apart instead of a whole K row apart
+// (a box of the K GEMM's X slices would otherwise touch 128 pages).
 struct SlicedOp {
   __nv_bfloat16 *data = nullptr;
   int *expo = nullptr;
-  int batch = 1, S = 0, rows = 0, rows_pad = 0, K = 0, kpitch = 0, nkb = 0;
+  int batch = 1, S = 0, rows = 0, rows_pad = 0, K = 0, kpitch = 0, nkb = 0, kblk = 0;
   size_t bytes() const {
     return (size_t)batch * S * rows_pad * kpitch * 2 + (size_t)batch * rows_pad * nkb * 4;
   }

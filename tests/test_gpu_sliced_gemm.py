@@ -44,6 +44,14 @@ def test_ragged_batched_multi_kblock(S):
     _check(A, B, S)
 
 
+@pytest.mark.parametrize("S", [6, 8])
+def test_long_k_blocked_layout(S):
+    """More than 4 exponent blocks along K: the slices are stored K-blocked
+    (1024-wide blocks, rows inside) and loaded through 4-D tensor maps."""
+    A, B = _case(2, 200, 70, 5300, 5)  # 6 K-blocks, last one partial
+    _check(A, B, S)
+
+
 def test_exact_for_small_integers():
     """Integer-valued operands that fit in the slices are multiplied exactly."""
     rng = np.random.default_rng(3)
