@@ -95,12 +95,18 @@ typedef struct {
                               evaluated in FP32.  0 = every pair in FP64;
                               negative = the precision's default (0 for
                               DFJK_FP64, 1e-6 for DFJK_MIXED)                 */
+  int32_t b_on_host;       /* 1: keep B in pinned host memory mapped into the
+                              device address space (the kernels read and
+                              write it in place over the host link; for
+                              molecules whose B does not fit in device
+                              memory); the mixed path then also slices B per
+                              build.  0 (default): B in device memory          */
 } dfjk_options;
 
 typedef struct dfjk_ctx *dfjk_handle;
 
 /* Fills *opt with the defaults: DFJK_FP64, 1e-12, no budget, 1<<26, host
- * energies, fp32_pair_thresh -1 (the precision's default).                   */
+ * energies, fp32_pair_thresh -1 (the precision's default), B on the device.  */
 void dfjk_default_options(dfjk_options *opt);
 
 /* Steps a0-a5: validates and normalises the bases, builds the shell-pair list

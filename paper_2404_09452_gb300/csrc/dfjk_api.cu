@@ -96,6 +96,44 @@ struct DBuf {
   ~DBuf() { release(); }
 };
 
+// B: device memory from the cache, or pinned host memory mapped into the device
+// address space, read and written by the kernels in place (NVLink-C2C on a
+// Grace-Blackwell node) so that molecules whose B does not fit next to the
+// build's work buffers still run.
+struct BStore {
+  double *p = nullptr;   // device-usable address
+  void *hp = nullptr;    // host allocation (host-resident only)
+  size_t n = 0;
+  bool host = false;
+  void alloc(size_t count, bool on_host) {
+    release();
+    if (on_host) {
+      if (cudaHostAlloc(&hp, std::max<size_t>(count, 1) * sizeof(double), cudaHostAllocMapped) != cudaSuccess) {
+        cudaGetLastError();
+        hp = nullptr;
+        throw Error{DFJK_ERR_OOM, "pinned host memory for B (" + std::to_string(count * 8) + " bytes)"};
+      }
+      void *d = nullptr;
+      DFJK_CUDA_CHECK(cudaHostGetDevicePointer(&d, hp, 0));
+      p = (double *)d;
+    } else {
+      p = (double *)pool_alloc(std::max<size_t>(count, 1) * sizeof(double));
+    }
+    host = on_host;
+    n = count;
+  }
+  void release() {
+    if (host && hp) cudaFreeHost(hp);
+    if (!host && p) pool_free(p, std::max<size_t>(n, 1) * sizeof(double));
+    p = nullptr;
+    hp = nullptr;
+    n = 0;
+  }
+  size_t bytes() const { return n * sizeof(double); }
+  size_t device_bytes() const { return host ? 0 : bytes(); }
+  ~BStore() { release(); }
+};
+
 // ---- Boys table per device ---------------------------------------------------------
 
 const double *boys_table_device() {
@@ -227,7 +265,7 @@ struct dfjk_ctx {
   DBuf<int> kseq;  // split counters of the ordered split-K GEMM
   // whitened tensor: FP64 B[(mu nao + nu) ldb + P]; in DFJK_MIXED also its
   // 6-slice form for the tensor-core X = B C (batch mu, rows P, K nu)
-  DBuf<double> B;
+  BStore B;
   long long ldb = 0;
   SlicedOp Bsl;
   // memory-lean mixed mode: B's slices are not kept; each build slices B in
@@ -316,9 +354,9 @@ bool choose_lean(int nao, int np) {
 size_t resident_estimate(const dfjk_ctx *h) {
   const size_t np2 = (size_t)h->naux_pad * h->naux_pad;
   const bool mixed = h->opt.precision == DFJK_MIXED;
-  const bool lean = mixed && choose_lean(h->nao, h->naux_pad);
+  const bool lean = mixed && (h->opt.b_on_host || choose_lean(h->nao, h->naux_pad));
   const size_t rows = lean ? (size_t)h->nao * (h->nao + 1) / 2 : (size_t)h->nao * h->nao;
-  size_t b = rows * h->naux_pad * sizeof(double);
+  size_t b = h->opt.b_on_host ? 0 : rows * h->naux_pad * sizeof(double);
   if (mixed && !lean) b += bslice_bytes(h->nao, h->naux_pad);
   return b + 3 * np2 * sizeof(double);
 }
@@ -547,8 +585,8 @@ void make_resident(dfjk_ctx *h, cudaStream_t st) {
 
   // a4 + a5: 3-centre integrals in column slabs, whitened into B
   h->ldb = np;
-  h->lean = mixed && choose_lean(h->nao, np);
-  h->B.alloc((h->lean ? (size_t)h->nao * (h->nao + 1) / 2 : (size_t)h->nao * h->nao) * np);
+  h->lean = mixed && (h->opt.b_on_host || choose_lean(h->nao, np));
+  h->B.alloc((h->lean ? (size_t)h->nao * (h->nao + 1) / 2 : (size_t)h->nao * h->nao) * np, h->opt.b_on_host != 0);
   DFJK_CUDA_CHECK(cudaMemsetAsync(h->B.p, 0, h->B.bytes(), st));
   const long long slab_budget = 4LL << 30;  // bytes of one T slab
   long long slab_cols = std::max<long long>(36, slab_budget / ((long long)np * 8));
@@ -840,6 +878,7 @@ void dfjk_default_options(dfjk_options *opt) {
   opt->timeout_iters = 1LL << 26;
   opt->energies_on_host = 1;
   opt->fp32_pair_thresh = -1.0;
+  opt->b_on_host = 0;
 }
 
 const char *dfjk_status_string(int code) {
@@ -926,7 +965,7 @@ int dfjk_query(dfjk_handle h, int32_t *nao, int32_t *naux, int32_t *npair_kept, 
   if (nao) *nao = h->nao;
   if (naux) *naux = h->naux;
   if (npair_kept) *npair_kept = h->npair_kept;
-  if (bytes) *bytes = h->B.bytes() + h->Bsl.bytes() + h->V.bytes() +
+  if (bytes) *bytes = h->B.device_bytes() + h->Bsl.bytes() + h->V.bytes() +
                       h->L.bytes() + h->Linv.bytes() + h->rec.bytes();
   return DFJK_OK;
 }

@@ -92,6 +92,7 @@ class Options(ctypes.Structure):
         ("timeout_iters", ctypes.c_int64),
         ("energies_on_host", ctypes.c_int32),
         ("fp32_pair_thresh", ctypes.c_double),
+        ("b_on_host", ctypes.c_int32),
     ]
 
 
@@ -189,7 +190,8 @@ class _BasisHolder:
 
 def default_options(precision: int = DFJK_FP64, schwarz_thresh: float = 1e-12,
                     hbm_budget_bytes: int = 0, energies_on_host: bool = True,
-                    timeout_iters: int = 0, fp32_pair_thresh: float = -1.0) -> Options:
+                    timeout_iters: int = 0, fp32_pair_thresh: float = -1.0,
+                    b_on_host: bool = False) -> Options:
     o = Options()
     load_library().dfjk_default_options(ctypes.byref(o))
     o.precision = precision
@@ -199,6 +201,7 @@ def default_options(precision: int = DFJK_FP64, schwarz_thresh: float = 1e-12,
     if timeout_iters > 0:
         o.timeout_iters = timeout_iters
     o.fp32_pair_thresh = fp32_pair_thresh
+    o.b_on_host = 1 if b_on_host else 0
     return o
 
 
@@ -207,7 +210,7 @@ class Handle:
 
     def __init__(self, mol, precision: int = DFJK_FP64, schwarz_thresh: float = 1e-12,
                  hbm_budget_bytes: int = 0, stream=None, timeout_iters: int = 0,
-                 fp32_pair_thresh: float = -1.0):
+                 fp32_pair_thresh: float = -1.0, b_on_host: bool = False):
         lib = load_library()
         _torch()
         self.mol = mol
@@ -215,7 +218,7 @@ class Handle:
         self._aux = _BasisHolder(mol.aux)
         xyz = np.ascontiguousarray(mol.coords, dtype=np.float64)
         opt = default_options(precision, schwarz_thresh, hbm_budget_bytes, timeout_iters=timeout_iters,
-                              fp32_pair_thresh=fp32_pair_thresh)
+                              fp32_pair_thresh=fp32_pair_thresh, b_on_host=b_on_host)
         h = ctypes.c_void_p()
         _check(
             lib.dfjk_setup(
