@@ -37,6 +37,43 @@ class Request:
     K: object = None
 
 
+class Residency:
+    """LRU residency under a byte budget.  Each resident molecule is charged
+    the bytes it was admitted with, and exactly that is returned when it is
+    evicted."""
+
+    def __init__(self, budget: int):
+        self.budget = budget
+        self.bytes = collections.OrderedDict()  # mol_id -> bytes (LRU order)
+        self.used = 0
+
+    def touch(self, mol_id) -> bool:
+        if mol_id in self.bytes:
+            self.bytes.move_to_end(mol_id)
+            return True
+        return False
+
+    def admit(self, mol_id, need: int, busy) -> tuple:
+        """Makes room for `need` bytes by evicting least recently used molecules
+        that are not in `busy`.  Returns (admitted, evicted ids).  A molecule
+        larger than the whole budget is admitted alone once nothing else is
+        resident (it cannot be served otherwise)."""
+        evicted = []
+        while self.used + need > self.budget and self.bytes:
+            victim = next((k for k in self.bytes if k not in busy), None)
+            if victim is None:
+                return False, evicted  # everything resident is in flight: wait
+            self.used -= self.bytes.pop(victim)
+            evicted.append(victim)
+        self.bytes[mol_id] = need
+        self.used += need
+        return True, evicted
+
+    def drop(self, mol_id):
+        if mol_id in self.bytes:
+            self.used -= self.bytes.pop(mol_id)
+
+
 @dataclass
 class Stats:
     latencies: list = field(default_factory=list)
@@ -66,8 +103,8 @@ class Server:
         self.precision = precision
         self.budget = budget_bytes
         self.keep = keep_outputs
-        self.resident = collections.OrderedDict()  # mol_id -> Handle (LRU order)
-        self.used = 0
+        self.resident = {}  # mol_id -> Handle
+        self.lru = Residency(budget_bytes)
         self.busy = set()  # mol_ids with a build in flight
         self.streams = [torch.cuda.Stream() for _ in range(slots)]
         self.free_slots = list(range(slots))
@@ -78,19 +115,15 @@ class Server:
         return resident_bytes(m.nao, m.naux, nocc, self.precision)
 
     def _ensure_resident(self, mol_id, nocc):
-        if mol_id in self.resident:
-            self.resident.move_to_end(mol_id)
+        if self.lru.touch(mol_id):
             return True
-        need = self._bytes(mol_id, nocc)
-        while self.used + need > self.budget:
-            victim = next((k for k in self.resident if k not in self.busy), None)
-            if victim is None:
-                return False  # everything resident is in flight: wait
-            self.resident.pop(victim).close()
-            self.used -= self._bytes(victim, nocc)
+        ok, evicted = self.lru.admit(mol_id, self._bytes(mol_id, nocc), self.busy)
+        for v in evicted:
+            self.resident.pop(v).close()
             self.stats.evictions += 1
+        if not ok:
+            return False
         self.resident[mol_id] = dfjk.Handle(self.mols[mol_id], precision=self.precision)
-        self.used += need
         self.stats.misses += 1
         return True
 
@@ -144,6 +177,9 @@ class Server:
                     time.sleep(20e-6)
                 elif pending and not waiting:
                     time.sleep(max(0.0, min(1e-3, pending[0].arrival - (time.perf_counter() - t0))))
+                elif waiting:
+                    # nothing in flight, so nothing is busy: admission cannot fail
+                    raise RuntimeError("serving stalled: a waiting request could not be admitted")
         self.stats.seconds = time.perf_counter() - t0
         return requests
 
@@ -151,7 +187,7 @@ class Server:
         for h in self.resident.values():
             h.close()
         self.resident.clear()
-        self.used = 0
+        self.lru = Residency(self.budget)
 
 
 def make_stream(mols, nreq, rate, repeat=0.7, seed=5000, c_of=None):
