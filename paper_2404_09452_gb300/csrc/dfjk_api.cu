@@ -804,7 +804,7 @@ void build_one(dfjk_ctx *h, int nocc, const double *C, double *J, double *Kout, 
           const int n = std::min(mc, nao - mu0);
           SlicedOp ck = h->Bchunk;  // view of the first n batches (the last chunk is short)
           ck.batch = n;
-          oz_slice_f64_packed(h->B.p, h->ldb, mu0, ck, st);
+          oz_slice_f64_packed(h->B.p, h->ldb, mu0, ck, h->B.host, st);
           OzGemmArgs xc = x;
           xc.nz = n;
           xc.out = h->X.p + (size_t)mu0 * np * nocc;

@@ -386,7 +386,20 @@ __global__ void __launch_bounds__(256) j_gemv_kernel(const double *__restrict__ 
   tri_row(r, mu, nu);
   const double *row = B + (packed ? r : (long long)mu * nao + nu) * ldb;
   double s = 0.0;
-  for (int P = lane; P < naux; P += 32) s = fma(row[P], __ldg(rho + P), s);
+  if ((naux & 1) == 0 && (ldb & 1) == 0) {  // 16-byte loads, two partial sums, 4 loads in flight
+    const double2 *row2 = reinterpret_cast<const double2 *>(row);
+    const double2 *rho2 = reinterpret_cast<const double2 *>(rho);
+    double s1 = 0.0;
+#pragma unroll 4
+    for (int q = lane; q < naux / 2; q += 32) {
+      const double2 b = row2[q], x = __ldg(rho2 + q);
+      s = fma(b.x, x.x, s);
+      s1 = fma(b.y, x.y, s1);
+    }
+    s += s1;
+  } else {
+    for (int P = lane; P < naux; P += 32) s = fma(row[P], __ldg(rho + P), s);
+  }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   if (lane == 0) {

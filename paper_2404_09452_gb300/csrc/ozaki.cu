@@ -187,13 +187,13 @@ __global__ void __launch_bounds__(256) oz_slice_tr_kernel(const double *__restri
 // K = 900) keeps the second read in L2 with every SM's blocks in flight; lanes
 // run along the rows (64 contiguous bytes per K index, four K indices per
 // warp load).
-template <int S, bool PACKED>
+template <int S, bool PACKED, int R = 8>
 __global__ void __launch_bounds__(256) oz_slice_tr_fused_kernel(const double *__restrict__ src, long long sz,
                                                                 long long sk, int rows, int K, int rows_pad,
                                                                 int kpitch, int nkb, int *__restrict__ expo,
                                                                 __nv_bfloat16 *__restrict__ out, int mu0,
                                                                 int kblk) {
-  constexpr int R = 8, KG = 256 / R, LD = 72, MAXKB = 8;
+  constexpr int KG = 256 / R, LD = 72, MAXKB = 8;
   __shared__ __nv_bfloat16 tile[S * R * LD];
   __shared__ unsigned long long rmax[R][MAXKB];
   __shared__ int rexp[R][MAXKB];
@@ -221,9 +221,9 @@ __global__ void __launch_bounds__(256) oz_slice_tr_fused_kernel(const double *__
 #pragma unroll 4
       for (int k = kb * OZ_KB + kq; k < k1; k += KG) mx = fmax(mx, fabs(at(k)));
     }
-    // lanes with the same row in a warp: 4 of them (32 lanes / 8 rows)
-    mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, 8));
-    mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, 16));
+    // lanes with the same row in a warp (32 / R of them)
+#pragma unroll
+    for (int o = R; o < 32; o <<= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if ((threadIdx.x & 31) < R) atomicMax(&rmax[rr][kb], (unsigned long long)__double_as_longlong(mx));
   }
   __syncthreads();
@@ -291,12 +291,18 @@ void oz_free(SlicedOp &op) {
   op.expo = nullptr;
 }
 
-void oz_slice_f64_packed(const double *B, long long ldb, int mu0, SlicedOp &op, cudaStream_t st) {
-  if (op.S != 6 || op.rows_pad % 8 != 0 || op.nkb > 8)
+void oz_slice_f64_packed(const double *B, long long ldb, int mu0, SlicedOp &op, bool b_on_host, cudaStream_t st) {
+  if (op.S != 6 || op.rows_pad % 32 != 0 || op.nkb > 8)
     throw Error{DFJK_ERR_UNSUPPORTED, "packed slicing: 6 slices, K <= 8192"};
-  dim3 grid((unsigned)(op.rows_pad / 8), (unsigned)op.batch);
-  oz_slice_tr_fused_kernel<6, true><<<grid, 256, 0, st>>>(B, 0, ldb, op.rows, op.K, op.rows_pad, op.kpitch,
-                                                          op.nkb, op.expo, op.data, mu0, op.kblk);
+  if (b_on_host) {  // 32 rows (256 contiguous bytes) per K index over the host link
+    dim3 grid((unsigned)(op.rows_pad / 32), (unsigned)op.batch);
+    oz_slice_tr_fused_kernel<6, true, 32><<<grid, 256, 0, st>>>(B, 0, ldb, op.rows, op.K, op.rows_pad, op.kpitch,
+                                                                op.nkb, op.expo, op.data, mu0, op.kblk);
+  } else {
+    dim3 grid((unsigned)(op.rows_pad / 8), (unsigned)op.batch);
+    oz_slice_tr_fused_kernel<6, true, 8><<<grid, 256, 0, st>>>(B, 0, ldb, op.rows, op.K, op.rows_pad, op.kpitch,
+                                                               op.nkb, op.expo, op.data, mu0, op.kblk);
+  }
   DFJK_LAUNCHED();
 }
 

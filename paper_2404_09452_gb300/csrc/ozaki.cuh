@@ -73,7 +73,8 @@ struct OzGemmArgs {
 
 // Slices of B stored as the packed mu >= nu triangle (row mu (mu + 1) / 2 + nu,
 // ldb doubles per row, P contiguous): batch z is mu = mu0 + z, rows P, K nu.
-void oz_slice_f64_packed(const double *B, long long ldb, int mu0, SlicedOp &op, cudaStream_t st);
+// b_on_host: B is in host memory (wider row groups per block for the host link).
+void oz_slice_f64_packed(const double *B, long long ldb, int mu0, SlicedOp &op, bool b_on_host, cudaStream_t st);
 
 // True when DFJK_OZ_SIMPLE=1 selects the one-tile-per-CTA kernel (no mode 2).
 bool oz_simple_mode();
