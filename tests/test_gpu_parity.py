@@ -1,5 +1,5 @@
 """GPU parity of the CUDA DF-J/K path against the FP64 CPU oracle, called
-through the C ABI.  Tolerances: the spec bar (|dE| <= 1e-6 Eh,
+through the C ABI.  Tolerances: the accuracy bar (|dE| <= 1e-6 Eh,
 max|dJ|, max|dK| <= 1e-7) is asserted everywhere; the FP64 path additionally
 must stay within 1e-9 of the oracle (FP64 rounding differences only)."""
 import numpy as np
