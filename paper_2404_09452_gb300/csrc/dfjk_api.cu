@@ -812,11 +812,20 @@ void build_one(dfjk_ctx *h, int nocc, const double *C, double *J, double *Kout, 
         }
       }
     }
-    {  // rho from X (5x smaller than B), then J over B
-      PhaseScope ph(6, st);
-      rho_from_x_f64(h->X.p, C, nao, np, nocc, h->rho.p, h->rho_work.p, st);
-      j_gemv_f64(h->B.p, h->ldb, nao, np, h->rho.p, J, h->lean ? 1 : 0, st);
+    // rho from X (5x smaller than B), then J over B, on the handle's side
+    // stream beside the K GEMM: both only read X, and the HBM-bound J GEMV
+    // fits next to the tensor-bound K kernel on the SMs
+    const cudaStream_t sj = h->side ? h->side : st;
+    if (h->side) {
+      DFJK_CUDA_CHECK(cudaEventRecord(h->ev_fork, st));
+      DFJK_CUDA_CHECK(cudaStreamWaitEvent(sj, h->ev_fork, 0));
     }
+    {
+      PhaseScope ph(6, sj);
+      rho_from_x_f64(h->X.p, C, nao, np, nocc, h->rho.p, h->rho_work.p, sj);
+      j_gemv_f64(h->B.p, h->ldb, nao, np, h->rho.p, J, h->lean ? 1 : 0, sj);
+    }
+    if (h->side) DFJK_CUDA_CHECK(cudaEventRecord(h->ev_join, sj));
     PhaseScope ph(5, st);
     if (!h->Xsl.data || h->Xsl.K != kt) oz_alloc(h->Xsl, 1, 6, nao, (int)kt, OZ_BM);
     oz_slice_f64(h->X.p, 0, kt, 1, h->Xsl, st);
@@ -861,6 +870,7 @@ void build_one(dfjk_ctx *h, int nocc, const double *C, double *J, double *Kout, 
       oz_gemm(h->Xsl, h->Xsl, k, st);
       reduce_sym_f64(h->Kpart.p, nsplit, nao, Kout, st);
     }
+    if (h->side) DFJK_CUDA_CHECK(cudaStreamWaitEvent(st, h->ev_join, 0));  // J ready
   }
   PhaseScope ph(7, st);
   energies_f64(h->D.p, J, Kout, nao, e, h->en_work.p, st);
