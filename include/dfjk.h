@@ -94,7 +94,7 @@ typedef struct {
                               max_P sqrt((P|P)) is below this value are
                               evaluated in FP32.  0 = every pair in FP64;
                               negative = the precision's default (0 for
-                              DFJK_FP64, 1e-6 for DFJK_MIXED)                 */
+                              DFJK_FP64, 1e-5 for DFJK_MIXED)                 */
   int32_t b_on_host;       /* 1: keep B in pinned host memory mapped into the
                               device address space (the kernels read and
                               write it in place over the host link; for

@@ -498,7 +498,7 @@ void make_resident(dfjk_ctx *h, cudaStream_t st) {
   // Schwarz-guided precision: kept pairs with bound below thr32 go to the FP32
   // kernels; within each class the FP64 pairs come first
   const double thr32 = h->opt.fp32_pair_thresh >= 0.0 ? h->opt.fp32_pair_thresh
-                       : (h->opt.precision == DFJK_MIXED ? 1e-6 : 0.0);
+                       : (h->opt.precision == DFJK_MIXED ? 1e-5 : 0.0);
   h->fp32_thresh = thr32;
 
   // kept list, columns, column -> (mu, nu) map (host bookkeeping)

@@ -309,22 +309,31 @@ void oz_slice_f64_packed(const double *B, long long ldb, int mu0, SlicedOp &op, 
 void oz_slice_f64(const double *src, long long sz, long long sr, long long sk, SlicedOp &op,
                   cudaStream_t st) {
   if (sr == 1 && op.rows_pad % 8 == 0 && op.nkb <= 8) {
-    // row-contiguous source: exponents and slices fused, one read from HBM
-    dim3 grid((unsigned)(op.rows_pad / 8), (unsigned)op.batch);
-    switch (op.S) {
-      case 6:
-        oz_slice_tr_fused_kernel<6, false><<<grid, 256, 0, st>>>(src, sz, sk, op.rows, op.K, op.rows_pad,
-                                                                 op.kpitch, op.nkb, op.expo, op.data, 0,
-                                                                 op.kblk);
-        break;
-      case 8:
-        oz_slice_tr_fused_kernel<8, false><<<grid, 256, 0, st>>>(src, sz, sk, op.rows, op.K, op.rows_pad,
-                                                                 op.kpitch, op.nkb, op.expo, op.data, 0,
-                                                                 op.kblk);
-        break;
-      default:
-        throw Error{DFJK_ERR_UNSUPPORTED, "slice count must be 6 or 8"};
+    // row-contiguous source: exponents and slices fused, one read from HBM;
+    // rows per block 16 (measured best of 8 / 16 / 32 at 60 atoms; the
+    // DFJK_SLICE_ROWS environment variable selects another)
+    static const int rows_per_block = [] {
+      const char *e = std::getenv("DFJK_SLICE_ROWS");
+      const int v = e ? std::atoi(e) : 16;
+      return (v == 8 || v == 32) ? v : 16;
+    }();
+    const int R = (op.rows_pad % rows_per_block == 0) ? rows_per_block : 8;
+    dim3 grid((unsigned)(op.rows_pad / R), (unsigned)op.batch);
+#define OZ_FUSED(SS, RR)                                                                                      \
+  oz_slice_tr_fused_kernel<SS, false, RR><<<grid, 256, 0, st>>>(src, sz, sk, op.rows, op.K, op.rows_pad, op.kpitch, \
+                                                                 op.nkb, op.expo, op.data, 0, op.kblk)
+    if (op.S == 6) {
+      if (R == 32) OZ_FUSED(6, 32);
+      else if (R == 16) OZ_FUSED(6, 16);
+      else OZ_FUSED(6, 8);
+    } else if (op.S == 8) {
+      if (R == 32) OZ_FUSED(8, 32);
+      else if (R == 16) OZ_FUSED(8, 16);
+      else OZ_FUSED(8, 8);
+    } else {
+      throw Error{DFJK_ERR_UNSUPPORTED, "slice count must be 6 or 8"};
     }
+#undef OZ_FUSED
     DFJK_LAUNCHED();
     return;
   }
