@@ -146,6 +146,20 @@ int dfjk_query_setup(dfjk_handle h, int32_t *nslab, int32_t *lean);
 int dfjk_build(dfjk_handle h, int32_t nset, int32_t nocc, const double *C_occ,
                double *J, double *K, double *E_J, double *E_K, void *stream);
 
+/* J and K from densities instead of orbitals: J = B^T (B vec D) and
+ * K = sum_P B_P D B_P, for any symmetric D (not necessarily C C^T), on the
+ * FP64 pipe whatever the handle's precision (two GEMMs of nao^3 naux each, so
+ * much slower than dfjk_build; it needs B stored in full, i.e. not the
+ * memory-lean mode).
+ *   D    : device, nset x nao x nao FP64, symmetric.
+ *   J, K : device, nset x nao x nao FP64.
+ *   E_J, E_K : nset doubles each, Tr(D J)/2 and Tr(D K)/2, host or device.
+ * Uses a work buffer of nao^2 naux_pad doubles for the duration of the call
+ * (synchronises the stream before returning).  Errors: DFJK_ERR_ARG,
+ * _UNSUPPORTED (memory-lean handle), _OOM, _CUDA.                            */
+int dfjk_build_density(dfjk_handle h, int32_t nset, const double *D, double *J, double *K,
+                       double *E_J, double *E_K, void *stream);
+
 /* Spin-unrestricted build: two occupied sets, alpha and beta, with their own
  * counts (the unrestricted case the paper's code supports alongside the
  * restricted one).  D_a = C_a C_a^T, D_b = C_b C_b^T.

@@ -270,3 +270,13 @@ def dfjk_uks(B: np.ndarray, C_a: np.ndarray, C_b: np.ndarray):
     K_a, K_b = exchange(C_a), exchange(C_b)
     return dict(D=D, J=J, K_a=K_a, K_b=K_b, E_J=0.5 * np.sum(D * J),
                 E_K_a=0.5 * np.sum(D_a * K_a), E_K_b=0.5 * np.sum(D_b * K_b))
+
+
+def jk_from_density(B: np.ndarray, D: np.ndarray):
+    """J and K from a symmetric density D (not necessarily C C^T): the same
+    definitions as steps O8-O10 with D given directly, K = sum_P B_P D B_P."""
+    naux, nao, _ = B.shape
+    B2 = B.reshape(naux, nao * nao)
+    J = ((B2 @ D.ravel()) @ B2).reshape(nao, nao)
+    K = np.einsum("Pml,ls,Psn->mn", B, D, B, optimize=True)
+    return dict(J=J, K=K, E_J=0.5 * np.sum(D * J), E_K=0.5 * np.sum(D * K))

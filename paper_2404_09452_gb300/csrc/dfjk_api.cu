@@ -1095,6 +1095,77 @@ int dfjk_build_uks(dfjk_handle h, int32_t nocc_a, const double *C_a, int32_t noc
   }
 }
 
+int dfjk_build_density(dfjk_handle h, int32_t nset, const double *D, double *J, double *K, double *EJ,
+                       double *EK, void *stream) {
+  try {
+    if (!h) throw Error{DFJK_ERR_ARG, "null handle"};
+    if (nset < 1 || !D || !J || !K || !EJ || !EK) throw Error{DFJK_ERR_ARG, "build_density arguments"};
+    cudaStream_t st = S(stream);
+    DFJK_CUDA_CHECK(cudaSetDevice(h->device));
+    if (!h->resident) make_resident(h, st);
+    if (h->lean) throw Error{DFJK_ERR_UNSUPPORTED, "build_density needs B stored in full (not memory-lean)"};
+    const int nao = h->nao, np = h->naux_pad;
+    const size_t nao2 = (size_t)nao * nao;
+    ensure_workspace(h, 1, nset);
+    DBuf<double> W;  // W[mu][sigma][P] = sum_lambda D[sigma][lambda] B[mu][lambda][P]
+    W.alloc(nao2 * h->ldb);
+    const long long kt = (long long)nao * h->ldb;
+    for (int s = 0; s < nset; ++s) {
+      const double *Ds = D + s * nao2;
+      double *Js = J + s * nao2, *Ks = K + s * nao2;
+      {  // J = B^T (B vec D)
+        PhaseScope ph(6, st);
+        rho_gemv_f64(h->B.p, h->ldb, nao, np, Ds, h->rho.p, h->rho_work.p, 128, st);
+        j_gemv_f64(h->B.p, h->ldb, nao, np, h->rho.p, Js, 0, st);
+      }
+      {
+        PhaseScope ph(4, st);
+        GemmArgs w;  // batch mu: W_mu (sigma x P) = D (sigma x lambda) B_mu (lambda x P)
+        w.M = nao; w.N = np; w.K = nao; w.batch = nao;
+        w.A = Ds; w.sAm = nao; w.sAk = 1; w.sAb = 0;
+        w.B = h->B.p; w.sBn = 1; w.sBk = h->ldb; w.sBb = (long long)nao * h->ldb;
+        w.C = W.p; w.sCm = h->ldb; w.sCn = 1; w.sCb = (long long)nao * h->ldb;
+        gemm_f64(w, st);
+      }
+      PhaseScope ph(5, st);
+      GemmArgs k;  // K[mu][nu] = sum_(sigma,P) W[mu][(sigma,P)] B[nu][(sigma,P)]
+      k.M = nao; k.N = nao; k.K = (int)kt;
+      k.A = W.p; k.sAm = kt; k.sAk = 1;
+      k.B = h->B.p; k.sBn = kt; k.sBk = 1;
+      k.C = h->Kpart.p; k.sCm = nao; k.sCn = 1; k.sCb = (long long)nao2;
+      k.k_split = (int)((kt + h->ksplit - 1) / h->ksplit);
+      k.k_split = ((k.k_split + 15) / 16) * 16;
+      k.lower_only = 1;
+      gemm_f64(k, st);
+      reduce_sym_f64(h->Kpart.p, ceil_div(kt, k.k_split), nao, Ks, st);
+      PhaseScope pe(7, st);
+      energies_f64(Ds, Js, Ks, nao, h->e.p + 2 * s, h->en_work.p, st);
+    }
+    cudaPointerAttributes pa{}, pb{};
+    DFJK_CUDA_CHECK(cudaPointerGetAttributes(&pa, EJ));
+    DFJK_CUDA_CHECK(cudaPointerGetAttributes(&pb, EK));
+    const bool dev_j = pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged;
+    const bool dev_k = pb.type == cudaMemoryTypeDevice || pb.type == cudaMemoryTypeManaged;
+    if (dev_j != dev_k) throw Error{DFJK_ERR_ARG, "E_J and E_K must both be host or both device memory"};
+    if (dev_j) {
+      split_energies_kernel<<<ceil_div(nset, 64), 64, 0, st>>>(h->e.p, nset, EJ, EK);
+      DFJK_LAUNCHED();
+      DFJK_CUDA_CHECK(cudaStreamSynchronize(st));  // W is released on return
+    } else {
+      std::vector<double> e(2 * nset);
+      DFJK_CUDA_CHECK(cudaMemcpyAsync(e.data(), h->e.p, e.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+      DFJK_CUDA_CHECK(cudaStreamSynchronize(st));
+      for (int s = 0; s < nset; ++s) {
+        EJ[s] = e[2 * s];
+        EK[s] = e[2 * s + 1];
+      }
+    }
+    return DFJK_OK;
+  } catch (const Error &e) {
+    return fail(e);
+  }
+}
+
 int dfjk_build_batch(int32_t nmol, const dfjk_handle *hs, const int32_t *nocc, const double *const *C,
                      double *const *J, double *const *K, double *EJ, double *EK, int32_t nstreams,
                      void *stream) {

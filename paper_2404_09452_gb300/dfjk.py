@@ -39,6 +39,7 @@ EXPORTS = [
     "dfjk_query_setup",
     "dfjk_build",
     "dfjk_build_uks",
+    "dfjk_build_density",
     "dfjk_build_batch",
     "dfjk_overlap",
     "dfjk_overlap_matrix",
@@ -305,6 +306,23 @@ class Handle:
             ctypes.c_void_p(C_b.data_ptr() if nb else None), ctypes.c_void_p(J.data_ptr()),
             ctypes.c_void_p(Ka.data_ptr()), ctypes.c_void_p(Kb.data_ptr()), pe, _stream(stream)))
         return J, Ka, Kb, E
+
+    def build_density(self, D, stream=None):
+        """J, K, E_J, E_K from densities D [nao x nao] or [nset x nao x nao]
+        (device FP64, symmetric), on the FP64 pipe."""
+        torch = _torch()
+        D = D.contiguous()
+        if D.dim() == 2:
+            D = D.unsqueeze(0)
+        nset = D.shape[0]
+        J = torch.empty_like(D)
+        K = torch.empty_like(D)
+        EJ, EK = np.zeros(nset), np.zeros(nset)
+        _check(load_library().dfjk_build_density(
+            self.h, nset, ctypes.c_void_p(D.data_ptr()), ctypes.c_void_p(J.data_ptr()),
+            ctypes.c_void_p(K.data_ptr()), ctypes.c_void_p(EJ.ctypes.data), ctypes.c_void_p(EK.ctypes.data),
+            _stream(stream)))
+        return J, K, EJ, EK
 
     def overlap(self, stream=None):
         torch = _torch()

@@ -157,3 +157,28 @@ def test_uks_coulomb_from_fitted_coefficients(sys_):
     for Cs, key in ((Ca, "E_K_a"), (Cb, "E_K_b")):
         M = np.einsum("mi,Pmn,nj->Pij", Cs, r["B"], Cs, optimize=True)
         assert abs(u[key] - 0.5 * np.sum(M * M)) < 1e-12 * abs(u[key])
+
+
+# ---- J and K from a density -------------------------------------------------------
+
+
+def test_density_path_equals_orbital_path(sys_):
+    """D = C C^T: the density route (K = sum_P B_P D B_P) equals the orbital
+    route (K = sum_P (B_P C)(B_P C)^T), which never forms D B_P."""
+    _, _, C, _, _, r = sys_
+    d = O.jk_from_density(r["B"], C @ C.T)
+    assert np.max(np.abs(d["J"] - r["J"])) < 1e-12 * np.abs(r["J"]).max()
+    assert np.max(np.abs(d["K"] - r["K"])) < 1e-12 * np.abs(r["K"]).max()
+    assert abs(d["E_K"] - r["E_K"]) < 1e-12 * abs(r["E_K"])
+
+
+def test_density_path_is_linear_and_signed(sys_):
+    """J and K are linear in D; for D = D1 - D2 (not positive semidefinite) the
+    result is the difference of the two orbital builds."""
+    _, _, C, _, _, r = sys_
+    n = C.shape[1]
+    C1, C2 = C[:, : (n + 1) // 2], C[:, (n + 1) // 2 :]
+    d = O.jk_from_density(r["B"], C1 @ C1.T - C2 @ C2.T)
+    r1, r2 = O.jk_from_B(r["B"], C1), O.jk_from_B(r["B"], C2)
+    assert np.max(np.abs(d["J"] - (r1["J"] - r2["J"]))) < 1e-12 * np.abs(r["J"]).max()
+    assert np.max(np.abs(d["K"] - (r1["K"] - r2["K"]))) < 1e-12 * np.abs(r["K"]).max()
