@@ -479,7 +479,7 @@ void make_resident(dfjk_ctx *h, cudaStream_t st) {
     PairClassArgs a{n, h->pair_a.p + b0, h->pair_b.p + b0, h->pair_rec_off.p + b0, h->rec.p, h->q.p + b0,
                     h->pair_npp.p + b0};
     launch_pair_kernel(cls[c][0], cls[c][1], a, orb_args(h), tab, st);
-    launch_schwarz(cls[c][0], cls[c][1], a, tab, st);
+    launch_schwarz(cls[c][0], cls[c][1], a, tab, tab32, h->opt.precision == DFJK_MIXED, st);
   }
   h->scal.alloc(1);
   max_sqrt_diag(h->V.p, h->naux, np, h->scal.p, st);

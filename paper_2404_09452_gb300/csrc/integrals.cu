@@ -44,9 +44,14 @@ void launch_pair_kernel(int la, int lb, const PairClassArgs &a, const OrbArgs &o
   DFJK_LAUNCHED();
 }
 
-void launch_schwarz(int la, int lb, const PairClassArgs &a, const double *tab, cudaStream_t st) {
+void launch_schwarz(int la, int lb, const PairClassArgs &a, const double *tab, const float *tab32, bool fp32,
+                    cudaStream_t st) {
   if (a.npair == 0) return;
-  DISPATCH_LALB(la, lb, (schwarz_kernel<A_, B_><<<a.npair, 64, 0, st>>>(a, tab)));
+  if (fp32) {
+    DISPATCH_LALB(la, lb, (schwarz_kernel<A_, B_, float><<<a.npair, 64, 0, st>>>(a, tab32)));
+  } else {
+    DISPATCH_LALB(la, lb, (schwarz_kernel<A_, B_, double><<<a.npair, 64, 0, st>>>(a, tab)));
+  }
   DFJK_LAUNCHED();
 }
 

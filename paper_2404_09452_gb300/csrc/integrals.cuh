@@ -63,7 +63,10 @@ struct OverlapArgs {
 
 void launch_pair_kernel(int la, int lb, const PairClassArgs &a, const OrbArgs &o, const double *tab,
                         cudaStream_t st);
-void launch_schwarz(int la, int lb, const PairClassArgs &a, const double *tab, cudaStream_t st);
+// fp32: the diagonal (ab|ab) on the FP32 pipe (it only decides screening and
+// the FP32 integral split, to about 1e-4 of its value).
+void launch_schwarz(int la, int lb, const PairClassArgs &a, const double *tab, const float *tab32, bool fp32,
+                    cudaStream_t st);
 void launch_eri3c_l0(int la, int lb, const Eri3cArgs &a, const AuxArgs &x, const double *tab,
                      cudaStream_t st);
 void launch_eri3c_l1(int la, int lb, const Eri3cArgs &a, const AuxArgs &x, const double *tab,

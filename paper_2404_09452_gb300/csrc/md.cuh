@@ -70,16 +70,16 @@ __device__ __forceinline__ void hermite_R(const Real *F, Real a, Real X, Real Y,
 
 // Same recursion with a runtime order (L <= 8), loops not unrolled: used by
 // the Schwarz diagonal, where compile time matters more than speed.
-static __device__ __noinline__ void hermite_R_rt(int L, const double *F, double a, double X, double Y,
-                                          double Z, double *R) {
-  double cur[ntuv(8)], nxt[ntuv(8)];
-  double pw = 1.0;
-  for (int n = 0; n < L; ++n) pw *= -2.0 * a;
+template <typename Real>
+static __device__ __noinline__ void hermite_R_rt(int L, const Real *F, Real a, Real X, Real Y, Real Z, Real *R) {
+  Real cur[ntuv(8)], nxt[ntuv(8)];
+  Real pw = 1;
+  for (int n = 0; n < L; ++n) pw *= Real(-2) * a;
   cur[0] = pw * F[L];
 #pragma unroll 1
   for (int n = L - 1; n >= 0; --n) {
-    pw = 1.0;
-    for (int k = 0; k < n; ++k) pw *= -2.0 * a;
+    pw = 1;
+    for (int k = 0; k < n; ++k) pw *= Real(-2) * a;
     nxt[0] = pw * F[n];
 #pragma unroll 1
     for (int N = 1; N <= L - n; ++N)
@@ -88,16 +88,16 @@ static __device__ __noinline__ void hermite_R_rt(int L, const double *F, double 
 #pragma unroll 1
         for (int u = N - t; u >= 0; --u) {
           const int v = N - t - u;
-          double r;
+          Real r;
           if (t > 0) {
             r = X * cur[tuv_idx(t - 1, u, v)];
-            if (t > 1) r = fma((double)(t - 1), cur[tuv_idx(t - 2, u, v)], r);
+            if (t > 1) r = fma(Real(t - 1), cur[tuv_idx(t - 2, u, v)], r);
           } else if (u > 0) {
             r = Y * cur[tuv_idx(t, u - 1, v)];
-            if (u > 1) r = fma((double)(u - 1), cur[tuv_idx(t, u - 2, v)], r);
+            if (u > 1) r = fma(Real(u - 1), cur[tuv_idx(t, u - 2, v)], r);
           } else {
             r = Z * cur[tuv_idx(t, u, v - 1)];
-            if (v > 1) r = fma((double)(v - 1), cur[tuv_idx(t, u, v - 2)], r);
+            if (v > 1) r = fma(Real(v - 1), cur[tuv_idx(t, u, v - 2)], r);
           }
           nxt[tuv_idx(t, u, v)] = r;
         }
@@ -206,32 +206,33 @@ __global__ void __launch_bounds__(128) pair_kernel(PairClassArgs args, OrbArgs o
 // of class (LA, LB): one block per pair, one thread per primitive quadruple
 // (kl, k'l') of the pair's records, then a block reduction.  Runtime loops:
 // this is a small share of the work and unrolling it costs minutes of compile.
-template <int LA, int LB>
-__global__ void __launch_bounds__(64) schwarz_kernel(PairClassArgs args, const double *__restrict__ boys_tab) {
+template <int LA, int LB, typename Real>
+__global__ void __launch_bounds__(64) schwarz_kernel(PairClassArgs args, const Real *__restrict__ boys_tab) {
   constexpr int NT = nterms(LA, LB);
   constexpr int REC = REC_HDR + NT;
   constexpr int NCA = ncart(LA), NCB = ncart(LB);
   constexpr int L4 = 2 * (LA + LB);
-  __shared__ double red[64][NCA * NCB + 1];
+  __shared__ Real red[64][NCA * NCB + 1];
   const int ip = blockIdx.x;
   const double *rec0 = args.rec + args.rec_off[ip];
   const int npp = args.npp_of[ip];
-  double diag[NCA * NCB];
-  for (int c = 0; c < NCA * NCB; ++c) diag[c] = 0.0;
+  Real diag[NCA * NCB];
+  for (int c = 0; c < NCA * NCB; ++c) diag[c] = 0;
 #pragma unroll 1
   for (int q = threadIdx.x; q < npp * npp; q += blockDim.x) {
     const double *ri = rec0 + (long long)(q / npp) * REC;
     const double *rj = rec0 + (long long)(q % npp) * REC;
-    const double p = ri[0], qq = rj[0];
-    const double s = rsqrt(p + qq);
-    const double al = p * qq * s * s;
-    const double X = ri[1] - rj[1], Y = ri[2] - rj[2], Z = ri[3] - rj[3];
-    double F[L4 + 1];
+    const Real p = (Real)ri[0], qq = (Real)rj[0];
+    const Real s = Real(1) / sqrt(p + qq);
+    const Real al = p * qq * s * s;
+    // centre differences in FP64 before rounding
+    const Real X = (Real)(ri[1] - rj[1]), Y = (Real)(ri[2] - rj[2]), Z = (Real)(ri[3] - rj[3]);
+    Real F[L4 + 1];
     boys_eval<L4>(al * (X * X + Y * Y + Z * Z), boys_tab, F);
-    double R[ntuv(8)];
-    hermite_R_rt(L4, F, al, X, Y, Z, R);
+    Real R[ntuv(8)];
+    hermite_R_rt<Real>(L4, F, al, X, Y, Z, R);
     // ri[4] rj[4] = c c K c c K (2 pi^2.5)^2 / (p q); wanted 2 pi^2.5 / (p q sqrt(p+q))
-    const double fac = ri[4] * rj[4] * s * (1.0 / (2.0 * 17.493418327624862846));
+    const Real fac = (Real)(ri[4] * rj[4] * (1.0 / (2.0 * 17.493418327624862846))) * s;
     int k = 0;
 #pragma unroll 1
     for (int ca = 0; ca < NCA; ++ca)
@@ -240,14 +241,14 @@ __global__ void __launch_bounds__(64) schwarz_kernel(PairClassArgs args, const d
         const int ax = cart_x(LA, ca), ay = cart_y(LA, ca), az = cart_z(LA, ca);
         const int bx = cart_x(LB, cb), by = cart_y(LB, cb), bz = cart_z(LB, cb);
         const int k0 = k;
-        double sum = 0.0;
+        Real sum = 0;
 #pragma unroll 1
         for (int t = 0; t <= ax + bx; ++t)
 #pragma unroll 1
           for (int u = 0; u <= ay + by; ++u)
 #pragma unroll 1
             for (int v = 0; v <= az + bz; ++v) {
-              double inner = 0.0;
+              Real inner = 0;
               int k2 = k0;
 #pragma unroll 1
               for (int t2 = 0; t2 <= ax + bx; ++t2)
@@ -255,11 +256,12 @@ __global__ void __launch_bounds__(64) schwarz_kernel(PairClassArgs args, const d
                 for (int u2 = 0; u2 <= ay + by; ++u2)
 #pragma unroll 1
                   for (int v2 = 0; v2 <= az + bz; ++v2) {
-                    const double e2 = ((t2 + u2 + v2) & 1) ? -rj[REC_HDR + k2] : rj[REC_HDR + k2];
+                    const Real e = (Real)rj[REC_HDR + k2];
+                    const Real e2 = ((t2 + u2 + v2) & 1) ? -e : e;
                     inner = fma(e2, R[tuv_idx(t + t2, u + u2, v + v2)], inner);
                     ++k2;
                   }
-              sum = fma(ri[REC_HDR + k], inner, sum);
+              sum = fma((Real)ri[REC_HDR + k], inner, sum);
               ++k;
             }
         diag[ca * NCB + cb] = fma(fac, sum, diag[ca * NCB + cb]);
@@ -271,10 +273,10 @@ __global__ void __launch_bounds__(64) schwarz_kernel(PairClassArgs args, const d
     double qmax = 0.0;
     for (int ca = 0; ca < NCA; ++ca)
       for (int cb = 0; cb < NCB; ++cb) {
-        double d = 0.0;
+        Real d = 0;
         for (int t = 0; t < 64; ++t) d += red[t][ca * NCB + cb];
         const double f = comp_factor(LA, ca) * comp_factor(LB, cb);
-        qmax = fmax(qmax, d * f * f);
+        qmax = fmax(qmax, (double)d * f * f);
       }
     args.q[ip] = sqrt(fmax(qmax, 0.0));
   }
