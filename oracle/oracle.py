@@ -280,3 +280,32 @@ def jk_from_density(B: np.ndarray, D: np.ndarray):
     J = ((B2 @ D.ravel()) @ B2).reshape(nao, nao)
     K = np.einsum("Pml,ls,Psn->mn", B, D, B, optimize=True)
     return dict(J=J, K=K, E_J=0.5 * np.sum(D * J), E_K=0.5 * np.sum(D * K))
+
+
+def coulomb_energy_geometry(basis, aux, coords, D):
+    """E_J = u^T V^-1 u / 2 with u_P = sum (P|mu nu) D_mu nu at the given atom
+    positions (the shells move with their atoms; D is held fixed in the AO
+    basis).  LU solve, no Cholesky."""
+    V = metric(aux, coords)
+    T = three_center(basis, aux, coords)
+    u = T.reshape(V.shape[0], -1) @ D.ravel()
+    return 0.5 * float(u @ np.linalg.solve(V, u))
+
+
+def coulomb_gradient_fd(basis, aux, coords, D, h: float = 2e-3):
+    """dE_J/dR for every atom and direction by central differences with
+    Richardson extrapolation (steps h and h/2, error O(h^4)): the derivative
+    taken from its definition, for checking an analytic gradient."""
+    coords = np.asarray(coords, float)
+    g = np.zeros_like(coords)
+    for a in range(coords.shape[0]):
+        for x in range(3):
+            d = []
+            for step in (h, h / 2):
+                cp, cm = coords.copy(), coords.copy()
+                cp[a, x] += step
+                cm[a, x] -= step
+                d.append((coulomb_energy_geometry(basis, aux, cp, D) -
+                          coulomb_energy_geometry(basis, aux, cm, D)) / (2 * step))
+            g[a, x] = (4 * d[1] - d[0]) / 3
+    return g
