@@ -160,6 +160,23 @@ int dfjk_build(dfjk_handle h, int32_t nset, int32_t nocc, const double *C_occ,
 int dfjk_build_density(dfjk_handle h, int32_t nset, const double *D, double *J, double *K,
                        double *E_J, double *E_K, void *stream);
 
+/* Nuclear gradient of the density-fitted Coulomb energy at fixed density,
+ * E_J = u^T V^-1 u / 2 with u_P = sum_{mu nu} (P|mu nu) D_mu nu (the E_J of
+ * dfjk_build / dfjk_build_density): the Coulomb part of the analytic
+ * density-fitted SCF gradient, one of the three modules the paper benchmarks
+ * (SCF, gradient, Hessian), computed as
+ *   dE_J/dR = sum_P d_P du_P/dR - d^T (dV/dR) d / 2,   d = V^-1 u = L^-T rho,
+ * with derivative 3-centre and 2-centre integrals in FP64 (the handle's
+ * precision does not matter) over the kept shell pairs.  The AO density is
+ * held fixed (no orbital response or overlap-derivative term: those belong to
+ * the full SCF gradient, not to the Coulomb build).
+ *   D    : device nao x nao FP64, symmetric (e.g. C C^T).
+ *   grad : device natom x 3 FP64, overwritten; atoms in the order of the
+ *          coordinates given to dfjk_setup.
+ * Allocates small work buffers and synchronises the stream before returning.
+ * Errors: DFJK_ERR_ARG, _UNSUPPORTED (memory-lean handle), _OOM, _CUDA.      */
+int dfjk_coulomb_gradient(dfjk_handle h, const double *D, double *grad, void *stream);
+
 /* Spin-unrestricted build: two occupied sets, alpha and beta, with their own
  * counts (the unrestricted case the paper's code supports alongside the
  * restricted one).  D_a = C_a C_a^T, D_b = C_b C_b^T.

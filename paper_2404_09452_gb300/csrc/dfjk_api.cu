@@ -13,6 +13,7 @@
 
 #include "boys.cuh"
 #include "common.cuh"
+#include "grad.cuh"
 #include "integrals.cuh"
 #include "linalg.cuh"
 #include "ozaki.cuh"
@@ -175,7 +176,7 @@ const float *boys_table_device_f32() {
 
 struct HostBasis {
   int nshell = 0, nfunc = 0;
-  std::vector<int> l, nprim, prim_off, func_off;
+  std::vector<int> l, nprim, prim_off, func_off, atom;
   std::vector<double> exps, coefs_raw, coefs, center;  // coefs: normalised radial
 };
 
@@ -193,6 +194,7 @@ static void read_basis(const dfjk_basis *b, int natom, const double *coords, Hos
     if (sh.atom < 0 || sh.atom >= natom) throw Error{DFJK_ERR_ARG, std::string(what) + ": atom index"};
     if (!sh.exps || !sh.coefs) throw Error{DFJK_ERR_ARG, std::string(what) + ": null exps/coefs"};
     hb.l.push_back(sh.l);
+    hb.atom.push_back(sh.atom);
     hb.nprim.push_back(sh.nprim);
     hb.prim_off.push_back((int)hb.exps.size());
     hb.func_off.push_back(hb.nfunc);
@@ -1160,6 +1162,58 @@ int dfjk_build_density(dfjk_handle h, int32_t nset, const double *D, double *J, 
         EK[s] = e[2 * s + 1];
       }
     }
+    return DFJK_OK;
+  } catch (const Error &e) {
+    return fail(e);
+  }
+}
+
+int dfjk_coulomb_gradient(dfjk_handle h, const double *D, double *grad, void *stream) {
+  try {
+    if (!h || !D || !grad) throw Error{DFJK_ERR_ARG, "coulomb_gradient arguments"};
+    cudaStream_t st = S(stream);
+    DFJK_CUDA_CHECK(cudaSetDevice(h->device));
+    if (!h->resident) make_resident(h, st);
+    if (h->lean) throw Error{DFJK_ERR_UNSUPPORTED, "coulomb_gradient needs B stored in full (not memory-lean)"};
+    const int nao = h->nao, np = h->naux_pad;
+    const double *tab = boys_table_device();
+    // rho = B vec D (= L^-1 u), then the fitted coefficients d = L^-T rho = V^-1 u
+    DBuf<double> rho, work, d;
+    rho.alloc(np);
+    work.alloc(std::max<size_t>((size_t)128 * ceil_div(np, 256) * 256, np));
+    d.alloc(np);
+    DFJK_CUDA_CHECK(cudaMemsetAsync(d.p, 0, d.bytes(), st));
+    rho_gemv_f64(h->B.p, h->ldb, nao, np, D, rho.p, work.p, 128, st);
+    fitted_coefficients(h->L.p, h->naux, np, rho.p, work.p, d.p, st);
+    DBuf<int> oat, aat, al;
+    oat.upload(h->orb.atom, st);
+    aat.upload(h->aux.atom, st);
+    al.upload(h->aux.l, st);
+    DFJK_CUDA_CHECK(cudaMemsetAsync(grad, 0, sizeof(double) * 3 * (size_t)h->natom, st));
+    GradArgs g{};
+    g.pair_a = h->pair_a.p;
+    g.pair_b = h->pair_b.p;
+    g.pair_chunk = 8;
+    g.d = d.p;
+    g.D = D;
+    g.nao = nao;
+    g.orb_atom = oat.p;
+    g.aux_atom = aat.p;
+    g.grad = grad;
+    static const int cls[6][2] = {{0, 0}, {1, 0}, {1, 1}, {2, 0}, {2, 1}, {2, 2}};
+    for (int c = 0; c < 6; ++c) {
+      const int lo = h->kept_cls_begin[c], hi = h->kept_cls_begin[c + 1];
+      if (hi <= lo) continue;
+      for (int lc = 0; lc < 3; ++lc) {
+        g.pairs = h->kept.p + lo;
+        g.npairs = hi - lo;
+        g.aux_shells = h->aux_cls[lc].p;
+        g.naux_shells = h->aux_cls_n[lc];
+        launch_grad3c(cls[c][0], cls[c][1], lc, g, orb_args(h), aux_args(h), tab, st);
+      }
+    }
+    launch_grad2c(g, aux_args(h), al.p, h->aux.nshell, tab, st);
+    DFJK_CUDA_CHECK(cudaStreamSynchronize(st));  // local buffers are released on return
     return DFJK_OK;
   } catch (const Error &e) {
     return fail(e);

@@ -1,0 +1,34 @@
+// Nuclear gradient of the density-fitted Coulomb energy (grad.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "integrals.cuh"
+
+namespace dfjk {
+
+struct GradArgs {
+  const int *pairs;  // global ids of the kept pairs of one class
+  int npairs;
+  const int *pair_a, *pair_b;  // shells of a pair, by global id
+  int pair_chunk;              // pairs per block
+  const int *aux_shells;       // aux shell ids of one class
+  int naux_shells;
+  const double *d;  // fitted coefficients V^-1 u, one per aux function
+  const double *D;  // density, nao x nao row-major
+  int nao;
+  const int *orb_atom, *aux_atom;  // atom of each shell
+  double *grad;                    // natom x 3, accumulated with atomicAdd
+};
+
+// d = L^-T rho by back substitution (L lower triangular, row-major, ld).
+void fitted_coefficients(const double *L, int n, int ld, const double *rho, double *work, double *d,
+                         cudaStream_t st);
+// sum_P d_P sum_{mu nu} D_mu nu d(P|mu nu)/dR for pair class (la, lb), aux class lc.
+void launch_grad3c(int la, int lb, int lc, const GradArgs &a, const OrbArgs &o, const AuxArgs &x,
+                   const double *tab, cudaStream_t st);
+// -d^T (dV/dR) d / 2 over all aux shells (aux_l: l of each shell).
+void launch_grad2c(const GradArgs &a, const AuxArgs &x, const int *aux_l, int nshell, const double *tab,
+                   cudaStream_t st);
+
+}  // namespace dfjk

@@ -40,6 +40,7 @@ EXPORTS = [
     "dfjk_build",
     "dfjk_build_uks",
     "dfjk_build_density",
+    "dfjk_coulomb_gradient",
     "dfjk_build_batch",
     "dfjk_overlap",
     "dfjk_overlap_matrix",
@@ -123,6 +124,7 @@ def load_library(path: str = LIB_PATH):
     ]
     lib.dfjk_build.argtypes = [vp, i32, i32, vp, vp, vp, vp, vp, vp]
     lib.dfjk_overlap.argtypes = [vp, vp, vp]
+    lib.dfjk_coulomb_gradient.argtypes = [vp, vp, vp, vp]
     lib.dfjk_overlap_matrix.argtypes = [ctypes.POINTER(BasisC), i32, f64p, vp, vp]
     lib.dfjk_build_batch.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, i32, vp]
     lib.dfjk_evict.argtypes = [vp]
@@ -218,6 +220,7 @@ class Handle:
         self._orb = _BasisHolder(mol.orb)
         self._aux = _BasisHolder(mol.aux)
         xyz = np.ascontiguousarray(mol.coords, dtype=np.float64)
+        self.natom = int(xyz.shape[0])
         opt = default_options(precision, schwarz_thresh, hbm_budget_bytes, timeout_iters=timeout_iters,
                               fp32_pair_thresh=fp32_pair_thresh, b_on_host=b_on_host)
         h = ctypes.c_void_p()
@@ -323,6 +326,16 @@ class Handle:
             ctypes.c_void_p(K.data_ptr()), ctypes.c_void_p(EJ.ctypes.data), ctypes.c_void_p(EK.ctypes.data),
             _stream(stream)))
         return J, K, EJ, EK
+
+    def coulomb_gradient(self, D, stream=None):
+        """dE_J/dR [natom x 3] at fixed density D [nao x nao] (device FP64,
+        symmetric), E_J = u^T V^-1 u / 2 with u = (P|mu nu) D."""
+        torch = _torch()
+        D = D.contiguous()
+        g = torch.empty((self.natom, 3), dtype=torch.float64, device=D.device)
+        _check(load_library().dfjk_coulomb_gradient(
+            self.h, ctypes.c_void_p(D.data_ptr()), ctypes.c_void_p(g.data_ptr()), _stream(stream)))
+        return g
 
     def overlap(self, stream=None):
         torch = _torch()

@@ -1,0 +1,66 @@
+"""dfjk_coulomb_gradient against the oracle's finite-difference gradient of
+E_J = u^T V^-1 u / 2 (density held fixed): FP64 and mixed handles, a density
+that is not C C^T, one atom (zero gradient), and translation invariance."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2404_09452_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2404_09452_gb300 import dfjk  # noqa: E402
+
+# Richardson-extrapolated central differences are good to ~1e-9 here; the
+# analytic gradient is FP64 throughout.
+GRAD_TOL = 1e-7
+
+
+def _density(m, seed=3000):
+    S = O.overlap(m.orb, m.coords)
+    C = I.orthonormalize(I.c_occ_raw(m.nao, I.default_nocc(m.nao), seed), S)
+    return C @ C.T
+
+
+def _check(m, D, precision):
+    h = dfjk.Handle(m, precision=precision)
+    g = h.coulomb_gradient(torch.from_numpy(D).cuda()).cpu().numpy()
+    h.close()
+    ref = O.coulomb_gradient_fd(m.orb, m.aux, m.coords, D)
+    err = np.max(np.abs(g - ref))
+    assert err < GRAD_TOL * max(1.0, np.abs(ref).max()), (err, g, ref)
+    assert np.max(np.abs(g.sum(axis=0))) < 1e-10 * max(1.0, np.abs(g).max())
+    return g
+
+
+@pytest.mark.parametrize("precision", [dfjk.DFJK_FP64, dfjk.DFJK_MIXED])
+def test_gradient_water(precision):
+    m = I.water()
+    _check(m, _density(m), precision)
+
+
+@pytest.mark.parametrize("precision", [dfjk.DFJK_FP64, dfjk.DFJK_MIXED])
+def test_gradient_six_atoms(precision):
+    m = I.molecule(6, seed=1006)
+    _check(m, _density(m), precision)
+
+
+def test_gradient_indefinite_density():
+    m = I.molecule(4, seed=1004)
+    S = O.overlap(m.orb, m.coords)
+    C = I.orthonormalize(I.c_occ_raw(m.nao, I.default_nocc(m.nao), 3001), S)
+    n = C.shape[1]
+    D = C[:, : n // 2] @ C[:, : n // 2].T - 0.5 * C[:, n // 2 :] @ C[:, n // 2 :].T
+    _check(m, D, dfjk.DFJK_FP64)
+
+
+def test_gradient_single_atom_is_zero():
+    m = I.molecule(1, seed=1001)
+    h = dfjk.Handle(m, precision=dfjk.DFJK_FP64)
+    g = h.coulomb_gradient(torch.from_numpy(_density(m)).cuda()).cpu().numpy()
+    h.close()
+    assert g.shape == (1, 3) and np.max(np.abs(g)) < 1e-10
