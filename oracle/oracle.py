@@ -13,6 +13,8 @@ dense steps from NumPy/SciPy FP64 LAPACK/BLAS, in the order of the method:
   O8  rho = B vec(D);  J = B^T rho
   O9  X_P = B_P C;     K = sum_P X_P X_P^T
   O10 E_J = Tr(D J)/2, E_K = Tr(D K)/2
+  O11 dE_J/dR, dE_K/dR at fixed D: central differences of O3-O10 with the
+      shells moved with their atoms (the definition of the derivative)
 
 The paper (Introduction, contribution 1) says only that density fitting first
 evaluates 3-centre integrals and then reduces to tensor contractions; it prints
@@ -292,10 +294,21 @@ def coulomb_energy_geometry(basis, aux, coords, D):
     return 0.5 * float(u @ np.linalg.solve(V, u))
 
 
-def coulomb_gradient_fd(basis, aux, coords, D, h: float = 2e-3):
-    """dE_J/dR for every atom and direction by central differences with
-    Richardson extrapolation (steps h and h/2, error O(h^4)): the derivative
-    taken from its definition, for checking an analytic gradient."""
+def exchange_energy_geometry(basis, aux, coords, D):
+    """E_K = sum_PQ (V^-1)_PQ Tr(D T_P D T_Q) / 2 at the given atom positions,
+    D held fixed: the same E_K as Tr(D K)/2 with K = sum_P B_P D B_P, written
+    without B.  LU solve, no Cholesky."""
+    V = metric(aux, coords)
+    T = three_center(basis, aux, coords)
+    A = np.einsum("mn,Pnl->Pml", D, T)  # A_P = D T_P
+    M = np.einsum("Pmn,Qnm->PQ", A, A)  # Tr(D T_P D T_Q)
+    return 0.5 * float(np.trace(np.linalg.solve(V, M)))
+
+
+def gradient_fd(energy, coords, h: float = 2e-3):
+    """d energy(coords)/dR for every atom and direction by central differences
+    with Richardson extrapolation (steps h and h/2, error O(h^4)): the
+    derivative taken from its definition, for checking an analytic gradient."""
     coords = np.asarray(coords, float)
     g = np.zeros_like(coords)
     for a in range(coords.shape[0]):
@@ -305,7 +318,16 @@ def coulomb_gradient_fd(basis, aux, coords, D, h: float = 2e-3):
                 cp, cm = coords.copy(), coords.copy()
                 cp[a, x] += step
                 cm[a, x] -= step
-                d.append((coulomb_energy_geometry(basis, aux, cp, D) -
-                          coulomb_energy_geometry(basis, aux, cm, D)) / (2 * step))
+                d.append((energy(cp) - energy(cm)) / (2 * step))
             g[a, x] = (4 * d[1] - d[0]) / 3
     return g
+
+
+def coulomb_gradient_fd(basis, aux, coords, D, h: float = 2e-3):
+    """dE_J/dR at fixed D by Richardson-extrapolated central differences."""
+    return gradient_fd(lambda c: coulomb_energy_geometry(basis, aux, c, D), coords, h)
+
+
+def exchange_gradient_fd(basis, aux, coords, D, h: float = 2e-3):
+    """dE_K/dR at fixed D by Richardson-extrapolated central differences."""
+    return gradient_fd(lambda c: exchange_energy_geometry(basis, aux, c, D), coords, h)
