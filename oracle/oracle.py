@@ -295,14 +295,17 @@ def coulomb_energy_geometry(basis, aux, coords, D):
 
 
 def exchange_energy_geometry(basis, aux, coords, D):
-    """E_K = sum_PQ (V^-1)_PQ Tr(D T_P D T_Q) / 2 at the given atom positions,
-    D held fixed: the same E_K as Tr(D K)/2 with K = sum_P B_P D B_P, written
-    without B.  LU solve, no Cholesky."""
+    """E_K = sum_P Tr(D B_P D B_P) / 2 at the given atom positions, D held
+    fixed, B = L^-1 T (steps O3-O6, O10 with K = sum_P B_P D B_P).  The
+    algebraically equal sum_PQ (V^-1)_PQ Tr(D T_P D T_Q) / 2 through a solve
+    with V loses ~1e-8 to cancellation when V is ill-conditioned (cond ~1e8
+    at six atoms), which finite differences turn into ~1e-5 errors."""
     V = metric(aux, coords)
     T = three_center(basis, aux, coords)
-    A = np.einsum("mn,Pnl->Pml", D, T)  # A_P = D T_P
-    M = np.einsum("Pmn,Qnm->PQ", A, A)  # Tr(D T_P D T_Q)
-    return 0.5 * float(np.trace(np.linalg.solve(V, M)))
+    L = np.linalg.cholesky(V)
+    B = scipy.linalg.solve_triangular(L, T.reshape(V.shape[0], -1), lower=True).reshape(T.shape)
+    A = np.einsum("mn,Pnl->Pml", D, B)  # D B_P
+    return 0.5 * float(np.einsum("Pmn,Pnm->", A, A))
 
 
 def gradient_fd(energy, coords, h: float = 2e-3):

@@ -63,3 +63,15 @@ def test_one_occupied_orbital_exchange_is_coulomb():
     gj = O.coulomb_gradient_fd(m.orb, m.aux, m.coords, D)
     gk = O.exchange_gradient_fd(m.orb, m.aux, m.coords, D)
     assert np.max(np.abs(gj - gk)) < 1e-9 * max(1.0, np.abs(gj).max())
+
+
+def test_exchange_gradient_step_independent():
+    """Roundoff in the energy would show as a step-size dependence of the
+    extrapolated difference (it grows like 1/h); truncation shrinks like h^4."""
+    m = I.molecule(4, seed=1004)
+    S = O.overlap(m.orb, m.coords)
+    C = I.orthonormalize(I.c_occ_raw(m.nao, I.default_nocc(m.nao), 3000), S)
+    D = C @ C.T
+    g1 = O.exchange_gradient_fd(m.orb, m.aux, m.coords, D, h=2e-3)
+    g2 = O.exchange_gradient_fd(m.orb, m.aux, m.coords, D, h=5e-4)
+    assert np.max(np.abs(g1 - g2)) < 1e-8 * max(1.0, np.abs(g1).max())
