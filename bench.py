@@ -70,7 +70,9 @@ def parse():
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
     ap.add_argument("--fp64-steps", type=int, default=2,
                     help="mixed runs: steps of the plain FP64 path timed alongside (0: skip)")
-    ap.add_argument("--workload", default="mol60", choices=list(WORKLOADS) + ["batch", "serve"])
+    ap.add_argument("--workload", default="mol60", choices=list(WORKLOADS) + ["batch", "serve", "gradient"])
+    ap.add_argument("--grad-mol", default="mol60", choices=list(WORKLOADS),
+                    help="molecule of --workload gradient")
     ap.add_argument("--batch-n", type=int, default=256)
     ap.add_argument("--compare-fp64", action="store_true",
                     help="batch/serve: also time the plain FP64 per-molecule path")
@@ -496,6 +498,42 @@ def run_batch_mode(args):
     print(json.dumps(out), flush=True)
 
 
+def run_gradient_mode(args):
+    """Nuclear gradient of E_J - E_K / 2 at fixed D = C C^T (derivative 3c and
+    2c integrals, FP64), after the setup; also the Coulomb-only gradient."""
+    import torch
+
+    from paper_2404_09452_gb300 import dfjk
+
+    m, nocc = make_molecule(args.grad_mol)
+    C = _orthonormal_cs([m], 3000)[0][:, :nocc].contiguous()
+    prec = dfjk.DFJK_MIXED if args.precision == "mixed" else dfjk.DFJK_FP64
+    h = dfjk.Handle(m, precision=prec)
+    res = {}
+    for name, ck in (("jk", -0.5), ("j", 0.0)):
+        for _ in range(args.warmup):
+            h.jk_gradient(C, 1.0, ck)
+        torch.cuda.synchronize()
+        n0 = dfjk.launch_count()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            g = h.jk_gradient(C, 1.0, ck)
+        e1.record()
+        torch.cuda.synchronize()
+        res[name] = (e0.elapsed_time(e1) / args.steps, (dfjk.launch_count() - n0) // args.steps)
+    h.close()
+    out = {"metric": "DF J/K nuclear gradients/s (after setup)", "value": 1e3 / res["jk"][0],
+           "unit": "gradients/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": res["jk"][0], "higher_is_better": True, "scaling": "weak", "dtype": "f64",
+           "data": "synthetic",
+           "config": {"workload": WORKLOADS[args.grad_mol]["note"], "energy": "E_J - E_K/2",
+                      "handle_precision": args.precision},
+           "ms_coulomb_only": res["j"][0], "gpu_launches": int(res["jk"][1]),
+           "max_abs_grad": float(g.abs().max())}
+    print(json.dumps(out), flush=True)
+
+
 def run_serve_mode(args):
     """Row a11: Poisson requests over a pool of molecules (atom counts
     log-uniform in [5, serve-max-atoms]), 70 % repeats of resident molecules,
@@ -554,6 +592,8 @@ def main():
         run_batch_mode(args)
     elif args.workload == "serve":
         run_serve_mode(args)
+    elif args.workload == "gradient":
+        run_gradient_mode(args)
     else:
         run_ours(args)
 

@@ -177,6 +177,22 @@ int dfjk_build_density(dfjk_handle h, int32_t nset, const double *D, double *J, 
  * Errors: DFJK_ERR_ARG, _UNSUPPORTED (memory-lean handle), _OOM, _CUDA.      */
 int dfjk_coulomb_gradient(dfjk_handle h, const double *D, double *grad, void *stream);
 
+/* Nuclear gradient of c_j E_J + c_k E_K at fixed D = C C^T, E_J and E_K as
+ * returned by dfjk_build (E_K = Tr(D K)/2, K = sum_P B_P D B_P).  Both are
+ * E = sum_PQ (V^-1)_PQ M_PQ / 2 with M_PQ = u_P u_Q or Tr(D T_P D T_Q), so
+ *   dE/dR = sum_P Tr(G_P dT_P/dR) - Tr(W dV/dR) / 2,
+ * G_P = d_P D (J) or C Z_P C^T (K), W = d d^T (J) or Z Z^T (K), with
+ * Z_P = sum_Q (L^-1)_QP C^T B_Q C (nocc x nocc per aux function).  FP64 on the
+ * CUDA cores; the K part forms Z, W (naux_pad^2) and G (naux_pad x nao^2
+ * doubles, the size of B) for the duration of the call.
+ *   C_occ : device nao x nocc FP64 row-major, 1 <= nocc <= nao.
+ *   c_j, c_k : finite weights of E_J and E_K (c_k = 0 skips the K part).
+ *   grad : device natom x 3 FP64, overwritten.
+ * Synchronises the stream.  Errors: DFJK_ERR_ARG, _UNSUPPORTED (memory-lean
+ * handle), _OOM, _CUDA.                                                      */
+int dfjk_jk_gradient(dfjk_handle h, int32_t nocc, const double *C_occ, double c_j, double c_k, double *grad,
+                     void *stream);
+
 /* Spin-unrestricted build: two occupied sets, alpha and beta, with their own
  * counts (the unrestricted case the paper's code supports alongside the
  * restricted one).  D_a = C_a C_a^T, D_b = C_b C_b^T.

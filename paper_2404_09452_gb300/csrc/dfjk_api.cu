@@ -1168,52 +1168,137 @@ int dfjk_build_density(dfjk_handle h, int32_t nset, const double *D, double *J, 
   }
 }
 
+// d(cj E_J + ck E_K)/dR at fixed D = C C^T (or the given D when ck = 0).
+// E = sum_PQ (V^-1)_PQ M_PQ / 2 for both energies, M_PQ = u_P u_Q (J) or
+// Tr(D T_P D T_Q) (K), so dE/dR = sum_P Tr(Gam_P dT_P/dR) - Tr(Wt dV/dR) / 2
+// with Gam_P = (V^-1 M-side)_P: d_P D for J and D (L^-T B)_P D = C Z_P C^T for
+// K, Z_P = sum_Q (L^-1)_QP C^T B_Q C; Wt = d d^T for J and Z Z^T for K.
+static void jk_gradient(dfjk_ctx *h, const double *Din, int nocc, const double *C, double cj, double ck,
+                 double *grad, cudaStream_t st) {
+  DFJK_CUDA_CHECK(cudaSetDevice(h->device));
+  if (!h->resident) make_resident(h, st);
+  if (h->lean) throw Error{DFJK_ERR_UNSUPPORTED, "gradient needs B stored in full (not memory-lean)"};
+  const int nao = h->nao, np = h->naux_pad;
+  const double *tab = boys_table_device();
+  DBuf<double> Dl;
+  const double *D = Din;
+  if (!D) {  // D = C C^T
+    Dl.alloc((size_t)nao * nao);
+    GemmArgs dd;
+    dd.M = nao; dd.N = nao; dd.K = nocc;
+    dd.A = C; dd.sAm = nocc; dd.sAk = 1;
+    dd.B = C; dd.sBn = nocc; dd.sBk = 1;
+    dd.C = Dl.p; dd.sCm = nao; dd.sCn = 1;
+    gemm_f64(dd, st);
+    D = Dl.p;
+  }
+  // rho = B vec D (= L^-1 u), then the fitted coefficients d = L^-T rho = V^-1 u
+  DBuf<double> rho, work, d;
+  rho.alloc(np);
+  work.alloc(std::max<size_t>((size_t)128 * ceil_div(np, 256) * 256, np));
+  d.alloc(np);
+  DFJK_CUDA_CHECK(cudaMemsetAsync(d.p, 0, d.bytes(), st));
+  rho_gemv_f64(h->B.p, h->ldb, nao, np, D, rho.p, work.p, 128, st);
+  fitted_coefficients(h->L.p, h->naux, np, rho.p, work.p, d.p, st);
+  DBuf<double> gam, W;
+  if (ck != 0.0) {
+    const long long no2 = (long long)nocc * nocc;
+    DBuf<double> X, Xt, Z;
+    X.alloc((size_t)nao * np * nocc);
+    Xt.alloc((size_t)np * no2);
+    Z.alloc((size_t)np * no2);
+    GemmArgs x;  // X[mu][P][i] = sum_nu B[(mu,nu)][P] C[nu][i]
+    x.M = np; x.N = nocc; x.K = nao; x.batch = nao;
+    x.A = h->B.p; x.sAm = 1; x.sAk = h->ldb; x.sAb = (long long)nao * h->ldb;
+    x.B = C; x.sBn = 1; x.sBk = nocc; x.sBb = 0;
+    x.C = X.p; x.sCm = nocc; x.sCn = 1; x.sCb = (long long)np * nocc;
+    gemm_f64(x, st);
+    GemmArgs t;  // Xt[P][i][j] = sum_mu C[mu][i] X[mu][P][j]
+    t.M = nocc; t.N = nocc; t.K = nao; t.batch = np;
+    t.A = C; t.sAm = 1; t.sAk = nocc; t.sAb = 0;
+    t.B = X.p; t.sBn = 1; t.sBk = (long long)np * nocc; t.sBb = nocc;
+    t.C = Xt.p; t.sCm = nocc; t.sCn = 1; t.sCb = no2;
+    gemm_f64(t, st);
+    GemmArgs z;  // Z[P][ij] = sum_Q Linv[Q][P] Xt[Q][ij]
+    z.M = np; z.N = (int)no2; z.K = np;
+    z.A = h->Linv.p; z.sAm = 1; z.sAk = np;
+    z.B = Xt.p; z.sBn = 1; z.sBk = no2;
+    z.C = Z.p; z.sCm = no2; z.sCn = 1;
+    gemm_f64(z, st);
+    W.alloc((size_t)np * np);
+    GemmArgs w;  // W = Z Z^T
+    w.M = np; w.N = np; w.K = (int)no2;
+    w.A = Z.p; w.sAm = no2; w.sAk = 1;
+    w.B = Z.p; w.sBn = no2; w.sBk = 1;
+    w.C = W.p; w.sCm = np; w.sCn = 1;
+    gemm_f64(w, st);
+    GemmArgs y;  // Y[P][mu][j] = sum_i C[mu][i] Z[P][i][j]   (Y reuses X)
+    y.M = nao; y.N = nocc; y.K = nocc; y.batch = np;
+    y.A = C; y.sAm = nocc; y.sAk = 1; y.sAb = 0;
+    y.B = Z.p; y.sBn = 1; y.sBk = nocc; y.sBb = no2;
+    y.C = X.p; y.sCm = nocc; y.sCn = 1; y.sCb = (long long)nao * nocc;
+    gemm_f64(y, st);
+    gam.alloc((size_t)np * nao * nao);
+    GemmArgs gm;  // Gam[P][mu][nu] = sum_j Y[P][mu][j] C[nu][j]
+    gm.M = nao; gm.N = nao; gm.K = nocc; gm.batch = np;
+    gm.A = X.p; gm.sAm = nocc; gm.sAk = 1; gm.sAb = (long long)nao * nocc;
+    gm.B = C; gm.sBn = nocc; gm.sBk = 1; gm.sBb = 0;
+    gm.C = gam.p; gm.sCm = nao; gm.sCn = 1; gm.sCb = (long long)nao * nao;
+    gemm_f64(gm, st);
+    DFJK_CUDA_CHECK(cudaStreamSynchronize(st));  // X, Xt, Z are released here
+  }
+  DBuf<int> oat, aat, al;
+  oat.upload(h->orb.atom, st);
+  aat.upload(h->aux.atom, st);
+  al.upload(h->aux.l, st);
+  DFJK_CUDA_CHECK(cudaMemsetAsync(grad, 0, sizeof(double) * 3 * (size_t)h->natom, st));
+  GradArgs g{};
+  g.pair_a = h->pair_a.p;
+  g.pair_b = h->pair_b.p;
+  g.pair_chunk = 8;
+  g.d = d.p;
+  g.D = D;
+  g.nao = nao;
+  g.cj = cj;
+  g.gam = gam.p;
+  g.W = W.p;
+  g.ldw = np;
+  g.ck = ck;
+  g.orb_atom = oat.p;
+  g.aux_atom = aat.p;
+  g.grad = grad;
+  static const int cls[6][2] = {{0, 0}, {1, 0}, {1, 1}, {2, 0}, {2, 1}, {2, 2}};
+  for (int c = 0; c < 6; ++c) {
+    const int lo = h->kept_cls_begin[c], hi = h->kept_cls_begin[c + 1];
+    if (hi <= lo) continue;
+    for (int lc = 0; lc < 3; ++lc) {
+      g.pairs = h->kept.p + lo;
+      g.npairs = hi - lo;
+      g.aux_shells = h->aux_cls[lc].p;
+      g.naux_shells = h->aux_cls_n[lc];
+      launch_grad3c(cls[c][0], cls[c][1], lc, g, orb_args(h), aux_args(h), tab, st);
+    }
+  }
+  launch_grad2c(g, aux_args(h), al.p, h->aux.nshell, tab, st);
+  DFJK_CUDA_CHECK(cudaStreamSynchronize(st));  // local buffers are released on return
+}
+
 int dfjk_coulomb_gradient(dfjk_handle h, const double *D, double *grad, void *stream) {
   try {
     if (!h || !D || !grad) throw Error{DFJK_ERR_ARG, "coulomb_gradient arguments"};
-    cudaStream_t st = S(stream);
-    DFJK_CUDA_CHECK(cudaSetDevice(h->device));
-    if (!h->resident) make_resident(h, st);
-    if (h->lean) throw Error{DFJK_ERR_UNSUPPORTED, "coulomb_gradient needs B stored in full (not memory-lean)"};
-    const int nao = h->nao, np = h->naux_pad;
-    const double *tab = boys_table_device();
-    // rho = B vec D (= L^-1 u), then the fitted coefficients d = L^-T rho = V^-1 u
-    DBuf<double> rho, work, d;
-    rho.alloc(np);
-    work.alloc(std::max<size_t>((size_t)128 * ceil_div(np, 256) * 256, np));
-    d.alloc(np);
-    DFJK_CUDA_CHECK(cudaMemsetAsync(d.p, 0, d.bytes(), st));
-    rho_gemv_f64(h->B.p, h->ldb, nao, np, D, rho.p, work.p, 128, st);
-    fitted_coefficients(h->L.p, h->naux, np, rho.p, work.p, d.p, st);
-    DBuf<int> oat, aat, al;
-    oat.upload(h->orb.atom, st);
-    aat.upload(h->aux.atom, st);
-    al.upload(h->aux.l, st);
-    DFJK_CUDA_CHECK(cudaMemsetAsync(grad, 0, sizeof(double) * 3 * (size_t)h->natom, st));
-    GradArgs g{};
-    g.pair_a = h->pair_a.p;
-    g.pair_b = h->pair_b.p;
-    g.pair_chunk = 8;
-    g.d = d.p;
-    g.D = D;
-    g.nao = nao;
-    g.orb_atom = oat.p;
-    g.aux_atom = aat.p;
-    g.grad = grad;
-    static const int cls[6][2] = {{0, 0}, {1, 0}, {1, 1}, {2, 0}, {2, 1}, {2, 2}};
-    for (int c = 0; c < 6; ++c) {
-      const int lo = h->kept_cls_begin[c], hi = h->kept_cls_begin[c + 1];
-      if (hi <= lo) continue;
-      for (int lc = 0; lc < 3; ++lc) {
-        g.pairs = h->kept.p + lo;
-        g.npairs = hi - lo;
-        g.aux_shells = h->aux_cls[lc].p;
-        g.naux_shells = h->aux_cls_n[lc];
-        launch_grad3c(cls[c][0], cls[c][1], lc, g, orb_args(h), aux_args(h), tab, st);
-      }
-    }
-    launch_grad2c(g, aux_args(h), al.p, h->aux.nshell, tab, st);
-    DFJK_CUDA_CHECK(cudaStreamSynchronize(st));  // local buffers are released on return
+    jk_gradient(h, D, 0, nullptr, 1.0, 0.0, grad, S(stream));
+    return DFJK_OK;
+  } catch (const Error &e) {
+    return fail(e);
+  }
+}
+
+int dfjk_jk_gradient(dfjk_handle h, int32_t nocc, const double *C_occ, double c_j, double c_k, double *grad,
+                     void *stream) {
+  try {
+    if (!h || !C_occ || !grad || nocc < 1 || nocc > h->nao || !std::isfinite(c_j) || !std::isfinite(c_k))
+      throw Error{DFJK_ERR_ARG, "jk_gradient arguments"};
+    jk_gradient(h, nullptr, nocc, C_occ, c_j, c_k, grad, S(stream));
     return DFJK_OK;
   } catch (const Error &e) {
     return fail(e);

@@ -37,13 +37,17 @@ __global__ void __launch_bounds__(128) grad3c_kernel(GradArgs g, OrbArgs orb, Au
   const double Cx = aux.center[3 * sc], Cy = aux.center[3 * sc + 1], Cz = aux.center[3 * sc + 2];
   const int pc0 = aux.prim_off[sc], nc = active ? aux.nprim[sc] : 0;
   double dP[NCC];
-  for (int cc = 0; cc < NCC; ++cc) dP[cc] = active ? g.d[aux.func_off[sc] + cc] : 0.0;
+  for (int cc = 0; cc < NCC; ++cc) dP[cc] = active ? g.cj * g.d[aux.func_off[sc] + cc] : 0.0;
+  const long long nao2 = (long long)g.nao * g.nao;
+  const double *gP = g.gam ? g.gam + (long long)(active ? aux.func_off[sc] : 0) * nao2 : nullptr;
   double gC[3] = {0.0, 0.0, 0.0};
   const int p0 = blockIdx.x * g.pair_chunk, p1 = min(g.npairs, p0 + g.pair_chunk);
 #pragma unroll 1
   for (int ip = p0; ip < p1; ++ip) {
     const int pair = g.pairs[ip];
     const int sa = g.pair_a[pair], sb = g.pair_b[pair];
+    const int mu0 = orb.func_off[sa], nu0 = orb.func_off[sb];
+    const double kf = g.ck * (sa == sb ? 1.0 : 2.0);
     __syncthreads();
     if (tid < NCA * NCB) {
       const int mu = orb.func_off[sa] + tid / NCB, nu = orb.func_off[sb] + tid % NCB;
@@ -116,12 +120,14 @@ __global__ void __launch_bounds__(128) grad3c_kernel(GradArgs g, OrbArgs orb, Au
                     }
                 W[tuv_idx(t, u, v)] = w;
               }
-          const double wc = pt * dP[cc] * comp_factor(LC, cc);
+          const double wc = pt * comp_factor(LC, cc);
 #pragma unroll 1
           for (int ca = 0; ca < NCA; ++ca)
 #pragma unroll 1
             for (int cb = 0; cb < NCB; ++cb) {
-              const double wt = wc * sD[ca * NCB + cb] * comp_factor(LA, ca) * comp_factor(LB, cb);
+              double wj = dP[cc] * sD[ca * NCB + cb];
+              if (gP) wj = fma(kf, __ldg(gP + cc * nao2 + (long long)(mu0 + ca) * g.nao + nu0 + cb), wj);
+              const double wt = wc * wj * comp_factor(LA, ca) * comp_factor(LB, cb);
               if (wt == 0.0) continue;
               const int ax[3] = {cart_x(LA, ca), cart_y(LA, ca), cart_z(LA, ca)};
               const int bx[3] = {cart_x(LB, cb), cart_y(LB, cb), cart_z(LB, cb)};
@@ -220,8 +226,10 @@ __global__ void __launch_bounds__(128) grad2c_kernel(GradArgs g, AuxArgs aux, co
         for (int cp = 0; cp < np_; ++cp)
 #pragma unroll 1
           for (int cq = 0; cq < nq_; ++cq) {
-            const double w = pref * g.d[aux.func_off[sp] + cp] * g.d[aux.func_off[sq] + cq] *
-                             comp_factor(lp, cp) * comp_factor(lq, cq);
+            const int P = aux.func_off[sp] + cp, Q = aux.func_off[sq] + cq;
+            double wpq = g.cj * g.d[P] * g.d[Q];
+            if (g.W) wpq = fma(g.ck, g.W[(long long)P * g.ldw + Q], wpq);
+            const double w = pref * wpq * comp_factor(lp, cp) * comp_factor(lq, cq);
             int tp[3][2], tq[3][2], npp[3], nqq[3];
             double fp[3][2], fq[3][2];
             npp[0] = one_centre_terms(cart_x(lp, cp), aux.g1[ip0], tp[0], fp[0]);

@@ -17,6 +17,12 @@ struct GradArgs {
   const double *d;  // fitted coefficients V^-1 u, one per aux function
   const double *D;  // density, nao x nao row-major
   int nao;
+  double cj;  // weight of the Coulomb term: 3c weights cj d_P D_mu nu, 2c cj d_P d_Q
+  // exchange term (gam == nullptr: none): 3c weights ck Gam[P][mu][nu],
+  // 2c weights ck W[P][ldw]
+  const double *gam, *W;
+  int ldw;
+  double ck;
   const int *orb_atom, *aux_atom;  // atom of each shell
   double *grad;                    // natom x 3, accumulated with atomicAdd
 };
@@ -24,10 +30,12 @@ struct GradArgs {
 // d = L^-T rho by back substitution (L lower triangular, row-major, ld).
 void fitted_coefficients(const double *L, int n, int ld, const double *rho, double *work, double *d,
                          cudaStream_t st);
-// sum_P d_P sum_{mu nu} D_mu nu d(P|mu nu)/dR for pair class (la, lb), aux class lc.
+// sum_P sum_{mu nu} Gam_P,mu nu d(P|mu nu)/dR for pair class (la, lb), aux
+// class lc, Gam = cj d_P D_mu nu + ck gam[P][mu][nu].
 void launch_grad3c(int la, int lb, int lc, const GradArgs &a, const OrbArgs &o, const AuxArgs &x,
                    const double *tab, cudaStream_t st);
-// -d^T (dV/dR) d / 2 over all aux shells (aux_l: l of each shell).
+// -sum_PQ Wt_PQ dV_PQ/dR / 2 over all aux shells, Wt = cj d d^T + ck W
+// (aux_l: l of each shell).
 void launch_grad2c(const GradArgs &a, const AuxArgs &x, const int *aux_l, int nshell, const double *tab,
                    cudaStream_t st);
 

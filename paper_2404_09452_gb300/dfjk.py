@@ -41,6 +41,7 @@ EXPORTS = [
     "dfjk_build_uks",
     "dfjk_build_density",
     "dfjk_coulomb_gradient",
+    "dfjk_jk_gradient",
     "dfjk_build_batch",
     "dfjk_overlap",
     "dfjk_overlap_matrix",
@@ -125,6 +126,7 @@ def load_library(path: str = LIB_PATH):
     lib.dfjk_build.argtypes = [vp, i32, i32, vp, vp, vp, vp, vp, vp]
     lib.dfjk_overlap.argtypes = [vp, vp, vp]
     lib.dfjk_coulomb_gradient.argtypes = [vp, vp, vp, vp]
+    lib.dfjk_jk_gradient.argtypes = [vp, i32, vp, ctypes.c_double, ctypes.c_double, vp, vp]
     lib.dfjk_overlap_matrix.argtypes = [ctypes.POINTER(BasisC), i32, f64p, vp, vp]
     lib.dfjk_build_batch.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, i32, vp]
     lib.dfjk_evict.argtypes = [vp]
@@ -335,6 +337,17 @@ class Handle:
         g = torch.empty((self.natom, 3), dtype=torch.float64, device=D.device)
         _check(load_library().dfjk_coulomb_gradient(
             self.h, ctypes.c_void_p(D.data_ptr()), ctypes.c_void_p(g.data_ptr()), _stream(stream)))
+        return g
+
+    def jk_gradient(self, C, c_j=1.0, c_k=1.0, stream=None):
+        """d(c_j E_J + c_k E_K)/dR [natom x 3] at fixed D = C C^T, C a device
+        FP64 tensor [nao x nocc]."""
+        torch = _torch()
+        C = C.contiguous()
+        g = torch.empty((self.natom, 3), dtype=torch.float64, device=C.device)
+        _check(load_library().dfjk_jk_gradient(
+            self.h, int(C.shape[1]), ctypes.c_void_p(C.data_ptr()), float(c_j), float(c_k),
+            ctypes.c_void_p(g.data_ptr()), _stream(stream)))
         return g
 
     def overlap(self, stream=None):

@@ -1,6 +1,7 @@
-"""dfjk_coulomb_gradient against the oracle's finite-difference gradient of
-E_J = u^T V^-1 u / 2 (density held fixed): FP64 and mixed handles, a density
-that is not C C^T, one atom (zero gradient), and translation invariance."""
+"""dfjk_coulomb_gradient and dfjk_jk_gradient against the oracle's
+finite-difference gradients of E_J = u^T V^-1 u / 2 and E_K (density held
+fixed): FP64 and mixed handles, a density that is not C C^T, one atom (zero
+gradient), one occupied orbital (E_J = E_K), translation invariance."""
 import numpy as np
 import pytest
 
@@ -64,3 +65,44 @@ def test_gradient_single_atom_is_zero():
     g = h.coulomb_gradient(torch.from_numpy(_density(m)).cuda()).cpu().numpy()
     h.close()
     assert g.shape == (1, 3) and np.max(np.abs(g)) < 1e-10
+
+
+def _orbitals(m, nocc=None, seed=3000):
+    S = O.overlap(m.orb, m.coords)
+    return I.orthonormalize(I.c_occ_raw(m.nao, nocc or I.default_nocc(m.nao), seed), S)
+
+
+@pytest.mark.parametrize("precision", [dfjk.DFJK_FP64, dfjk.DFJK_MIXED])
+@pytest.mark.parametrize("natom", [3, 6])
+def test_jk_gradient(precision, natom):
+    m = I.water() if natom == 3 else I.molecule(natom, seed=1000 + natom)
+    C = _orbitals(m)
+    D = C @ C.T
+    h = dfjk.Handle(m, precision=precision)
+    Cd = torch.from_numpy(C).cuda()
+    gk = h.jk_gradient(Cd, 0.0, 1.0).cpu().numpy()
+    gjk = h.jk_gradient(Cd, 1.0, -0.5).cpu().numpy()
+    gj = h.jk_gradient(Cd, 1.0, 0.0).cpu().numpy()
+    gj_density = h.coulomb_gradient(torch.from_numpy(D).cuda()).cpu().numpy()
+    h.close()
+    refk = O.exchange_gradient_fd(m.orb, m.aux, m.coords, D)
+    refj = O.coulomb_gradient_fd(m.orb, m.aux, m.coords, D)
+    scale = max(1.0, np.abs(refk).max())
+    assert np.max(np.abs(gk - refk)) < GRAD_TOL * scale, (gk, refk)
+    assert np.max(np.abs(gjk - (refj - 0.5 * refk))) < GRAD_TOL * scale
+    assert np.max(np.abs(gj - gj_density)) < 1e-12 * max(1.0, np.abs(gj).max())
+    assert np.max(np.abs(gk.sum(axis=0))) < 1e-10 * scale
+
+
+def test_jk_gradient_one_orbital_cancels():
+    """One occupied orbital: E_K = E_J at every geometry, so the gradient of
+    E_J - E_K vanishes."""
+    m = I.molecule(4, seed=1004)
+    C = _orbitals(m, nocc=1, seed=3002)
+    h = dfjk.Handle(m, precision=dfjk.DFJK_FP64)
+    Cd = torch.from_numpy(C).cuda()
+    g = h.jk_gradient(Cd, 1.0, -1.0).cpu().numpy()
+    gj = h.jk_gradient(Cd, 1.0, 0.0).cpu().numpy()
+    h.close()
+    assert np.abs(gj).max() > 1e-3
+    assert np.max(np.abs(g)) < 1e-11 * np.abs(gj).max()
