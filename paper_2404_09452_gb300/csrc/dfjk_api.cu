@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <deque>
 #include <map>
 #include <mutex>
 #include <string>
@@ -1201,50 +1202,104 @@ static void jk_gradient(dfjk_ctx *h, const double *Din, int nocc, const double *
   rho_gemv_f64(h->B.p, h->ldb, nao, np, D, rho.p, work.p, 128, st);
   fitted_coefficients(h->L.p, h->naux, np, rho.p, work.p, d.p, st);
   DBuf<double> gam, W;
+  std::deque<SlicedOp> ops;  // slices of the tensor-core GEMMs, freed after the final sync
+  struct OpsFree {
+    std::deque<SlicedOp> &v;
+    ~OpsFree() {
+      for (SlicedOp &o : v) oz_free(o);
+    }
+  } ops_free{ops};
+  // view x(z, r, k) = p[z sz + r sr + k sk] in sliced form (6 slices)
+  auto slice = [&](const double *p, long long sz, long long sr, long long sk, int batch, int rows, int K,
+                   int tile) -> SlicedOp & {
+    ops.emplace_back();
+    SlicedOp &o = ops.back();
+    oz_alloc(o, batch, 6, rows, K, tile);
+    oz_slice_f64(p, sz, sr, sk, o, st);
+    return o;
+  };
+  // out[z][m][n] = sum_k A(z, m, k) B(n, k) on the tensor cores (A batched when nz > 1)
+  auto tc_gemm = [&](const SlicedOp &A, const SlicedOp &Bo, int M, int N, int K, int nz, double *out,
+                     long long ldo, long long obs, int lower) {
+    OzGemmArgs o;
+    o.M = M; o.N = N; o.K = K; o.nz = nz; o.a_batched = nz > 1 ? 1 : 0;
+    o.lower_only = lower; o.mode = 0; o.out = out; o.ldo = ldo; o.out_bs = obs;
+    o.status = h->status.p; o.timeout = h->opt.timeout_iters; o.tile_ctr = h->tctr.p;
+    oz_gemm(A, Bo, o, st);
+  };
   if (ck != 0.0) {
+    // exact sliced tensor-core GEMMs when the handle is mixed (B's slices are
+    // resident), FP64 CUDA-core GEMMs otherwise
+    const bool tc = h->opt.precision == DFJK_MIXED && h->Bsl.data != nullptr;
     const long long no2 = (long long)nocc * nocc;
     DBuf<double> X, Xt, Z;
     X.alloc((size_t)nao * np * nocc);
     Xt.alloc((size_t)np * no2);
     Z.alloc((size_t)np * no2);
-    GemmArgs x;  // X[mu][P][i] = sum_nu B[(mu,nu)][P] C[nu][i]
-    x.M = np; x.N = nocc; x.K = nao; x.batch = nao;
-    x.A = h->B.p; x.sAm = 1; x.sAk = h->ldb; x.sAb = (long long)nao * h->ldb;
-    x.B = C; x.sBn = 1; x.sBk = nocc; x.sBb = 0;
-    x.C = X.p; x.sCm = nocc; x.sCn = 1; x.sCb = (long long)np * nocc;
-    gemm_f64(x, st);
-    GemmArgs t;  // Xt[P][i][j] = sum_mu C[mu][i] X[mu][P][j]
-    t.M = nocc; t.N = nocc; t.K = nao; t.batch = np;
-    t.A = C; t.sAm = 1; t.sAk = nocc; t.sAb = 0;
-    t.B = X.p; t.sBn = 1; t.sBk = (long long)np * nocc; t.sBb = nocc;
-    t.C = Xt.p; t.sCm = nocc; t.sCn = 1; t.sCb = no2;
-    gemm_f64(t, st);
-    GemmArgs z;  // Z[P][ij] = sum_Q Linv[Q][P] Xt[Q][ij]
-    z.M = np; z.N = (int)no2; z.K = np;
-    z.A = h->Linv.p; z.sAm = 1; z.sAk = np;
-    z.B = Xt.p; z.sBn = 1; z.sBk = no2;
-    z.C = Z.p; z.sCm = no2; z.sCn = 1;
-    gemm_f64(z, st);
     W.alloc((size_t)np * np);
-    GemmArgs w;  // W = Z Z^T
-    w.M = np; w.N = np; w.K = (int)no2;
-    w.A = Z.p; w.sAm = no2; w.sAk = 1;
-    w.B = Z.p; w.sBn = no2; w.sBk = 1;
-    w.C = W.p; w.sCm = np; w.sCn = 1;
-    gemm_f64(w, st);
-    GemmArgs y;  // Y[P][mu][j] = sum_i C[mu][i] Z[P][i][j]   (Y reuses X)
-    y.M = nao; y.N = nocc; y.K = nocc; y.batch = np;
-    y.A = C; y.sAm = nocc; y.sAk = 1; y.sAb = 0;
-    y.B = Z.p; y.sBn = 1; y.sBk = nocc; y.sBb = no2;
-    y.C = X.p; y.sCm = nocc; y.sCn = 1; y.sCb = (long long)nao * nocc;
-    gemm_f64(y, st);
     gam.alloc((size_t)np * nao * nao);
-    GemmArgs gm;  // Gam[P][mu][nu] = sum_j Y[P][mu][j] C[nu][j]
-    gm.M = nao; gm.N = nao; gm.K = nocc; gm.batch = np;
-    gm.A = X.p; gm.sAm = nocc; gm.sAk = 1; gm.sAb = (long long)nao * nocc;
-    gm.B = C; gm.sBn = nocc; gm.sBk = 1; gm.sBb = 0;
-    gm.C = gam.p; gm.sCm = nao; gm.sCn = 1; gm.sCb = (long long)nao * nao;
-    gemm_f64(gm, st);
+    if (tc) {
+      const SlicedOp &csl = slice(C, 0, 1, nocc, 1, nocc, nao, OZ_BN);  // rows i, K nu
+      const SlicedOp &cn = slice(C, 0, nocc, 1, 1, nao, nocc, OZ_BN);   // rows mu, K i
+      // X[mu][P][i] = sum_nu B[(mu,nu)][P] C[nu][i]
+      tc_gemm(h->Bsl, csl, np, nocc, nao, nao, X.p, nocc, (long long)np * nocc, 0);
+      // Xt[P][j][i] = sum_mu X[mu][P][j] C[mu][i]  (symmetric in i, j)
+      const SlicedOp &xs = slice(X.p, nocc, 1, (long long)np * nocc, np, nocc, nao, OZ_BM);
+      tc_gemm(xs, csl, nocc, nocc, nao, np, Xt.p, nocc, no2, 0);
+      // Z[P][ij] = sum_Q Linv[Q][P] Xt[Q][ij]
+      const SlicedOp &lt = slice(h->Linv.p, 0, 1, np, 1, np, np, OZ_BM);
+      const SlicedOp &xts = slice(Xt.p, 0, 1, no2, 1, (int)no2, np, OZ_BN);
+      tc_gemm(lt, xts, np, (int)no2, np, 1, Z.p, no2, 0, 0);
+      // W = Z Z^T, lower triangle, then mirrored
+      const SlicedOp &zs = slice(Z.p, 0, no2, 1, 1, np, (int)no2, OZ_BM);
+      tc_gemm(zs, zs, np, np, (int)no2, 1, W.p, np, 0, 1);
+      mirror_lower_f64(W.p, np, st);
+      // Yt[P][j][mu] = sum_i Z[P][i][j] C[mu][i]   (Yt reuses X)
+      const SlicedOp &zb = slice(Z.p, no2, 1, nocc, np, nocc, nocc, OZ_BM);
+      tc_gemm(zb, cn, nocc, nao, nocc, np, X.p, nao, (long long)nao * nocc, 0);
+      // Gam[P][mu][nu] = sum_j Yt[P][j][mu] C[nu][j]
+      const SlicedOp &ys = slice(X.p, (long long)nao * nocc, 1, nao, np, nao, nocc, OZ_BM);
+      tc_gemm(ys, cn, nao, nao, nocc, np, gam.p, nao, (long long)nao * nao, 0);
+    } else {
+      GemmArgs x;  // X[mu][P][i] = sum_nu B[(mu,nu)][P] C[nu][i]
+      x.M = np; x.N = nocc; x.K = nao; x.batch = nao;
+      x.A = h->B.p; x.sAm = 1; x.sAk = h->ldb; x.sAb = (long long)nao * h->ldb;
+      x.B = C; x.sBn = 1; x.sBk = nocc; x.sBb = 0;
+      x.C = X.p; x.sCm = nocc; x.sCn = 1; x.sCb = (long long)np * nocc;
+      gemm_f64(x, st);
+      GemmArgs t;  // Xt[P][i][j] = sum_mu C[mu][i] X[mu][P][j]
+      t.M = nocc; t.N = nocc; t.K = nao; t.batch = np;
+      t.A = C; t.sAm = 1; t.sAk = nocc; t.sAb = 0;
+      t.B = X.p; t.sBn = 1; t.sBk = (long long)np * nocc; t.sBb = nocc;
+      t.C = Xt.p; t.sCm = nocc; t.sCn = 1; t.sCb = no2;
+      gemm_f64(t, st);
+      GemmArgs z;  // Z[P][ij] = sum_{Q >= P} Linv[Q][P] Xt[Q][ij]
+      z.M = np; z.N = (int)no2; z.K = np;
+      z.A = h->Linv.p; z.sAm = 1; z.sAk = np; z.k_from_m = 1;
+      z.B = Xt.p; z.sBn = 1; z.sBk = no2;
+      z.C = Z.p; z.sCm = no2; z.sCn = 1;
+      gemm_f64(z, st);
+      GemmArgs w;  // W = Z Z^T, lower triangle, then mirrored
+      w.M = np; w.N = np; w.K = (int)no2;
+      w.A = Z.p; w.sAm = no2; w.sAk = 1;
+      w.B = Z.p; w.sBn = no2; w.sBk = 1;
+      w.C = W.p; w.sCm = np; w.sCn = 1;
+      w.lower_only = 1;
+      gemm_f64(w, st);
+      mirror_lower_f64(W.p, np, st);
+      GemmArgs y;  // Y[P][mu][j] = sum_i C[mu][i] Z[P][i][j]   (Y reuses X)
+      y.M = nao; y.N = nocc; y.K = nocc; y.batch = np;
+      y.A = C; y.sAm = nocc; y.sAk = 1; y.sAb = 0;
+      y.B = Z.p; y.sBn = 1; y.sBk = nocc; y.sBb = no2;
+      y.C = X.p; y.sCm = nocc; y.sCn = 1; y.sCb = (long long)nao * nocc;
+      gemm_f64(y, st);
+      GemmArgs gm;  // Gam[P][mu][nu] = sum_j Y[P][mu][j] C[nu][j]
+      gm.M = nao; gm.N = nao; gm.K = nocc; gm.batch = np;
+      gm.A = X.p; gm.sAm = nocc; gm.sAk = 1; gm.sAb = (long long)nao * nocc;
+      gm.B = C; gm.sBn = nocc; gm.sBk = 1; gm.sBb = 0;
+      gm.C = gam.p; gm.sCm = nao; gm.sCn = 1; gm.sCb = (long long)nao * nao;
+      gemm_f64(gm, st);
+    }
     DFJK_CUDA_CHECK(cudaStreamSynchronize(st));  // X, Xt, Z are released here
   }
   DBuf<int> oat, aat, al;
@@ -1281,6 +1336,12 @@ static void jk_gradient(dfjk_ctx *h, const double *Din, int nocc, const double *
   }
   launch_grad2c(g, aux_args(h), al.p, h->aux.nshell, tab, st);
   DFJK_CUDA_CHECK(cudaStreamSynchronize(st));  // local buffers are released on return
+  int status = 0;
+  DFJK_CUDA_CHECK(cudaMemcpy(&status, h->status.p, sizeof(int), cudaMemcpyDeviceToHost));
+  if (status & STATUS_TIMEOUT) {
+    DFJK_CUDA_CHECK(cudaMemset(h->status.p, 0, sizeof(int)));
+    throw Error{DFJK_ERR_TIMEOUT, "a bounded device wait expired during the gradient"};
+  }
 }
 
 int dfjk_coulomb_gradient(dfjk_handle h, const double *D, double *grad, void *stream) {

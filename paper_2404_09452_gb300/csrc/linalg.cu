@@ -44,6 +44,7 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(GemmArgs g) {
   if (g.k_upto_n) kend = min(kend, (long long)(n0 + GBN));
   if (g.k_upto_m) kend = min(kend, (long long)(m0 + GBM));
   if (g.k_from_n) kbeg = max(kbeg, (long long)n0);
+  if (g.k_from_m) kbeg = max(kbeg, (long long)m0);
   int Mz = g.M;
   if (g.rag_step > 0) {
     const int valid = g.rag_n - (z * g.rag_step + g.rag_off);

@@ -22,6 +22,7 @@ struct GemmArgs {
                        // (B lower triangular in (n, k))
   int k_from_n = 0;    // K range starts at the tile's first n (B(n, k) = 0 for k < n)
   int k_upto_m = 0;    // K range ends at the tile's last m (A(m, k) = 0 for k > m)
+  int k_from_m = 0;    // K range starts at the tile's first m (A(m, k) = 0 for k < m)
   int k_split = 0;     // >0: blockIdx.z selects K range [z k_split, ...) and C += z sCb
   // ragged diagonal-block batches: batch z has rag_n - (z rag_step + rag_off)
   // valid rows (and, with rag_clip_k, as many K); z with none returns
