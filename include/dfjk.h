@@ -182,9 +182,12 @@ int dfjk_coulomb_gradient(dfjk_handle h, const double *D, double *grad, void *st
  * E = sum_PQ (V^-1)_PQ M_PQ / 2 with M_PQ = u_P u_Q or Tr(D T_P D T_Q), so
  *   dE/dR = sum_P Tr(G_P dT_P/dR) - Tr(W dV/dR) / 2,
  * G_P = d_P D (J) or C Z_P C^T (K), W = d d^T (J) or Z Z^T (K), with
- * Z_P = sum_Q (L^-1)_QP C^T B_Q C (nocc x nocc per aux function).  FP64 on the
- * CUDA cores; the K part forms Z, W (naux_pad^2) and G (naux_pad x nao^2
- * doubles, the size of B) for the duration of the call.
+ * Z_P = sum_Q (L^-1)_QP C^T B_Q C (nocc x nocc per aux function).  The
+ * derivative integrals are FP64; the K part's contractions (X = B C, C^T X,
+ * Z, Z Z^T, C Z_P C^T) run on the FP64 pipe for a DFJK_FP64 handle and as
+ * exact sliced tensor-core products (as in the build) for a DFJK_MIXED one.
+ * The K part holds Z, W (naux_pad^2) and G (naux_pad x nao^2 doubles, the
+ * size of B), plus their sliced forms, for the duration of the call.
  *   C_occ : device nao x nocc FP64 row-major, 1 <= nocc <= nao.
  *   c_j, c_k : finite weights of E_J and E_K (c_k = 0 skips the K part).
  *   grad : device natom x 3 FP64, overwritten.
