@@ -1196,11 +1196,11 @@ static void jk_gradient(dfjk_ctx *h, const double *Din, int nocc, const double *
   // rho = B vec D (= L^-1 u), then the fitted coefficients d = L^-T rho = V^-1 u
   DBuf<double> rho, work, d;
   rho.alloc(np);
-  work.alloc(std::max<size_t>((size_t)128 * ceil_div(np, 256) * 256, np));
+  work.alloc(std::max<size_t>((size_t)128 * ceil_div(np, 256) * 256, (size_t)16 * np));
   d.alloc(np);
   DFJK_CUDA_CHECK(cudaMemsetAsync(d.p, 0, d.bytes(), st));
   rho_gemv_f64(h->B.p, h->ldb, nao, np, D, rho.p, work.p, 128, st);
-  fitted_coefficients(h->L.p, h->naux, np, rho.p, work.p, d.p, st);
+  fitted_coefficients(h->Linv.p, h->naux, np, rho.p, work.p, d.p, st);
   DBuf<double> gam, W;
   std::deque<SlicedOp> ops;  // slices of the tensor-core GEMMs, freed after the final sync
   struct OpsFree {
@@ -1310,7 +1310,7 @@ static void jk_gradient(dfjk_ctx *h, const double *Din, int nocc, const double *
   GradArgs g{};
   g.pair_a = h->pair_a.p;
   g.pair_b = h->pair_b.p;
-  g.pair_chunk = 8;
+  g.pair_chunk = 1;  // one pair per block: the classes with few pairs still fill the GPU
   g.d = d.p;
   g.D = D;
   g.nao = nao;

@@ -98,24 +98,34 @@ __global__ void __launch_bounds__(128) grad2c_kernel(GradArgs g, AuxArgs aux, co
   if (tid < 3) atomicAdd(&g.grad[3 * atom_p + tid], sRed[0][tid] + sRed[1][tid] + sRed[2][tid] + sRed[3][tid]);
 }
 
-// Back substitution L^T d = r, one block: step i fixes d_i and removes it from
-// the rows above (row i of L is contiguous, so the update is coalesced).
-__global__ void __launch_bounds__(1024) lt_solve_kernel(const double *__restrict__ L, int n, int ld,
-                                                        double *__restrict__ r, double *__restrict__ d) {
-#pragma unroll 1
-  for (int i = n - 1; i >= 0; --i) {
-    __syncthreads();
-    const double di = r[i] / L[(long long)i * ld + i];
-    for (int j = threadIdx.x; j < i; j += blockDim.x) r[j] = fma(-L[(long long)i * ld + j], di, r[j]);
-    if (threadIdx.x == 0) d[i] = di;
-  }
+// d[Q] = sum_{P >= Q} Linv[P][Q] rho[P] (Linv = L^-1, lower triangular, row
+// P contiguous): a thread per Q, the P range split over blockIdx.y into
+// partial sums that a second kernel adds in a fixed order (deterministic).
+constexpr int LT_SPLIT = 16;
+__global__ void linv_t_partial_kernel(const double *__restrict__ Linv, int n, int ld,
+                                      const double *__restrict__ rho, double *__restrict__ part) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  const int len = (n + LT_SPLIT - 1) / LT_SPLIT, p0 = blockIdx.y * len, p1 = min(n, p0 + len);
+  double s = 0.0;
+  if (q < n)
+    for (int p = max(p0, q); p < p1; ++p) s = fma(Linv[(long long)p * ld + q], rho[p], s);
+  if (q < n) part[(long long)blockIdx.y * n + q] = s;
 }
 
-void fitted_coefficients(const double *L, int n, int ld, const double *rho, double *work, double *d,
+__global__ void linv_t_sum_kernel(const double *__restrict__ part, int n, double *__restrict__ d) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  double s = 0.0;
+  for (int k = 0; k < LT_SPLIT; ++k) s += part[(long long)k * n + q];
+  d[q] = s;
+}
+
+void fitted_coefficients(const double *Linv, int n, int ld, const double *rho, double *work, double *d,
                          cudaStream_t st) {
   if (n == 0) return;
-  DFJK_CUDA_CHECK(cudaMemcpyAsync(work, rho, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
-  lt_solve_kernel<<<1, 1024, 0, st>>>(L, n, ld, work, d);
+  linv_t_partial_kernel<<<dim3(ceil_div(n, 128), LT_SPLIT), 128, 0, st>>>(Linv, n, ld, rho, work);
+  DFJK_LAUNCHED();
+  linv_t_sum_kernel<<<ceil_div(n, 128), 128, 0, st>>>(work, n, d);
   DFJK_LAUNCHED();
 }
 

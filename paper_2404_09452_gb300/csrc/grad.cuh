@@ -27,8 +27,9 @@ struct GradArgs {
   double *grad;                    // natom x 3, accumulated with atomicAdd
 };
 
-// d = L^-T rho by back substitution (L lower triangular, row-major, ld).
-void fitted_coefficients(const double *L, int n, int ld, const double *rho, double *work, double *d,
+// d = L^-T rho = (L^-1)^T rho from the resident inverse (row-major, ld); work
+// holds 16 n doubles.
+void fitted_coefficients(const double *Linv, int n, int ld, const double *rho, double *work, double *d,
                          cudaStream_t st);
 // sum_P sum_{mu nu} Gam_P,mu nu d(P|mu nu)/dR for pair class (la, lb), aux
 // class lc, Gam = cj d_P D_mu nu + ck gam[P][mu][nu].

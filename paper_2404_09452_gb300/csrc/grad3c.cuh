@@ -81,11 +81,13 @@ __global__ void __launch_bounds__(128) grad3c_kernel(GradArgs g, OrbArgs orb, Au
   constexpr int LAB = LA + LB, L1 = LA + LB + LC + 1;
   constexpr int EI = LA + 2, EJ = LB + 1, ET = LA + LB + 2;  // E[i <= LA+1][j <= LB][t <= LAB+1]
   constexpr int NT1 = ntuv(LAB + 1), NT0 = ntuv(LAB);
-  __shared__ double sE[3][EI][EJ][ET];
-  __shared__ double sR1[3][LA + 1][EJ][ET];  // 2 alpha E^{i+1, j} - i E^{i-1, j}
-  __shared__ double sHdr[6];                 // 2 alpha, prefactor, Px, Py, Pz
+  // tables of up to KK primitive pairs at a time (one barrier round per group)
+  constexpr int KK = 4, NH = 3 * NT1 + NT0;
+  __shared__ double sE[KK][3][EI][EJ][ET];
+  __shared__ double sR1[KK][3][LA + 1][EJ][ET];  // 2 alpha E^{i+1, j} - i E^{i-1, j}
+  __shared__ double sHdr[KK][6];                 // 2 alpha, prefactor, Px, Py, Pz
   __shared__ double sD[NCA * NCB];
-  __shared__ double sHA[3][NT1], sH0[NT0];
+  __shared__ double sHA[KK][3][NT1], sH0[KK][NT0];
   __shared__ double sRed[4][6];
   const bool cj_on = g.cj != 0.0;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -118,12 +120,14 @@ __global__ void __launch_bounds__(128) grad3c_kernel(GradArgs g, OrbArgs orb, Au
     const int pa0 = orb.prim_off[sa], na = orb.nprim[sa], pb0 = orb.prim_off[sb], nb = orb.nprim[sb];
     double gA[3] = {0.0, 0.0, 0.0}, gCp[3] = {0.0, 0.0, 0.0};
 #pragma unroll 1
-    for (int kk = 0; kk < na * nb; ++kk) {
+    for (int k0 = 0; k0 < na * nb; k0 += KK) {
+      const int cnt = min(KK, na * nb - k0);
       __syncthreads();
-      if (tid < 3) {  // one thread per direction builds that direction's tables
+      if (tid < 3 * cnt) {  // one thread per (primitive pair, direction) builds its tables
+        const int k = tid / 3, dir = tid % 3, kk = k0 + k;
         const int ka = kk / nb, kb = kk % nb;
         const double a = orb.exps[pa0 + ka], b = orb.exps[pb0 + kb], p = a + b, ip_ = 1.0 / p;
-        const double A = tid == 0 ? Ax : tid == 1 ? Ay : Az, Bc = tid == 0 ? Bx : tid == 1 ? By : Bz;
+        const double A = dir == 0 ? Ax : dir == 1 ? Ay : Az, Bc = dir == 0 ? Bx : dir == 1 ? By : Bz;
         const double P = (a * A + b * Bc) * ip_;
         double E[EI][EJ][ET];
         hermite_E<LA + 1, LB>(0.5 * ip_, P - A, P - Bc, E);
@@ -133,19 +137,20 @@ __global__ void __launch_bounds__(128) grad3c_kernel(GradArgs g, OrbArgs orb, Au
           for (int j = 0; j < EJ; ++j)
 #pragma unroll
             for (int t = 0; t < ET; ++t) {
-              sE[tid][i][j][t] = E[i][j][t];
-              if (i <= LA) sR1[tid][i][j][t] = 2.0 * a * E[i + 1][j][t] - (i > 0 ? i * E[i - 1][j][t] : 0.0);
+              sE[k][dir][i][j][t] = E[i][j][t];
+              if (i <= LA) sR1[k][dir][i][j][t] = 2.0 * a * E[i + 1][j][t] - (i > 0 ? i * E[i - 1][j][t] : 0.0);
             }
-        sHdr[2 + tid] = P;
-        if (tid == 0) {
-          sHdr[0] = 2.0 * a;
-          sHdr[1] = orb.coefs[pa0 + ka] * orb.coefs[pb0 + kb] * exp(-a * b * ip_ * AB2) *
-                    (2.0 * 17.493418327624862846 * ip_);  // c_a c_b K_ab 2 pi^(5/2) / p
+        sHdr[k][2 + dir] = P;
+        if (dir == 0) {
+          sHdr[k][0] = 2.0 * a;
+          sHdr[k][1] = orb.coefs[pa0 + ka] * orb.coefs[pb0 + kb] * exp(-a * b * ip_ * AB2) *
+                       (2.0 * 17.493418327624862846 * ip_);  // c_a c_b K_ab 2 pi^(5/2) / p
         }
       }
       __syncthreads();
       if (cj_on) {  // Coulomb weights contracted with the Hermite coefficients
-        for (int e = tid; e < 3 * NT1 + NT0; e += blockDim.x) {
+        for (int ek = tid; ek < cnt * NH; ek += blockDim.x) {
+          const int k = ek / NH, e = ek % NH;
           const int q = e < 3 * NT1 ? e / NT1 : 3;
           int tt[3];
           tuv_decode(q < 3 ? e - q * NT1 : e - 3 * NT1, tt[0], tt[1], tt[2]);
@@ -158,86 +163,89 @@ __global__ void __launch_bounds__(128) grad3c_kernel(GradArgs g, OrbArgs orb, Au
               const int bx[3] = {cart_x(LB, cb), cart_y(LB, cb), cart_z(LB, cb)};
               double f = sD[ca * NCB + cb] * comp_factor(LA, ca) * comp_factor(LB, cb);
               for (int r = 0; r < 3; ++r)
-                f *= (r == q) ? sR1[r][ax[r]][bx[r]][tt[r]] : sE[r][ax[r]][bx[r]][tt[r]];
+                f *= (r == q) ? sR1[k][r][ax[r]][bx[r]][tt[r]] : sE[k][r][ax[r]][bx[r]][tt[r]];
               h += f;
             }
-          if (q < 3) sHA[q][e - q * NT1] = h;
-          else sH0[e - 3 * NT1] = h;
+          if (q < 3) sHA[k][q][e - q * NT1] = h;
+          else sH0[k][e - 3 * NT1] = h;
         }
         __syncthreads();
       }
-      const double X = sHdr[2] - Cx, Y = sHdr[3] - Cy, Z = sHdr[4] - Cz;
-      const int ka = kk / nb, kb = kk % nb;
-      const double p = orb.exps[pa0 + ka] + orb.exps[pb0 + kb];
 #pragma unroll 1
-      for (int kc = 0; kc < nc; ++kc) {
-        const double gm = aux.exps[pc0 + kc], g1 = aux.g1[pc0 + kc];
-        const double s = rsqrt(p + gm);
-        const double al = p * gm * (s * s);
-        double F[L1 + 1];
-        boys_eval<L1>(al * (X * X + Y * Y + Z * Z), boys_tab, F);
-        double R[ntuv(L1)];
-        hermite_R<L1>(F, al, X, Y, Z, R);
-        const double pt = sHdr[1] * aux.cdiv[pc0 + kc] * s;
+      for (int k = 0; k < cnt; ++k) {
+        const double X = sHdr[k][2] - Cx, Y = sHdr[k][3] - Cy, Z = sHdr[k][4] - Cz;
+        const int ka = (k0 + k) / nb, kb = (k0 + k) % nb;
+        const double p = orb.exps[pa0 + ka] + orb.exps[pb0 + kb];
 #pragma unroll 1
-        for (int cc = 0; cc < NCC; ++cc) {
-          // aux Hermite terms (t, coefficient) per direction
-          int tc[3][2];
-          double fc[3][2];
-          const int n0 = one_centre_terms(cart_x(LC, cc), g1, tc[0], fc[0]);
-          const int n1 = one_centre_terms(cart_y(LC, cc), g1, tc[1], fc[1]);
-          const int n2 = one_centre_terms(cart_z(LC, cc), g1, tc[2], fc[2]);
-          // W[tuv] = sum over aux terms (-1)^(t'+u'+v') coef R[t + t', ...], t+u+v <= LAB + 1
-          double W[NT1];
+        for (int kc = 0; kc < nc; ++kc) {
+          const double gm = aux.exps[pc0 + kc], g1 = aux.g1[pc0 + kc];
+          const double s = rsqrt(p + gm);
+          const double al = p * gm * (s * s);
+          double F[L1 + 1];
+          boys_eval<L1>(al * (X * X + Y * Y + Z * Z), boys_tab, F);
+          double R[ntuv(L1)];
+          hermite_R<L1>(F, al, X, Y, Z, R);
+          const double pt = sHdr[k][1] * aux.cdiv[pc0 + kc] * s;
+#pragma unroll 1
+          for (int cc = 0; cc < NCC; ++cc) {
+            // aux Hermite terms (t, coefficient) per direction
+            int tc[3][2];
+            double fc[3][2];
+            const int n0 = one_centre_terms(cart_x(LC, cc), g1, tc[0], fc[0]);
+            const int n1 = one_centre_terms(cart_y(LC, cc), g1, tc[1], fc[1]);
+            const int n2 = one_centre_terms(cart_z(LC, cc), g1, tc[2], fc[2]);
+            // W[tuv] = sum over aux terms (-1)^(t'+u'+v') coef R[t + t', ...], t+u+v <= LAB + 1
+            double W[NT1];
 #pragma unroll
-          for (int N = 0; N <= LAB + 1; ++N)
-#pragma unroll
-            for (int t = N; t >= 0; --t)
-#pragma unroll
-              for (int u = N - t; u >= 0; --u) {
-                const int v = N - t - u;
-                double w = 0.0;
-                for (int i0 = 0; i0 < n0; ++i0)
-                  for (int i1 = 0; i1 < n1; ++i1)
-                    for (int i2 = 0; i2 < n2; ++i2) {
-                      const int ts = tc[0][i0] + tc[1][i1] + tc[2][i2];
-                      const double c = fc[0][i0] * fc[1][i1] * fc[2][i2] * ((ts & 1) ? -1.0 : 1.0);
-                      w = fma(c, R[tuv_idx(t + tc[0][i0], u + tc[1][i1], v + tc[2][i2])], w);
-                    }
-                W[tuv_idx(t, u, v)] = w;
-              }
-          const double wc = pt * comp_factor(LC, cc);
-          if (cj_on) {
-            const double sj = wc * dP[cc];
-            double hA0 = 0.0, hA1 = 0.0, hA2 = 0.0, hC0 = 0.0, hC1 = 0.0, hC2 = 0.0;
-#pragma unroll
-            for (int e = 0; e < NT1; ++e) {
-              hA0 = fma(sHA[0][e], W[e], hA0);
-              hA1 = fma(sHA[1][e], W[e], hA1);
-              hA2 = fma(sHA[2][e], W[e], hA2);
-            }
-#pragma unroll
-            for (int N = 0; N <= LAB; ++N)
+            for (int N = 0; N <= LAB + 1; ++N)
 #pragma unroll
               for (int t = N; t >= 0; --t)
 #pragma unroll
                 for (int u = N - t; u >= 0; --u) {
                   const int v = N - t - u;
-                  const double h0 = sH0[tuv_idx(t, u, v)];
-                  hC0 = fma(h0, W[tuv_idx(t + 1, u, v)], hC0);
-                  hC1 = fma(h0, W[tuv_idx(t, u + 1, v)], hC1);
-                  hC2 = fma(h0, W[tuv_idx(t, u, v + 1)], hC2);
+                  double w = 0.0;
+                  for (int i0 = 0; i0 < n0; ++i0)
+                    for (int i1 = 0; i1 < n1; ++i1)
+                      for (int i2 = 0; i2 < n2; ++i2) {
+                        const int ts = tc[0][i0] + tc[1][i1] + tc[2][i2];
+                        const double c = fc[0][i0] * fc[1][i1] * fc[2][i2] * ((ts & 1) ? -1.0 : 1.0);
+                        w = fma(c, R[tuv_idx(t + tc[0][i0], u + tc[1][i1], v + tc[2][i2])], w);
+                      }
+                  W[tuv_idx(t, u, v)] = w;
                 }
-            gA[0] = fma(sj, hA0, gA[0]);
-            gA[1] = fma(sj, hA1, gA[1]);
-            gA[2] = fma(sj, hA2, gA[2]);
-            gCp[0] = fma(-sj, hC0, gCp[0]);
-            gCp[1] = fma(-sj, hC1, gCp[1]);
-            gCp[2] = fma(-sj, hC2, gCp[2]);
+            const double wc = pt * comp_factor(LC, cc);
+            if (cj_on) {
+              const double sj = wc * dP[cc];
+              double hA0 = 0.0, hA1 = 0.0, hA2 = 0.0, hC0 = 0.0, hC1 = 0.0, hC2 = 0.0;
+#pragma unroll
+              for (int e = 0; e < NT1; ++e) {
+                hA0 = fma(sHA[k][0][e], W[e], hA0);
+                hA1 = fma(sHA[k][1][e], W[e], hA1);
+                hA2 = fma(sHA[k][2][e], W[e], hA2);
+              }
+#pragma unroll
+              for (int N = 0; N <= LAB; ++N)
+#pragma unroll
+                for (int t = N; t >= 0; --t)
+#pragma unroll
+                  for (int u = N - t; u >= 0; --u) {
+                    const int v = N - t - u;
+                    const double h0 = sH0[k][tuv_idx(t, u, v)];
+                    hC0 = fma(h0, W[tuv_idx(t + 1, u, v)], hC0);
+                    hC1 = fma(h0, W[tuv_idx(t, u + 1, v)], hC1);
+                    hC2 = fma(h0, W[tuv_idx(t, u, v + 1)], hC2);
+                  }
+              gA[0] = fma(sj, hA0, gA[0]);
+              gA[1] = fma(sj, hA1, gA[1]);
+              gA[2] = fma(sj, hA2, gA[2]);
+              gCp[0] = fma(-sj, hC0, gCp[0]);
+              gCp[1] = fma(-sj, hC1, gCp[1]);
+              gCp[2] = fma(-sj, hC2, gCp[2]);
+            }
+            if (gP)
+              k_weights<LA, LB, NT1>(sE[k], sR1[k], W, gP + cc * nao2 + (long long)mu0 * g.nao + nu0, g.nao,
+                                     wc * kf, gA, gCp);
           }
-          if (gP)
-            k_weights<LA, LB, NT1>(sE, sR1, W, gP + cc * nao2 + (long long)mu0 * g.nao + nu0, g.nao, wc * kf, gA,
-                                   gCp);
         }
       }
     }
