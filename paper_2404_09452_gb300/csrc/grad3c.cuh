@@ -28,7 +28,9 @@ __device__ __forceinline__ void tuv_decode(int idx, int &t, int &u, int &v) {
 // function and run component by component.
 // Exchange weights, one (ca, cb) component pair at a time, every loop unrolled
 // at compile time so that W stays in registers: dA_q = sum_tuv E1_q E0 E0 W,
-// dC_q = -sum_tuv E0 E0 E0 W[tuv + 1_q].
+// dC_q = -sum_tuv E0 E0 E0 W[tuv + 1_q].  The sums are taken as
+// sum_t E_x sum_u E_y (sum_v E_z W): the v contractions (plain, raised, and
+// against the three shifted W) first, then the (t, u) lines.
 template <int LA, int LB, int NT>
 __device__ __forceinline__ void k_weights(const double (*sE)[LA + 2][LB + 1][LA + LB + 2],
                                           const double (*sR1)[LA + 1][LB + 1][LA + LB + 2], const double *W,
@@ -46,25 +48,39 @@ __device__ __forceinline__ void k_weights(const double (*sE)[LA + 2][LB + 1][LA 
 #pragma unroll
       for (int t = 0; t <= ax + bx + 1; ++t)
 #pragma unroll
-        for (int u = 0; u <= ay + by + 1; ++u)
+        for (int u = 0; u <= ay + by + 1; ++u) {
+          if (t + u > LAB + 1) continue;
+          const bool in_x = t <= ax + bx, in_y = u <= ay + by;
+          if (!in_x && !in_y) continue;  // no term has both raised
+          double vz0 = 0.0, vz1 = 0.0, vsx = 0.0, vsy = 0.0, vsz = 0.0;
 #pragma unroll
           for (int v = 0; v <= az + bz + 1; ++v) {
             if (t + u + v > LAB + 1) continue;
-            const bool in_x = t <= ax + bx, in_y = u <= ay + by, in_z = v <= az + bz;
-            const double e0x = in_x ? sE[0][ax][bx][t] : 0.0, e1x = sR1[0][ax][bx][t];
-            const double e0y = in_y ? sE[1][ay][by][u] : 0.0, e1y = sR1[1][ay][by][u];
-            const double e0z = in_z ? sE[2][az][bz][v] : 0.0, e1z = sR1[2][az][bz][v];
             const double w = W[tuv_idx(t, u, v)];
-            if (in_y && in_z) dA0 = fma(e1x * e0y * e0z, w, dA0);
-            if (in_x && in_z) dA1 = fma(e0x * e1y * e0z, w, dA1);
-            if (in_x && in_y) dA2 = fma(e0x * e0y * e1z, w, dA2);
-            if (in_x && in_y && in_z) {
-              const double e000 = e0x * e0y * e0z;
-              dC0 = fma(-e000, W[tuv_idx(t + 1, u, v)], dC0);
-              dC1 = fma(-e000, W[tuv_idx(t, u + 1, v)], dC1);
-              dC2 = fma(-e000, W[tuv_idx(t, u, v + 1)], dC2);
+            const double e1z = sR1[2][az][bz][v];
+            if (in_x && in_y) vz1 = fma(e1z, w, vz1);
+            if (v <= az + bz) {
+              const double e0z = sE[2][az][bz][v];
+              vz0 = fma(e0z, w, vz0);
+              if (in_x && in_y) {
+                vsx = fma(e0z, W[tuv_idx(t + 1, u, v)], vsx);
+                vsy = fma(e0z, W[tuv_idx(t, u + 1, v)], vsy);
+                vsz = fma(e0z, W[tuv_idx(t, u, v + 1)], vsz);
+              }
             }
           }
+          const double e0x = in_x ? sE[0][ax][bx][t] : 0.0, e1x = sR1[0][ax][bx][t];
+          const double e0y = in_y ? sE[1][ay][by][u] : 0.0, e1y = sR1[1][ay][by][u];
+          if (in_y) dA0 = fma(e1x * e0y, vz0, dA0);
+          if (in_x) dA1 = fma(e0x * e1y, vz0, dA1);
+          if (in_x && in_y) {
+            const double exy = e0x * e0y;
+            dA2 = fma(exy, vz1, dA2);
+            dC0 = fma(-exy, vsx, dC0);
+            dC1 = fma(-exy, vsy, dC1);
+            dC2 = fma(-exy, vsz, dC2);
+          }
+        }
       gA[0] = fma(wt, dA0, gA[0]);
       gA[1] = fma(wt, dA1, gA[1]);
       gA[2] = fma(wt, dA2, gA[2]);
@@ -75,7 +91,7 @@ __device__ __forceinline__ void k_weights(const double (*sE)[LA + 2][LB + 1][LA 
 }
 
 template <int LA, int LB, int LC>
-__global__ void __launch_bounds__(128) grad3c_kernel(GradArgs g, OrbArgs orb, AuxArgs aux,
+__global__ void __launch_bounds__(128, 2) grad3c_kernel(GradArgs g, OrbArgs orb, AuxArgs aux,
                                                      const double *__restrict__ boys_tab) {
   constexpr int NCA = ncart(LA), NCB = ncart(LB), NCC = ncart(LC);
   constexpr int LAB = LA + LB, L1 = LA + LB + LC + 1;
