@@ -300,12 +300,22 @@ def exchange_energy_geometry(basis, aux, coords, D):
     algebraically equal sum_PQ (V^-1)_PQ Tr(D T_P D T_Q) / 2 through a solve
     with V loses ~1e-8 to cancellation when V is ill-conditioned (cond ~1e8
     at six atoms), which finite differences turn into ~1e-5 errors."""
+    return energies_geometry(basis, aux, coords, D)[1]
+
+
+def energies_geometry(basis, aux, coords, D):
+    """(E_J, E_K) at the given atom positions from one metric and one set of
+    3-centre integrals: E_J = u^T V^-1 u / 2 (LU solve), E_K through
+    B = L^-1 T as in exchange_energy_geometry."""
     V = metric(aux, coords)
     T = three_center(basis, aux, coords)
+    u = T.reshape(V.shape[0], -1) @ D.ravel()
+    e_j = 0.5 * float(u @ np.linalg.solve(V, u))
     L = np.linalg.cholesky(V)
     B = scipy.linalg.solve_triangular(L, T.reshape(V.shape[0], -1), lower=True).reshape(T.shape)
-    A = np.einsum("mn,Pnl->Pml", D, B)  # D B_P
-    return 0.5 * float(np.einsum("Pmn,Pnm->", A, A))
+    A = np.matmul(D, B)  # D B_P for every P
+    e_k = 0.5 * float(np.sum(A * A.transpose(0, 2, 1)))  # sum_P Tr(D B_P D B_P)
+    return e_j, e_k
 
 
 def gradient_fd(energy, coords, h: float = 2e-3):

@@ -106,3 +106,28 @@ def test_jk_gradient_one_orbital_cancels():
     h.close()
     assert np.abs(gj).max() > 1e-3
     assert np.max(np.abs(g)) < 1e-11 * np.abs(gj).max()
+
+
+def test_jk_gradient_sampled_20_atoms():
+    """20 atoms (nao 300, naux 720), the mixed handle: three components of the
+    gradient of E_J - E_K/2 against central differences of the oracle's
+    energies, one component at a time; the rest by the translation sum rule."""
+    m = I.molecule(20, seed=1020)
+    C = _orbitals(m)
+    D = C @ C.T
+    h = dfjk.Handle(m, precision=dfjk.DFJK_MIXED)
+    g = h.jk_gradient(torch.from_numpy(C).cuda(), 1.0, -0.5).cpu().numpy()
+    h.close()
+    assert np.max(np.abs(g.sum(axis=0))) < 1e-10 * np.abs(g).max()
+    for a, x in ((0, 0), (7, 1), (13, 2)):
+        d = []
+        for step in (2e-3, 1e-3):
+            e = []
+            for sgn in (1, -1):
+                c = m.coords.copy()
+                c[a, x] += sgn * step
+                ej, ek = O.energies_geometry(m.orb, m.aux, c, D)
+                e.append(ej - 0.5 * ek)
+            d.append((e[0] - e[1]) / (2 * step))
+        ref = (4 * d[1] - d[0]) / 3
+        assert abs(g[a, x] - ref) < GRAD_TOL * max(1.0, abs(ref)), (a, x, g[a, x], ref)
