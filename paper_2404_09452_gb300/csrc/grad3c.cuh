@@ -90,7 +90,35 @@ __device__ __forceinline__ void k_weights(const double (*sE)[LA + 2][LB + 1][LA 
     }
 }
 
-template <int LA, int LB, int LC>
+// W[tuv] = sum over the Hermite terms of aux component cc of
+// (-1)^(t'+u'+v') coef R[t + t', u + u', v + v'], for t + u + v <= LAB + 1.
+template <int LAB, int LC>
+__device__ __forceinline__ void aux_w(int cc, double g1, const double *R, double *W) {
+  int tc[3][2];
+  double fc[3][2];
+  const int n0 = one_centre_terms(cart_x(LC, cc), g1, tc[0], fc[0]);
+  const int n1 = one_centre_terms(cart_y(LC, cc), g1, tc[1], fc[1]);
+  const int n2 = one_centre_terms(cart_z(LC, cc), g1, tc[2], fc[2]);
+#pragma unroll
+  for (int N = 0; N <= LAB + 1; ++N)
+#pragma unroll
+    for (int t = N; t >= 0; --t)
+#pragma unroll
+      for (int u = N - t; u >= 0; --u) {
+        const int v = N - t - u;
+        double w = 0.0;
+        for (int i0 = 0; i0 < n0; ++i0)
+          for (int i1 = 0; i1 < n1; ++i1)
+            for (int i2 = 0; i2 < n2; ++i2) {
+              const int ts = tc[0][i0] + tc[1][i1] + tc[2][i2];
+              const double c = fc[0][i0] * fc[1][i1] * fc[2][i2] * ((ts & 1) ? -1.0 : 1.0);
+              w = fma(c, R[tuv_idx(t + tc[0][i0], u + tc[1][i1], v + tc[2][i2])], w);
+            }
+        W[tuv_idx(t, u, v)] = w;
+      }
+}
+
+template <int LA, int LB, int LC, bool EXCH>
 __global__ void __launch_bounds__(128, 2) grad3c_kernel(GradArgs g, OrbArgs orb, AuxArgs aux,
                                                      const double *__restrict__ boys_tab) {
   constexpr int NCA = ncart(LA), NCB = ncart(LB), NCC = ncart(LC);
@@ -116,7 +144,9 @@ __global__ void __launch_bounds__(128, 2) grad3c_kernel(GradArgs g, OrbArgs orb,
 #pragma unroll
   for (int cc = 0; cc < NCC; ++cc) dP[cc] = active ? g.cj * g.d[aux.func_off[sc] + cc] : 0.0;
   const long long nao2 = (long long)g.nao * g.nao;
-  const double *gP = g.gam ? g.gam + (long long)(active ? aux.func_off[sc] : 0) * nao2 : nullptr;
+  // EXCH: exchange weights present (g.gam); a separate instantiation keeps the
+  // Coulomb-only kernel's registers free of the exchange loop
+  const double *gP = EXCH ? g.gam + (long long)(active ? aux.func_off[sc] : 0) * nao2 : nullptr;
   double gC[3] = {0.0, 0.0, 0.0};
   const int p0 = blockIdx.x * g.pair_chunk, p1 = min(g.npairs, p0 + g.pair_chunk);
 #pragma unroll 1
@@ -202,65 +232,81 @@ __global__ void __launch_bounds__(128, 2) grad3c_kernel(GradArgs g, OrbArgs orb,
           double R[ntuv(L1)];
           hermite_R<L1>(F, al, X, Y, Z, R);
           const double pt = sHdr[k][1] * aux.cdiv[pc0 + kc] * s;
-#pragma unroll 1
-          for (int cc = 0; cc < NCC; ++cc) {
-            // aux Hermite terms (t, coefficient) per direction
-            int tc[3][2];
-            double fc[3][2];
-            const int n0 = one_centre_terms(cart_x(LC, cc), g1, tc[0], fc[0]);
-            const int n1 = one_centre_terms(cart_y(LC, cc), g1, tc[1], fc[1]);
-            const int n2 = one_centre_terms(cart_z(LC, cc), g1, tc[2], fc[2]);
-            // W[tuv] = sum over aux terms (-1)^(t'+u'+v') coef R[t + t', ...], t+u+v <= LAB + 1
-            double W[NT1];
+          if (!EXCH && cj_on) {  // Coulomb alone: sum_cc s_cc W_cc first, then one set of dot products
+            double Ws[NT1];
 #pragma unroll
-            for (int N = 0; N <= LAB + 1; ++N)
+            for (int e = 0; e < NT1; ++e) Ws[e] = 0.0;
+#pragma unroll 1
+            for (int cc = 0; cc < NCC; ++cc) {
+              double W[NT1];
+              aux_w<LAB, LC>(cc, g1, R, W);
+              const double sj = pt * comp_factor(LC, cc) * dP[cc];
+#pragma unroll
+              for (int e = 0; e < NT1; ++e) Ws[e] = fma(sj, W[e], Ws[e]);
+            }
+            double hA0 = 0.0, hA1 = 0.0, hA2 = 0.0, hC0 = 0.0, hC1 = 0.0, hC2 = 0.0;
+#pragma unroll
+            for (int e = 0; e < NT1; ++e) {
+              hA0 = fma(sHA[k][0][e], Ws[e], hA0);
+              hA1 = fma(sHA[k][1][e], Ws[e], hA1);
+              hA2 = fma(sHA[k][2][e], Ws[e], hA2);
+            }
+#pragma unroll
+            for (int N = 0; N <= LAB; ++N)
 #pragma unroll
               for (int t = N; t >= 0; --t)
 #pragma unroll
                 for (int u = N - t; u >= 0; --u) {
                   const int v = N - t - u;
-                  double w = 0.0;
-                  for (int i0 = 0; i0 < n0; ++i0)
-                    for (int i1 = 0; i1 < n1; ++i1)
-                      for (int i2 = 0; i2 < n2; ++i2) {
-                        const int ts = tc[0][i0] + tc[1][i1] + tc[2][i2];
-                        const double c = fc[0][i0] * fc[1][i1] * fc[2][i2] * ((ts & 1) ? -1.0 : 1.0);
-                        w = fma(c, R[tuv_idx(t + tc[0][i0], u + tc[1][i1], v + tc[2][i2])], w);
-                      }
-                  W[tuv_idx(t, u, v)] = w;
+                  const double h0 = sH0[k][tuv_idx(t, u, v)];
+                  hC0 = fma(h0, Ws[tuv_idx(t + 1, u, v)], hC0);
+                  hC1 = fma(h0, Ws[tuv_idx(t, u + 1, v)], hC1);
+                  hC2 = fma(h0, Ws[tuv_idx(t, u, v + 1)], hC2);
                 }
-            const double wc = pt * comp_factor(LC, cc);
-            if (cj_on) {
-              const double sj = wc * dP[cc];
-              double hA0 = 0.0, hA1 = 0.0, hA2 = 0.0, hC0 = 0.0, hC1 = 0.0, hC2 = 0.0;
+            gA[0] += hA0;
+            gA[1] += hA1;
+            gA[2] += hA2;
+            gCp[0] -= hC0;
+            gCp[1] -= hC1;
+            gCp[2] -= hC2;
+          }
+          if (EXCH) {  // exchange (and Coulomb, if on) per aux component
+#pragma unroll 1
+            for (int cc = 0; cc < NCC; ++cc) {
+              double W[NT1];
+              aux_w<LAB, LC>(cc, g1, R, W);
+              const double wc = pt * comp_factor(LC, cc);
+              if (cj_on) {
+                const double sj = wc * dP[cc];
+                double hA0 = 0.0, hA1 = 0.0, hA2 = 0.0, hC0 = 0.0, hC1 = 0.0, hC2 = 0.0;
 #pragma unroll
-              for (int e = 0; e < NT1; ++e) {
-                hA0 = fma(sHA[k][0][e], W[e], hA0);
-                hA1 = fma(sHA[k][1][e], W[e], hA1);
-                hA2 = fma(sHA[k][2][e], W[e], hA2);
+                for (int e = 0; e < NT1; ++e) {
+                  hA0 = fma(sHA[k][0][e], W[e], hA0);
+                  hA1 = fma(sHA[k][1][e], W[e], hA1);
+                  hA2 = fma(sHA[k][2][e], W[e], hA2);
+                }
+#pragma unroll
+                for (int N = 0; N <= LAB; ++N)
+#pragma unroll
+                  for (int t = N; t >= 0; --t)
+#pragma unroll
+                    for (int u = N - t; u >= 0; --u) {
+                      const int v = N - t - u;
+                      const double h0 = sH0[k][tuv_idx(t, u, v)];
+                      hC0 = fma(h0, W[tuv_idx(t + 1, u, v)], hC0);
+                      hC1 = fma(h0, W[tuv_idx(t, u + 1, v)], hC1);
+                      hC2 = fma(h0, W[tuv_idx(t, u, v + 1)], hC2);
+                    }
+                gA[0] = fma(sj, hA0, gA[0]);
+                gA[1] = fma(sj, hA1, gA[1]);
+                gA[2] = fma(sj, hA2, gA[2]);
+                gCp[0] = fma(-sj, hC0, gCp[0]);
+                gCp[1] = fma(-sj, hC1, gCp[1]);
+                gCp[2] = fma(-sj, hC2, gCp[2]);
               }
-#pragma unroll
-              for (int N = 0; N <= LAB; ++N)
-#pragma unroll
-                for (int t = N; t >= 0; --t)
-#pragma unroll
-                  for (int u = N - t; u >= 0; --u) {
-                    const int v = N - t - u;
-                    const double h0 = sH0[k][tuv_idx(t, u, v)];
-                    hC0 = fma(h0, W[tuv_idx(t + 1, u, v)], hC0);
-                    hC1 = fma(h0, W[tuv_idx(t, u + 1, v)], hC1);
-                    hC2 = fma(h0, W[tuv_idx(t, u, v + 1)], hC2);
-                  }
-              gA[0] = fma(sj, hA0, gA[0]);
-              gA[1] = fma(sj, hA1, gA[1]);
-              gA[2] = fma(sj, hA2, gA[2]);
-              gCp[0] = fma(-sj, hC0, gCp[0]);
-              gCp[1] = fma(-sj, hC1, gCp[1]);
-              gCp[2] = fma(-sj, hC2, gCp[2]);
-            }
-            if (gP)
               k_weights<LA, LB, NT1>(sE[k], sR1[k], W, gP + cc * nao2 + (long long)mu0 * g.nao + nu0, g.nao,
                                      wc * kf, gA, gCp);
+            }
           }
         }
       }
