@@ -285,7 +285,9 @@ def jk_from_density(B: np.ndarray, D: np.ndarray):
 
 
 def coulomb_energy_geometry(basis, aux, coords, D):
-    """E_J = u^T V^-1 u / 2 with u_P = sum (P|mu nu) D_mu nu at the given atom
+    """Energy side of the gradient module the paper benchmarks next to SCF and
+    Hessians (section "Speedup of SCF, Gradient, and Hessian Calculations").
+    E_J = u^T V^-1 u / 2 with u_P = sum (P|mu nu) D_mu nu at the given atom
     positions (the shells move with their atoms; D is held fixed in the AO
     basis).  LU solve, no Cholesky."""
     V = metric(aux, coords)
@@ -319,7 +321,9 @@ def energies_geometry(basis, aux, coords, D):
 
 
 def gradient_fd(energy, coords, h: float = 2e-3):
-    """d energy(coords)/dR for every atom and direction by central differences
+    """O11 (the gradients of the section "Speedup of SCF, Gradient, and
+    Hessian Calculations", which the paper reports but does not derive):
+    d energy(coords)/dR for every atom and direction by central differences
     with Richardson extrapolation (steps h and h/2, error O(h^4)): the
     derivative taken from its definition, for checking an analytic gradient."""
     coords = np.asarray(coords, float)
