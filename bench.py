@@ -409,6 +409,20 @@ def run_ours(args):
                 "algorithmic_bytes_per_launch": algorithmic_bytes(m.nao, m.naux, nocc, ncol)[dom] / nl,
                 "launches_per_step": nl}
     roof["frac"] = roof["achieved"] / roof["peak"]
+    # per-row units of the measurement table: a4 as shell triples/s and
+    # integrals/s, a8 (rho from X, then J over the mu >= nu rows of B) as GB/s
+    triples = int(fp32_pairs["kept_shell_pairs"]) * len(m.aux.shells)
+    n_int = int(ncol) * int(m.naux)
+    eri_ms = per_step.get("eri3c", 0.0)
+    np_pad = (m.naux + 63) // 64 * 64
+    j_bytes = (m.nao * (m.nao + 1) // 2 * np_pad + m.nao * np_pad * nocc) * 8
+    j_ms = per_step.get("rho+J", 0.0)
+    units = {"a4_integrals": {"shell_triples": triples, "integrals": n_int, "ms": eri_ms,
+                              "shell_triples_per_s": triples / (eri_ms / 1e3) if eri_ms else None,
+                              "integrals_per_s": n_int / (eri_ms / 1e3) if eri_ms else None},
+             "a8_rho_J": {"bytes": j_bytes, "ms": j_ms,
+                          "GB_per_s": j_bytes / (j_ms / 1e3) / 1e9 if j_ms else None,
+                          "note": "side stream, beside the K GEMM"}}
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -426,6 +440,7 @@ def run_ours(args):
         sorted(step_ms)[int(0.99 * len(step_ms))],
         "phase_ms": per_step, "E_J": float(energies[0]), "E_K": float(energies[1]),
         "roofline": roof,
+        "units": units,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(launches),
