@@ -166,8 +166,10 @@ int dfjk_build_density(dfjk_handle h, int32_t nset, const double *D, double *J, 
  * density-fitted SCF gradient, one of the three modules the paper benchmarks
  * (SCF, gradient, Hessian), computed as
  *   dE_J/dR = sum_P d_P du_P/dR - d^T (dV/dR) d / 2,   d = V^-1 u = L^-T rho,
- * with derivative 3-centre and 2-centre integrals in FP64 (the handle's
- * precision does not matter) over the kept shell pairs.  The AO density is
+ * with derivative 3-centre and 2-centre integrals over the kept shell pairs:
+ * FP64, except that a DFJK_MIXED handle evaluates the pairs whose integrals
+ * its build evaluates in FP32 (Schwarz bound below fp32_pair_thresh) in FP32
+ * too, accumulated in FP64.  The AO density is
  * held fixed (no orbital response or overlap-derivative term: those belong to
  * the full SCF gradient, not to the Coulomb build).
  *   D    : device nao x nao FP64, symmetric (e.g. C C^T).
@@ -183,7 +185,8 @@ int dfjk_coulomb_gradient(dfjk_handle h, const double *D, double *grad, void *st
  *   dE/dR = sum_P Tr(G_P dT_P/dR) - Tr(W dV/dR) / 2,
  * G_P = d_P D (J) or C Z_P C^T (K), W = d d^T (J) or Z Z^T (K), with
  * Z_P = sum_Q (L^-1)_QP C^T B_Q C (nocc x nocc per aux function).  The
- * derivative integrals are FP64; the K part's contractions (X = B C, C^T X,
+ * derivative integrals are FP64 when c_k != 0 (with c_k = 0 the precision
+ * split of dfjk_coulomb_gradient applies); the K part's contractions (X = B C, C^T X,
  * Z, Z Z^T, C Z_P C^T) run on the FP64 pipe for a DFJK_FP64 handle and as
  * exact sliced tensor-core products (as in the build) for a DFJK_MIXED one.
  * The K part holds Z, W (naux_pad^2) and G (naux_pad x nao^2 doubles, the

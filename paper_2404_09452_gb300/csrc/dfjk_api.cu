@@ -1323,15 +1323,24 @@ static void jk_gradient(dfjk_ctx *h, const double *Din, int nocc, const double *
   g.aux_atom = aat.p;
   g.grad = grad;
   static const int cls[6][2] = {{0, 0}, {1, 0}, {1, 1}, {2, 0}, {2, 1}, {2, 2}};
+  // Coulomb-only gradients of a mixed handle take the build's precision split:
+  // the kept pairs it evaluates in FP32 (Schwarz bound below fp32_pair_thresh)
+  // get FP32 derivative weights, the others FP64
+  const bool split32 = ck == 0.0 && h->opt.precision == DFJK_MIXED;
+  const float *tab32 = boys_table_device_f32();
   for (int c = 0; c < 6; ++c) {
     const int lo = h->kept_cls_begin[c], hi = h->kept_cls_begin[c + 1];
     if (hi <= lo) continue;
+    const int mid = split32 ? std::min(std::max(lo, h->kept32_begin[c]), hi) : hi;
     for (int lc = 0; lc < 3; ++lc) {
-      g.pairs = h->kept.p + lo;
-      g.npairs = hi - lo;
       g.aux_shells = h->aux_cls[lc].p;
       g.naux_shells = h->aux_cls_n[lc];
-      launch_grad3c(cls[c][0], cls[c][1], lc, g, orb_args(h), aux_args(h), tab, st);
+      g.pairs = h->kept.p + lo;
+      g.npairs = mid - lo;
+      launch_grad3c(cls[c][0], cls[c][1], lc, g, orb_args(h), aux_args(h), tab, tab32, false, st);
+      g.pairs = h->kept.p + mid;
+      g.npairs = hi - mid;
+      launch_grad3c(cls[c][0], cls[c][1], lc, g, orb_args(h), aux_args(h), tab, tab32, true, st);
     }
   }
   launch_grad2c(g, aux_args(h), al.p, h->aux.nshell, tab, st);

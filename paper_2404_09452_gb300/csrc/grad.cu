@@ -130,12 +130,13 @@ void fitted_coefficients(const double *Linv, int n, int ld, const double *rho, d
 }
 
 void launch_grad3c(int la, int lb, int lc, const GradArgs &a, const OrbArgs &o, const AuxArgs &x,
-                   const double *tab, cudaStream_t st) {
+                   const double *tab, const float *tab32, bool f32, cudaStream_t st) {
   if (a.npairs == 0 || a.naux_shells == 0) return;
+  if (f32 && a.gam) throw Error{DFJK_ERR_UNSUPPORTED, "FP32 gradient weights are Coulomb-only"};
   switch (lc) {
-    case 0: launch_grad3c_l0(la, lb, a, o, x, tab, st); break;
-    case 1: launch_grad3c_l1(la, lb, a, o, x, tab, st); break;
-    case 2: launch_grad3c_l2(la, lb, a, o, x, tab, st); break;
+    case 0: launch_grad3c_l0(la, lb, a, o, x, tab, tab32, f32, st); break;
+    case 1: launch_grad3c_l1(la, lb, a, o, x, tab, tab32, f32, st); break;
+    case 2: launch_grad3c_l2(la, lb, a, o, x, tab, tab32, f32, st); break;
     default: throw Error{DFJK_ERR_UNSUPPORTED, "aux class"};
   }
   DFJK_LAUNCHED();

@@ -33,14 +33,15 @@ void fitted_coefficients(const double *Linv, int n, int ld, const double *rho, d
                          cudaStream_t st);
 // sum_P sum_{mu nu} Gam_P,mu nu d(P|mu nu)/dR for pair class (la, lb), aux
 // class lc, Gam = cj d_P D_mu nu + ck gam[P][mu][nu].
+// f32: Coulomb-only weights evaluated in FP32 (pairs below the FP32 threshold).
 void launch_grad3c(int la, int lb, int lc, const GradArgs &a, const OrbArgs &o, const AuxArgs &x,
-                   const double *tab, cudaStream_t st);
+                   const double *tab, const float *tab32, bool f32, cudaStream_t st);
 void launch_grad3c_l0(int la, int lb, const GradArgs &a, const OrbArgs &o, const AuxArgs &x, const double *tab,
-                      cudaStream_t st);
+                      const float *tab32, bool f32, cudaStream_t st);
 void launch_grad3c_l1(int la, int lb, const GradArgs &a, const OrbArgs &o, const AuxArgs &x, const double *tab,
-                      cudaStream_t st);
+                      const float *tab32, bool f32, cudaStream_t st);
 void launch_grad3c_l2(int la, int lb, const GradArgs &a, const OrbArgs &o, const AuxArgs &x, const double *tab,
-                      cudaStream_t st);
+                      const float *tab32, bool f32, cudaStream_t st);
 // -sum_PQ Wt_PQ dV_PQ/dR / 2 over all aux shells, Wt = cj d d^T + ck W
 // (aux_l: l of each shell).
 void launch_grad2c(const GradArgs &a, const AuxArgs &x, const int *aux_l, int nshell, const double *tab,

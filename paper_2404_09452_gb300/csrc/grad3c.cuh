@@ -92,8 +92,8 @@ __device__ __forceinline__ void k_weights(const double (*sE)[LA + 2][LB + 1][LA 
 
 // W[tuv] = sum over the Hermite terms of aux component cc of
 // (-1)^(t'+u'+v') coef R[t + t', u + u', v + v'], for t + u + v <= LAB + 1.
-template <int LAB, int LC>
-__device__ __forceinline__ void aux_w(int cc, double g1, const double *R, double *W) {
+template <int LAB, int LC, typename Real>
+__device__ __forceinline__ void aux_w(int cc, double g1, const Real *R, Real *W) {
   int tc[3][2];
   double fc[3][2];
   const int n0 = one_centre_terms(cart_x(LC, cc), g1, tc[0], fc[0]);
@@ -106,21 +106,74 @@ __device__ __forceinline__ void aux_w(int cc, double g1, const double *R, double
 #pragma unroll
       for (int u = N - t; u >= 0; --u) {
         const int v = N - t - u;
-        double w = 0.0;
+        Real w = Real(0);
         for (int i0 = 0; i0 < n0; ++i0)
           for (int i1 = 0; i1 < n1; ++i1)
             for (int i2 = 0; i2 < n2; ++i2) {
               const int ts = tc[0][i0] + tc[1][i1] + tc[2][i2];
               const double c = fc[0][i0] * fc[1][i1] * fc[2][i2] * ((ts & 1) ? -1.0 : 1.0);
-              w = fma(c, R[tuv_idx(t + tc[0][i0], u + tc[1][i1], v + tc[2][i2])], w);
+              w = fma(Real(c), R[tuv_idx(t + tc[0][i0], u + tc[1][i1], v + tc[2][i2])], w);
             }
         W[tuv_idx(t, u, v)] = w;
       }
 }
 
-template <int LA, int LB, int LC, bool EXCH>
+// Coulomb weights alone, one aux primitive: Boys, R, the aux components' W
+// summed with their weights cj d_P (times the prefactor), then one set of dot
+// products with the block's HA_q / H0.  Real = float for the shell pairs whose
+// integrals the build also evaluates in FP32 (Schwarz bound below the FP32
+// threshold); the sums over terms are added to FP64 accumulators.
+template <int LAB, int LC, int L1, typename Real>
+__device__ __forceinline__ void coulomb_alone(double al, double X, double Y, double Z, double pt, double g1,
+                                              const double *dP, const double *sHA, const double *sH0,
+                                              const Real *tab, double *gA, double *gCp) {
+  constexpr int NT1 = ntuv(LAB + 1), NCC = ncart(LC);
+  Real F[L1 + 1];
+  boys_eval<L1>(Real(al * (X * X + Y * Y + Z * Z)), tab, F);
+  Real R[ntuv(L1)];
+  hermite_R<L1, Real>(F, Real(al), Real(X), Real(Y), Real(Z), R);
+  Real Ws[NT1];
+#pragma unroll
+  for (int e = 0; e < NT1; ++e) Ws[e] = Real(0);
+#pragma unroll 1
+  for (int cc = 0; cc < NCC; ++cc) {
+    Real W[NT1];
+    aux_w<LAB, LC, Real>(cc, g1, R, W);
+    const Real sj = Real(pt * comp_factor(LC, cc) * dP[cc]);
+#pragma unroll
+    for (int e = 0; e < NT1; ++e) Ws[e] = fma(sj, W[e], Ws[e]);
+  }
+  Real hA0 = 0, hA1 = 0, hA2 = 0, hC0 = 0, hC1 = 0, hC2 = 0;
+#pragma unroll
+  for (int e = 0; e < NT1; ++e) {
+    hA0 = fma(Real(sHA[e]), Ws[e], hA0);
+    hA1 = fma(Real(sHA[NT1 + e]), Ws[e], hA1);
+    hA2 = fma(Real(sHA[2 * NT1 + e]), Ws[e], hA2);
+  }
+#pragma unroll
+  for (int N = 0; N <= LAB; ++N)
+#pragma unroll
+    for (int t = N; t >= 0; --t)
+#pragma unroll
+      for (int u = N - t; u >= 0; --u) {
+        const int v = N - t - u;
+        const Real h0 = Real(sH0[tuv_idx(t, u, v)]);
+        hC0 = fma(h0, Ws[tuv_idx(t + 1, u, v)], hC0);
+        hC1 = fma(h0, Ws[tuv_idx(t, u + 1, v)], hC1);
+        hC2 = fma(h0, Ws[tuv_idx(t, u, v + 1)], hC2);
+      }
+  gA[0] += double(hA0);
+  gA[1] += double(hA1);
+  gA[2] += double(hA2);
+  gCp[0] -= double(hC0);
+  gCp[1] -= double(hC1);
+  gCp[2] -= double(hC2);
+}
+
+template <int LA, int LB, int LC, bool EXCH, bool F32>
 __global__ void __launch_bounds__(128, 2) grad3c_kernel(GradArgs g, OrbArgs orb, AuxArgs aux,
-                                                     const double *__restrict__ boys_tab) {
+                                                        const double *__restrict__ boys_tab,
+                                                        const float *__restrict__ boys_tab32) {
   constexpr int NCA = ncart(LA), NCB = ncart(LB), NCC = ncart(LC);
   constexpr int LAB = LA + LB, L1 = LA + LB + LC + 1;
   constexpr int EI = LA + 2, EJ = LB + 1, ET = LA + LB + 2;  // E[i <= LA+1][j <= LB][t <= LAB+1]
@@ -227,49 +280,22 @@ __global__ void __launch_bounds__(128, 2) grad3c_kernel(GradArgs g, OrbArgs orb,
           const double gm = aux.exps[pc0 + kc], g1 = aux.g1[pc0 + kc];
           const double s = rsqrt(p + gm);
           const double al = p * gm * (s * s);
+          const double pt = sHdr[k][1] * aux.cdiv[pc0 + kc] * s;
+          if (!EXCH) {  // Coulomb alone: sum_cc s_cc W_cc first, then one set of dot products
+            if (cj_on) {
+              if (F32)
+                coulomb_alone<LAB, LC, L1, float>(al, X, Y, Z, pt, g1, dP, &sHA[k][0][0], sH0[k], boys_tab32, gA,
+                                                  gCp);
+              else
+                coulomb_alone<LAB, LC, L1, double>(al, X, Y, Z, pt, g1, dP, &sHA[k][0][0], sH0[k], boys_tab, gA,
+                                                   gCp);
+            }
+            continue;
+          }
           double F[L1 + 1];
           boys_eval<L1>(al * (X * X + Y * Y + Z * Z), boys_tab, F);
           double R[ntuv(L1)];
           hermite_R<L1>(F, al, X, Y, Z, R);
-          const double pt = sHdr[k][1] * aux.cdiv[pc0 + kc] * s;
-          if (!EXCH && cj_on) {  // Coulomb alone: sum_cc s_cc W_cc first, then one set of dot products
-            double Ws[NT1];
-#pragma unroll
-            for (int e = 0; e < NT1; ++e) Ws[e] = 0.0;
-#pragma unroll 1
-            for (int cc = 0; cc < NCC; ++cc) {
-              double W[NT1];
-              aux_w<LAB, LC>(cc, g1, R, W);
-              const double sj = pt * comp_factor(LC, cc) * dP[cc];
-#pragma unroll
-              for (int e = 0; e < NT1; ++e) Ws[e] = fma(sj, W[e], Ws[e]);
-            }
-            double hA0 = 0.0, hA1 = 0.0, hA2 = 0.0, hC0 = 0.0, hC1 = 0.0, hC2 = 0.0;
-#pragma unroll
-            for (int e = 0; e < NT1; ++e) {
-              hA0 = fma(sHA[k][0][e], Ws[e], hA0);
-              hA1 = fma(sHA[k][1][e], Ws[e], hA1);
-              hA2 = fma(sHA[k][2][e], Ws[e], hA2);
-            }
-#pragma unroll
-            for (int N = 0; N <= LAB; ++N)
-#pragma unroll
-              for (int t = N; t >= 0; --t)
-#pragma unroll
-                for (int u = N - t; u >= 0; --u) {
-                  const int v = N - t - u;
-                  const double h0 = sH0[k][tuv_idx(t, u, v)];
-                  hC0 = fma(h0, Ws[tuv_idx(t + 1, u, v)], hC0);
-                  hC1 = fma(h0, Ws[tuv_idx(t, u + 1, v)], hC1);
-                  hC2 = fma(h0, Ws[tuv_idx(t, u, v + 1)], hC2);
-                }
-            gA[0] += hA0;
-            gA[1] += hA1;
-            gA[2] += hA2;
-            gCp[0] -= hC0;
-            gCp[1] -= hC1;
-            gCp[2] -= hC2;
-          }
           if (EXCH) {  // exchange (and Coulomb, if on) per aux component
 #pragma unroll 1
             for (int cc = 0; cc < NCC; ++cc) {

@@ -5,12 +5,14 @@
 namespace dfjk {
 
 void launch_grad3c_l0(int la, int lb, const GradArgs &a, const OrbArgs &o, const AuxArgs &x, const double *tab,
-                      cudaStream_t st) {
+                      const float *tab32, bool f32, cudaStream_t st) {
   dim3 grid(ceil_div(a.npairs, a.pair_chunk), ceil_div(a.naux_shells, 128));
   if (a.gam) {
-    DISPATCH_LALB(la, lb, (grad3c_kernel<A_, B_, 0, true><<<grid, 128, 0, st>>>(a, o, x, tab)));
+    DISPATCH_LALB(la, lb, (grad3c_kernel<A_, B_, 0, true, false><<<grid, 128, 0, st>>>(a, o, x, tab, tab32)));
+  } else if (f32) {
+    DISPATCH_LALB(la, lb, (grad3c_kernel<A_, B_, 0, false, true><<<grid, 128, 0, st>>>(a, o, x, tab, tab32)));
   } else {
-    DISPATCH_LALB(la, lb, (grad3c_kernel<A_, B_, 0, false><<<grid, 128, 0, st>>>(a, o, x, tab)));
+    DISPATCH_LALB(la, lb, (grad3c_kernel<A_, B_, 0, false, false><<<grid, 128, 0, st>>>(a, o, x, tab, tab32)));
   }
 }
 

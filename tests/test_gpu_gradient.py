@@ -131,3 +131,20 @@ def test_jk_gradient_sampled_20_atoms():
             d.append((e[0] - e[1]) / (2 * step))
         ref = (4 * d[1] - d[0]) / 3
         assert abs(g[a, x] - ref) < GRAD_TOL * max(1.0, abs(ref)), (a, x, g[a, x], ref)
+
+
+def test_coulomb_gradient_fp32_pairs():
+    """The mixed handle's Coulomb gradient evaluates the pairs below the FP32
+    threshold in FP32 (as its build does their integrals): against the FP64
+    handle at 20 atoms the difference stays at the level of the integrals'."""
+    m = I.molecule(20, seed=1020)
+    D = torch.from_numpy(_density(m)).cuda()
+    h64 = dfjk.Handle(m, precision=dfjk.DFJK_FP64)
+    g64 = h64.coulomb_gradient(D).cpu().numpy()
+    h64.close()
+    hm = dfjk.Handle(m, precision=dfjk.DFJK_MIXED)
+    assert hm.npair_fp32 > 0
+    gm = hm.coulomb_gradient(D).cpu().numpy()
+    hm.close()
+    err = np.max(np.abs(gm - g64))
+    assert err < 1e-8 * max(1.0, np.abs(g64).max()), err
