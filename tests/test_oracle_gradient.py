@@ -75,3 +75,54 @@ def test_exchange_gradient_step_independent():
     g1 = O.exchange_gradient_fd(m.orb, m.aux, m.coords, D, h=2e-3)
     g2 = O.exchange_gradient_fd(m.orb, m.aux, m.coords, D, h=5e-4)
     assert np.max(np.abs(g1 - g2)) < 1e-8 * max(1.0, np.abs(g1).max())
+
+
+def _ssc_and_grad(xa, XA, xb, XB, g, C):
+    """(ab|c) for normalised s primitives and its derivatives with respect to
+    A, B and C, written out from the closed form
+    (ab|c) = N 2 pi^2.5 / (p g sqrt(p + g)) K_ab F_0(x), x = p g / (p + g) |P - C|^2,
+    with dF_0/dx = -F_1 and F_1 = (F_0 - e^-x) / (2x)."""
+    import math
+    p = xa + xb
+    P = (xa * XA + xb * XB) / p
+    AB = XA - XB
+    K = math.exp(-xa * xb / p * AB @ AB)
+    rho = p * g / (p + g)
+    PC = P - C
+    x = rho * PC @ PC
+    F0 = 0.5 * math.sqrt(math.pi / x) * math.erf(math.sqrt(x))
+    F1 = (F0 - math.exp(-x)) / (2 * x)
+    N = (2 * xa / math.pi) ** 0.75 * (2 * xb / math.pi) ** 0.75 * (2 * g / math.pi) ** 0.75
+    pref = N * 2 * math.pi**2.5 / (p * g * math.sqrt(p + g))
+    dK_dA = K * (-2 * xa * xb / p) * AB
+    dx_dP = 2 * rho * PC
+    dA = pref * (dK_dA * F0 - K * F1 * dx_dP * (xa / p))
+    dB = pref * (-dK_dA * F0 - K * F1 * dx_dP * (xb / p))
+    dC = pref * (K * F1 * dx_dP)
+    return pref * K * F0, dA, dB, dC
+
+
+def test_coulomb_gradient_closed_form():
+    """Two s orbitals and one s aux function on three atoms: V = (c|c) does
+    not move, so E_J = u^2 / (2V) and dE_J/dR = (u / V) du/dR with u written
+    from the closed-form (ab|c) above; the finite-difference oracle agrees."""
+    import math
+    A, B, Cc = np.array([0.1, -0.4, 0.3]), np.array([1.2, 0.5, -0.7]), np.array([-0.9, 1.4, 2.2])
+    a, b, g = 0.7, 1.9, 0.45
+    coords = np.array([A, B, Cc])
+    orb = I.Basis([I.Shell(0, 0, np.array([a]), np.array([1.0])), I.Shell(1, 0, np.array([b]), np.array([1.0]))])
+    aux = I.Basis([I.Shell(2, 0, np.array([g]), np.array([1.0]))])
+    D = np.array([[0.9, -0.35], [-0.35, 0.6]])
+    V = 2 * math.pi**2.5 / (g * g * math.sqrt(2 * g)) * (2 * g / math.pi) ** 1.5  # (c|c)
+    u, gA, gB, gC = 0.0, np.zeros(3), np.zeros(3), np.zeros(3)
+    for (i, xi, Xi), (j, xj, Xj) in (((0, a, A), (0, a, A)), ((0, a, A), (1, b, B)), ((1, b, B), (1, b, B))):
+        w = D[i, j] * (1.0 if i == j else 2.0)
+        val, dX, dY, dC = _ssc_and_grad(xi, Xi, xj, Xj, g, Cc)
+        u += w * val
+        for atom, d in ((i, dX), (j, dY)):
+            (gA if atom == 0 else gB)[:] += w * d
+        gC += w * dC
+    ref = (u / V) * np.array([gA, gB, gC])
+    assert abs(O.coulomb_energy_geometry(orb, aux, coords, D) - 0.5 * u * u / V) < 1e-13 * u * u / V
+    g_fd = O.coulomb_gradient_fd(orb, aux, coords, D)
+    assert np.max(np.abs(g_fd - ref)) < 1e-9 * np.abs(ref).max(), (g_fd, ref)
