@@ -126,3 +126,31 @@ def test_coulomb_gradient_closed_form():
     assert abs(O.coulomb_energy_geometry(orb, aux, coords, D) - 0.5 * u * u / V) < 1e-13 * u * u / V
     g_fd = O.coulomb_gradient_fd(orb, aux, coords, D)
     assert np.max(np.abs(g_fd - ref)) < 1e-9 * np.abs(ref).max(), (g_fd, ref)
+
+
+def test_exchange_gradient_closed_form():
+    """Same three-atom system: with one aux function E_K = Tr(D T D T) / (2V)
+    for the 2 x 2 matrix T_ab = (ab|c), so dE_K/dR = Tr(D dT/dR D T) / V."""
+    import math
+    A, B, Cc = np.array([0.1, -0.4, 0.3]), np.array([1.2, 0.5, -0.7]), np.array([-0.9, 1.4, 2.2])
+    a, b, g = 0.7, 1.9, 0.45
+    coords = np.array([A, B, Cc])
+    orb = I.Basis([I.Shell(0, 0, np.array([a]), np.array([1.0])), I.Shell(1, 0, np.array([b]), np.array([1.0]))])
+    aux = I.Basis([I.Shell(2, 0, np.array([g]), np.array([1.0]))])
+    D = np.array([[0.9, -0.35], [-0.35, 0.6]])
+    V = 2 * math.pi**2.5 / (g * g * math.sqrt(2 * g)) * (2 * g / math.pi) ** 1.5
+    ex, X = (a, b), (A, B)
+    T = np.zeros((2, 2))
+    dT = np.zeros((3, 3, 2, 2))  # [atom][direction][mu][nu]
+    for i in range(2):
+        for j in range(2):
+            val, dX, dY, dC = _ssc_and_grad(ex[i], X[i], ex[j], X[j], g, Cc)
+            T[i, j] = val
+            dT[i, :, i, j] += dX
+            dT[j, :, i, j] += dY
+            dT[2, :, i, j] += dC
+    DT = D @ T
+    assert abs(O.exchange_energy_geometry(orb, aux, coords, D) - 0.5 * np.trace(DT @ DT) / V) < 1e-13
+    ref = np.array([[np.trace(D @ dT[k, x] @ DT) / V for x in range(3)] for k in range(3)])
+    g_fd = O.exchange_gradient_fd(orb, aux, coords, D)
+    assert np.max(np.abs(g_fd - ref)) < 1e-9 * np.abs(ref).max(), (g_fd, ref)
