@@ -19,13 +19,6 @@ __device__ __forceinline__ void tuv_decode(int idx, int &t, int &u, int &v) {
   t = N - sl;
 }
 
-// Block: a chunk of kept pairs of class (LA, LB) x 128 aux shells of class LC.
-// The Coulomb weights cj d_P D_mu nu factor into an aux part and a pair part,
-// so the pair part is contracted with the Hermite coefficients once per
-// primitive pair (shared memory, all threads): HA_q[tuv] = sum_{ab} D_ab
-// dE_ab/dA_q [tuv] and H0[tuv] = sum_{ab} D_ab E_ab[tuv].  Each thread then
-// needs dot products with its W.  The exchange weights (gam) differ per aux
-// function and run component by component.
 // Exchange weights, one (ca, cb) component pair at a time, every loop unrolled
 // at compile time so that W stays in registers: dA_q = sum_tuv E1_q E0 E0 W,
 // dC_q = -sum_tuv E0 E0 E0 W[tuv + 1_q].  The sums are taken as
@@ -170,6 +163,14 @@ __device__ __forceinline__ void coulomb_alone(double al, double X, double Y, dou
   gCp[2] -= double(hC2);
 }
 
+// Block: pair_chunk kept pairs of class (LA, LB) (one in practice) x 128 aux
+// shells of class LC, a thread per aux shell.  The Coulomb weights
+// cj d_P D_mu nu factor into an aux part and a pair part, so the pair part is
+// contracted with the Hermite coefficients once per primitive pair (shared
+// memory, all threads): HA_q[tuv] = sum_{ab} D_ab dE_ab/dA_q [tuv] and
+// H0[tuv] = sum_{ab} D_ab E_ab[tuv]; each thread then needs dot products with
+// its W.  The exchange weights (gam, EXCH) differ per aux function and run
+// component by component.  F32: the Coulomb-only per-thread part in FP32.
 template <int LA, int LB, int LC, bool EXCH, bool F32>
 __global__ void __launch_bounds__(128, 2) grad3c_kernel(GradArgs g, OrbArgs orb, AuxArgs aux,
                                                         const double *__restrict__ boys_tab,
