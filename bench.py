@@ -11,8 +11,8 @@ resident in HBM (device time, CUDA events, max over ranks); `e2e` is the same
 metric through the public API with pinned host buffers and the host<->device
 copies inside the timed region.  For N > 1 (torchrun) every rank runs its own
 molecule (independent units, no data-path collective): weak scaling.
---impl reference times the FP64 CPU oracle on a bounded sample of the same
-workload (rank 0 only).
+--impl reference times one complete FP64 CPU oracle build of the same
+molecule, split into --steps consecutive pieces (rank 0 only).
 """
 from __future__ import annotations
 
@@ -76,11 +76,15 @@ def parse():
     ap.add_argument("--batch-n", type=int, default=256)
     ap.add_argument("--compare-fp64", action="store_true",
                     help="batch/serve: also time the plain FP64 per-molecule path")
-    ap.add_argument("--serve-rates", default="10,50,200,500")
-    ap.add_argument("--serve-requests", type=int, default=300)
-    ap.add_argument("--serve-pool", type=int, default=24)
-    ap.add_argument("--serve-max-atoms", type=int, default=60)
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--serve-rates", default="10,20,50,100,200,500")
+    ap.add_argument("--serve-requests", type=int, default=2000, help="measured requests per rate")
+    ap.add_argument("--serve-warmup", type=int, default=200, help="requests before the measured ones")
+    ap.add_argument("--serve-max-atoms", type=int, default=150)
+    ap.add_argument("--serve-slots", type=int, default=8)
+    ap.add_argument("--serve-fp64-rates", default="10,50")
+    ap.add_argument("--serve-fp64-requests", type=int, default=100)
+    ap.add_argument("--e2e-steps", type=int, default=-1,
+                    help="steps of the end-to-end timing (-1: the same as --steps)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--b-on-host", action="store_true",
                     help="keep B in pinned host memory, read in place by the kernels")
@@ -181,68 +185,103 @@ class ClockSampler:
                 "reasons": sorted(reasons)}
 
 
-# ---- CPU baseline: the oracle on a bounded sample --------------------------------------
+# ---- CPU baseline: one complete oracle build, in pieces ---------------------------------
 
-def oracle_sample(m, nocc):
-    """Times the FP64 CPU oracle on a bounded sample of one build and scales it
-    to a whole build.  Returns (seconds per build, sample description, cores)."""
+def oracle_pieces(m, C, nsteps):
+    """One complete FP64 CPU oracle build (steps O3-O10) of molecule `m` with
+    orbitals C, as `nsteps` consecutive pieces, each a call of the oracle's
+    own functions on the real inputs: the metric and the 3-centre integrals
+    for consecutive ranges of aux shells (sym=True, the oracle's mirrored
+    evaluation of mu >= nu pairs), then the whitening (Cholesky + triangular
+    solve), then J, K and the energies.  Running all pieces in order is
+    exactly one build; nothing is extrapolated.  Returns (pieces, state,
+    kinds): callables, the dict they fill, and "setup"/"build" per piece."""
     import numpy as np
-    import scipy.linalg
 
     from oracle import oracle as O
 
-    natom = m.natom
-    nao, naux = m.nao, m.naux
-    t = {}
-    t0 = time.perf_counter()
-    V = O.metric(m.aux, m.coords)
-    L = scipy.linalg.cholesky(V, lower=True)
-    t["metric+cholesky"] = time.perf_counter() - t0
-    # 3-centre integrals for the aux shells of one atom (every l class), x natom
-    per_atom = len(m.aux.shells) // max(natom, 1)
-    t0 = time.perf_counter()
-    T = O.three_center(m.orb, m.aux, m.coords, sym=True, aux_shells=(0, per_atom))
-    t["three_center"] = (time.perf_counter() - t0) * natom
-    # whitening: triangular solve on a column sample of the full mu,nu layout
-    rng = np.random.default_rng(0)
-    ncs = min(nao * nao, 8192)
-    Tc = rng.standard_normal((naux, ncs))
-    t0 = time.perf_counter()
-    scipy.linalg.solve_triangular(L, Tc, lower=True)
-    t["whiten"] = (time.perf_counter() - t0) * (nao * nao / ncs)
-    # J and K contractions on a sample of P
-    nps = min(naux, 48)
-    Bs = rng.standard_normal((nps, nao, nao))
-    C = rng.standard_normal((nao, nocc))
-    t0 = time.perf_counter()
-    O.jk_from_B(Bs, C)
-    t["jk"] = (time.perf_counter() - t0) * (naux / nps)
-    total = sum(t.values())
-    desc = (f"oracle: full metric+Cholesky; 3-centre for the {per_atom} aux shells of one atom "
-            f"x{natom}; triangular solve on {ncs} of {nao * nao} columns; J/K on {nps} of "
-            f"{naux} aux functions; scaled to one build")
-    del T
-    return total, desc, O.num_threads(), t
+    na = len(m.aux.shells)
+    nt = max(1, nsteps - 2) if nsteps >= 3 else 1
+    bounds = np.linspace(0, na, nt + 1).astype(int)
+    st = {"T": []}
+
+    def t_piece(i):
+        def f():
+            if i == 0:
+                st["V"] = O.metric(m.aux, m.coords)
+            st["T"].append(O.three_center(m.orb, m.aux, m.coords, sym=True,
+                                          aux_shells=(int(bounds[i]), int(bounds[i + 1]))))
+        return f
+
+    def whiten():
+        T = np.concatenate(st.pop("T"), axis=0)
+        st["L"], st["B"] = O.whiten(st["V"], T)
+
+    def jk():
+        st["out"] = O.jk_from_B(st.pop("B"), C)
+
+    pieces = [t_piece(i) for i in range(nt)] + [whiten, jk]
+    kinds = ["setup"] * (nt + 1) + ["build"]
+    if nsteps == 2:  # [metric + integrals] [whitening + J/K]
+        pieces = [pieces[0], lambda: (whiten(), jk())]
+        kinds = ["setup", "setup+build"]
+    elif nsteps == 1:
+        pieces = [lambda: (t_piece(0)(), whiten(), jk())]
+        kinds = ["setup+build"]
+    return pieces, st, kinds
+
+
+def oracle_build_timed(m, C, nsteps, nwarm=0):
+    """Times oracle_pieces piece by piece (after `nwarm` untimed pieces of
+    another build's integrals).  Returns (seconds per piece, kinds, state)."""
+    if nwarm:
+        wp, _, _ = oracle_pieces(m, C, max(3, nwarm + 2))
+        for f in wp[:nwarm]:
+            f()
+    pieces, st, kinds = oracle_pieces(m, C, nsteps)
+    secs = []
+    for f in pieces:
+        t0 = time.perf_counter()
+        f()
+        secs.append(time.perf_counter() - t0)
+    return secs, kinds, st
+
+
+def oracle_c_occ(m, nocc, seed):
+    """C_occ of the workload for the CPU arm: orthonormal in the oracle's own
+    overlap (the GPU arm uses the library's; the two agree to rounding)."""
+    from oracle import oracle as O
+    from paper_2404_09452_gb300 import inputs as I
+
+    return I.orthonormalize(I.c_occ_raw(m.nao, nocc, seed), O.overlap(m.orb, m.coords))
 
 
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    from oracle import oracle as O
+
     m, nocc = make_molecule(args.workload)
-    secs = []
-    for i in range(args.warmup + args.steps):
-        s, desc, cores, _ = oracle_sample(m, nocc)
-        if i >= args.warmup:
-            secs.append(s)
-    value = 1.0 / statistics.mean(secs)
+    C = oracle_c_occ(m, nocc, 3000)
+    secs, kinds, st = oracle_build_timed(m, C, args.steps, nwarm=args.warmup)
+    total = sum(secs)
+    value = 1.0 / total
+    split = "setup+build" not in kinds  # with fewer than 3 steps a piece holds both
+    setup_s = sum(t for t, k in zip(secs, kinds) if k == "setup") if split else None
+    build_s = sum(t for t, k in zip(secs, kinds) if k == "build") if split else None
+    desc = (f"one complete oracle build (metric, 3-centre integrals of every aux shell with sym=True, "
+            f"Cholesky + triangular solve, J/K/energies) of the {m.natom}-atom workload on the real inputs, "
+            f"in {len(secs)} consecutive pieces (one per step); value = 1 / total seconds")
     out = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(secs),
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(secs),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": args.workload, "note": WORKLOADS[args.workload]["note"]},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+                         "sample": desc, "setup_s": setup_s, "build_s": build_s,
+                         "E_J": float(st["out"]["E_J"]), "E_K": float(st["out"]["E_K"])},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out), flush=True)
@@ -329,8 +368,9 @@ def run_ours(args):
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
+    e2e_steps = args.steps if args.e2e_steps < 0 else args.e2e_steps
     t0 = time.perf_counter()
-    for _ in range(args.e2e_steps):
+    for _ in range(e2e_steps):
         Cd = Ch.to("cuda", non_blocking=True)
         h = dfjk.Handle(m, precision=prec, fp32_pair_thresh=args.fp32_pair_thresh, b_on_host=args.b_on_host)
         Jd, Kd, EJ, EK = h.build(Cd)
@@ -339,7 +379,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         h.close()
     e2e_s = D.max_over_ranks(time.perf_counter() - t0, device="cuda")
-    e2e_value = world * args.e2e_steps / e2e_s if args.e2e_steps > 0 else None
+    e2e_value = world * e2e_steps / e2e_s if e2e_steps > 0 else None
 
     # the plain FP64 GPU path on the same input, same clocks: builds/s and the
     # energy deviation of the timed path from it
@@ -450,9 +490,17 @@ def run_ours(args):
         out.update(fp64_cmp)
         out["vs_fp64"] = value / fp64_cmp["fp64_builds_per_s"]
     if world == 1 and not args.no_cpu_baseline:
-        s, desc, cores, parts = oracle_sample(m, nocc)
-        out["cpu_baseline"] = {"value": 1.0 / s, "unit": UNIT, "cores": cores, "kind": "oracle",
-                               "sample": desc}
+        from oracle import oracle as O
+
+        secs, kinds, st = oracle_build_timed(m, oracle_c_occ(m, nocc, 3000), 3)
+        out["cpu_baseline"] = {
+            "value": 1.0 / sum(secs), "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+            "sample": f"one complete oracle build of the {m.natom}-atom workload (metric, 3-centre integrals "
+                      f"sym=True, Cholesky + triangular solve, J/K/energies) on the real inputs, timed "
+                      f"once; value = 1 / seconds",
+            "setup_s": secs[0] + secs[1], "build_s": secs[2],
+            "dE_J_vs_timed_path": abs(float(st["out"]["E_J"]) - float(energies[0])),
+            "dE_K_vs_timed_path": abs(float(st["out"]["E_K"]) - float(energies[1]))}
     print(json.dumps(out), flush=True)
     if dist:
         dist.destroy_process_group()
@@ -472,7 +520,7 @@ def _orthonormal_cs(mols, seed0):
 
 
 def run_batch_mode(args):
-    """Row a10: a batch of uneven molecules (atom counts uniform in [5, 80],
+    """Batching: a batch of uneven molecules (atom counts uniform in [5, 80],
     seed 4000), each set up and built once per step; waves under a 150 GB
     budget, concurrent setups, one multi-stream build call per wave."""
     import torch
@@ -550,16 +598,25 @@ def run_gradient_mode(args):
 
 
 def run_serve_mode(args):
-    """Row a11: Poisson requests over a pool of molecules (atom counts
-    log-uniform in [5, serve-max-atoms]), 70 % repeats of resident molecules,
-    150 GB residency budget; p50/p99 latency and builds/s per arrival rate."""
+    """Serving: Poisson requests for molecules with atom counts log-uniform in
+    [5, serve-max-atoms]; with probability 0.7 a request repeats a molecule
+    already requested (new C_occ: an SCF-iteration pattern), otherwise it
+    brings the next molecule of the pool; 150 GB residency budget with LRU
+    eviction and recompute.  Per arrival rate: p50/p99 latency and builds/s
+    over the requests after the warm-up ones, for the mixed path and (on a
+    shorter stream) the plain FP64 path with the same slots."""
     import torch
 
     from paper_2404_09452_gb300 import dfjk, inputs as I, serve
 
-    counts = I.serve_atom_counts(args.serve_pool, hi=args.serve_max_atoms)
+    nreq, nwarm = args.serve_requests, args.serve_warmup
+    total = nreq + nwarm
+    npool = int(0.3 * total * 1.2) + 8  # new molecules are ~30 % of the requests
+    counts = I.serve_atom_counts(npool, hi=args.serve_max_atoms)
     pool = [I.molecule(int(n), seed=6100 + i) for i, n in enumerate(counts)]
+    t_prep = time.perf_counter()
     Cbase = _orthonormal_cs(pool, 3100)
+    t_prep = time.perf_counter() - t_prep
     # four orbital sets per molecule (an SCF-like sequence of new C_occ)
     rng_sets = {}
 
@@ -572,29 +629,48 @@ def run_serve_mode(args):
             rng_sets[key] = (C @ Q.cuda()).contiguous()
         return rng_sets[key]
 
+    def measure(prec, rate, n, warm, slots):
+        reqs = serve.make_stream(pool, n + warm, rate, repeat=0.7, seed=5000 + int(rate), c_of=c_of)
+        srv = serve.Server(pool, precision=prec, budget_bytes=150 << 30, slots=slots)
+        srv.run(reqs)
+        st = srv.stats
+        srv.close()
+        meas = [r for r in reqs[warm:] if not r.error]
+        lat = np.array([r.done - r.arrival for r in meas]) * 1e3
+        span = max(r.done for r in meas) - min(r.arrival for r in reqs[warm:])
+        sizes = [pool[r.mol_id].natom for r in reqs[warm:]]
+        return {"rate": rate, "requests": len(meas), "warmup_requests": warm,
+                "failed": sum(1 for r in reqs[warm:] if r.error),
+                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "builds_per_s": len(meas) / span, "misses": st.misses, "evictions": st.evictions,
+                "distinct_molecules": len(set(r.mol_id for r in reqs)),
+                "atoms_median": float(np.median(sizes)), "atoms_max": int(max(sizes)), "slots": slots}
+
+    import numpy as np
+
     rates = [float(r) for r in args.serve_rates.split(",")]
-    precs = [("mixed", dfjk.DFJK_MIXED, 8)] + ([("fp64", dfjk.DFJK_FP64, 1)] if args.compare_fp64 else [])
     rows = []
     for rate in rates:
-        for name, prec, slots in precs:
-            reqs = serve.make_stream(pool, args.serve_requests, rate, repeat=0.7, seed=5000 + int(rate), c_of=c_of)
-            srv = serve.Server(pool, precision=prec, budget_bytes=150 << 30, slots=slots)
-            srv.run(reqs[: max(1, args.serve_requests // 10)])  # warm-up: first tenth of the stream
-            srv.stats = serve.Stats()
-            off = reqs[0].arrival
-            for r in reqs:
-                r.arrival -= off
-            srv.run(reqs)
-            s = srv.stats.summary()
-            srv.close()
-            s.update(rate=rate, precision=name, slots=slots)
-            rows.append(s)
+        row = measure(dfjk.DFJK_MIXED, rate, nreq, nwarm, args.serve_slots)
+        row["precision"] = "mixed"
+        rows.append(row)
+        print(json.dumps(row), file=sys.stderr, flush=True)
+    if args.compare_fp64:
+        for rate in [float(r) for r in args.serve_fp64_rates.split(",")]:
+            row = measure(dfjk.DFJK_FP64, rate, args.serve_fp64_requests, max(1, args.serve_fp64_requests // 10),
+                          args.serve_slots)
+            row["precision"] = "fp64"
+            rows.append(row)
+            print(json.dumps(row), file=sys.stderr, flush=True)
     best = max(r["builds_per_s"] for r in rows if r["precision"] == "mixed")
     out = {"metric": "DF-J/K serving: builds/s and p50/p99 latency under Poisson arrivals",
            "value": best, "unit": UNIT, "n_gpus": 1, "higher_is_better": True, "scaling": "weak",
            "dtype": "f64+bf16-sliced", "data": "synthetic",
-           "config": {"workload": f"pool of {len(pool)} molecules, atoms log-uniform in [5, {args.serve_max_atoms}], "
-                                  f"70% repeats, {args.serve_requests} requests per rate, 150 GB budget"},
+           "config": {"workload": f"Poisson requests, molecules with atoms log-uniform in [5, {args.serve_max_atoms}] "
+                                  f"(pool of {len(pool)}), 70% repeats of a requested molecule, {nreq} requests per "
+                                  f"rate after {nwarm} warm-up requests, 150 GB residency budget, "
+                                  f"{args.serve_slots} build slots",
+                      "input_prep_s": t_prep},
            "rates": rows}
     print(json.dumps(out), flush=True)
 

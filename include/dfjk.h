@@ -70,11 +70,27 @@ typedef struct {
   const dfjk_shell *shells;
 } dfjk_basis;
 
+/* Precision of a handle.  The paper moves its tensor contractions onto tensor
+ * cores (Introduction, contribution 2: "up to twice the speed"; Sec.
+ * "Improved Interfaces to External Libraries": cuTENSOR contractions on
+ * tensor cores); DFJK_MIXED does the same for the three dense contractions
+ * while keeping FP64-level results.                                          */
 typedef enum {
-  DFJK_FP64 = 0, /* every step in FP64 on the FP64 pipe (the plain path)     */
-  DFJK_MIXED = 1 /* integrals, Cholesky and energies FP64; B stored FP32 and the
-                    whitening and J/K contractions on tensor cores with exact
-                    sliced BF16 products and FP64 recombination                */
+  DFJK_FP64 = 0, /* every step in FP64 on the FP64 pipe (the plain path); B is
+                    kept in both triangles, nao^2 naux_pad doubles            */
+  DFJK_MIXED = 1 /* integrals (FP64; FP32 for the pairs below
+                    fp32_pair_thresh), Cholesky and inverse, rho, J and the
+                    energies in FP64.  B is kept in FP64 as the packed
+                    mu >= nu triangle, nao (nao + 1) / 2 naux_pad doubles (8
+                    bytes per stored element, half the FP64 path's bytes).
+                    The whitening, X = B C and K run on the tensor cores as
+                    exact sliced products: each FP64 operand row is cut into 6
+                    (8 for the whitening) 6-bit integer slices stored as BF16
+                    (2 bytes per slice) under a power-of-two exponent per
+                    1024-element block, products accumulate exactly in FP32
+                    TMEM and are recombined in int64/FP64.  Each build slices
+                    B again, chunk by chunk of aux rows P (work buffers of at
+                    most DFJK_BUILD_WS_MB megabytes, default 8192, or 128 rows) */
 } dfjk_precision;
 
 typedef struct {
@@ -99,8 +115,10 @@ typedef struct {
                               device address space (the kernels read and
                               write it in place over the host link; for
                               molecules whose B does not fit in device
-                              memory); the mixed path then also slices B per
-                              build.  0 (default): B in device memory          */
+                              memory: the paper's CPU-memory storage of the
+                              intermediates of large systems, Sec. "Dataset
+                              and Performance").  0 (default): B in device
+                              memory                                        */
 } dfjk_options;
 
 typedef struct dfjk_ctx *dfjk_handle;
@@ -109,10 +127,14 @@ typedef struct dfjk_ctx *dfjk_handle;
  * energies, fp32_pair_thresh -1 (the precision's default), B on the device.  */
 void dfjk_default_options(dfjk_options *opt);
 
-/* Steps a0-a5: validates and normalises the bases, builds the shell-pair list
- * with Schwarz screening, the metric (P|Q), its Cholesky factor and inverse,
- * the 3-centre integrals and the whitened tensor B, which stays resident on
- * the current device until dfjk_destroy/dfjk_evict.
+/* Setup: the first half of the paper's density-fitting scheme (Introduction,
+ * contribution 1: the 3-centre integrals are computed first, everything after
+ * them is tensor operations), with the intermediates of the molecule kept in
+ * GPU memory (Sec. "Dataset and Performance").  Validates and normalises the
+ * bases, builds the shell-pair list with Schwarz screening, the metric (P|Q),
+ * its Cholesky factor and inverse, the 3-centre integrals and the whitened
+ * tensor B, which stays resident on the current device until
+ * dfjk_destroy/dfjk_evict.
  *   orb, aux : host shell lists (copied).  natom, coords: natom x 3 host doubles.
  *   opt      : may be NULL (defaults).  out: receives the handle.
  * Errors: DFJK_ERR_ARG, _UNSUPPORTED, _NOT_PD, _OOM, _BUDGET, _CUDA.           */
@@ -131,12 +153,25 @@ int dfjk_query(dfjk_handle h, int32_t *nao, int32_t *naux, int32_t *npair_kept,
 int dfjk_query_precision(dfjk_handle h, int32_t *npair_fp32, double *fp32_thresh);
 
 /* Layout of a handle's setup: the number of 3-centre column slabs (T is
- * built and whitened slab by slab, at most 4 GB each) and whether the mixed
- * path runs memory-lean (B kept as the packed mu >= nu triangle, sliced per
- * build).  Either output pointer may be NULL.                                 */
+ * built and whitened slab by slab, at most 4 GiB each, 2 GiB in the mixed
+ * path) and whether B is kept as the packed mu >= nu triangle (1 for every
+ * DFJK_MIXED handle, 0 for DFJK_FP64).  Either output pointer may be NULL.   */
 int dfjk_query_setup(dfjk_handle h, int32_t *nslab, int32_t *lean);
 
-/* Steps a6-a9 for nset occupied-orbital sets.
+/* Device bytes a molecule with nao AOs and naux aux functions takes at the
+ * given precision, before any setup (no device work): `resident` = what a
+ * handle holds between builds (B and the metric, its Cholesky factor and
+ * inverse), `build_ws` = the work buffers a build at nocc occupied orbitals
+ * adds (kept by the handle for its next builds), `setup_ws` = the transient
+ * peak of the setup beyond the resident data (released when it returns).
+ * Used to admit molecules under a memory budget (batching, serving).
+ * Any output pointer may be NULL.  Errors: DFJK_ERR_ARG.                     */
+int dfjk_estimate_bytes(int32_t nao, int32_t naux, int32_t nocc, int32_t precision, size_t *resident,
+                        size_t *build_ws, size_t *setup_ws);
+
+/* Build: the tensor-operation half of the paper's density-fitting scheme
+ * (Introduction, contribution 1) for nset occupied-orbital sets:
+ * X_P = B_P C, K = sum_P X_P X_P^T, rho = B vec(D), J = B^T rho, energies.
  *   C_occ : device, nset x nao x nocc, row-major FP64 (caller-owned).
  *   J, K  : device, nset x nao x nao FP64, written in full (symmetric).
  *   E_J, E_K : nset doubles each, both host or both device memory (detected;
@@ -149,14 +184,14 @@ int dfjk_build(dfjk_handle h, int32_t nset, int32_t nocc, const double *C_occ,
 /* J and K from densities instead of orbitals: J = B^T (B vec D) and
  * K = sum_P B_P D B_P, for any symmetric D (not necessarily C C^T), on the
  * FP64 pipe whatever the handle's precision (two GEMMs of nao^3 naux each, so
- * much slower than dfjk_build; it needs B stored in full, i.e. not the
- * memory-lean mode).
+ * much slower than dfjk_build).
  *   D    : device, nset x nao x nao FP64, symmetric.
  *   J, K : device, nset x nao x nao FP64.
  *   E_J, E_K : nset doubles each, Tr(D J)/2 and Tr(D K)/2, host or device.
- * Uses a work buffer of nao^2 naux_pad doubles for the duration of the call
- * (synchronises the stream before returning).  Errors: DFJK_ERR_ARG,
- * _UNSUPPORTED (memory-lean handle), _OOM, _CUDA.                            */
+ * Uses a work buffer of nao^2 naux_pad doubles for the duration of the call,
+ * and for a DFJK_MIXED handle (B packed) a second one holding B in both
+ * triangles; synchronises the stream before returning.  Errors:
+ * DFJK_ERR_ARG, _OOM, _CUDA.                            */
 int dfjk_build_density(dfjk_handle h, int32_t nset, const double *D, double *J, double *K,
                        double *E_J, double *E_K, void *stream);
 
@@ -176,7 +211,7 @@ int dfjk_build_density(dfjk_handle h, int32_t nset, const double *D, double *J, 
  *   grad : device natom x 3 FP64, overwritten; atoms in the order of the
  *          coordinates given to dfjk_setup.
  * Allocates small work buffers and synchronises the stream before returning.
- * Errors: DFJK_ERR_ARG, _UNSUPPORTED (memory-lean handle), _OOM, _CUDA.      */
+ * Errors: DFJK_ERR_ARG, _OOM, _CUDA.                                          */
 int dfjk_coulomb_gradient(dfjk_handle h, const double *D, double *grad, void *stream);
 
 /* Nuclear gradient of c_j E_J + c_k E_K at fixed D = C C^T, E_J and E_K as
@@ -194,14 +229,14 @@ int dfjk_coulomb_gradient(dfjk_handle h, const double *D, double *grad, void *st
  *   C_occ : device nao x nocc FP64 row-major, 1 <= nocc <= nao.
  *   c_j, c_k : finite weights of E_J and E_K (c_k = 0 skips the K part).
  *   grad : device natom x 3 FP64, overwritten.
- * Synchronises the stream.  Errors: DFJK_ERR_ARG, _UNSUPPORTED (memory-lean
- * handle), _OOM, _CUDA.                                                      */
+ * Synchronises the stream.  Errors: DFJK_ERR_ARG, _OOM, _CUDA.               */
 int dfjk_jk_gradient(dfjk_handle h, int32_t nocc, const double *C_occ, double c_j, double c_k, double *grad,
                      void *stream);
 
 /* Spin-unrestricted build: two occupied sets, alpha and beta, with their own
- * counts (the unrestricted case the paper's code supports alongside the
- * restricted one).  D_a = C_a C_a^T, D_b = C_b C_b^T.
+ * counts (the "unrestricted" row of the paper's functionality table, Sec.
+ * "Accelerated Functionalities", marked optimised for SCF, gradient and
+ * Hessian).  D_a = C_a C_a^T, D_b = C_b C_b^T.
  *   C_a : device nao x nocc_a, C_b : device nao x nocc_b (row-major FP64);
  *         1 <= nocc_a, 0 <= nocc_b <= nocc_a (nocc_b = 0: C_b may be NULL).
  *   J   : device nao x nao, Coulomb matrix of the total density D_a + D_b.
@@ -215,7 +250,9 @@ int dfjk_build_uks(dfjk_handle h, int32_t nocc_a, const double *C_a, int32_t noc
                    const double *C_b, double *J, double *K_a, double *K_b, double *E,
                    void *stream);
 
-/* Steps a6-a9 for nmol resident handles at once (row a10, batching): the builds
+/* dfjk_build for nmol resident handles at once (batching many molecules of
+ * uneven size on one GPU; the paper runs one molecule per job and has no
+ * counterpart): the builds
  * are spread over `nstreams` internal streams forked from and joined back to
  * `stream`, so small molecules run concurrently.  Handle i uses nocc[i],
  * C_occ[i] (device nao_i x nocc_i), J[i], K[i] (device nao_i x nao_i), and
@@ -237,7 +274,10 @@ int dfjk_overlap_matrix(const dfjk_basis *orb, int32_t natom, const double *coor
                         void *stream);
 
 /* Frees B and the work buffers but keeps the host copy of the inputs, so a
- * later dfjk_build recomputes steps a0-a5 first (resident-set eviction).     */
+ * later dfjk_build recomputes the setup first (resident-set eviction: the
+ * paper keeps the intermediates of small molecules in GPU memory and those
+ * of large ones elsewhere, Sec. "Dataset and Performance"; a server that
+ * holds many molecules under a memory budget evicts and recomputes).        */
 int dfjk_evict(dfjk_handle h);
 
 /* Releases everything the handle owns.  NULL is accepted.                    */
@@ -253,9 +293,9 @@ uint64_t dfjk_launch_count(void);
  * record a CUDA event pair around each phase, on the stream the phase is
  * launched on; dfjk_phase_times waits for those events, writes the
  * accumulated milliseconds of phases 0..n-1 to ms[] and clears them.
- * Phases: 0 shell pairs + Schwarz + metric (a0-a2), 1 Cholesky + inverse
- * (a3), 2 3-centre integrals (a4), 3 whitening (a5), 4 X = B C (a6),
- * 5 K = sum X X^T (a7), 6 D, rho and J (a8), 7 energies (a9); in
+ * Phases: 0 shell pairs + Schwarz + metric, 1 Cholesky + inverse,
+ * 2 3-centre integrals, 3 whitening, 4 X = B C (with the per-build slicing
+ * of B), 5 K = sum X X^T, 6 D, rho and J, 7 energies; in
  * DFJK_MIXED also the tensor-core GEMM launches alone: 8 whitening, 9 X = B C,
  * 10 K (each also counted inside phases 3, 4, 5).                          */
 #define DFJK_NPHASE 11
@@ -283,6 +323,13 @@ int dfjk_get_cholesky(dfjk_handle h, double *L, void *stream);
 int dfjk_get_B(dfjk_handle h, double *B, void *stream);
 int dfjk_get_pair_mask(dfjk_handle h, int32_t *keep, void *stream);
 
+/* Columns of B without expanding all of it (for checks at sizes where the
+ * full naux x nao x nao copy would not fit): out[c][P] = B[P][mu[c]][nu[c]],
+ * c < ncol, P < naux.  mu, nu: host int32 arrays; out: device FP64
+ * ncol x naux.  Synchronises the stream.                                     */
+int dfjk_get_B_columns(dfjk_handle h, int32_t ncol, const int32_t *mu, const int32_t *nu, double *out,
+                       void *stream);
+
 /* Raw 3-centre integrals T[P][mu][nu] (before whitening), device FP64
  * naux x nao x nao; recomputed on demand.                                    */
 int dfjk_get_three_center(dfjk_handle h, double *T, void *stream);
@@ -298,9 +345,11 @@ int dfjk_debug_sliced_gemm(int32_t batch, int32_t M, int32_t N, int32_t K, int32
 
 /* ---- allocation-free variant ------------------------------------------------ */
 
-/* E[0] = Tr(D J)/2 and E[1] = Tr(D K)/2 for caller-owned device matrices
- * D, J, K (n x n FP64, row-major) into E (device, 2 doubles), allocating
- * nothing.  For callers that must not call cudaMalloc: an application whose
+/* E[0] = sum_ij D_ij J_ij / 2 and E[1] = sum_ij D_ij K_ij / 2 for
+ * caller-owned device matrices D, J, K (n x n FP64, row-major) into E
+ * (device, 2 doubles), allocating nothing.  For the symmetric J and K that
+ * dfjk_build writes these are Tr(D J)/2 and Tr(D K)/2; for a non-symmetric
+ * J or K they are Tr(D J^T)/2 and Tr(D K^T)/2.  For callers that must not call cudaMalloc: an application whose
  * memory pool already owns the device memory, or code that cannot take the
  * device-wide synchronisation of cudaMalloc/cudaFree.  The paper has no
  * counterpart.

@@ -18,20 +18,13 @@ from . import dfjk
 
 
 def resident_bytes(nao: int, naux: int, nocc: int, precision: int) -> int:
-    """Device bytes one molecule holds while set up and built (B in FP64 plus,
-    for the mixed path, its 6 BF16 slices -- or, above 64 GiB of slices, B as
-    the packed mu >= nu triangle and 4 GiB of per-build slice chunks; work
-    buffers of one build; the setup's T slab)."""
-    npad = (naux + 63) // 64 * 64
-    mixed = precision == dfjk.DFJK_MIXED
-    bsl = nao * 6 * ((npad + 127) // 128 * 128) * ((nao + 31) // 32 * 32) * 2
-    if mixed and bsl > (64 << 30):
-        b = nao * (nao + 1) // 2 * npad * 8 + (4 << 30)
-    else:
-        b = nao * nao * npad * 8 + (bsl if mixed else 0)
-    work = nao * npad * nocc * (8 + (12 if precision == dfjk.DFJK_MIXED else 0))
-    slab = min(4 << 30, nao * (nao + 1) // 2 * npad * 8) * (3 if precision == dfjk.DFJK_MIXED else 1)
-    return int(1.1 * (b + work) + slab + 3 * npad * npad * 8)
+    """Device bytes one molecule holds while set up and built, as the library
+    states them (dfjk_estimate_bytes): its resident data (B -- the packed
+    mu >= nu triangle in the mixed path, both triangles in the FP64 path --
+    and the metric, its Cholesky factor and inverse) plus the larger of the
+    build's work buffers and the setup's transient peak."""
+    e = dfjk.estimate_bytes(nao, naux, nocc, precision)
+    return int(e["resident"] + max(e["build_ws"], e["setup_ws"]))
 
 
 def make_waves(sizes, budget: int):

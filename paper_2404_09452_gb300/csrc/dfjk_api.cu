@@ -1,5 +1,5 @@
-// C ABI of the DF-J/K build: handle lifetime, setup (steps a0-a5) and build
-// (steps a6-a9) orchestration, diagnostic accessors and error plumbing.
+// C ABI of the DF-J/K build: handle lifetime, setup (integrals, metric,
+// Cholesky, whitening) and build (X, K, rho, J, energies) orchestration, diagnostic accessors and error plumbing.
 // Paper: Introduction, contribution 1 (density fitting: 3-centre integrals,
 // then tensor contractions) and Sec. "Dataset and Performance" (intermediates
 // of small and medium molecules kept resident in GPU memory).
@@ -266,15 +266,16 @@ struct dfjk_ctx {
   DBuf<int> status;
   DBuf<int> tctr;  // tile counter of the tensor-core GEMM launches (stream-ordered)
   DBuf<int> kseq;  // split counters of the ordered split-K GEMM
-  // whitened tensor: FP64 B[(mu nao + nu) ldb + P]; in DFJK_MIXED also its
-  // 6-slice form for the tensor-core X = B C (batch mu, rows P, K nu)
+  // whitened tensor B, P contiguous: DFJK_FP64 keeps both triangles,
+  // B[(mu nao + nu) ldb + P]; DFJK_MIXED keeps the packed mu >= nu triangle,
+  // B[(mu (mu + 1) / 2 + nu) ldb + P], and slices it per build, chunk by chunk
+  // of rows P (Bchunk: batch mu, rows P of the chunk, K nu), just before
+  // X = B C of that chunk
   BStore B;
   long long ldb = 0;
-  SlicedOp Bsl;
-  // memory-lean mixed mode: B's slices are not kept; each build slices B in
-  // chunks of mu (Bchunk) just before X = B C of that chunk
-  bool lean = false;    // mixed path: B packed (mu >= nu rows), sliced per build
+  bool lean = false;    // B packed (the mixed path)
   SlicedOp Bchunk;
+  int chunk_rows = 0;   // rows P per build chunk (mixed path)
   // build workspace
   int ws_nocc = -1;
   DBuf<double> D, rho, rho_work, X, Kpart, en_work, e;
@@ -284,7 +285,6 @@ struct dfjk_ctx {
   cudaStream_t side = nullptr;  // setup: Cholesky + inverse beside the integrals
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   ~dfjk_ctx() {
-    oz_free(Bsl);
     oz_free(Bchunk);
     oz_free(Csl);
     oz_free(Xsl);
@@ -338,29 +338,14 @@ void enumerate_pairs(dfjk_ctx *h) {
   h->cls_begin[6] = (int)h->pa_h.size();
 }
 
-// Bytes of B's resident 6-slice form; above the limit (DFJK_BSLICE_MAX_BYTES,
-// default 64 GiB) the mixed path runs memory-lean: B is kept as the packed
-// mu >= nu triangle in FP64 (half the bytes of the full square) and sliced per
-// build in chunks of mu.
-size_t bslice_bytes(int nao, int np) {
-  const size_t rows = ((size_t)np + 127) / 128 * 128, kp = ((size_t)nao + 31) / 32 * 32;
-  return (size_t)nao * 6 * rows * kp * 2;
-}
-bool choose_lean(int nao, int np) {
-  static const size_t lim = [] {
-    const char *e = std::getenv("DFJK_BSLICE_MAX_BYTES");
-    return e ? (size_t)std::strtoull(e, nullptr, 10) : ((size_t)64 << 30);
-  }();
-  return bslice_bytes(nao, np) > lim;
-}
-
+// Device bytes of a handle's resident data: B (packed triangle in the mixed
+// path, both triangles in the FP64 path; none when B is in host memory) and
+// the metric, its Cholesky factor and inverse.
 size_t resident_estimate(const dfjk_ctx *h) {
   const size_t np2 = (size_t)h->naux_pad * h->naux_pad;
   const bool mixed = h->opt.precision == DFJK_MIXED;
-  const bool lean = mixed && (h->opt.b_on_host || choose_lean(h->nao, h->naux_pad));
-  const size_t rows = lean ? (size_t)h->nao * (h->nao + 1) / 2 : (size_t)h->nao * h->nao;
-  size_t b = h->opt.b_on_host ? 0 : rows * h->naux_pad * sizeof(double);
-  if (mixed && !lean) b += bslice_bytes(h->nao, h->naux_pad);
+  const size_t rows = mixed ? (size_t)h->nao * (h->nao + 1) / 2 : (size_t)h->nao * h->nao;
+  const size_t b = h->opt.b_on_host ? 0 : rows * h->naux_pad * sizeof(double);
   return b + 3 * np2 * sizeof(double);
 }
 
@@ -443,7 +428,8 @@ void compute_metric(dfjk_ctx *h, const double *tab, cudaStream_t st) {
   }
 }
 
-// Steps a0-a5 on the device.
+// The setup on the device: shell pairs and screening, metric, Cholesky and
+// inverse, 3-centre integrals, whitening.
 void make_resident(dfjk_ctx *h, cudaStream_t st) {
   const double *tab = boys_table_device();
   const float *tab32 = boys_table_device_f32();
@@ -588,10 +574,12 @@ void make_resident(dfjk_ctx *h, cudaStream_t st) {
 
   // a4 + a5: 3-centre integrals in column slabs, whitened into B
   h->ldb = np;
-  h->lean = mixed && (h->opt.b_on_host || choose_lean(h->nao, np));
+  h->lean = mixed;
   h->B.alloc((h->lean ? (size_t)h->nao * (h->nao + 1) / 2 : (size_t)h->nao * h->nao) * np, h->opt.b_on_host != 0);
   DFJK_CUDA_CHECK(cudaMemsetAsync(h->B.p, 0, h->B.bytes(), st));
-  const long long slab_budget = 4LL << 30;  // bytes of one T slab
+  // bytes of one T slab: 4 GiB, or 2 GiB in the mixed path, whose slab also
+  // has an 8-slice copy (twice the bytes) during the whitening
+  const long long slab_budget = mixed ? (2LL << 30) : (4LL << 30);
   long long slab_cols = std::max<long long>(36, slab_budget / ((long long)np * 8));
   slab_cols = std::min<long long>(slab_cols, std::max<long long>(h->ncol, 1));
   DBuf<double> T;
@@ -664,13 +652,6 @@ void make_resident(dfjk_ctx *h, cudaStream_t st) {
     DFJK_CUDA_CHECK(cudaStreamSynchronize(st));
     oz_free(T8);
     oz_free(Linv8);
-    // B as the A operand of X = B C: batch mu, rows P, K nu (6 slices),
-    // resident unless that would exceed the slice-memory limit
-    if (!h->lean) {
-      PhaseScope ph(3, st);
-      oz_alloc(h->Bsl, h->nao, 6, np, h->nao, OZ_BM);
-      oz_slice_f64(h->B.p, (long long)h->nao * h->ldb, 1, h->ldb, h->Bsl, st);
-    }
   }
   int status = 0;
   DFJK_CUDA_CHECK(cudaMemcpyAsync(&status, h->status.p, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -683,7 +664,7 @@ void make_resident(dfjk_ctx *h, cudaStream_t st) {
 
 void release_device(dfjk_ctx *h) {
   h->B.release();
-  oz_free(h->Bsl);
+  oz_free(h->Bchunk);
   h->V.release();
   h->L.release();
   h->Linv.release();
@@ -701,23 +682,51 @@ void release_device(dfjk_ctx *h) {
   h->e.release();
   oz_free(h->Csl);
   oz_free(h->Xsl);
+  h->chunk_rows = 0;
   h->uks_D.release();
   h->uks_J.release();
   h->ws_nocc = -1;
   h->resident = false;
 }
 
+// Rows P per chunk of the mixed build: the largest multiple of 128 whose work
+// buffers (X in FP64 and its 6 slices, the 6 slices of B for the chunk) stay
+// within DFJK_BUILD_WS_MB megabytes (default 8192), at least 128, at most the
+// whole (padded) aux range.
+int build_chunk_rows(int nao, int np, int nocc) {
+  static const size_t cap = [] {
+    const char *e = std::getenv("DFJK_BUILD_WS_MB");
+    const long v = e ? std::atol(e) : 0;
+    return (size_t)(v > 0 ? v : 8192) << 20;
+  }();
+  const size_t kp = ((size_t)nao + OZ_BK - 1) / OZ_BK * OZ_BK;
+  const size_t per_row = (size_t)nao * ((size_t)nocc * 8 + (size_t)nocc * 12 + 12 * kp);
+  size_t rows = std::max<size_t>(128, cap / per_row / 128 * 128);
+  return (int)std::min<size_t>(rows, (size_t)np);
+}
+
+// Build buffers, sized on the first build at a given nocc and reused after.
 void ensure_workspace(dfjk_ctx *h, int nocc, int nset) {
   const size_t nao2 = (size_t)h->nao * h->nao;
+  const bool mixed = h->opt.precision == DFJK_MIXED;
   if (h->ws_nocc < nocc || !h->D.p) {
     h->D.alloc(nao2);
     h->rho.alloc(h->naux_pad);
-    h->rho_work.alloc(std::max((size_t)128 * ceil_div(h->naux_pad, 256) * 256, (size_t)h->nao * h->naux_pad));
-    h->X.alloc((size_t)h->nao * h->naux_pad * nocc);
-    const int t = ceil_div(h->nao, 64);
-    const int tiles = t * (t + 1) / 2;
-    h->ksplit = std::max(1, std::min(64, ceil_div(4 * 152, tiles)));
-    h->Kpart.alloc(nao2 * h->ksplit);
+    if (mixed) {
+      const int pc = build_chunk_rows(h->nao, h->naux_pad, nocc);
+      h->chunk_rows = pc;
+      h->X.alloc((size_t)h->nao * pc * nocc);
+      h->rho_work.alloc((size_t)h->nao * pc);
+      oz_alloc(h->Xsl, 1, 6, h->nao, pc * nocc, OZ_BM);
+      oz_alloc(h->Bchunk, h->nao, 6, pc, h->nao, OZ_BM);
+    } else {
+      h->rho_work.alloc(std::max((size_t)128 * ceil_div(h->naux_pad, 256) * 256, (size_t)h->nao * h->naux_pad));
+      h->X.alloc((size_t)h->nao * h->naux_pad * nocc);
+      const int t = ceil_div(h->nao, 64);
+      const int tiles = t * (t + 1) / 2;
+      h->ksplit = std::max(1, std::min(64, ceil_div(4 * 152, tiles)));
+      h->Kpart.alloc(nao2 * h->ksplit);
+    }
     h->en_work.alloc(2 * 256);
     h->ws_nocc = nocc;
   }
@@ -743,7 +752,54 @@ void add_inplace(double *y, const double *x, long long n, cudaStream_t st) {
   DFJK_LAUNCHED();
 }
 
-// Steps a6-a9 for one occupied set.  DFJK_FP64 runs X = B C and K on the
+// K (lower triangle) += Xs Xs^T for one chunk of the reduction range (K
+// dimension kt = rows P of the chunk x nocc), on the tensor cores.  Split-K
+// ranges of about 64 MB of operand slices (all rows): the tiles in flight
+// (work is handed out split-major, a few ranges at a time) then reuse their
+// operands from L2.  The persistent kernel adds the splits of a tile into K in
+// split order (deterministic, no partial buffers; `add` makes the first split
+// add onto the previous chunks' sum as well); the one-tile-per-CTA kernel
+// writes partials (capped at 4 GiB) and reduces them in the same order.
+void k_gemm_sliced(dfjk_ctx *h, const SlicedOp &xs, int nao, long long kt, double *Kout, bool add,
+                   cudaStream_t st) {
+  const int mt = ceil_div(nao, OZ_BM), nt = ceil_div(nao, OZ_BN);
+  int tiles = 0;
+  for (int i = 0; i < mt; ++i)
+    for (int j = 0; j < nt; ++j)
+      if (j * OZ_BN <= i * OZ_BM + OZ_BM - 1) ++tiles;
+  static const size_t range_bytes = [] {
+    const char *e = std::getenv("DFJK_K_RANGE_MB");
+    const long v = e ? std::atol(e) : 0;
+    return (size_t)(v > 0 ? v : 64) << 20;
+  }();
+  const int nkb = xs.nkb;
+  const size_t chunk_kb_bytes = (size_t)xs.rows_pad * 6 * 2 * OZ_KB;
+  int per = (int)std::max<size_t>(1, range_bytes / chunk_kb_bytes);
+  const bool ordered = !oz_simple_mode();
+  const int max_split = ordered ? nkb : (int)std::max<size_t>(1, ((size_t)4 << 30) / ((size_t)nao * nao * 8));
+  int nsplit = std::min(ceil_div(nkb, per), max_split);
+  nsplit = std::max(nsplit, std::min(nkb, (2 * 152 + tiles - 1) / tiles));
+  per = ceil_div(nkb, nsplit);
+  nsplit = ceil_div(nkb, per);
+  OzGemmArgs k;
+  k.M = nao; k.N = nao; k.K = (int)kt; k.nz = nsplit; k.kb_per_split = per; k.lower_only = 1;
+  k.status = h->status.p; k.timeout = h->opt.timeout_iters;
+  k.tile_ctr = h->tctr.p;
+  k.phase = 10;
+  if (ordered) {
+    const size_t nseq = oz_tile_seq_count(nao, nao);
+    if (h->kseq.n < nseq) h->kseq.alloc(nseq);
+    k.mode = 2; k.out = Kout; k.ldo = nao; k.tile_seq = h->kseq.p; k.accumulate = add ? 1 : 0;
+    oz_gemm(xs, xs, k, st);
+  } else {
+    if (h->Kpart.n < (size_t)nsplit * nao * nao) h->Kpart.alloc((size_t)nsplit * nao * nao);
+    k.mode = 0; k.out = h->Kpart.p; k.ldo = nao; k.out_bs = (long long)nao * nao;
+    oz_gemm(xs, xs, k, st);
+    reduce_sym_f64(h->Kpart.p, nsplit, nao, Kout, st, add ? 1 : 0);
+  }
+}
+
+// The build for one occupied set.  DFJK_FP64 runs X = B C and K on the
 // FP64 pipe; DFJK_MIXED runs both on the tensor cores as exact sliced
 // products (6 slices); D, rho, J and the energies are FP64 in both.
 void build_one(dfjk_ctx *h, int nocc, const double *C, double *J, double *Kout, double *e,
@@ -787,92 +843,58 @@ void build_one(dfjk_ctx *h, int nocc, const double *C, double *J, double *Kout, 
     gemm_f64(k, st);
     reduce_sym_f64(h->Kpart.p, ceil_div(kt, k.k_split), nao, Kout, st);
   } else {
+    // The mixed path keeps B as the packed mu >= nu triangle (FP64) and works
+    // through the aux index in chunks of rows P: per chunk, the 6 slices of
+    // B[mu][nu][P in chunk] (all mu, nu), X_P = B_P C for P in the chunk,
+    // rho of the chunk from X, the slices of X and its contribution to K
+    // (added in chunk order).  One chunk holds the whole aux range unless the
+    // build's work buffers would exceed the workspace cap.
     {
       PhaseScope ph(4, st);
       if (!h->Csl.data || h->Csl.rows != nocc) oz_alloc(h->Csl, 1, 6, nocc, nao, OZ_BN);
       oz_slice_f64(C, 0, 1, nocc, h->Csl, st);  // rows i, K nu
-      OzGemmArgs x;
-      x.M = np; x.N = nocc; x.K = nao; x.nz = nao; x.a_batched = 1;
-      x.mode = 0; x.out = h->X.p; x.ldo = nocc; x.out_bs = (long long)np * nocc;
-      x.status = h->status.p; x.timeout = h->opt.timeout_iters;
-      x.tile_ctr = h->tctr.p;
-      x.phase = 9;
-      if (!h->lean) {
-        oz_gemm(h->Bsl, h->Csl, x, st);
-      } else {  // slice B per chunk of mu (about 4 GiB of slices), then X for it
-        const size_t per_mu = (size_t)6 * ((np + 127) / 128 * 128) * ((nao + 31) / 32 * 32) * 2;
-        const int mc = (int)std::max<size_t>(1, std::min<size_t>(nao, ((size_t)4 << 30) / per_mu));
-        if (!h->Bchunk.data || h->Bchunk.batch != mc) oz_alloc(h->Bchunk, mc, 6, np, nao, OZ_BM);
-        for (int mu0 = 0; mu0 < nao; mu0 += mc) {
-          const int n = std::min(mc, nao - mu0);
-          SlicedOp ck = h->Bchunk;  // view of the first n batches (the last chunk is short)
-          ck.batch = n;
-          oz_slice_f64_packed(h->B.p, h->ldb, mu0, ck, h->B.host, st);
-          OzGemmArgs xc = x;
-          xc.nz = n;
-          xc.out = h->X.p + (size_t)mu0 * np * nocc;
-          oz_gemm(ck, h->Csl, xc, st);
-        }
-      }
     }
-    // rho from X (5x smaller than B), then J over B, on the handle's side
-    // stream beside the K GEMM: both only read X, and the HBM-bound J GEMV
-    // fits next to the tensor-bound K kernel on the SMs
+    const int pc_max = h->chunk_rows;
+    const int nchunk = ceil_div(np, pc_max);
     const cudaStream_t sj = h->side ? h->side : st;
-    if (h->side) {
-      DFJK_CUDA_CHECK(cudaEventRecord(h->ev_fork, st));
-      DFJK_CUDA_CHECK(cudaStreamWaitEvent(sj, h->ev_fork, 0));
+    for (int c = 0; c < nchunk; ++c) {
+      const int p0 = c * pc_max, pc = std::min(pc_max, np - p0);
+      const long long kt = (long long)pc * nocc;
+      double *Xc = h->X.p;  // X[mu][p][i] of this chunk
+      {
+        PhaseScope ph(4, st);
+        SlicedOp bv = oz_view(h->Bchunk, pc, nao);  // batch mu, rows P of the chunk, K nu
+        oz_slice_f64_packed(h->B.p + p0, h->ldb, 0, bv, h->B.host, st);
+        OzGemmArgs x;
+        x.M = pc; x.N = nocc; x.K = nao; x.nz = nao; x.a_batched = 1;
+        x.mode = 0; x.out = Xc; x.ldo = nocc; x.out_bs = kt;
+        x.status = h->status.p; x.timeout = h->opt.timeout_iters;
+        x.tile_ctr = h->tctr.p;
+        x.phase = 9;
+        oz_gemm(bv, h->Csl, x, st);
+      }
+      {  // rho of the chunk from X (5x smaller than B)
+        PhaseScope ph(6, st);
+        rho_from_x_f64(Xc, C, nao, pc, nocc, h->rho.p + p0, h->rho_work.p, st);
+      }
+      if (c == nchunk - 1) {
+        // J = B^T rho over the packed B, on the handle's side stream beside the
+        // last K GEMM: both only read finished data, and the HBM-bound GEMV
+        // fits next to the tensor-bound GEMM on the SMs
+        if (h->side) {
+          DFJK_CUDA_CHECK(cudaEventRecord(h->ev_fork, st));
+          DFJK_CUDA_CHECK(cudaStreamWaitEvent(sj, h->ev_fork, 0));
+        }
+        PhaseScope ph(6, sj);
+        j_gemv_f64(h->B.p, h->ldb, nao, np, h->rho.p, J, 1, sj);
+        if (h->side) DFJK_CUDA_CHECK(cudaEventRecord(h->ev_join, sj));
+      }
+      PhaseScope ph(5, st);
+      SlicedOp xs = oz_view(h->Xsl, nao, (int)kt);  // rows mu, K (p, i)
+      oz_slice_f64(Xc, 0, kt, 1, xs, st);
+      k_gemm_sliced(h, xs, nao, kt, Kout, c > 0, st);
     }
-    {
-      PhaseScope ph(6, sj);
-      rho_from_x_f64(h->X.p, C, nao, np, nocc, h->rho.p, h->rho_work.p, sj);
-      j_gemv_f64(h->B.p, h->ldb, nao, np, h->rho.p, J, h->lean ? 1 : 0, sj);
-    }
-    if (h->side) DFJK_CUDA_CHECK(cudaEventRecord(h->ev_join, sj));
-    PhaseScope ph(5, st);
-    if (!h->Xsl.data || h->Xsl.K != kt) oz_alloc(h->Xsl, 1, 6, nao, (int)kt, OZ_BM);
-    oz_slice_f64(h->X.p, 0, kt, 1, h->Xsl, st);
-    const int mt = ceil_div(nao, OZ_BM), nt = ceil_div(nao, OZ_BN);
-    int tiles = 0;
-    for (int i = 0; i < mt; ++i)
-      for (int j = 0; j < nt; ++j)
-        if (j * OZ_BN <= i * OZ_BM + OZ_BM - 1) ++tiles;
-    // K ranges of about 64 MB of operand slices (all rows): the tiles in
-    // flight (work is handed out split-major, a few ranges at a time) then
-    // reuse their operands from L2.  The persistent kernel adds the splits of
-    // a tile into K in split order (deterministic, no partial buffers); the
-    // one-tile-per-CTA kernel writes partials (capped at 4 GiB) and reduces.
-    static const size_t range_bytes = [] {
-      const char *e = std::getenv("DFJK_K_RANGE_MB");
-      const long v = e ? std::atol(e) : 0;
-      return (size_t)(v > 0 ? v : 64) << 20;
-    }();
-    const int nkb = h->Xsl.nkb;
-    const size_t chunk_kb_bytes = (size_t)h->Xsl.rows_pad * 6 * 2 * OZ_KB;
-    int per = (int)std::max<size_t>(1, range_bytes / chunk_kb_bytes);
-    const bool ordered = !oz_simple_mode();
-    const int max_split = ordered ? nkb : (int)std::max<size_t>(1, ((size_t)4 << 30) / ((size_t)nao * nao * 8));
-    int nsplit = std::min(ceil_div(nkb, per), max_split);
-    nsplit = std::max(nsplit, std::min(nkb, (2 * 152 + tiles - 1) / tiles));
-    per = ceil_div(nkb, nsplit);
-    nsplit = ceil_div(nkb, per);
-    OzGemmArgs k;
-    k.M = nao; k.N = nao; k.K = (int)kt; k.nz = nsplit; k.kb_per_split = per; k.lower_only = 1;
-    k.status = h->status.p; k.timeout = h->opt.timeout_iters;
-    k.tile_ctr = h->tctr.p;
-    k.phase = 10;
-    if (ordered) {
-      const size_t nseq = oz_tile_seq_count(nao, nao);
-      if (h->kseq.n < nseq) h->kseq.alloc(nseq);
-      k.mode = 2; k.out = Kout; k.ldo = nao; k.tile_seq = h->kseq.p;
-      oz_gemm(h->Xsl, h->Xsl, k, st);
-      mirror_lower_f64(Kout, nao, st);
-    } else {
-      if (h->Kpart.n < (size_t)nsplit * nao * nao) h->Kpart.alloc((size_t)nsplit * nao * nao);
-      k.mode = 0; k.out = h->Kpart.p; k.ldo = nao; k.out_bs = (long long)nao * nao;
-      oz_gemm(h->Xsl, h->Xsl, k, st);
-      reduce_sym_f64(h->Kpart.p, nsplit, nao, Kout, st);
-    }
+    mirror_lower_f64(Kout, nao, st);
     if (h->side) DFJK_CUDA_CHECK(cudaStreamWaitEvent(st, h->ev_join, 0));  // J ready
   }
   PhaseScope ph(7, st);
@@ -978,7 +1000,7 @@ int dfjk_query(dfjk_handle h, int32_t *nao, int32_t *naux, int32_t *npair_kept, 
   if (nao) *nao = h->nao;
   if (naux) *naux = h->naux;
   if (npair_kept) *npair_kept = h->npair_kept;
-  if (bytes) *bytes = h->B.device_bytes() + h->Bsl.bytes() + h->V.bytes() +
+  if (bytes) *bytes = h->B.device_bytes() + h->V.bytes() +
                       h->L.bytes() + h->Linv.bytes() + h->rec.bytes();
   return DFJK_OK;
 }
@@ -987,6 +1009,39 @@ int dfjk_query_precision(dfjk_handle h, int32_t *npair_fp32, double *fp32_thresh
   if (!h) return fail(Error{DFJK_ERR_ARG, "null handle"});
   if (npair_fp32) *npair_fp32 = h->npair_fp32;
   if (fp32_thresh) *fp32_thresh = h->fp32_thresh;
+  return DFJK_OK;
+}
+
+int dfjk_estimate_bytes(int32_t nao, int32_t naux, int32_t nocc, int32_t precision, size_t *resident,
+                        size_t *build_ws, size_t *setup_ws) {
+  if (nao < 1 || naux < 1 || nocc < 1 || nocc > nao || (precision != DFJK_FP64 && precision != DFJK_MIXED))
+    return fail(Error{DFJK_ERR_ARG, "estimate_bytes arguments"});
+  const size_t np = ((size_t)naux + 63) / 64 * 64, n = (size_t)nao, no = (size_t)nocc;
+  const bool mixed = precision == DFJK_MIXED;
+  const size_t npack = n * (n + 1) / 2;
+  const size_t b = (mixed ? npack : n * n) * np * 8;
+  const size_t r = b + 3 * np * np * 8;
+  auto rup = [](size_t x, size_t m) { return (x + m - 1) / m * m; };
+  size_t ws = n * n * 8 + np * 8 * 2;  // D, rho
+  if (mixed) {
+    const size_t pc = (size_t)build_chunk_rows(nao, (int)np, nocc);
+    const size_t kt = pc * no, nkb = (kt + OZ_KB - 1) / OZ_KB;
+    const size_t kpx = nkb > 4 ? nkb * OZ_KB : rup(kt, OZ_BK);
+    ws += n * pc * no * 8 + n * pc * 8;                       // X of a chunk, rho partials
+    ws += 6 * rup(n, OZ_BM) * kpx * 2 + rup(n, OZ_BM) * nkb * 4;  // X slices
+    ws += n * 6 * rup(pc, OZ_BM) * rup(n, OZ_BK) * 2 + n * rup(pc, OZ_BM) * 4;  // B slices
+    ws += 6 * rup(no, OZ_BN) * rup(n, OZ_BK) * 2;            // C slices
+  } else {
+    const size_t t = (n + 63) / 64, ksplit = std::max<size_t>(1, std::min<size_t>(64, (4 * 152 + t * (t + 1) / 2 - 1) / (t * (t + 1) / 2)));
+    ws += n * np * no * 8 + n * n * ksplit * 8 + n * np * 8;  // X, K partials, rho partials
+  }
+  // setup: one T slab of at most 4 GiB (2 GiB plus its 8 slices in the mixed path),
+  // L^-1 and a work copy (plus L^-1's 8 slices in the mixed path)
+  const size_t slab = std::min<size_t>((size_t)(mixed ? 2 : 4) << 30, npack * np * 8);
+  size_t sw = slab * (mixed ? 3 : 1) + 2 * np * np * 8 + (mixed ? np * np * 16 : 0);
+  if (resident) *resident = r;
+  if (build_ws) *build_ws = ws;
+  if (setup_ws) *setup_ws = sw;
   return DFJK_OK;
 }
 
@@ -1106,10 +1161,25 @@ int dfjk_build_density(dfjk_handle h, int32_t nset, const double *D, double *J, 
     cudaStream_t st = S(stream);
     DFJK_CUDA_CHECK(cudaSetDevice(h->device));
     if (!h->resident) make_resident(h, st);
-    if (h->lean) throw Error{DFJK_ERR_UNSUPPORTED, "build_density needs B stored in full (not memory-lean)"};
     const int nao = h->nao, np = h->naux_pad;
     const size_t nao2 = (size_t)nao * nao;
     ensure_workspace(h, 1, nset);
+    if (!h->Kpart.p || h->ksplit < 1) {  // the FP64 split-K partials (mixed handles have none yet)
+      const int t = ceil_div(nao, 64);
+      h->ksplit = std::max(1, std::min(64, ceil_div(4 * 152, t * (t + 1) / 2)));
+      h->Kpart.alloc(nao2 * h->ksplit);
+    }
+    if (!h->rho_work.p || h->rho_work.n < (size_t)128 * ceil_div(np, 256) * 256)
+      h->rho_work.alloc((size_t)128 * ceil_div(np, 256) * 256);
+    // the GEMMs below take B in both triangles: a packed B is expanded into a
+    // temporary copy for the duration of the call
+    DBuf<double> Bfull;
+    const double *Bf = h->B.p;
+    if (h->lean) {
+      Bfull.alloc(nao2 * h->ldb);
+      unpack_tri_f64(h->B.p, h->ldb, nao, Bfull.p, st);
+      Bf = Bfull.p;
+    }
     DBuf<double> W;  // W[mu][sigma][P] = sum_lambda D[sigma][lambda] B[mu][lambda][P]
     W.alloc(nao2 * h->ldb);
     const long long kt = (long long)nao * h->ldb;
@@ -1118,15 +1188,15 @@ int dfjk_build_density(dfjk_handle h, int32_t nset, const double *D, double *J, 
       double *Js = J + s * nao2, *Ks = K + s * nao2;
       {  // J = B^T (B vec D)
         PhaseScope ph(6, st);
-        rho_gemv_f64(h->B.p, h->ldb, nao, np, Ds, h->rho.p, h->rho_work.p, 128, st);
-        j_gemv_f64(h->B.p, h->ldb, nao, np, h->rho.p, Js, 0, st);
+        rho_gemv_f64(Bf, h->ldb, nao, np, Ds, h->rho.p, h->rho_work.p, 128, st);
+        j_gemv_f64(Bf, h->ldb, nao, np, h->rho.p, Js, 0, st);
       }
       {
         PhaseScope ph(4, st);
         GemmArgs w;  // batch mu: W_mu (sigma x P) = D (sigma x lambda) B_mu (lambda x P)
         w.M = nao; w.N = np; w.K = nao; w.batch = nao;
         w.A = Ds; w.sAm = nao; w.sAk = 1; w.sAb = 0;
-        w.B = h->B.p; w.sBn = 1; w.sBk = h->ldb; w.sBb = (long long)nao * h->ldb;
+        w.B = Bf; w.sBn = 1; w.sBk = h->ldb; w.sBb = (long long)nao * h->ldb;
         w.C = W.p; w.sCm = h->ldb; w.sCn = 1; w.sCb = (long long)nao * h->ldb;
         gemm_f64(w, st);
       }
@@ -1134,7 +1204,7 @@ int dfjk_build_density(dfjk_handle h, int32_t nset, const double *D, double *J, 
       GemmArgs k;  // K[mu][nu] = sum_(sigma,P) W[mu][(sigma,P)] B[nu][(sigma,P)]
       k.M = nao; k.N = nao; k.K = (int)kt;
       k.A = W.p; k.sAm = kt; k.sAk = 1;
-      k.B = h->B.p; k.sBn = kt; k.sBk = 1;
+      k.B = Bf; k.sBn = kt; k.sBk = 1;
       k.C = h->Kpart.p; k.sCm = nao; k.sCn = 1; k.sCb = (long long)nao2;
       k.k_split = (int)((kt + h->ksplit - 1) / h->ksplit);
       k.k_split = ((k.k_split + 15) / 16) * 16;
@@ -1178,7 +1248,6 @@ static void jk_gradient(dfjk_ctx *h, const double *Din, int nocc, const double *
                  double *grad, cudaStream_t st) {
   DFJK_CUDA_CHECK(cudaSetDevice(h->device));
   if (!h->resident) make_resident(h, st);
-  if (h->lean) throw Error{DFJK_ERR_UNSUPPORTED, "gradient needs B stored in full (not memory-lean)"};
   const int nao = h->nao, np = h->naux_pad;
   const double *tab = boys_table_device();
   DBuf<double> Dl;
@@ -1199,7 +1268,7 @@ static void jk_gradient(dfjk_ctx *h, const double *Din, int nocc, const double *
   work.alloc(std::max<size_t>((size_t)128 * ceil_div(np, 256) * 256, (size_t)16 * np));
   d.alloc(np);
   DFJK_CUDA_CHECK(cudaMemsetAsync(d.p, 0, d.bytes(), st));
-  rho_gemv_f64(h->B.p, h->ldb, nao, np, D, rho.p, work.p, 128, st);
+  rho_gemv_f64(h->B.p, h->ldb, nao, np, D, rho.p, work.p, 128, st, h->lean ? 1 : 0);
   fitted_coefficients(h->Linv.p, h->naux, np, rho.p, work.p, d.p, st);
   DBuf<double> gam, W;
   std::deque<SlicedOp> ops;  // slices of the tensor-core GEMMs, freed after the final sync
@@ -1228,9 +1297,9 @@ static void jk_gradient(dfjk_ctx *h, const double *Din, int nocc, const double *
     oz_gemm(A, Bo, o, st);
   };
   if (ck != 0.0) {
-    // exact sliced tensor-core GEMMs when the handle is mixed (B's slices are
-    // resident), FP64 CUDA-core GEMMs otherwise
-    const bool tc = h->opt.precision == DFJK_MIXED && h->Bsl.data != nullptr;
+    // exact sliced tensor-core GEMMs when the handle is mixed (B packed),
+    // FP64 CUDA-core GEMMs otherwise (B in both triangles)
+    const bool tc = h->opt.precision == DFJK_MIXED;
     const long long no2 = (long long)nocc * nocc;
     DBuf<double> X, Xt, Z;
     X.alloc((size_t)nao * np * nocc);
@@ -1241,8 +1310,18 @@ static void jk_gradient(dfjk_ctx *h, const double *Din, int nocc, const double *
     if (tc) {
       const SlicedOp &csl = slice(C, 0, 1, nocc, 1, nocc, nao, OZ_BN);  // rows i, K nu
       const SlicedOp &cn = slice(C, 0, nocc, 1, 1, nao, nocc, OZ_BN);   // rows mu, K i
-      // X[mu][P][i] = sum_nu B[(mu,nu)][P] C[nu][i]
-      tc_gemm(h->Bsl, csl, np, nocc, nao, nao, X.p, nocc, (long long)np * nocc, 0);
+      // X[mu][P][i] = sum_nu B[(mu,nu)][P] C[nu][i], slicing the packed B chunk
+      // by chunk of rows P as the build does
+      const int pcm = build_chunk_rows(nao, np, nocc);
+      ops.emplace_back();
+      SlicedOp &bck = ops.back();
+      oz_alloc(bck, nao, 6, pcm, nao, OZ_BM);
+      for (int p0 = 0; p0 < np; p0 += pcm) {
+        const int pc = std::min(pcm, np - p0);
+        SlicedOp bv = oz_view(bck, pc, nao);
+        oz_slice_f64_packed(h->B.p + p0, h->ldb, 0, bv, h->B.host, st);
+        tc_gemm(bv, csl, pc, nocc, nao, nao, X.p + (size_t)p0 * nocc, nocc, (long long)np * nocc, 0);
+      }
       // Xt[P][j][i] = sum_mu X[mu][P][j] C[mu][i]  (symmetric in i, j)
       const SlicedOp &xs = slice(X.p, nocc, 1, (long long)np * nocc, np, nocc, nao, OZ_BM);
       tc_gemm(xs, csl, nocc, nocc, nao, np, Xt.p, nocc, no2, 0);
@@ -1542,6 +1621,31 @@ int dfjk_get_B(dfjk_handle h, double *Bout, void *stream) {
     DBuf<int> perm;
     perm.upload(ident, st);
     gather_B_f64(h->B.p, h->ldb, h->nao, perm.p, h->naux, Bout, h->lean ? 1 : 0, st);
+    DFJK_CUDA_CHECK(cudaStreamSynchronize(st));
+    return DFJK_OK;
+  } catch (const Error &e) {
+    return fail(e);
+  }
+}
+
+int dfjk_get_B_columns(dfjk_handle h, int32_t ncol, const int32_t *mu, const int32_t *nu, double *out,
+                       void *stream) {
+  try {
+    if (!h || ncol < 0 || (ncol > 0 && (!mu || !nu || !out))) throw Error{DFJK_ERR_ARG, "null argument"};
+    if (!h->resident) throw Error{DFJK_ERR_STATE, "handle evicted"};
+    if (ncol == 0) return DFJK_OK;
+    cudaStream_t st = S(stream);
+    std::vector<int> rows(ncol), ident(h->naux);
+    for (int c = 0; c < ncol; ++c) {
+      if (mu[c] < 0 || mu[c] >= h->nao || nu[c] < 0 || nu[c] >= h->nao) throw Error{DFJK_ERR_ARG, "AO index"};
+      const long long hi = std::max(mu[c], nu[c]), lo = std::min(mu[c], nu[c]);
+      rows[c] = (int)(h->lean ? hi * (hi + 1) / 2 + lo : (long long)mu[c] * h->nao + nu[c]);
+    }
+    for (int i = 0; i < h->naux; ++i) ident[i] = i;
+    DBuf<int> r, p;
+    r.upload(rows, st);
+    p.upload(ident, st);
+    gather2d_f64(h->B.p, h->ldb, r.p, p.p, ncol, h->naux, out, h->naux, st);
     DFJK_CUDA_CHECK(cudaStreamSynchronize(st));
     return DFJK_OK;
   } catch (const Error &e) {

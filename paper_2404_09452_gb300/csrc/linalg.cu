@@ -308,7 +308,7 @@ __global__ void __launch_bounds__(256) rho_partial_kernel(const double *__restri
                                                           long long ldb, int nao, int naux,
                                                           const double *__restrict__ D,
                                                           double *__restrict__ work, int ldw,
-                                                          long long rows_per) {
+                                                          long long rows_per, int packed) {
   const int P = blockIdx.x * 256 + threadIdx.x;
   const long long nrows = (long long)nao * (nao + 1) / 2;
   const long long r0 = (long long)blockIdx.y * rows_per;
@@ -319,7 +319,8 @@ __global__ void __launch_bounds__(256) rho_partial_kernel(const double *__restri
     tri_row(r0, mu, nu);
     for (long long r = r0; r < r1; ++r) {
       const double w = D[(long long)mu * nao + nu] * (mu == nu ? 1.0 : 2.0);
-      if (P < naux) acc = fma(w, B[((long long)mu * nao + nu) * ldb + P], acc);
+      const long long row = packed ? r : (long long)mu * nao + nu;
+      if (P < naux) acc = fma(w, B[row * ldb + P], acc);
       if (++nu > mu) {
         ++mu;
         nu = 0;
@@ -339,11 +340,11 @@ __global__ void column_sum_kernel(const double *__restrict__ work, int ldw, int 
 }
 
 void rho_gemv_f64(const double *B, long long ldb, int nao, int naux, const double *D,
-                  double *rho, double *work, int nchunk, cudaStream_t st) {
+                  double *rho, double *work, int nchunk, cudaStream_t st, int packed) {
   const long long nrows = (long long)nao * (nao + 1) / 2;
   const long long rows_per = (nrows + nchunk - 1) / nchunk;
   const int gx = ceil_div(naux, 256), ldw = gx * 256;
-  rho_partial_kernel<<<dim3(gx, nchunk), 256, 0, st>>>(B, ldb, nao, naux, D, work, ldw, rows_per);
+  rho_partial_kernel<<<dim3(gx, nchunk), 256, 0, st>>>(B, ldb, nao, naux, D, work, ldw, rows_per, packed);
   DFJK_LAUNCHED();
   column_sum_kernel<<<ceil_div(naux, 256), 256, 0, st>>>(work, ldw, nchunk, naux, rho);
   DFJK_LAUNCHED();
@@ -416,23 +417,42 @@ void j_gemv_f64(const double *B, long long ldb, int nao, int naux, const double 
   DFJK_LAUNCHED();
 }
 
+// Bfull[(mu nao + nu) ldb + P] = Bp[(max (max + 1) / 2 + min) ldb + P]: one
+// block per (mu, nu) pair, threads along P (coalesced).
+__global__ void __launch_bounds__(256) unpack_tri_kernel(const double *__restrict__ Bp, long long ldb, int nao,
+                                                         double *__restrict__ Bf) {
+  const long long e = blockIdx.x;  // mu nao + nu
+  const int mu = (int)(e / nao), nu = (int)(e % nao);
+  const long long hi = mu > nu ? mu : nu, lo = mu > nu ? nu : mu;
+  const double *src = Bp + (hi * (hi + 1) / 2 + lo) * ldb;
+  double *dst = Bf + e * ldb;
+  for (long long P = threadIdx.x; P < ldb; P += 256) dst[P] = src[P];
+}
+
+void unpack_tri_f64(const double *Bp, long long ldb, int nao, double *Bfull, cudaStream_t st) {
+  const long long n2 = (long long)nao * nao;
+  if (n2 == 0) return;
+  unpack_tri_kernel<<<(unsigned)n2, 256, 0, st>>>(Bp, ldb, nao, Bfull);
+  DFJK_LAUNCHED();
+}
+
 // ---- reductions -----------------------------------------------------------------------
 
 __global__ void reduce_sym_kernel(const double *__restrict__ part, int nsplit, int n,
-                                  double *__restrict__ out) {
+                                  double *__restrict__ out, int add) {
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (long long)n * n) return;
   const int mu = (int)(e / n), nu = (int)(e % n);
   if (nu > mu) return;
-  double s = 0.0;
+  double s = add ? out[e] : 0.0;
   for (int k = 0; k < nsplit; ++k) s += part[(long long)k * n * n + e];
   out[e] = s;
   out[(long long)nu * n + mu] = s;
 }
 
-void reduce_sym_f64(const double *part, int nsplit, int n, double *out, cudaStream_t st) {
+void reduce_sym_f64(const double *part, int nsplit, int n, double *out, cudaStream_t st, int add) {
   const long long n2 = (long long)n * n;
-  reduce_sym_kernel<<<(unsigned)((n2 + 255) / 256), 256, 0, st>>>(part, nsplit, n, out);
+  reduce_sym_kernel<<<(unsigned)((n2 + 255) / 256), 256, 0, st>>>(part, nsplit, n, out, add);
   DFJK_LAUNCHED();
 }
 

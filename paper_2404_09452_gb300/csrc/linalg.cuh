@@ -51,11 +51,14 @@ void cholesky_f64(double *A, int n, int lda, double *Dinv, int *status, double *
 void tri_inverse_f64(const double *L, int n, int ld, const double *Dinv, double *Linv,
                      double *work, cudaStream_t st);
 
-// rho[P] = sum_{mu >= nu} w D[mu][nu] B[(mu nao + nu) ldb + P], w = 2 off the
-// diagonal; partial sums in `work` (ceil(naux/256) x nchunk) then a fixed-order
-// reduction.
+// rho[P] = sum_{mu >= nu} w D[mu][nu] B[row ldb + P], w = 2 off the diagonal,
+// row = mu nao + nu (both triangles stored) or mu (mu + 1) / 2 + nu (packed);
+// partial sums in `work` (ceil(naux/256) x nchunk) then a fixed-order reduction.
 void rho_gemv_f64(const double *B, long long ldb, int nao, int naux, const double *D,
-                  double *rho, double *work, int nchunk, cudaStream_t st);
+                  double *rho, double *work, int nchunk, cudaStream_t st, int packed = 0);
+// Both triangles of a packed B: Bfull[(mu nao + nu) ldb + P] =
+// Bp[(max (max + 1) / 2 + min) ldb + P] (nao^2 rows of ldb doubles).
+void unpack_tri_f64(const double *Bp, long long ldb, int nao, double *Bfull, cudaStream_t st);
 // rho[P] = sum_{mu,i} C[mu][i] X[mu][P][i]  (= sum_{mu nu} B[mu][nu][P] D[mu][nu]
 // since X_P = B_P C and D = C C^T); per-mu partials in `part` (nao x np).
 void rho_from_x_f64(const double *X, const double *C, int nao, int np, int nocc, double *rho,
@@ -64,8 +67,9 @@ void rho_from_x_f64(const double *X, const double *C, int nao, int np, int nocc,
 // row = mu nao + nu (full storage) or mu (mu + 1) / 2 + nu (packed triangle).
 void j_gemv_f64(const double *B, long long ldb, int nao, int naux, const double *rho, double *J,
                 int packed, cudaStream_t st);
-// out[mu][nu] = out[nu][mu] = sum_s part[s][mu][nu] (mu >= nu).
-void reduce_sym_f64(const double *part, int nsplit, int n, double *out, cudaStream_t st);
+// out[mu][nu] = out[nu][mu] = sum_s part[s][mu][nu] (mu >= nu), summed in
+// split order; add = 1 starts the sum from the current out[mu][nu].
+void reduce_sym_f64(const double *part, int nsplit, int n, double *out, cudaStream_t st, int add = 0);
 // K[mu][nu] = K[nu][mu] for nu > mu (the lower triangle is the result).
 void mirror_lower_f64(double *K, int n, cudaStream_t st);
 // e[0] = Tr(D J)/2, e[1] = Tr(D K)/2 (fixed-order two-level reduction).

@@ -262,16 +262,30 @@ __global__ void __launch_bounds__(256) oz_slice_tr_fused_kernel(const double *__
   }
 }
 
-void oz_alloc(SlicedOp &op, int batch, int S, int rows, int K, int row_tile) {
-  oz_free(op);
+static void oz_shape(SlicedOp &op, int batch, int S, int rows, int K, int row_tile) {
   op.batch = batch;
   op.S = S;
   op.rows = rows;
+  op.row_tile = row_tile;
   op.rows_pad = ((rows + row_tile - 1) / row_tile) * row_tile;
   op.K = K;
   op.nkb = (K + OZ_KB - 1) / OZ_KB;
   op.kblk = op.nkb > 4 ? 1 : 0;
   op.kpitch = op.kblk ? op.nkb * OZ_KB : ((K + OZ_BK - 1) / OZ_BK) * OZ_BK;
+}
+
+SlicedOp oz_view(const SlicedOp &op, int rows, int K) {
+  if (rows > op.rows || K > op.K || rows < 1 || K < 1) throw Error{DFJK_ERR_ARG, "oz_view: larger than the buffer"};
+  SlicedOp v;
+  oz_shape(v, op.batch, op.S, rows, K, op.row_tile);
+  v.data = op.data;
+  v.expo = op.expo;
+  return v;
+}
+
+void oz_alloc(SlicedOp &op, int batch, int S, int rows, int K, int row_tile) {
+  oz_free(op);
+  oz_shape(op, batch, S, rows, K, row_tile);
   const size_t nd = (size_t)batch * S * op.rows_pad * op.kpitch;
   const size_t ne = (size_t)batch * op.rows_pad * op.nkb;
   op.data = (__nv_bfloat16 *)pool_alloc(nd * sizeof(__nv_bfloat16));
@@ -909,7 +923,7 @@ __global__ void __launch_bounds__(OZ_WS_THREADS, 1)
           double *o = g.out + (long long)m * g.ldo + nh;
 #pragma unroll
           for (int j = 0; j < NH; ++j)
-            if (nh + j < g.N) o[j] = (z == 0) ? acc[j] : __ldcg(o + j) + acc[j];  // L2, not a stale L1 line
+            if (nh + j < g.N) o[j] = (z == 0 && !g.accumulate) ? acc[j] : __ldcg(o + j) + acc[j];  // L2, not a stale L1 line
         }
         __threadfence();
         __syncwarp();

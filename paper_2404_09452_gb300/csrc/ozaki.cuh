@@ -30,7 +30,7 @@ constexpr int OZ_BM = 128, OZ_BN = 64, OZ_BK = 32;
 struct SlicedOp {
   __nv_bfloat16 *data = nullptr;
   int *expo = nullptr;
-  int batch = 1, S = 0, rows = 0, rows_pad = 0, K = 0, kpitch = 0, nkb = 0, kblk = 0;
+  int batch = 1, S = 0, rows = 0, rows_pad = 0, K = 0, kpitch = 0, nkb = 0, kblk = 0, row_tile = 0;
   size_t bytes() const {
     return (size_t)batch * S * rows_pad * kpitch * 2 + (size_t)batch * rows_pad * nkb * 4;
   }
@@ -39,6 +39,11 @@ struct SlicedOp {
 // Sizes an operand (rows padded to `row_tile`, K pitch to OZ_BK) and allocates it.
 void oz_alloc(SlicedOp &op, int batch, int S, int rows, int K, int row_tile);
 void oz_free(SlicedOp &op);
+// A view of op's buffers sized for `rows` rows and K columns (at most the
+// allocated rows and K): the layout a fresh allocation of that size would
+// have, placed at the start of op's buffers.  Used for the short last chunk
+// of a chunked reduction without reallocating.
+SlicedOp oz_view(const SlicedOp &op, int rows, int K);
 
 // Fills `op` from the FP64 view x(z, r, k) = src[z sz + r sr + k sk]
 // (rows >= op.rows and k >= op.K are zero).
@@ -57,6 +62,8 @@ struct OzGemmArgs {
                          // 2: split-K in order, out[m ldo + n] (+)= C of split z
                          //    after splits 0..z-1 (persistent kernel only)
   int *tile_seq = nullptr;  // mode 2: per (tile, drain warp) split counters
+  int accumulate = 0;    // mode 2: split 0 also adds onto out (a later chunk of
+                         // the reduction range, in chunk order)
   int packed = 0;        // mode 1: out holds the mu >= nu triangle, row mu (mu + 1) / 2 + nu
   double *out = nullptr;
   long long ldo = 0, out_bs = 0;

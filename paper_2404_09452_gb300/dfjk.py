@@ -37,6 +37,7 @@ EXPORTS = [
     "dfjk_query",
     "dfjk_query_precision",
     "dfjk_query_setup",
+    "dfjk_estimate_bytes",
     "dfjk_build",
     "dfjk_build_uks",
     "dfjk_build_density",
@@ -55,6 +56,7 @@ EXPORTS = [
     "dfjk_get_cholesky",
     "dfjk_get_B",
     "dfjk_get_pair_mask",
+    "dfjk_get_B_columns",
     "dfjk_get_three_center",
     "dfjk_debug_sliced_gemm",
     "dfjk_set_timing",
@@ -124,6 +126,9 @@ def load_library(path: str = LIB_PATH):
         vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_size_t)
     ]
     lib.dfjk_build.argtypes = [vp, i32, i32, vp, vp, vp, vp, vp, vp]
+    szp = ctypes.POINTER(ctypes.c_size_t)
+    lib.dfjk_estimate_bytes.argtypes = [i32, i32, i32, i32, szp, szp, szp]
+    lib.dfjk_get_B_columns.argtypes = [vp, i32, vp, vp, vp, vp]
     lib.dfjk_overlap.argtypes = [vp, vp, vp]
     lib.dfjk_coulomb_gradient.argtypes = [vp, vp, vp, vp]
     lib.dfjk_jk_gradient.argtypes = [vp, i32, vp, ctypes.c_double, ctypes.c_double, vp, vp]
@@ -211,7 +216,7 @@ def default_options(precision: int = DFJK_FP64, schwarz_thresh: float = 1e-12,
 
 
 class Handle:
-    """A molecule set up on the device (steps a0-a5); B stays resident."""
+    """A molecule set up on the device (integrals, metric, Cholesky, whitening); B stays resident."""
 
     def __init__(self, mol, precision: int = DFJK_FP64, schwarz_thresh: float = 1e-12,
                  hbm_budget_bytes: int = 0, stream=None, timeout_iters: int = 0,
@@ -375,6 +380,17 @@ class Handle:
     def B(self):
         return self._get("dfjk_get_B", (self.naux, self.nao, self.nao))
 
+    def B_columns(self, mu, nu):
+        """B[:, mu[c], nu[c]] for each c, as a device tensor [ncol, naux]."""
+        torch = _torch()
+        mu = np.ascontiguousarray(mu, dtype=np.int32)
+        nu = np.ascontiguousarray(nu, dtype=np.int32)
+        out = torch.empty((len(mu), self.naux), dtype=torch.float64, device="cuda")
+        _check(load_library().dfjk_get_B_columns(self.h, len(mu), ctypes.c_void_p(mu.ctypes.data),
+                                                 ctypes.c_void_p(nu.ctypes.data),
+                                                 ctypes.c_void_p(out.data_ptr()), _stream()))
+        return out
+
     def three_center(self):
         return self._get("dfjk_get_three_center", (self.naux, self.nao, self.nao))
 
@@ -386,7 +402,7 @@ class Handle:
 
 def build_batch(handles, Cs, Js=None, Ks=None, E=None, nstreams=8, stream=None):
     """Builds every resident handle with its C (device [nao_i, nocc_i]) in one
-    call (row a10).  Returns (Js, Ks, E) with E a device tensor [2, nmol]
+    call (batching).  Returns (Js, Ks, E) with E a device tensor [2, nmol]
     (E_J, E_K); nothing is synchronised."""
     torch = _torch()
     n = len(handles)
@@ -455,6 +471,16 @@ def energies_noalloc(D, J, K, E, stream=None):
         n, ctypes.c_void_p(D.data_ptr()), ctypes.c_void_p(J.data_ptr()),
         ctypes.c_void_p(K.data_ptr()), ctypes.c_void_p(E.data_ptr()), _stream(stream)))
     return E
+
+
+def estimate_bytes(nao: int, naux: int, nocc: int, precision: int) -> dict:
+    """Device bytes of a molecule before setup (dfjk_estimate_bytes): resident
+    data, the build's work buffers at nocc, the setup's transient peak."""
+    lib = load_library()
+    r, w, s = ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_size_t()
+    _check(lib.dfjk_estimate_bytes(int(nao), int(naux), int(nocc), int(precision), ctypes.byref(r),
+                                   ctypes.byref(w), ctypes.byref(s)))
+    return {"resident": r.value, "build_ws": w.value, "setup_ws": s.value}
 
 
 def launch_count() -> int:

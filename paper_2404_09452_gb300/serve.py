@@ -3,11 +3,11 @@
 Requests (molecule, C_occ) arrive as a stream.  The server keeps each
 molecule's whitened tensor B resident under a device-memory budget (LRU order;
 a miss evicts the least recently used idle molecules and recomputes B with
-`dfjk_setup`).  Requests that arrive while others are on the GPU are admitted
-as soon as a build slot and their molecule are free: each build runs on one
-of `slots` CUDA streams, so builds of different molecules overlap on the
-device.  Builds of the same molecule are serialised (its work buffers are
-shared).  Latency is measured from arrival to the host observing completion
+`dfjk_setup` on a worker thread, while other requests keep being admitted).
+Requests that arrive while others are on the GPU are admitted as soon as a
+build slot and their molecule are free: each build runs on one of `slots`
+CUDA streams, so builds of different molecules overlap on the device.
+Builds of the same molecule are serialised (its work buffers are shared).  Latency is measured from arrival to the host observing completion
 of the build's event.  The paper's SCF loop (Sec. "Compatibility", the
 `kernel()` call) repeats J/K builds for one molecule with new orbitals; the
 ~70 % repeat rate of the request stream models that.
@@ -32,6 +32,7 @@ class Request:
     mol_id: int
     C: object  # device tensor [nao, nocc]
     done: float = -1.0
+    error: str = ""  # set when the request could not be served (its setup failed)
     E: tuple = ()
     J: object = None
     K: object = None
@@ -79,6 +80,7 @@ class Stats:
     latencies: list = field(default_factory=list)
     misses: int = 0
     evictions: int = 0
+    failed: int = 0
     seconds: float = 0.0
 
     def summary(self):
@@ -90,12 +92,24 @@ class Stats:
             "builds_per_s": len(lat) / self.seconds if self.seconds else None,
             "misses": self.misses,
             "evictions": self.evictions,
+            "failed": self.failed,
         }
 
 
 class Server:
+    """Continuous batching with asynchronous admission: a request whose
+    molecule is resident and idle starts its build on a free slot at once; a
+    miss reserves the molecule's bytes (evicting idle molecules in LRU order)
+    and runs its setup on a worker thread with a stream of its own, so that
+    hits keep being admitted and completions keep being retired while the
+    setup runs.  Builds of one molecule are serialised (its work buffers are
+    shared)."""
+
     def __init__(self, mols, precision=dfjk.DFJK_MIXED, budget_bytes=150 << 30, slots=8,
-                 keep_outputs=False):
+                 keep_outputs=False, setup_workers=2):
+        import threading
+        from concurrent.futures import ThreadPoolExecutor
+
         import torch
 
         self.torch = torch
@@ -103,27 +117,43 @@ class Server:
         self.precision = precision
         self.budget = budget_bytes
         self.keep = keep_outputs
-        self.resident = {}  # mol_id -> Handle
+        self.resident = {}  # mol_id -> Handle (set up, ready)
+        self.setting_up = {}  # mol_id -> Future of its Handle
         self.lru = Residency(budget_bytes)
-        self.busy = set()  # mol_ids with a build in flight
+        self.busy = set()  # mol_ids with a build or a setup in flight
         self.streams = [torch.cuda.Stream() for _ in range(slots)]
         self.free_slots = list(range(slots))
         self.stats = Stats()
+        self._local = threading.local()
+        self._pool = ThreadPoolExecutor(max_workers=max(1, setup_workers))
+        self.device = torch.cuda.current_device()
 
     def _bytes(self, mol_id, nocc):
         m = self.mols[mol_id]
         return resident_bytes(m.nao, m.naux, nocc, self.precision)
 
-    def _ensure_resident(self, mol_id, nocc):
-        if self.lru.touch(mol_id):
-            return True
+    def _setup(self, mol_id):
+        torch = self.torch
+        if not hasattr(self._local, "stream"):
+            torch.cuda.set_device(self.device)
+            self._local.stream = torch.cuda.Stream()
+        s = self._local.stream
+        with torch.cuda.stream(s):
+            h = dfjk.Handle(self.mols[mol_id], precision=self.precision, stream=s)
+        s.synchronize()
+        return h
+
+    def _start_setup(self, mol_id, nocc) -> bool:
+        """Reserves the molecule's bytes and starts its setup; False when the
+        budget cannot be met now (every resident molecule is busy)."""
         ok, evicted = self.lru.admit(mol_id, self._bytes(mol_id, nocc), self.busy)
         for v in evicted:
             self.resident.pop(v).close()
             self.stats.evictions += 1
         if not ok:
             return False
-        self.resident[mol_id] = dfjk.Handle(self.mols[mol_id], precision=self.precision)
+        self.busy.add(mol_id)
+        self.setting_up[mol_id] = self._pool.submit(self._setup, mol_id)
         self.stats.misses += 1
         return True
 
@@ -133,30 +163,53 @@ class Server:
         waiting = collections.deque()
         inflight = []  # (request, slot, event, outputs)
         t0 = time.perf_counter()
-        while pending or waiting or inflight:
+        while pending or waiting or inflight or self.setting_up:
             now = time.perf_counter() - t0
             while pending and pending[0].arrival <= now:
                 waiting.append(pending.popleft())
-            # admit: oldest waiting requests first, skipping molecules already in flight
             progressed = False
+            # setups that finished: their molecules become resident and idle
+            for mid, fut in list(self.setting_up.items()):
+                if fut.done():
+                    del self.setting_up[mid]
+                    self.busy.discard(mid)
+                    progressed = True
+                    try:
+                        self.resident[mid] = fut.result()
+                    except dfjk.DfjkError as e:
+                        # the molecule cannot be set up (device memory, budget):
+                        # its waiting requests fail, its reservation is returned
+                        self.lru.drop(mid)
+                        for req in [r for r in waiting if r.mol_id == mid]:
+                            req.error = str(e)
+                            req.done = time.perf_counter() - t0
+                            waiting.remove(req)
+                            self.stats.failed += 1
+            # admission, oldest waiting request first: a hit builds at once on a
+            # free slot; a miss starts its setup; requests whose molecule is busy
+            # (a build or a setup in flight) wait
+            started = set()
             for req in list(waiting):
-                if not self.free_slots:
-                    break
-                if req.mol_id in self.busy:
+                mid = req.mol_id
+                if mid in self.busy or mid in started:
                     continue
-                if not self._ensure_resident(req.mol_id, int(req.C.shape[1])):
-                    break
-                h = self.resident[req.mol_id]
-                slot = self.free_slots.pop()
-                s = self.streams[slot]
-                with torch.cuda.stream(s):
-                    J, K, EJ, EK = h.build(req.C, stream=s, energies_on_device=True)
-                    ev = torch.cuda.Event()
-                    ev.record(s)
-                self.busy.add(req.mol_id)
-                inflight.append((req, slot, ev, (J, K, EJ, EK)))
-                waiting.remove(req)
-                progressed = True
+                if self.lru.touch(mid):
+                    if not self.free_slots:
+                        continue
+                    h = self.resident[mid]
+                    slot = self.free_slots.pop()
+                    s = self.streams[slot]
+                    with torch.cuda.stream(s):
+                        J, K, EJ, EK = h.build(req.C, stream=s, energies_on_device=True)
+                        ev = torch.cuda.Event()
+                        ev.record(s)
+                    self.busy.add(mid)
+                    inflight.append((req, slot, ev, (J, K, EJ, EK)))
+                    waiting.remove(req)
+                    progressed = True
+                elif self._start_setup(mid, int(req.C.shape[1])):
+                    started.add(mid)
+                    progressed = True
             still = []
             for req, slot, ev, out in inflight:
                 if ev.query():
@@ -173,7 +226,7 @@ class Server:
                     still.append((req, slot, ev, out))
             inflight = still
             if not progressed:
-                if inflight:
+                if inflight or self.setting_up:
                     time.sleep(20e-6)
                 elif pending and not waiting:
                     time.sleep(max(0.0, min(1e-3, pending[0].arrival - (time.perf_counter() - t0))))
@@ -184,6 +237,13 @@ class Server:
         return requests
 
     def close(self):
+        for fut in self.setting_up.values():
+            try:
+                fut.result().close()
+            except dfjk.DfjkError:
+                pass
+        self.setting_up.clear()
+        self._pool.shutdown(wait=True)
         for h in self.resident.values():
             h.close()
         self.resident.clear()

@@ -116,9 +116,13 @@ def test_expired_device_wait_is_reported_and_context_survives():
     h.close()
 
 
-def test_memory_lean_mode_matches_resident_slices(tmp_path):
-    """With the resident slice limit set to 0 the mixed path slices B per build
-    in chunks of mu; results are identical to the resident-slice mode."""
+def test_chunked_build_matches_one_chunk_and_oracle(tmp_path):
+    """The mixed build works through the aux index in chunks of rows P when its
+    work buffers would exceed DFJK_BUILD_WS_MB (here forced to the 128-row
+    minimum: four chunks at 12 atoms, the last one short).  K accumulates the
+    chunks in order, so the result differs from the one-chunk build only by
+    the rounding of the sliced products: both meet the bar against the
+    oracle and agree to 1e-9."""
     import os
     import subprocess
     import sys
@@ -127,23 +131,37 @@ def test_memory_lean_mode_matches_resident_slices(tmp_path):
     code = (
         "import sys, numpy as np, torch; sys.path.insert(0, %r);"
         "from paper_2404_09452_gb300 import dfjk, inputs as I;"
-        "m = I.molecule(12, seed=1012); h = dfjk.Handle(m, precision=dfjk.DFJK_MIXED);"
-        "C = torch.from_numpy(dfjk.orthonormal_c_occ(h, I.c_occ_raw(m.nao, 36, 3000))).cuda();"
-        "J, K, EJ, EK = h.build(C); np.save(sys.argv[1], np.concatenate([J[0].cpu().numpy().ravel(), "
-        "K[0].cpu().numpy().ravel(), [EJ[0], EK[0]]]))"
+        "m = I.molecule(12, seed=1012); C = np.load(sys.argv[2]);"
+        "h = dfjk.Handle(m, precision=dfjk.DFJK_MIXED);"
+        "J, K, EJ, EK = h.build(torch.from_numpy(C).cuda()); np.save(sys.argv[1], np.concatenate(["
+        "J[0].cpu().numpy().ravel(), K[0].cpu().numpy().ravel(), [EJ[0], EK[0]]]))"
     ) % root
+    m = I.molecule(12, seed=1012)
+    S = O.overlap(m.orb, m.coords)
+    C = I.orthonormalize(I.c_occ_raw(m.nao, I.default_nocc(m.nao), 3000), S)
+    cpath = str(tmp_path / "C.npy")
+    np.save(cpath, C)
     outs = []
-    for lim in ("0", str(1 << 40)):
-        out = str(tmp_path / f"r{lim}.npy")
-        env = dict(os.environ, DFJK_BSLICE_MAX_BYTES=lim)
-        subprocess.run([sys.executable, "-c", code, out], check=True, env=env, timeout=300)
+    for ws in ("1", "8192"):
+        out = str(tmp_path / f"r{ws}.npy")
+        env = dict(os.environ, DFJK_BUILD_WS_MB=ws)
+        subprocess.run([sys.executable, "-c", code, out, cpath], check=True, env=env, timeout=300)
         outs.append(np.load(out))
-    assert np.array_equal(outs[0], outs[1])
+    n2 = m.nao * m.nao
+    ref = O.dfjk(m.orb, m.aux, m.coords, C)
+    for r in outs:
+        J, K = r[:n2].reshape(m.nao, m.nao), r[n2:2 * n2].reshape(m.nao, m.nao)
+        assert np.abs(J - ref["J"]).max() <= JK_TOL and np.abs(K - ref["K"]).max() <= JK_TOL
+        assert abs(r[-2] - ref["E_J"]) <= E_TOL and abs(r[-1] - ref["E_K"]) <= E_TOL
+        assert np.array_equal(K, K.T)
+    assert np.abs(outs[0] - outs[1]).max() < 1e-9
+    assert not np.array_equal(outs[0][n2:2 * n2], outs[1][n2:2 * n2])  # the chunked path did run
 
 
 def test_config_120_atoms_mixed_vs_fp64_gpu():
-    """The 120-atom mixed configuration (nao 1800, naux 4320, nocc 360; B
-    sliced per build, memory-lean) against the FP64 GPU path at the same size."""
+    """The 120-atom mixed configuration (nao 1800, naux 4320, nocc 360; B kept
+    as the packed triangle, sliced per build in chunks of aux rows) against the
+    FP64 GPU path at the same size."""
     m = I.molecule(120, seed=1003)
     nocc = I.default_nocc(m.nao)
     h64 = dfjk.Handle(m, precision=dfjk.DFJK_FP64)
@@ -184,3 +202,43 @@ def test_ordered_split_k_matches_partial_reduction(tmp_path):
         outs.append(np.load(out))
     assert np.array_equal(outs[0], outs[1])
     assert np.array_equal(outs[0], outs[0].T)
+
+
+def test_config_120_atoms_sampled_B_columns_vs_oracle():
+    """At the full 120-atom size (nao 1800, naux 4320): whitened columns
+    B[:, mu, nu] of 40 sampled kept shell pairs against the oracle, which
+    evaluates (P|mu nu) for those pairs against every aux shell, the metric
+    (P|Q) in full, its Cholesky factor and the triangular solve.  This covers
+    the integrals and the tensor-core whitening at a size where the oracle's
+    full build does not fit a test."""
+    import scipy.linalg
+
+    m = I.molecule(120, seed=1003)
+    h = dfjk.Handle(m, precision=dfjk.DFJK_MIXED)
+    mask = h.pair_mask().cpu().numpy()
+    rng = np.random.default_rng(1)
+    kept = np.argwhere(np.tril(mask))
+    pairs = kept[rng.choice(len(kept), size=40, replace=False)]
+    oo = np.cumsum([0] + [(s.l + 1) * (s.l + 2) // 2 for s in m.orb.shells])
+    oa = np.cumsum([0] + [(s.l + 1) * (s.l + 2) // 2 for s in m.aux.shells])
+    na = len(m.aux.shells)
+    trip = [(int(a), int(b), c) for a, b in pairs for c in range(na)]
+    blocks = O.three_center_triples(m.orb, m.aux, m.coords, trip)
+    V = O.metric(m.aux, m.coords)
+    L = scipy.linalg.cholesky(V, lower=True)
+    cols_mu, cols_nu, T = [], [], []
+    k = 0
+    for a, b in pairs:
+        blk = blocks[k:k + na]
+        k += na
+        for ca in range(oo[a + 1] - oo[a]):
+            for cb in range(oo[b + 1] - oo[b]):
+                cols_mu.append(oo[a] + ca)
+                cols_nu.append(oo[b] + cb)
+                T.append(np.concatenate([blk[c][ca, cb, :] for c in range(na)]))
+    Bref = scipy.linalg.solve_triangular(L, np.array(T).T, lower=True).T
+    Bgpu = h.B_columns(cols_mu, cols_nu).cpu().numpy()
+    err = np.abs(Bgpu - Bref).max()
+    print(f"mol120 sampled B columns: {len(cols_mu)} columns, max|dB| {err:.2e}, max|B| {np.abs(Bref).max():.2e}")
+    assert err < 1e-6 * max(1.0, np.abs(Bref).max())
+    h.close()
