@@ -24,6 +24,7 @@ import subprocess
 import sys
 import threading
 import time
+import types
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
@@ -38,8 +39,67 @@ WORKLOADS = {
     "water": dict(natom=0, seed=1001, note="3-atom water, nao 18, naux 30, nocc 5"),
 }
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
-FP64_PEAK_GFLOPS = 1199.0  # measured FP64 DFMA throughput of this GB300 pool (FMA chains)
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_mol60.md")
+ERI_COUNTS_FILE = os.path.join(ROOT, "profiles", "eri3c_mol20.md")
+PAIR_CLASSES = [(0, 0), (1, 0), (1, 1), (2, 0), (2, 1), (2, 2)]
+
+
+def eri_flops_per_triple():
+    """FP64 and FP32 flops per primitive triple of each 3-centre integral
+    kernel, {(LA, LB, LC, "fp64"|"fp32"): (dflop, sflop)}: the ncu instruction
+    counts of one capture (DFMA x2 + DMUL + DADD; FFMA x2 + FFMA2 x4 + FMUL +
+    FADD) divided by the primitive triples that launch processed, both
+    recorded in profiles/eri3c_mol20.md; empty when the kernel source
+    (csrc/md.cuh) changed since the capture."""
+    import hashlib
+
+    src = os.path.join(ROOT, "paper_2404_09452_gb300", "csrc", "md.cuh")
+    if not os.path.exists(ERI_COUNTS_FILE) or not os.path.exists(src):
+        return {}
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    out = {}
+    for line in open(ERI_COUNTS_FILE):
+        f = line.split()
+        # eri3c-count <LA> <LB> <LC> <fp64|fp32> <primitive triples> <dflop> <sflop> <sha16 of md.cuh>
+        if len(f) == 9 and f[0] == "eri3c-count" and f[8] == sha and int(f[5]) > 0:
+            n = float(f[5])
+            out[(int(f[1]), int(f[2]), int(f[3]), f[4])] = (float(f[6]) / n, float(f[7]) / n)
+    return out
+
+
+def eri_roofline(h, m, ms64, ms32, fp64_peak, fp32_peak):
+    """Roofline of the 3-centre integral phase (FP64-ALU bound): counted
+    flops of the step's primitive triples per precision, divided by the
+    phase's CUDA-event time, against the measured FMA rates."""
+    per = eri_flops_per_triple()
+    if not per:
+        return None
+    naux_prims = [sum(len(sh.exps) for sh in m.aux.shells if sh.l == lc) for lc in range(3)]
+    f64 = f32_s = f32_d = 0.0
+    trip64 = trip32 = 0
+    for c, (la, lb) in enumerate(PAIR_CLASSES):
+        for lc in range(3):
+            t64 = h.prim_pairs_fp64[c] * naux_prims[lc]
+            t32 = h.prim_pairs_fp32[c] * naux_prims[lc]
+            trip64 += t64
+            trip32 += t32
+            d, _ = per.get((la, lb, lc, "fp64"), (0.0, 0.0))
+            d32, s32 = per.get((la, lb, lc, "fp32"), (0.0, 0.0))
+            f64 += t64 * d
+            f32_d += t32 * d32
+            f32_s += t32 * s32
+    out = {"bound": "alu", "unit": "TFLOP/s", "primitive_triples_fp64": trip64,
+           "primitive_triples_fp32": trip32, "flop_source": "ncu instruction counts per primitive triple "
+           "(profiles/eri3c_mol20.md)"}
+    if ms64:
+        a = f64 / (ms64 / 1e3) / 1e12
+        out["fp64"] = {"flops": f64, "ms": ms64, "achieved": a, "peak": fp64_peak, "frac": a / fp64_peak,
+                       "peak_source": "dfjk_fma_rate(64), measured in this run"}
+    if ms32:
+        a = f32_s / (ms32 / 1e3) / 1e12
+        out["fp32"] = {"flops": f32_s, "fp64_flops": f32_d, "ms": ms32, "achieved": a, "peak": fp32_peak,
+                       "frac": a / fp32_peak, "peak_source": "dfjk_fma_rate(32), measured in this run"}
+    return out
 
 
 def recorded_traffic(key: str, workload: str):
@@ -74,6 +134,9 @@ def parse():
     ap.add_argument("--grad-mol", default="mol60", choices=list(WORKLOADS),
                     help="molecule of --workload gradient")
     ap.add_argument("--batch-n", type=int, default=256)
+    ap.add_argument("--autotune", action="store_true",
+                    help="batch: run the autotuner (tune.py) first and use its table")
+    ap.add_argument("--tune-table", default=None, help="tuning table to use (or to write with --autotune)")
     ap.add_argument("--compare-fp64", action="store_true",
                     help="batch/serve: also time the plain FP64 per-molecule path")
     ap.add_argument("--serve-rates", default="10,20,50,100,200,500")
@@ -313,6 +376,7 @@ def run_ours(args):
     fp32_pairs = {"thresh": h0.fp32_pair_thresh, "fp32_shell_pairs": h0.npair_fp32,
                   "kept_shell_pairs": h0.npair_kept}
     nslab, lean = h0.nslab, h0.lean
+    pair_work = types.SimpleNamespace(prim_pairs_fp64=h0.prim_pairs_fp64, prim_pairs_fp32=h0.prim_pairs_fp32)
     S = h0.overlap().cpu().numpy()
     Cnp = I.orthonormalize(I.c_occ_raw(m.nao, nocc, 3000 + rank), S)
     mask = h0.pair_mask().cpu().numpy()
@@ -331,6 +395,8 @@ def run_ours(args):
         h.close()
         return EJ[0], EK[0]
 
+    # FP64 / FP32 FMA throughput of this GPU (the integral kernels' roofline)
+    fp64_peak, fp32_peak = dfjk.fma_rate(64), dfjk.fma_rate(32)
     for _ in range(args.warmup):
         energies = step()
     torch.cuda.synchronize()
@@ -427,8 +493,8 @@ def run_ours(args):
         dom_ms = per_step[dom]
         achieved = flops[dom] / (dom_ms / 1e3) / 1e12
         roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "unit": "TFLOP/s",
-                "peak": FP64_PEAK_GFLOPS / 1e3,
-                "peak_source": "measured FP64 DFMA rate of this GPU pool (FP64 FMA-chain probe)",
+                "peak": fp64_peak,
+                "peak_source": "dfjk_fma_rate(64): FP64 FMA chains on every SM, measured in this run",
                 "traffic": None, "algorithmic_flops_per_launch": flops[dom], "ms_per_launch": dom_ms,
                 "launches_per_step": 1}
     else:
@@ -453,7 +519,7 @@ def run_ours(args):
     # integrals/s, a8 (rho from X, then J over the mu >= nu rows of B) as GB/s
     triples = int(fp32_pairs["kept_shell_pairs"]) * len(m.aux.shells)
     n_int = int(ncol) * int(m.naux)
-    eri_ms = per_step.get("eri3c", 0.0)
+    eri_ms = per_step.get("eri3c", 0.0) + per_step.get("eri3c32", 0.0)
     np_pad = (m.naux + 63) // 64 * 64
     j_bytes = (m.nao * (m.nao + 1) // 2 * np_pad + m.nao * np_pad * nocc) * 8
     j_ms = per_step.get("rho+J", 0.0)
@@ -481,6 +547,9 @@ def run_ours(args):
         "phase_ms": per_step, "E_J": float(energies[0]), "E_K": float(energies[1]),
         "roofline": roof,
         "units": units,
+        "roofline_a4": eri_roofline(pair_work, m, per_step.get("eri3c", 0.0), per_step.get("eri3c32", 0.0),
+                                    fp64_peak, fp32_peak),
+        "fma_peaks_tflops": {"fp64": fp64_peak, "fp32": fp32_peak},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(launches),
@@ -531,13 +600,22 @@ def run_batch_mode(args):
     mols = [I.molecule(int(n), seed=4100 + i) for i, n in enumerate(counts)]
     Cs = _orthonormal_cs(mols, 3000)
     prec = dfjk.DFJK_MIXED if args.precision == "mixed" else dfjk.DFJK_FP64
+    table, tune_rows, tune_s = args.tune_table, None, None
+    if args.autotune:  # the project's autotuner picks the launch shapes on this GPU first
+        from paper_2404_09452_gb300 import tune
+
+        table = table or os.path.join(ROOT, "_build", "dfjk_tune.txt")
+        os.makedirs(os.path.dirname(table), exist_ok=True)
+        t0 = time.perf_counter()
+        tune_rows = tune.tune(table, precision=prec)
+        tune_s = time.perf_counter() - t0
     for _ in range(args.warmup):
-        batch.run_batch(mols, Cs, precision=prec)
+        batch.run_batch(mols, Cs, precision=prec, tune_table=table)
     torch.cuda.synchronize()
     n0 = dfjk.launch_count()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        E, _, st = batch.run_batch(mols, Cs, precision=prec)
+        E, _, st = batch.run_batch(mols, Cs, precision=prec, tune_table=table)
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
     out = {"metric": "DF-J/K builds/s, batch of uneven molecules (setup + build each)",
@@ -547,7 +625,8 @@ def run_batch_mode(args):
            "data": "synthetic",
            "config": {"workload": f"batch of {len(mols)} molecules, atoms uniform in [5, 80] (seed 4000)",
                       "atoms_total": int(sum(counts)), "waves": st["waves"], "precision": args.precision,
-                      "budget_bytes": 150 << 30},
+                      "budget_bytes": 150 << 30, "tune_table": table, "tuned": tune_rows,
+                      "tuning_s": tune_s},
            "gpu_launches": int(dfjk.launch_count() - n0)}
     if args.compare_fp64:
         t0 = time.perf_counter()

@@ -119,12 +119,23 @@ typedef struct {
                               intermediates of large systems, Sec. "Dataset
                               and Performance").  0 (default): B in device
                               memory                                        */
+  const char *tune_table;  /* path of a tuning table (written by the
+                              package's autotuner, tune.py): per range of
+                              nao, rows per block of the slicing kernels, the
+                              K GEMM's split-K range and the mixed build's
+                              work-buffer cap; read during dfjk_setup (not
+                              kept).  NULL: the DFJK_TUNE_TABLE environment
+                              variable, else built-in defaults.  These only
+                              change launch shapes: the slicing choices leave
+                              results bitwise equal, the K range and the cap
+                              regroup FP64 sums (differences ~1e-12)       */
 } dfjk_options;
 
 typedef struct dfjk_ctx *dfjk_handle;
 
 /* Fills *opt with the defaults: DFJK_FP64, 1e-12, no budget, 1<<26, host
- * energies, fp32_pair_thresh -1 (the precision's default), B on the device.  */
+ * energies, fp32_pair_thresh -1 (the precision's default), B on the device,
+ * no tuning table.                                                           */
 void dfjk_default_options(dfjk_options *opt);
 
 /* Setup: the first half of the paper's density-fitting scheme (Introduction,
@@ -151,6 +162,17 @@ int dfjk_query(dfjk_handle h, int32_t *nao, int32_t *naux, int32_t *npair_kept,
  * shell pairs evaluated in FP32 and the bound threshold that selected them
  * (0 when every pair is FP64).  Either output pointer may be NULL.           */
 int dfjk_query_precision(dfjk_handle h, int32_t *npair_fp32, double *fp32_thresh);
+
+/* Work of a handle's 3-centre integrals: the kept primitive pairs of each
+ * orbital shell-pair class (ss, ps, pp, ds, dp, dd), evaluated in FP64
+ * (prim_pairs_fp64[6]) and in FP32 (prim_pairs_fp32[6]).  Each meets every
+ * aux primitive once (one primitive triple).  Either pointer may be NULL.   */
+int dfjk_query_pair_classes(dfjk_handle h, int64_t *prim_pairs_fp64, int64_t *prim_pairs_fp32);
+
+/* The launch-shape choices a handle took from its tuning table, vals[4] =
+ * {slicing rows per block, packed-B slicing rows per block, K GEMM split-K
+ * range in MB, build work-buffer cap in MB}; 0 = the built-in default.       */
+int dfjk_query_tuning(dfjk_handle h, int32_t *vals);
 
 /* Layout of a handle's setup: the number of 3-centre column slabs (T is
  * built and whitened slab by slab, at most 4 GiB each, 2 GiB in the mixed
@@ -286,6 +308,13 @@ int dfjk_destroy(dfjk_handle h);
 const char *dfjk_status_string(int code);
 const char *dfjk_last_error(void);
 
+/* Measured fused multiply-add throughput of the current GPU in TFLOP/s
+ * (2 flop per FMA), bits = 64 (FP64 pipe) or 32 (FP32 pipe): independent FMA
+ * chains on every SM for about 40 ms after three calibration launches.  The
+ * roofline of the integral kernels, which are bound by these pipes.
+ * Synchronises `stream`.  Errors: DFJK_ERR_ARG, _CUDA.                     */
+int dfjk_fma_rate(int32_t bits, double *tflops, void *stream);
+
 /* Number of kernels this library has launched in this process.             */
 uint64_t dfjk_launch_count(void);
 
@@ -297,8 +326,9 @@ uint64_t dfjk_launch_count(void);
  * 2 3-centre integrals, 3 whitening, 4 X = B C (with the per-build slicing
  * of B), 5 K = sum X X^T, 6 D, rho and J, 7 energies; in
  * DFJK_MIXED also the tensor-core GEMM launches alone: 8 whitening, 9 X = B C,
- * 10 K (each also counted inside phases 3, 4, 5).                          */
-#define DFJK_NPHASE 11
+ * 10 K (each also counted inside phases 3, 4, 5); 11 the 3-centre integrals
+ * of the shell pairs evaluated in FP32 (phase 2 then holds the FP64 ones).  */
+#define DFJK_NPHASE 12
 int dfjk_set_timing(int32_t enable);
 
 /* Frees the device blocks the library keeps cached for reuse after handles

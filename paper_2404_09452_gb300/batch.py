@@ -43,8 +43,9 @@ def make_waves(sizes, budget: int):
 
 
 def run_batch(mols, Cs, precision=dfjk.DFJK_MIXED, budget_bytes=150 << 30, workers=4, nstreams=8,
-              keep_results=False):
-    """Setup + build for every molecule.  `Cs` are device tensors [nao_i, nocc_i].
+              keep_results=False, tune_table=None):
+    """Setup + build for every molecule.  `Cs` are device tensors [nao_i, nocc_i];
+    `tune_table`: launch shapes from the autotuner (tune.py), or None.
     Returns (energies [n, 2] numpy, results or None, stats dict)."""
     import numpy as np
     import torch
@@ -60,7 +61,7 @@ def run_batch(mols, Cs, precision=dfjk.DFJK_MIXED, budget_bytes=150 << 30, worke
         if not hasattr(local, "stream"):
             local.stream = torch.cuda.Stream()
         with torch.cuda.stream(local.stream):
-            h = dfjk.Handle(mols[i], precision=precision, stream=local.stream)
+            h = dfjk.Handle(mols[i], precision=precision, stream=local.stream, tune_table=tune_table)
         local.stream.synchronize()
         return h
 

@@ -227,6 +227,51 @@ static void read_basis(const dfjk_basis *b, int natom, const double *coords, Hos
   }
 }
 
+// Launch-shape choices that do not change what is computed, only how fast:
+// rows per block of the slicing kernels, the K GEMM's split-K range and the
+// mixed build's work-buffer cap (which sets the aux-row chunk).  0 = the
+// built-in default (or the corresponding environment variable).
+struct Tuning {
+  int slice_rows = 0;   // DFJK_SLICE_ROWS: 8, 16, 32
+  int pslice_rows = 0;  // DFJK_PSLICE_ROWS: 8, 16, 32
+  int k_range_mb = 0;   // DFJK_K_RANGE_MB
+  int build_ws_mb = 0;  // DFJK_BUILD_WS_MB
+};
+
+// A tuning table: text lines "nao_lo nao_hi slice_rows pslice_rows k_range_mb
+// build_ws_mb [anything]" ('#' starts a comment); the first line with
+// nao_lo <= nao < nao_hi applies.  Tables are parsed once per path.
+static bool lookup_tuning(const char *path, int nao, Tuning &t) {
+  if (!path || !*path) return false;
+  static std::mutex mu;
+  static std::map<std::string, std::vector<std::vector<long>>> tables;
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = tables.find(path);
+  if (it == tables.end()) {
+    std::vector<std::vector<long>> rows;
+    FILE *f = std::fopen(path, "r");
+    if (!f) throw Error{DFJK_ERR_ARG, std::string("tuning table not readable: ") + path};
+    char line[512];
+    while (std::fgets(line, sizeof line, f)) {
+      if (char *c = std::strchr(line, '#')) *c = 0;
+      long v[6];
+      if (std::sscanf(line, "%ld %ld %ld %ld %ld %ld", &v[0], &v[1], &v[2], &v[3], &v[4], &v[5]) == 6)
+        rows.push_back(std::vector<long>(v, v + 6));
+    }
+    std::fclose(f);
+    it = tables.emplace(path, rows).first;
+  }
+  for (const auto &r : it->second)
+    if (r[0] <= nao && nao < r[1]) {
+      t.slice_rows = (int)r[2];
+      t.pslice_rows = (int)r[3];
+      t.k_range_mb = (int)r[4];
+      t.build_ws_mb = (int)r[5];
+      return true;
+    }
+  return false;
+}
+
 }  // namespace dfjk
 
 using namespace dfjk;
@@ -257,6 +302,7 @@ struct dfjk_ctx {
   long long ncol = 0;
   int npair_kept = 0;
   std::vector<int> kept32_begin;  // per class: first kept index evaluated in FP32
+  long long prim_pairs64[6] = {0, 0, 0, 0, 0, 0}, prim_pairs32[6] = {0, 0, 0, 0, 0, 0};
   int npair_fp32 = 0;
   double fp32_thresh = 0.0;
   int nslab = 0;  // T column slabs of the last setup (one whitening launch each)
@@ -276,6 +322,9 @@ struct dfjk_ctx {
   bool lean = false;    // B packed (the mixed path)
   SlicedOp Bchunk;
   int chunk_rows = 0;   // rows P per build chunk (mixed path)
+  DBuf<int> Bexpo;      // slice exponents of the packed B, [mu][expo_rows][nkb]
+  int expo_rows = 0;    // rows P of Bexpo (naux_pad rounded up to 128)
+  Tuning tune;          // launch-shape choices (tuning table entry or defaults)
   // build workspace
   int ws_nocc = -1;
   DBuf<double> D, rho, rho_work, X, Kpart, en_work, e;
@@ -522,6 +571,11 @@ void make_resident(dfjk_ctx *h, cudaStream_t st) {
     }
   }
   h->kept_cls_begin[6] = (int)h->kept_h.size();
+  for (int c = 0; c < 6; ++c) {  // primitive pairs per class and precision
+    h->prim_pairs64[c] = h->prim_pairs32[c] = 0;
+    for (int i = h->kept_cls_begin[c]; i < h->kept_cls_begin[c + 1]; ++i)
+      (i < h->kept32_begin[c] ? h->prim_pairs64 : h->prim_pairs32)[c] += h->npp_h[h->kept_h[i]];
+  }
   h->npair_kept = (int)h->kept_h.size();
   h->ncol = col;
   h->kept.upload(h->kept_h, st);
@@ -599,28 +653,27 @@ void make_resident(dfjk_ctx *h, cudaStream_t st) {
       ++r1;
     }
     const long long c1 = (r1 < h->npair_kept) ? h->pair_col_h[h->kept_h[r1]] : h->ncol;
-    PhaseScope *ph2 = new PhaseScope(2, st);
-    for (int c = 0; c < 6; ++c) {
-      const int lo = std::max(r0, h->kept_cls_begin[c]), hi = std::min(r1, h->kept_cls_begin[c + 1]);
-      if (hi <= lo) continue;
-      const int mid = std::min(std::max(lo, h->kept32_begin[c]), hi);  // [lo, mid) FP64, [mid, hi) FP32
-      for (int lc = 0; lc < 3; ++lc) {
-        Eri3cArgs a{h->kept.p + lo, mid - lo, h->pair_rec_off.p, h->pair_npp.p, h->pair_col.p, h->rec.p,
-                    h->aux_cls[lc].p, h->aux_cls_n[lc], T.p, c0, np};
-        launch_eri3c(cls[c][0], cls[c][1], lc, a, aux_args(h), tab, st);
-        Eri3cArgs a32 = a;
-        a32.pairs = h->kept.p + mid;
-        a32.npairs = hi - mid;
-        launch_eri3c32(cls[c][0], cls[c][1], lc, a32, aux_args(h), tab32, st);
+    // the FP64 pairs of every class, then the FP32 ones (phase timers 2 and 11)
+    for (int prec32 = 0; prec32 < 2; ++prec32) {
+      PhaseScope ph2(prec32 ? 11 : 2, st);
+      for (int c = 0; c < 6; ++c) {
+        const int lo = std::max(r0, h->kept_cls_begin[c]), hi = std::min(r1, h->kept_cls_begin[c + 1]);
+        if (hi <= lo) continue;
+        const int mid = std::min(std::max(lo, h->kept32_begin[c]), hi);  // [lo, mid) FP64, [mid, hi) FP32
+        for (int lc = 0; lc < 3; ++lc) {
+          Eri3cArgs a{h->kept.p + (prec32 ? mid : lo), prec32 ? hi - mid : mid - lo, h->pair_rec_off.p,
+                      h->pair_npp.p, h->pair_col.p, h->rec.p, h->aux_cls[lc].p, h->aux_cls_n[lc], T.p, c0, np};
+          if (prec32) launch_eri3c32(cls[c][0], cls[c][1], lc, a, aux_args(h), tab32, st);
+          else launch_eri3c(cls[c][0], cls[c][1], lc, a, aux_args(h), tab, st);
+        }
       }
     }
-    delete ph2;
     PhaseScope ph3(3, st);
     const int ncols = (int)(c1 - c0);
     if (mixed) {  // slices of T need only T: taken before waiting for L^-1
       if (!T8.data || T8.rows_pad < ncols) oz_alloc(T8, 1, 8, (int)slab_cols, np, OZ_BM);
       T8.rows = ncols;
-      oz_slice_f64(T.p, 0, np, 1, T8, st);
+      oz_slice_f64(T.p, 0, np, 1, T8, st, h->tune.slice_rows);
     }
     if (!joined) {  // L^-1 (and its slices) ready
       DFJK_CUDA_CHECK(cudaStreamWaitEvent(st, h->ev_join, 0));
@@ -652,6 +705,12 @@ void make_resident(dfjk_ctx *h, cudaStream_t st) {
     DFJK_CUDA_CHECK(cudaStreamSynchronize(st));
     oz_free(T8);
     oz_free(Linv8);
+    // the slice exponents of B (per mu, P and 1024-block of nu) do not change
+    // between builds: computed once here, each build's slicing reads B once
+    PhaseScope ph(3, st);
+    h->expo_rows = (np + OZ_BM - 1) / OZ_BM * OZ_BM;
+    h->Bexpo.alloc((size_t)h->nao * h->expo_rows * ((h->nao + OZ_KB - 1) / OZ_KB));
+    oz_expo_packed(h->B.p, h->ldb, h->nao, np, h->expo_rows, h->Bexpo.p, st);
   }
   int status = 0;
   DFJK_CUDA_CHECK(cudaMemcpyAsync(&status, h->status.p, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -664,6 +723,7 @@ void make_resident(dfjk_ctx *h, cudaStream_t st) {
 
 void release_device(dfjk_ctx *h) {
   h->B.release();
+  h->Bexpo.release();
   oz_free(h->Bchunk);
   h->V.release();
   h->L.release();
@@ -693,12 +753,13 @@ void release_device(dfjk_ctx *h) {
 // buffers (X in FP64 and its 6 slices, the 6 slices of B for the chunk) stay
 // within DFJK_BUILD_WS_MB megabytes (default 8192), at least 128, at most the
 // whole (padded) aux range.
-int build_chunk_rows(int nao, int np, int nocc) {
-  static const size_t cap = [] {
+int build_chunk_rows(int nao, int np, int nocc, int ws_mb = 0) {
+  static const size_t cap_env = [] {
     const char *e = std::getenv("DFJK_BUILD_WS_MB");
     const long v = e ? std::atol(e) : 0;
     return (size_t)(v > 0 ? v : 8192) << 20;
   }();
+  const size_t cap = ws_mb > 0 ? (size_t)ws_mb << 20 : cap_env;
   const size_t kp = ((size_t)nao + OZ_BK - 1) / OZ_BK * OZ_BK;
   const size_t per_row = (size_t)nao * ((size_t)nocc * 8 + (size_t)nocc * 12 + 12 * kp);
   size_t rows = std::max<size_t>(128, cap / per_row / 128 * 128);
@@ -713,7 +774,7 @@ void ensure_workspace(dfjk_ctx *h, int nocc, int nset) {
     h->D.alloc(nao2);
     h->rho.alloc(h->naux_pad);
     if (mixed) {
-      const int pc = build_chunk_rows(h->nao, h->naux_pad, nocc);
+      const int pc = build_chunk_rows(h->nao, h->naux_pad, nocc, h->tune.build_ws_mb);
       h->chunk_rows = pc;
       h->X.alloc((size_t)h->nao * pc * nocc);
       h->rho_work.alloc((size_t)h->nao * pc);
@@ -767,11 +828,12 @@ void k_gemm_sliced(dfjk_ctx *h, const SlicedOp &xs, int nao, long long kt, doubl
   for (int i = 0; i < mt; ++i)
     for (int j = 0; j < nt; ++j)
       if (j * OZ_BN <= i * OZ_BM + OZ_BM - 1) ++tiles;
-  static const size_t range_bytes = [] {
+  static const size_t range_env = [] {
     const char *e = std::getenv("DFJK_K_RANGE_MB");
     const long v = e ? std::atol(e) : 0;
     return (size_t)(v > 0 ? v : 64) << 20;
   }();
+  const size_t range_bytes = h->tune.k_range_mb > 0 ? (size_t)h->tune.k_range_mb << 20 : range_env;
   const int nkb = xs.nkb;
   const size_t chunk_kb_bytes = (size_t)xs.rows_pad * 6 * 2 * OZ_KB;
   int per = (int)std::max<size_t>(1, range_bytes / chunk_kb_bytes);
@@ -852,7 +914,7 @@ void build_one(dfjk_ctx *h, int nocc, const double *C, double *J, double *Kout, 
     {
       PhaseScope ph(4, st);
       if (!h->Csl.data || h->Csl.rows != nocc) oz_alloc(h->Csl, 1, 6, nocc, nao, OZ_BN);
-      oz_slice_f64(C, 0, 1, nocc, h->Csl, st);  // rows i, K nu
+      oz_slice_f64(C, 0, 1, nocc, h->Csl, st, h->tune.slice_rows);  // rows i, K nu
     }
     const int pc_max = h->chunk_rows;
     const int nchunk = ceil_div(np, pc_max);
@@ -864,7 +926,7 @@ void build_one(dfjk_ctx *h, int nocc, const double *C, double *J, double *Kout, 
       {
         PhaseScope ph(4, st);
         SlicedOp bv = oz_view(h->Bchunk, pc, nao);  // batch mu, rows P of the chunk, K nu
-        oz_slice_f64_packed(h->B.p + p0, h->ldb, 0, bv, h->B.host, st);
+        oz_slice_f64_packed_pre(h->B.p, h->ldb, h->Bexpo.p, h->expo_rows, p0, bv, st, h->tune.pslice_rows);
         OzGemmArgs x;
         x.M = pc; x.N = nocc; x.K = nao; x.nz = nao; x.a_batched = 1;
         x.mode = 0; x.out = Xc; x.ldo = nocc; x.out_bs = kt;
@@ -914,6 +976,7 @@ void dfjk_default_options(dfjk_options *opt) {
   opt->energies_on_host = 1;
   opt->fp32_pair_thresh = -1.0;
   opt->b_on_host = 0;
+  opt->tune_table = nullptr;
 }
 
 const char *dfjk_status_string(int code) {
@@ -983,6 +1046,9 @@ int dfjk_setup(const dfjk_basis *orb, const dfjk_basis *aux, int32_t natom, cons
     h->naux = h->aux.nfunc;
     if (h->nao == 0 || h->naux == 0) throw Error{DFJK_ERR_ARG, "empty basis"};
     h->naux_pad = ((h->naux + 63) / 64) * 64;
+    const char *tab = h->opt.tune_table ? h->opt.tune_table : std::getenv("DFJK_TUNE_TABLE");
+    lookup_tuning(tab, h->nao, h->tune);
+    h->opt.tune_table = nullptr;  // the caller's string is not kept
     make_resident(h, S(stream));
     *out = h;
     return DFJK_OK;
@@ -1000,7 +1066,7 @@ int dfjk_query(dfjk_handle h, int32_t *nao, int32_t *naux, int32_t *npair_kept, 
   if (nao) *nao = h->nao;
   if (naux) *naux = h->naux;
   if (npair_kept) *npair_kept = h->npair_kept;
-  if (bytes) *bytes = h->B.device_bytes() + h->V.bytes() +
+  if (bytes) *bytes = h->B.device_bytes() + h->Bexpo.bytes() + h->V.bytes() +
                       h->L.bytes() + h->Linv.bytes() + h->rec.bytes();
   return DFJK_OK;
 }
@@ -1020,7 +1086,8 @@ int dfjk_estimate_bytes(int32_t nao, int32_t naux, int32_t nocc, int32_t precisi
   const bool mixed = precision == DFJK_MIXED;
   const size_t npack = n * (n + 1) / 2;
   const size_t b = (mixed ? npack : n * n) * np * 8;
-  const size_t r = b + 3 * np * np * 8;
+  auto rup0 = [](size_t x, size_t m) { return (x + m - 1) / m * m; };
+  const size_t r = b + 3 * np * np * 8 + (mixed ? n * rup0(np, OZ_BM) * ((n + OZ_KB - 1) / OZ_KB) * 4 : 0);
   auto rup = [](size_t x, size_t m) { return (x + m - 1) / m * m; };
   size_t ws = n * n * 8 + np * 8 * 2;  // D, rho
   if (mixed) {
@@ -1042,6 +1109,24 @@ int dfjk_estimate_bytes(int32_t nao, int32_t naux, int32_t nocc, int32_t precisi
   if (resident) *resident = r;
   if (build_ws) *build_ws = ws;
   if (setup_ws) *setup_ws = sw;
+  return DFJK_OK;
+}
+
+int dfjk_query_pair_classes(dfjk_handle h, int64_t *prim_pairs_fp64, int64_t *prim_pairs_fp32) {
+  if (!h) return fail(Error{DFJK_ERR_ARG, "null handle"});
+  for (int c = 0; c < 6; ++c) {
+    if (prim_pairs_fp64) prim_pairs_fp64[c] = h->prim_pairs64[c];
+    if (prim_pairs_fp32) prim_pairs_fp32[c] = h->prim_pairs32[c];
+  }
+  return DFJK_OK;
+}
+
+int dfjk_query_tuning(dfjk_handle h, int32_t *vals) {
+  if (!h || !vals) return fail(Error{DFJK_ERR_ARG, "null argument"});
+  vals[0] = h->tune.slice_rows;
+  vals[1] = h->tune.pslice_rows;
+  vals[2] = h->tune.k_range_mb;
+  vals[3] = h->tune.build_ws_mb;
   return DFJK_OK;
 }
 
@@ -1312,14 +1397,14 @@ static void jk_gradient(dfjk_ctx *h, const double *Din, int nocc, const double *
       const SlicedOp &cn = slice(C, 0, nocc, 1, 1, nao, nocc, OZ_BN);   // rows mu, K i
       // X[mu][P][i] = sum_nu B[(mu,nu)][P] C[nu][i], slicing the packed B chunk
       // by chunk of rows P as the build does
-      const int pcm = build_chunk_rows(nao, np, nocc);
+      const int pcm = build_chunk_rows(nao, np, nocc, h->tune.build_ws_mb);
       ops.emplace_back();
       SlicedOp &bck = ops.back();
       oz_alloc(bck, nao, 6, pcm, nao, OZ_BM);
       for (int p0 = 0; p0 < np; p0 += pcm) {
         const int pc = std::min(pcm, np - p0);
         SlicedOp bv = oz_view(bck, pc, nao);
-        oz_slice_f64_packed(h->B.p + p0, h->ldb, 0, bv, h->B.host, st);
+        oz_slice_f64_packed_pre(h->B.p, h->ldb, h->Bexpo.p, h->expo_rows, p0, bv, st, h->tune.pslice_rows);
         tc_gemm(bv, csl, pc, nocc, nao, nao, X.p + (size_t)p0 * nocc, nocc, (long long)np * nocc, 0);
       }
       // Xt[P][j][i] = sum_mu X[mu][P][j] C[mu][i]  (symmetric in i, j)

@@ -6,6 +6,12 @@ namespace dfjk {
 
 void launch_eri3c32_l1(int la, int lb, const Eri3cArgs &a, const AuxArgs &x, const float *tab,
                        cudaStream_t st) {
+  if (eri3c_coop_enabled()) {  // the NCC threads of an aux shell share its work
+    using Sh = CoopShape<1>;
+    dim3 grid(a.npairs, ceil_div(a.naux_shells, Sh::NS));
+    DISPATCH_LALB(la, lb, (eri3c_coop_kernel<A_, B_, 1, float><<<grid, Sh::THREADS, 0, st>>>(a, x, tab)));
+    return;
+  }
   dim3 grid(a.npairs, ceil_div(a.naux_shells, 128));
   DISPATCH_LALB(la, lb, (eri3c32_kernel<A_, B_, 1><<<grid, 128, 0, st>>>(a, x, tab)));
 }

@@ -2,6 +2,8 @@
 // The scheme and its equations are described in integrals.cu.
 #pragma once
 
+#include <cstdlib>
+
 #include "boys.cuh"
 #include "common.cuh"
 #include "integrals.cuh"
@@ -505,6 +507,195 @@ __global__ void __launch_bounds__(128) eri3c32_kernel(Eri3cArgs args, AuxArgs au
         args.T[(col0 + ca * NCB + cb) * args.ldT + P0 + cc] =
             (double)acc[(ca * NCB + cb) * NCC + cc] *
             (comp_factor(LA, ca) * comp_factor(LB, cb) * comp_factor(LC, cc));
+}
+
+// ---- cooperative 3-centre kernel for aux shells with l >= 1 ------------------
+//
+// The one-thread-per-aux-shell kernels above keep every output of a shell
+// triple in registers: 216 for (dd|d), plus R (84 terms at L = 6) and W, far
+// beyond the 255 registers of a thread, so they spill to local memory and
+// wait on it (ncu at 20 atoms: (dd|d) keeps the FP64 pipe 15 % busy).  Here
+// the NCC = ncart(LC) threads of an aux shell (adjacent lanes of one warp)
+// share its work: all of them evaluate the Boys function (free within the warp
+// instruction), they build R^(n) level by level into shared memory, each
+// computing every NCC-th entry, and then each thread forms W for its own aux
+// component and contracts it with every orbital component pair: NCA NCB
+// outputs (36 for dd) and ntuv(LAB) W terms (35) in registers.
+
+// (t, u, v) of the k-th Hermite index in tuv_idx order, k < ntuv(8).
+struct TuvTable {
+  signed char t[ntuv(8)], u[ntuv(8)], v[ntuv(8)];
+};
+__host__ __device__ constexpr TuvTable make_tuv_table() {
+  TuvTable T{};
+  int k = 0;
+  for (int n = 0; n <= 8; ++n)
+    for (int t = n; t >= 0; --t)
+      for (int u = n - t; u >= 0; --u) {
+        T.t[k] = (signed char)t;
+        T.u[k] = (signed char)u;
+        T.v[k] = (signed char)(n - t - u);
+        ++k;
+      }
+  return T;
+}
+__constant__ TuvTable c_tuv = make_tuv_table();
+
+__device__ __forceinline__ int tuv_idx_rt(int t, int u, int v) { return tuv_idx(t, u, v); }
+__device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
+__device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
+
+// The cooperative kernels are the default for aux l >= 1; DFJK_ERI_COOP=0
+// selects the one-thread-per-aux-shell kernels (same integrals).
+inline bool eri3c_coop_enabled() {
+  static const bool on = [] {
+    const char *e = std::getenv("DFJK_ERI_COOP");
+    return !(e && e[0] == '0');
+  }();
+  return on;
+}
+
+template <int LC>
+struct CoopShape {
+  static constexpr int G = ncart(LC);          // threads per aux shell
+  static constexpr int SPW = 32 / G;           // aux shells per warp
+  static constexpr int NW = LC == 2 ? 6 : 4;   // warps per block (static shared memory <= 48 KB)
+  static constexpr int NS = NW * SPW;          // aux shells per block
+  static constexpr int THREADS = NW * 32;
+};
+
+template <int LA, int LB, int LC, typename Real>
+__global__ void __launch_bounds__(CoopShape<LC>::THREADS, 1) eri3c_coop_kernel(Eri3cArgs args, AuxArgs aux,
+                                                                            const Real *__restrict__ boys_tab) {
+  using Sh = CoopShape<LC>;
+  constexpr int G = Sh::G, SPW = Sh::SPW, NS = Sh::NS;
+  constexpr int NT = nterms(LA, LB);
+  constexpr int REC = REC_HDR + NT;
+  constexpr int NCA = ncart(LA), NCB = ncart(LB);
+  constexpr int LAB = LA + LB, L = LA + LB + LC;
+  constexpr int NR = ntuv(L);
+  __shared__ Real srec[REC];
+  __shared__ double sP[3];
+  __shared__ Real Rbuf[2][NS][NR];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = lane / G, cc = lane - g * G;  // aux shell within the warp, aux component
+  const bool lane_used = lane < SPW * G;
+  const int slot = warp * SPW + (lane_used ? g : 0);  // aux shell within the block
+  const int as = blockIdx.y * NS + slot;
+  const bool active = lane_used && as < args.naux_shells;
+  const int sc = active ? args.aux_shells[as] : 0;
+  const double Cx = aux.center[3 * sc], Cy = aux.center[3 * sc + 1], Cz = aux.center[3 * sc + 2];
+  const int pc0 = aux.prim_off[sc], nc = active ? aux.nprim[sc] : 0;
+  // this thread's aux component: a power 2 along one axis (xx, yy, zz) or
+  // powers 1 (p, and xy, xz, yz)
+  const int cx = cart_x(LC, cc), cy = cart_y(LC, cc), cz = cart_z(LC, cc);
+  const int two = (cx == 2) ? 0 : (cy == 2) ? 1 : (cz == 2) ? 2 : -1;
+  Real acc[NCA * NCB];
+#pragma unroll
+  for (int i = 0; i < NCA * NCB; ++i) acc[i] = Real(0);
+  const double *rec0 = args.rec + args.rec_off[args.pairs[blockIdx.x]];
+  const int npp = args.npp[args.pairs[blockIdx.x]];
+  // every thread of the warp runs the same number of primitive iterations
+  // (aux shells of a class share nprim here; nc is uniform within a group and
+  // the warp-wide maximum bounds the loop)
+  int ncmax = nc;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) ncmax = max(ncmax, __shfl_xor_sync(0xffffffffu, ncmax, o));
+  for (int ipp = 0; ipp < npp; ++ipp) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < REC; i += blockDim.x) {
+      const double v = rec0[(long long)ipp * REC + i];
+      srec[i] = (Real)v;
+      if (i >= 1 && i <= 3) sP[i - 1] = v;
+    }
+    __syncthreads();
+    for (int kc = 0; kc < ncmax; ++kc) {
+      const bool live = kc < nc;
+      const Real gexp = live ? (Real)aux.exps[pc0 + kc] : Real(1);
+      const Real g1 = live ? (Real)aux.g1[pc0 + kc] : Real(0);
+      const Real p = srec[0];
+      // pair-to-aux-centre vector formed in FP64 before any rounding
+      const Real X = (Real)(sP[0] - Cx), Y = (Real)(sP[1] - Cy), Z = (Real)(sP[2] - Cz);
+      const Real sr = rsq(p + gexp);
+      const Real al = p * gexp * (sr * sr);
+      Real F[L + 1];
+      boys_eval<L>(al * (X * X + Y * Y + Z * Z), boys_tab, F);
+      // R^(n), n = L .. 0, level by level in shared memory; R^(L) has one entry
+      Real *cur = Rbuf[0][slot], *nxt = Rbuf[1][slot];
+      Real pw = Real(1);
+#pragma unroll
+      for (int n = 0; n < L; ++n) pw *= Real(-2) * al;
+      if (lane_used && cc == 0) cur[0] = pw * F[L];
+      __syncwarp();
+#pragma unroll
+      for (int n = L - 1; n >= 0; --n) {
+        pw = Real(1);
+#pragma unroll
+        for (int q = 0; q < n; ++q) pw *= Real(-2) * al;
+        const int cnt = ntuv(L - n);
+        if (lane_used)
+          for (int k = cc; k < cnt; k += G) {
+            const int t = c_tuv.t[k], u = c_tuv.u[k], v = c_tuv.v[k];
+            Real r;
+            if (k == 0) {
+              r = pw * F[n];
+            } else if (t > 0) {
+              r = X * cur[tuv_idx_rt(t - 1, u, v)];
+              if (t > 1) r = fma(Real(t - 1), cur[tuv_idx_rt(t - 2, u, v)], r);
+            } else if (u > 0) {
+              r = Y * cur[tuv_idx_rt(t, u - 1, v)];
+              if (u > 1) r = fma(Real(u - 1), cur[tuv_idx_rt(t, u - 2, v)], r);
+            } else {
+              r = Z * cur[tuv_idx_rt(t, u, v - 1)];
+              if (v > 1) r = fma(Real(v - 1), cur[tuv_idx_rt(t, u, v - 2)], r);
+            }
+            nxt[k] = r;
+          }
+        __syncwarp();
+        Real *tmp = cur;
+        cur = nxt;
+        nxt = tmp;
+      }
+      // cur = R^(0); W for this thread's aux component (t + u + v <= LAB) is
+      // read from it term by term in the contraction
+      const Real *Rs = cur;
+      auto wval = [&](int t, int u, int v) -> Real {
+        if (two == 0) return fma(g1, Rs[tuv_idx_rt(t + 2, u, v)], Rs[tuv_idx(t, u, v)]);
+        if (two == 1) return fma(g1, Rs[tuv_idx_rt(t, u + 2, v)], Rs[tuv_idx(t, u, v)]);
+        if (two == 2) return fma(g1, Rs[tuv_idx_rt(t, u, v + 2)], Rs[tuv_idx(t, u, v)]);
+        return Rs[tuv_idx_rt(t + cx, u + cy, v + cz)];
+      };
+      const Real scale = (two >= 0) ? g1 : (LC == 1 ? -g1 : g1 * g1);
+      const Real ps = live ? srec[4] * (Real)aux.cdiv[pc0 + kc] * sr * scale : Real(0);
+      int k = 0;
+#pragma unroll
+      for (int ca = 0; ca < NCA; ++ca)
+#pragma unroll
+        for (int cb = 0; cb < NCB; ++cb) {
+          const int ax = cart_x(LA, ca), ay = cart_y(LA, ca), az = cart_z(LA, ca);
+          const int bx = cart_x(LB, cb), by = cart_y(LB, cb), bz = cart_z(LB, cb);
+          Real sum = Real(0);
+#pragma unroll
+          for (int t = 0; t <= ax + bx; ++t)
+#pragma unroll
+            for (int u = 0; u <= ay + by; ++u)
+#pragma unroll
+              for (int v = 0; v <= az + bz; ++v) sum = fma(srec[REC_HDR + k++], wval(t, u, v), sum);
+          acc[ca * NCB + cb] = fma(ps, sum, acc[ca * NCB + cb]);
+        }
+      __syncwarp();  // R reads done before the next aux primitive overwrites it
+    }
+  }
+  if (!active) return;
+  const long long col0 = args.pair_col[args.pairs[blockIdx.x]] - args.col_begin;
+  const int P = aux.func_off[sc] + cc;
+  const double fc = comp_factor(LC, cc);
+#pragma unroll
+  for (int ca = 0; ca < NCA; ++ca)
+#pragma unroll
+    for (int cb = 0; cb < NCB; ++cb)
+      args.T[(col0 + ca * NCB + cb) * args.ldT + P] =
+          (double)acc[ca * NCB + cb] * (comp_factor(LA, ca) * comp_factor(LB, cb) * fc);
 }
 
 // ---- 2-centre metric and overlap ----------------------------------------------

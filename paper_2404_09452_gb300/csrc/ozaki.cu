@@ -187,12 +187,17 @@ __global__ void __launch_bounds__(256) oz_slice_tr_kernel(const double *__restri
 // K = 900) keeps the second read in L2 with every SM's blocks in flight; lanes
 // run along the rows (64 contiguous bytes per K index, four K indices per
 // warp load).
-template <int S, bool PACKED, int R = 8>
+// MODE 0: both passes.  MODE 1: exponents only (pass 1; no slices).  MODE 2:
+// slices only, with the exponents of row r taken from a precomputed array
+// pre[(z pre_rows + pre_row0 + r) nkb + kb] (and copied to `expo` for the
+// GEMM), so the source is read once.
+template <int S, bool PACKED, int R = 8, int MODE = 0>
 __global__ void __launch_bounds__(256) oz_slice_tr_fused_kernel(const double *__restrict__ src, long long sz,
                                                                 long long sk, int rows, int K, int rows_pad,
                                                                 int kpitch, int nkb, int *__restrict__ expo,
                                                                 __nv_bfloat16 *__restrict__ out, int mu0,
-                                                                int kblk) {
+                                                                int kblk, const int *__restrict__ pre = nullptr,
+                                                                long long pre_rows = 0, int pre_row0 = 0) {
   constexpr int KG = 256 / R, LD = 72, MAXKB = 8;
   __shared__ __nv_bfloat16 tile[S * R * LD];
   __shared__ unsigned long long rmax[R][MAXKB];
@@ -211,10 +216,19 @@ __global__ void __launch_bounds__(256) oz_slice_tr_fused_kernel(const double *__
     }
     return src[z * sz + (long long)k * sk + r];
   };
-  if (threadIdx.x < R * MAXKB) rmax[threadIdx.x / MAXKB][threadIdx.x % MAXKB] = 0ull;
+  if (MODE == 2) {
+    if (threadIdx.x < R * nkb) {
+      const int q = threadIdx.x / nkb, kb = threadIdx.x % nkb;
+      const int e = pre[((long long)z * pre_rows + pre_row0 + r0 + q) * nkb + kb];
+      rexp[q][kb] = e;
+      expo[((long long)z * rows_pad + r0 + q) * nkb + kb] = e;
+    }
+    __syncthreads();
+  }
+  if (MODE != 2 && threadIdx.x < R * MAXKB) rmax[threadIdx.x / MAXKB][threadIdx.x % MAXKB] = 0ull;
   __syncthreads();
   // pass 1: |x| maxima per K block (non-negative doubles order like their bits)
-  for (int kb = 0; kb < nkb; ++kb) {
+  for (int kb = 0; kb < nkb && MODE != 2; ++kb) {
     double mx = 0.0;
     if (live) {
       const int k1 = min(K, (kb + 1) * OZ_KB);
@@ -227,12 +241,13 @@ __global__ void __launch_bounds__(256) oz_slice_tr_fused_kernel(const double *__
     if ((threadIdx.x & 31) < R) atomicMax(&rmax[rr][kb], (unsigned long long)__double_as_longlong(mx));
   }
   __syncthreads();
-  if (threadIdx.x < R * nkb) {
+  if (MODE != 2 && threadIdx.x < R * nkb) {
     const int q = threadIdx.x / nkb, kb = threadIdx.x % nkb;
     const int e = oz_expo_of(__longlong_as_double((long long)rmax[q][kb]));
     rexp[q][kb] = e;
     expo[((long long)z * rows_pad + r0 + q) * nkb + kb] = e;
   }
+  if (MODE == 1) return;
   __syncthreads();
   // pass 2: slices, 64 K at a time, staged [s][row][k] and written along K
   for (int k0 = 0; k0 < kpitch; k0 += 64) {
@@ -305,7 +320,8 @@ void oz_free(SlicedOp &op) {
   op.expo = nullptr;
 }
 
-void oz_slice_f64_packed(const double *B, long long ldb, int mu0, SlicedOp &op, bool b_on_host, cudaStream_t st) {
+void oz_slice_f64_packed(const double *B, long long ldb, int mu0, SlicedOp &op, bool b_on_host, cudaStream_t st,
+                         int rows_per_block) {
   if (op.S != 6 || op.rows_pad % 32 != 0 || op.nkb > 8)
     throw Error{DFJK_ERR_UNSUPPORTED, "packed slicing: 6 slices, K <= 8192"};
   if (b_on_host) {  // 32 rows (256 contiguous bytes) per K index over the host link
@@ -313,24 +329,72 @@ void oz_slice_f64_packed(const double *B, long long ldb, int mu0, SlicedOp &op, 
     oz_slice_tr_fused_kernel<6, true, 32><<<grid, 256, 0, st>>>(B, 0, ldb, op.rows, op.K, op.rows_pad, op.kpitch,
                                                                 op.nkb, op.expo, op.data, mu0, op.kblk);
   } else {
-    dim3 grid((unsigned)(op.rows_pad / 8), (unsigned)op.batch);
-    oz_slice_tr_fused_kernel<6, true, 8><<<grid, 256, 0, st>>>(B, 0, ldb, op.rows, op.K, op.rows_pad, op.kpitch,
-                                                               op.nkb, op.expo, op.data, mu0, op.kblk);
+    // rows P per block (8 contiguous doubles = 64 bytes per packed row and K
+    // index); DFJK_PSLICE_ROWS selects 16 or 32 instead
+    static const int R_env = [] {
+      const char *e = std::getenv("DFJK_PSLICE_ROWS");
+      const int v = e ? std::atoi(e) : 8;
+      return (v == 16 || v == 32) ? v : 8;
+    }();
+    const int R = (rows_per_block == 8 || rows_per_block == 16 || rows_per_block == 32) ? rows_per_block : R_env;
+    dim3 grid((unsigned)(op.rows_pad / R), (unsigned)op.batch);
+    if (R == 32)
+      oz_slice_tr_fused_kernel<6, true, 32><<<grid, 256, 0, st>>>(B, 0, ldb, op.rows, op.K, op.rows_pad, op.kpitch,
+                                                                  op.nkb, op.expo, op.data, mu0, op.kblk);
+    else if (R == 16)
+      oz_slice_tr_fused_kernel<6, true, 16><<<grid, 256, 0, st>>>(B, 0, ldb, op.rows, op.K, op.rows_pad, op.kpitch,
+                                                                  op.nkb, op.expo, op.data, mu0, op.kblk);
+    else
+      oz_slice_tr_fused_kernel<6, true, 8><<<grid, 256, 0, st>>>(B, 0, ldb, op.rows, op.K, op.rows_pad, op.kpitch,
+                                                                 op.nkb, op.expo, op.data, mu0, op.kblk);
   }
   DFJK_LAUNCHED();
 }
 
+void oz_expo_packed(const double *B, long long ldb, int nao, int np, int pre_rows, int *expo, cudaStream_t st) {
+  const int nkb = (nao + OZ_KB - 1) / OZ_KB;
+  if (pre_rows % 32 != 0 || pre_rows < np || nkb > 8) throw Error{DFJK_ERR_UNSUPPORTED, "packed exponents: K <= 8192"};
+  dim3 grid((unsigned)(pre_rows / 32), (unsigned)nao);
+  oz_slice_tr_fused_kernel<6, true, 32, 1><<<grid, 256, 0, st>>>(B, 0, ldb, np, nao, pre_rows, 0, nkb, expo, nullptr,
+                                                                 0, 0);
+  DFJK_LAUNCHED();
+}
+
+void oz_slice_f64_packed_pre(const double *B, long long ldb, const int *pre, int pre_rows, int p0, SlicedOp &op,
+                             cudaStream_t st, int rows_per_block) {
+  // every row a block touches, padding included, has a precomputed exponent
+  if (op.S != 6 || op.rows_pad % 32 != 0 || op.nkb > 8 || p0 % 32 != 0 || p0 + op.rows_pad > pre_rows)
+    throw Error{DFJK_ERR_UNSUPPORTED, "packed slicing: 6 slices, K <= 8192, exponent rows"};
+  static const int R_env = [] {
+    const char *e = std::getenv("DFJK_PSLICE_ROWS");
+    const int v = e ? std::atoi(e) : 32;
+    return (v == 8 || v == 16) ? v : 32;
+  }();
+  const int R = (rows_per_block == 8 || rows_per_block == 16 || rows_per_block == 32) ? rows_per_block : R_env;
+  dim3 grid((unsigned)(op.rows_pad / R), (unsigned)op.batch);
+#define OZ_PRE(RR)                                                                                           \
+  oz_slice_tr_fused_kernel<6, true, RR, 2><<<grid, 256, 0, st>>>(B + p0, 0, ldb, op.rows, op.K, op.rows_pad,   \
+                                                                  op.kpitch, op.nkb, op.expo, op.data, 0,     \
+                                                                  op.kblk, pre, pre_rows, p0)
+  if (R == 32) OZ_PRE(32);
+  else if (R == 16) OZ_PRE(16);
+  else OZ_PRE(8);
+#undef OZ_PRE
+  DFJK_LAUNCHED();
+}
+
 void oz_slice_f64(const double *src, long long sz, long long sr, long long sk, SlicedOp &op,
-                  cudaStream_t st) {
+                  cudaStream_t st, int rows_req) {
   if (sr == 1 && op.rows_pad % 8 == 0 && op.nkb <= 8) {
     // row-contiguous source: exponents and slices fused, one read from HBM;
     // rows per block 16 (measured best of 8 / 16 / 32 at 60 atoms; the
     // DFJK_SLICE_ROWS environment variable selects another)
-    static const int rows_per_block = [] {
+    static const int rows_env = [] {
       const char *e = std::getenv("DFJK_SLICE_ROWS");
       const int v = e ? std::atoi(e) : 16;
       return (v == 8 || v == 32) ? v : 16;
     }();
+    const int rows_per_block = (rows_req == 8 || rows_req == 16 || rows_req == 32) ? rows_req : rows_env;
     const int R = (op.rows_pad % rows_per_block == 0) ? rows_per_block : 8;
     dim3 grid((unsigned)(op.rows_pad / R), (unsigned)op.batch);
 #define OZ_FUSED(SS, RR)                                                                                      \

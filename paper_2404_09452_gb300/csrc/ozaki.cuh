@@ -47,8 +47,10 @@ SlicedOp oz_view(const SlicedOp &op, int rows, int K);
 
 // Fills `op` from the FP64 view x(z, r, k) = src[z sz + r sr + k sk]
 // (rows >= op.rows and k >= op.K are zero).
+// rows_per_block: rows of a row-contiguous source per block of the fused
+// slicing kernel (8, 16 or 32; 0 = the default, 16, or DFJK_SLICE_ROWS).
 void oz_slice_f64(const double *src, long long sz, long long sr, long long sk, SlicedOp &op,
-                  cudaStream_t st);
+                  cudaStream_t st, int rows_per_block = 0);
 
 struct OzGemmArgs {
   int M = 0, N = 0, K = 0;
@@ -81,7 +83,22 @@ struct OzGemmArgs {
 // Slices of B stored as the packed mu >= nu triangle (row mu (mu + 1) / 2 + nu,
 // ldb doubles per row, P contiguous): batch z is mu = mu0 + z, rows P, K nu.
 // b_on_host: B is in host memory (wider row groups per block for the host link).
-void oz_slice_f64_packed(const double *B, long long ldb, int mu0, SlicedOp &op, bool b_on_host, cudaStream_t st);
+// rows_per_block: rows P per block for device memory (8, 16 or 32; 0 = the
+// default, 8, or DFJK_PSLICE_ROWS).
+void oz_slice_f64_packed(const double *B, long long ldb, int mu0, SlicedOp &op, bool b_on_host, cudaStream_t st,
+                         int rows_per_block = 0);
+
+// Exponents of the slices of a packed B (the same per-(mu, P, 1024-block of
+// nu) exponents oz_slice_f64_packed computes), for every mu and the rows P <
+// pre_rows (rows np..pre_rows-1 get 0): expo[(mu pre_rows + P) nkb + kb].  B
+// does not change between builds, so a handle computes them once.
+void oz_expo_packed(const double *B, long long ldb, int nao, int np, int pre_rows, int *expo, cudaStream_t st);
+// oz_slice_f64_packed for the chunk of rows P [p0, p0 + op.rows) of all mu
+// (mu0 = 0, batch = nao), reading B once: the exponents come from `pre`
+// (oz_expo_packed) and are copied into op.expo.  p0 % 32 == 0 and
+// p0 + op.rows_pad <= pre_rows.
+void oz_slice_f64_packed_pre(const double *B, long long ldb, const int *pre, int pre_rows, int p0, SlicedOp &op,
+                             cudaStream_t st, int rows_per_block = 0);
 
 // True when DFJK_OZ_SIMPLE=1 selects the one-tile-per-CTA kernel (no mode 2).
 bool oz_simple_mode();

@@ -37,6 +37,8 @@ EXPORTS = [
     "dfjk_query",
     "dfjk_query_precision",
     "dfjk_query_setup",
+    "dfjk_query_pair_classes",
+    "dfjk_query_tuning",
     "dfjk_estimate_bytes",
     "dfjk_build",
     "dfjk_build_uks",
@@ -51,6 +53,7 @@ EXPORTS = [
     "dfjk_status_string",
     "dfjk_last_error",
     "dfjk_launch_count",
+    "dfjk_fma_rate",
     "dfjk_boys",
     "dfjk_get_metric",
     "dfjk_get_cholesky",
@@ -66,7 +69,7 @@ EXPORTS = [
 ]
 
 PHASES = ["pairs+metric", "cholesky", "eri3c", "whiten", "X=BC", "K", "rho+J", "energies",
-          "tc:whiten", "tc:X=BC", "tc:K"]
+          "tc:whiten", "tc:X=BC", "tc:K", "eri3c32"]
 
 
 class DfjkError(RuntimeError):
@@ -98,6 +101,7 @@ class Options(ctypes.Structure):
         ("energies_on_host", ctypes.c_int32),
         ("fp32_pair_thresh", ctypes.c_double),
         ("b_on_host", ctypes.c_int32),
+        ("tune_table", ctypes.c_char_p),
     ]
 
 
@@ -129,6 +133,9 @@ def load_library(path: str = LIB_PATH):
     szp = ctypes.POINTER(ctypes.c_size_t)
     lib.dfjk_estimate_bytes.argtypes = [i32, i32, i32, i32, szp, szp, szp]
     lib.dfjk_get_B_columns.argtypes = [vp, i32, vp, vp, vp, vp]
+    lib.dfjk_query_pair_classes.argtypes = [vp, vp, vp]
+    lib.dfjk_fma_rate.argtypes = [i32, vp, vp]
+    lib.dfjk_query_tuning.argtypes = [vp, vp]
     lib.dfjk_overlap.argtypes = [vp, vp, vp]
     lib.dfjk_coulomb_gradient.argtypes = [vp, vp, vp, vp]
     lib.dfjk_jk_gradient.argtypes = [vp, i32, vp, ctypes.c_double, ctypes.c_double, vp, vp]
@@ -201,7 +208,7 @@ class _BasisHolder:
 def default_options(precision: int = DFJK_FP64, schwarz_thresh: float = 1e-12,
                     hbm_budget_bytes: int = 0, energies_on_host: bool = True,
                     timeout_iters: int = 0, fp32_pair_thresh: float = -1.0,
-                    b_on_host: bool = False) -> Options:
+                    b_on_host: bool = False, tune_table: str | None = None) -> Options:
     o = Options()
     load_library().dfjk_default_options(ctypes.byref(o))
     o.precision = precision
@@ -212,6 +219,7 @@ def default_options(precision: int = DFJK_FP64, schwarz_thresh: float = 1e-12,
         o.timeout_iters = timeout_iters
     o.fp32_pair_thresh = fp32_pair_thresh
     o.b_on_host = 1 if b_on_host else 0
+    o.tune_table = tune_table.encode() if tune_table else None
     return o
 
 
@@ -220,7 +228,7 @@ class Handle:
 
     def __init__(self, mol, precision: int = DFJK_FP64, schwarz_thresh: float = 1e-12,
                  hbm_budget_bytes: int = 0, stream=None, timeout_iters: int = 0,
-                 fp32_pair_thresh: float = -1.0, b_on_host: bool = False):
+                 fp32_pair_thresh: float = -1.0, b_on_host: bool = False, tune_table: str | None = None):
         lib = load_library()
         _torch()
         self.mol = mol
@@ -229,7 +237,7 @@ class Handle:
         xyz = np.ascontiguousarray(mol.coords, dtype=np.float64)
         self.natom = int(xyz.shape[0])
         opt = default_options(precision, schwarz_thresh, hbm_budget_bytes, timeout_iters=timeout_iters,
-                              fp32_pair_thresh=fp32_pair_thresh, b_on_host=b_on_host)
+                              fp32_pair_thresh=fp32_pair_thresh, b_on_host=b_on_host, tune_table=tune_table)
         h = ctypes.c_void_p()
         _check(
             lib.dfjk_setup(
@@ -252,6 +260,15 @@ class Handle:
         ns, lean = ctypes.c_int32(), ctypes.c_int32()
         _check(lib.dfjk_query_setup(h, ctypes.byref(ns), ctypes.byref(lean)))
         self.nslab, self.lean = ns.value, bool(lean.value)
+        p64, p32 = (ctypes.c_int64 * 6)(), (ctypes.c_int64 * 6)()
+        _check(lib.dfjk_query_pair_classes(h, p64, p32))
+        # kept primitive pairs per class (ss, ps, pp, ds, dp, dd) in FP64 / FP32
+        self.prim_pairs_fp64, self.prim_pairs_fp32 = list(p64), list(p32)
+        tv = (ctypes.c_int32 * 4)()
+        _check(lib.dfjk_query_tuning(h, tv))
+        # launch shapes from the tuning table (0 = default): slicing rows,
+        # packed-B slicing rows, K range MB, build work-buffer cap MB
+        self.tuning = list(tv)
 
     def close(self):
         if getattr(self, "h", None):
@@ -481,6 +498,13 @@ def estimate_bytes(nao: int, naux: int, nocc: int, precision: int) -> dict:
     _check(lib.dfjk_estimate_bytes(int(nao), int(naux), int(nocc), int(precision), ctypes.byref(r),
                                    ctypes.byref(w), ctypes.byref(s)))
     return {"resident": r.value, "build_ws": w.value, "setup_ws": s.value}
+
+
+def fma_rate(bits: int = 64, stream=None) -> float:
+    """Measured FMA throughput of the GPU in TFLOP/s (dfjk_fma_rate)."""
+    r = ctypes.c_double()
+    _check(load_library().dfjk_fma_rate(int(bits), ctypes.byref(r), _stream(stream)))
+    return r.value
 
 
 def launch_count() -> int:

@@ -106,12 +106,17 @@ class Server:
     shared)."""
 
     def __init__(self, mols, precision=dfjk.DFJK_MIXED, budget_bytes=150 << 30, slots=8,
-                 keep_outputs=False, setup_workers=2):
+                 keep_outputs=False, setup_workers=2, backend=None):
+        """`backend`: (torch, handle class, bytes function) to use instead of
+        torch, dfjk.Handle and resident_bytes (host-logic tests on CPU)."""
         import threading
         from concurrent.futures import ThreadPoolExecutor
 
-        import torch
+        if backend is None:
+            import torch
 
+            backend = (torch, dfjk.Handle, resident_bytes)
+        torch, self._handle_cls, self._bytes_fn = backend
         self.torch = torch
         self.mols = mols
         self.precision = precision
@@ -130,7 +135,7 @@ class Server:
 
     def _bytes(self, mol_id, nocc):
         m = self.mols[mol_id]
-        return resident_bytes(m.nao, m.naux, nocc, self.precision)
+        return self._bytes_fn(m.nao, m.naux, nocc, self.precision)
 
     def _setup(self, mol_id):
         torch = self.torch
@@ -139,14 +144,15 @@ class Server:
             self._local.stream = torch.cuda.Stream()
         s = self._local.stream
         with torch.cuda.stream(s):
-            h = dfjk.Handle(self.mols[mol_id], precision=self.precision, stream=s)
+            h = self._handle_cls(self.mols[mol_id], precision=self.precision, stream=s)
         s.synchronize()
         return h
 
-    def _start_setup(self, mol_id, nocc) -> bool:
+    def _start_setup(self, mol_id, nocc, keep) -> bool:
         """Reserves the molecule's bytes and starts its setup; False when the
-        budget cannot be met now (every resident molecule is busy)."""
-        ok, evicted = self.lru.admit(mol_id, self._bytes(mol_id, nocc), self.busy)
+        budget cannot be met now (every resident molecule is busy or needed
+        by an older waiting request: `keep`)."""
+        ok, evicted = self.lru.admit(mol_id, self._bytes(mol_id, nocc), self.busy | keep)
         for v in evicted:
             self.resident.pop(v).close()
             self.stats.evictions += 1
@@ -186,14 +192,21 @@ class Server:
                             waiting.remove(req)
                             self.stats.failed += 1
             # admission, oldest waiting request first: a hit builds at once on a
-            # free slot; a miss starts its setup; requests whose molecule is busy
-            # (a build or a setup in flight) wait
-            started = set()
+            # free slot; requests whose molecule is busy (a build or a setup in
+            # flight) wait.  Misses start their setups in arrival order: once
+            # one cannot be admitted, younger misses wait too (they would take
+            # the memory it waits for), and a miss never evicts a molecule an
+            # older waiting request needs -- without these two rules a setup
+            # could evict a molecule whose own setup had just finished, before
+            # its request was built, and setups would chase each other forever
+            started, keep, miss_blocked = set(), set(), False
             for req in list(waiting):
                 mid = req.mol_id
                 if mid in self.busy or mid in started:
+                    keep.add(mid)
                     continue
                 if self.lru.touch(mid):
+                    keep.add(mid)
                     if not self.free_slots:
                         continue
                     h = self.resident[mid]
@@ -207,9 +220,13 @@ class Server:
                     inflight.append((req, slot, ev, (J, K, EJ, EK)))
                     waiting.remove(req)
                     progressed = True
-                elif self._start_setup(mid, int(req.C.shape[1])):
-                    started.add(mid)
-                    progressed = True
+                elif not miss_blocked:
+                    if self._start_setup(mid, int(req.C.shape[1]), keep):
+                        started.add(mid)
+                        progressed = True
+                    else:
+                        miss_blocked = True
+                    keep.add(mid)
             still = []
             for req, slot, ev, out in inflight:
                 if ev.query():

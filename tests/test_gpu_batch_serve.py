@@ -96,3 +96,76 @@ def test_serving_same_alone_and_in_mix():
         J, K, EJ, EK = alone[key]
         assert r.E == (EJ, EK)
         assert torch.equal(r.J, J) and torch.equal(r.K, K)
+
+
+def test_build_batch_captured_in_a_cuda_graph():
+    """Once every handle has been built at its nocc (work buffers exist), a
+    dfjk_build_batch call records into a CUDA graph: the replay gives the
+    direct call's results bitwise, and replaying after new orbitals are
+    copied into the same input buffers (an SCF iteration) gives the direct
+    build of those orbitals."""
+    mols = _mols([3, 6, 2, 5], seed0=7200)
+    hs = [dfjk.Handle(m, precision=dfjk.DFJK_MIXED) for m in mols]
+    C0 = [_c(m, i) for i, m in enumerate(mols)]
+    C1 = [_c(m, 10 + i) for i, m in enumerate(mols)]
+    Cs = [c.clone() for c in C0]
+    Js = [torch.empty((h.nao, h.nao), dtype=torch.float64, device="cuda") for h in hs]
+    Ks = [torch.empty_like(j) for j in Js]
+    E = torch.empty((2, len(hs)), dtype=torch.float64, device="cuda")
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        dfjk.build_batch(hs, Cs, Js=Js, Ks=Ks, E=E, nstreams=3, stream=s)  # buffers exist from here
+    s.synchronize()
+    ref0 = [(j.clone(), k.clone()) for j, k in zip(Js, Ks)], E.clone()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        dfjk.build_batch(hs, Cs, Js=Js, Ks=Ks, E=E, nstreams=3, stream=s)
+    for j, k in zip(Js, Ks):
+        j.zero_()
+        k.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    for (j0, k0), j, k in zip(ref0[0], Js, Ks):
+        assert torch.equal(j0, j) and torch.equal(k0, k)
+    assert torch.equal(ref0[1], E)
+    for c, c1 in zip(Cs, C1):
+        c.copy_(c1)
+    g.replay()
+    torch.cuda.synchronize()
+    for h, c1, j, k, i in zip(hs, C1, Js, Ks, range(len(hs))):
+        J, K, EJ, EK = h.build(c1)
+        assert torch.equal(J[0], j) and torch.equal(K[0], k)
+        assert E[0, i].item() == EJ[0] and E[1, i].item() == EK[0]
+    for h in hs:
+        h.close()
+
+
+def test_batch_with_a_60_atom_molecule_matches_the_oracle():
+    """A multi-wave batch whose largest member is the 60-atom workload
+    molecule (mixed path: B packed, built in four aux-row chunks): that
+    member's J, K and energies against the FP64 CPU oracle at full size, and
+    a small member against the oracle too."""
+    from oracle import oracle as O
+
+    big = I.molecule(60, seed=1002)
+    mols = [I.molecule(5, seed=7300), big, I.molecule(9, seed=7301)]
+    Cs, Cnp = [], []
+    for i, m in enumerate(mols):
+        C = I.orthonormalize(I.c_occ_raw(m.nao, I.default_nocc(m.nao), 3100 + i), O.overlap(m.orb, m.coords))
+        Cnp.append(C)
+        Cs.append(torch.from_numpy(C).cuda())
+    prec = dfjk.DFJK_MIXED
+    budget = int(1.05 * batch.resident_bytes(big.nao, big.naux, Cs[1].shape[1], prec))
+    E, res, st = batch.run_batch(mols, Cs, precision=prec, budget_bytes=budget, workers=2, nstreams=2,
+                                 keep_results=True)
+    assert st["waves"] > 1
+    for i in (1, 2):
+        ref = O.dfjk(mols[i].orb, mols[i].aux, mols[i].coords, Cnp[i])
+        J, K = res[i][0].cpu().numpy(), res[i][1].cpu().numpy()
+        dJ, dK = np.abs(J - ref["J"]).max(), np.abs(K - ref["K"]).max()
+        print(f"batch member {mols[i].natom} atoms vs oracle: dJ {dJ:.2e} dK {dK:.2e} "
+              f"dEJ {abs(E[i, 0] - ref['E_J']):.2e} dEK {abs(E[i, 1] - ref['E_K']):.2e}")
+        assert dJ <= 1e-7 and dK <= 1e-7
+        assert abs(E[i, 0] - ref["E_J"]) <= 1e-6 and abs(E[i, 1] - ref["E_K"]) <= 1e-6
+        del ref
