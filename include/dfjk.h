@@ -310,7 +310,8 @@ const char *dfjk_last_error(void);
 
 /* Measured fused multiply-add throughput of the current GPU in TFLOP/s
  * (2 flop per FMA), bits = 64 (FP64 pipe) or 32 (FP32 pipe): independent FMA
- * chains on every SM for about 40 ms after three calibration launches.  The
+ * chains on every SM, the best of four occupancy / chain-count shapes, each
+ * timed for about 40 ms after three calibration launches.  The
  * roofline of the integral kernels, which are bound by these pipes.
  * Synchronises `stream`.  Errors: DFJK_ERR_ARG, _CUDA.                     */
 int dfjk_fma_rate(int32_t bits, double *tflops, void *stream);

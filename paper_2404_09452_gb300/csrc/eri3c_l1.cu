@@ -6,7 +6,7 @@ namespace dfjk {
 
 void launch_eri3c_l1(int la, int lb, const Eri3cArgs &a, const AuxArgs &x, const double *tab,
                      cudaStream_t st) {
-  if (eri3c_coop_enabled()) {  // the NCC threads of an aux shell share its work
+  if (eri3c_use_coop(la, lb, 1, false)) {  // the NCC threads of an aux shell share its work
     using Sh = CoopShape<1>;
     dim3 grid(a.npairs, ceil_div(a.naux_shells, Sh::NS));
     DISPATCH_LALB(la, lb, (eri3c_coop_kernel<A_, B_, 1, double><<<grid, Sh::THREADS, 0, st>>>(a, x, tab)));

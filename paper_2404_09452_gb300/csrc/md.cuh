@@ -539,20 +539,55 @@ __host__ __device__ constexpr TuvTable make_tuv_table() {
       }
   return T;
 }
-__constant__ TuvTable c_tuv = make_tuv_table();
+// The recursion step of entry k >= 1 of R^(n) from R^(n+1), packed as
+// idx1 | idx2 << 8 | dir << 16 | coef << 18: R_k = P_dir R'_idx1 + coef R'_idx2
+// (dir 0, 1, 2 = the first of t, u, v that is > 0; coef = that index - 1, and
+// idx2 = 0 when coef = 0).
+struct RecTable {
+  int e[ntuv(8)];
+};
+__host__ __device__ constexpr RecTable make_rec_table() {
+  RecTable R{};
+  const TuvTable T = make_tuv_table();
+  for (int k = 1; k < ntuv(8); ++k) {
+    const int t = T.t[k], u = T.u[k], v = T.v[k];
+    int d = 0, i1 = 0, i2 = 0, c = 0;
+    if (t > 0) {
+      d = 0; i1 = tuv_idx(t - 1, u, v);
+      if (t > 1) { c = t - 1; i2 = tuv_idx(t - 2, u, v); }
+    } else if (u > 0) {
+      d = 1; i1 = tuv_idx(t, u - 1, v);
+      if (u > 1) { c = u - 1; i2 = tuv_idx(t, u - 2, v); }
+    } else {
+      d = 2; i1 = tuv_idx(t, u, v - 1);
+      if (v > 1) { c = v - 1; i2 = tuv_idx(t, u, v - 2); }
+    }
+    R.e[k] = i1 | (i2 << 8) | (d << 16) | (c << 18);
+  }
+  return R;
+}
+__constant__ RecTable c_rec = make_rec_table();
 
 __device__ __forceinline__ int tuv_idx_rt(int t, int u, int v) { return tuv_idx(t, u, v); }
 __device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
 __device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
 
-// The cooperative kernels are the default for aux l >= 1; DFJK_ERI_COOP=0
-// selects the one-thread-per-aux-shell kernels (same integrals).
-inline bool eri3c_coop_enabled() {
-  static const bool on = [] {
+// Which kernel evaluates a class: the cooperative one where it measured
+// faster (the classes whose one-thread kernel spills: (dp|p), (dd|p), (dd|d),
+// and in FP32 also (dp|d)); the one-thread kernel elsewhere, where every
+// thread of a warp works on its own aux shell and the cooperative kernel's
+// per-lane Boys evaluations would cost more than they save.  DFJK_ERI_COOP=0
+// or 1 forces one kernel for every class with aux l >= 1.
+inline bool eri3c_use_coop(int la, int lb, int lc, bool fp32) {
+  static const int mode = [] {
     const char *e = std::getenv("DFJK_ERI_COOP");
-    return !(e && e[0] == '0');
+    return e ? (e[0] == '0' ? 0 : (e[0] == '1' ? 1 : 2)) : 2;
   }();
-  return on;
+  if (lc == 0 || mode == 0) return false;
+  if (mode == 1) return true;
+  if (la == 2 && lb == 2) return true;               // (dd|p), (dd|d)
+  if (la == 2 && lb == 1) return lc == 1 || fp32;    // (dp|p); (dp|d) in FP32
+  return false;
 }
 
 template <int LC>
@@ -577,6 +612,8 @@ __global__ void __launch_bounds__(CoopShape<LC>::THREADS, 1) eri3c_coop_kernel(E
   __shared__ Real srec[REC];
   __shared__ double sP[3];
   __shared__ Real Rbuf[2][NS][NR];
+  __shared__ int srt[NR];  // recursion table of the entries this kernel uses
+  for (int i = threadIdx.x; i < NR; i += blockDim.x) srt[i] = c_rec.e[i];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int g = lane / G, cc = lane - g * G;  // aux shell within the warp, aux component
   const bool lane_used = lane < SPW * G;
@@ -590,6 +627,9 @@ __global__ void __launch_bounds__(CoopShape<LC>::THREADS, 1) eri3c_coop_kernel(E
   // powers 1 (p, and xy, xz, yz)
   const int cx = cart_x(LC, cc), cy = cart_y(LC, cc), cz = cart_z(LC, cc);
   const int two = (cx == 2) ? 0 : (cy == 2) ? 1 : (cz == 2) ? 2 : -1;
+  // shift of the W index: 2 along the doubled axis (xx, yy, zz), else the powers
+  const int sh_y = two >= 0 ? (two == 1 ? 2 : 0) : cy, sh_z = two >= 0 ? (two == 2 ? 2 : 0) : cz;
+  const int sh_yz = sh_y + sh_z;
   Real acc[NCA * NCB];
 #pragma unroll
   for (int i = 0; i < NCA * NCB; ++i) acc[i] = Real(0);
@@ -635,19 +675,14 @@ __global__ void __launch_bounds__(CoopShape<LC>::THREADS, 1) eri3c_coop_kernel(E
         const int cnt = ntuv(L - n);
         if (lane_used)
           for (int k = cc; k < cnt; k += G) {
-            const int t = c_tuv.t[k], u = c_tuv.u[k], v = c_tuv.v[k];
             Real r;
             if (k == 0) {
               r = pw * F[n];
-            } else if (t > 0) {
-              r = X * cur[tuv_idx_rt(t - 1, u, v)];
-              if (t > 1) r = fma(Real(t - 1), cur[tuv_idx_rt(t - 2, u, v)], r);
-            } else if (u > 0) {
-              r = Y * cur[tuv_idx_rt(t, u - 1, v)];
-              if (u > 1) r = fma(Real(u - 1), cur[tuv_idx_rt(t, u - 2, v)], r);
             } else {
-              r = Z * cur[tuv_idx_rt(t, u, v - 1)];
-              if (v > 1) r = fma(Real(v - 1), cur[tuv_idx_rt(t, u, v - 2)], r);
+              const int e = srt[k];
+              const int d = (e >> 16) & 3;
+              const Real P = d == 0 ? X : (d == 1 ? Y : Z);
+              r = fma(Real((e >> 18) & 15), cur[(e >> 8) & 255], P * cur[e & 255]);
             }
             nxt[k] = r;
           }
@@ -658,12 +693,17 @@ __global__ void __launch_bounds__(CoopShape<LC>::THREADS, 1) eri3c_coop_kernel(E
       }
       // cur = R^(0); W for this thread's aux component (t + u + v <= LAB) is
       // read from it term by term in the contraction
+      // W_tuv = c1 R_{t+dx, u+dy, v+dz} + c2 R_tuv with the shift of this
+      // lane's component (dx + dy + dz = LC): xx-type c1 = 1/(2 gamma), c2 = 1;
+      // xy-type and p c1 = 1, c2 = 0.  Branch-free, so the lanes of the
+      // different components of a warp do not diverge.
       const Real *Rs = cur;
+      const Real c1 = two >= 0 ? g1 : Real(1), c2 = two >= 0 ? Real(1) : Real(0);
       auto wval = [&](int t, int u, int v) -> Real {
-        if (two == 0) return fma(g1, Rs[tuv_idx_rt(t + 2, u, v)], Rs[tuv_idx(t, u, v)]);
-        if (two == 1) return fma(g1, Rs[tuv_idx_rt(t, u + 2, v)], Rs[tuv_idx(t, u, v)]);
-        if (two == 2) return fma(g1, Rs[tuv_idx_rt(t, u, v + 2)], Rs[tuv_idx(t, u, v)]);
-        return Rs[tuv_idx_rt(t + cx, u + cy, v + cz)];
+        const int n1 = t + u + v + LC;                 // level of the shifted index
+        const int s1 = u + v + sh_yz;                  // (u + dy) + (v + dz)
+        const int i1 = n1 * (n1 + 1) * (n1 + 2) / 6 + s1 * (s1 + 1) / 2 + v + sh_z;
+        return fma(c1, Rs[i1], c2 * Rs[tuv_idx(t, u, v)]);
       };
       const Real scale = (two >= 0) ? g1 : (LC == 1 ? -g1 : g1 * g1);
       const Real ps = live ? srec[4] * (Real)aux.cdiv[pc0 + kc] * sr * scale : Real(0);

@@ -10,13 +10,11 @@
 namespace dfjk {
 namespace {
 
-constexpr int PROBE_CHAINS = 8;
 constexpr int PROBE_THREADS = 256;
-constexpr int PROBE_BLOCKS_PER_SM = 4;
 
 // x <- x b + c per chain; with b < 1 every chain converges to c / (1 - b),
 // so no value overflows or becomes subnormal whatever the iteration count.
-template <typename Real>
+template <typename Real, int PROBE_CHAINS>
 __global__ void __launch_bounds__(PROBE_THREADS) fma_chain_kernel(long long iters, Real b, Real c, Real *out) {
   Real x[PROBE_CHAINS];
 #pragma unroll
@@ -31,12 +29,14 @@ __global__ void __launch_bounds__(PROBE_THREADS) fma_chain_kernel(long long iter
   out[blockIdx.x * PROBE_THREADS + threadIdx.x] = s;
 }
 
-template <typename Real>
-double run_probe(cudaStream_t st) {
+// One configuration: `chains` independent FMA chains per thread, `per_sm`
+// blocks of 256 threads per SM; calibrated towards ~40 ms per launch.
+template <typename Real, int CHAINS>
+double run_config(int per_sm, cudaStream_t st) {
   int dev = 0, nsm = 0;
   DFJK_CUDA_CHECK(cudaGetDevice(&dev));
   DFJK_CUDA_CHECK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  const int blocks = nsm * PROBE_BLOCKS_PER_SM;
+  const int blocks = nsm * per_sm;
   Real *out = nullptr;
   DFJK_CUDA_CHECK(cudaMalloc(&out, sizeof(Real) * (size_t)blocks * PROBE_THREADS));
   cudaEvent_t e0, e1;
@@ -44,21 +44,32 @@ double run_probe(cudaStream_t st) {
   DFJK_CUDA_CHECK(cudaEventCreate(&e1));
   double tflops = 0.0;
   long long iters = 1024;
-  for (int pass = 0; pass < 4; ++pass) {  // calibrate towards ~40 ms per launch, keep the last
+  for (int pass = 0; pass < 4; ++pass) {  // the last pass is the measurement
     DFJK_CUDA_CHECK(cudaEventRecord(e0, st));
-    fma_chain_kernel<Real><<<blocks, PROBE_THREADS, 0, st>>>(iters, Real(0.999999), Real(1e-6), out);
+    fma_chain_kernel<Real, CHAINS><<<blocks, PROBE_THREADS, 0, st>>>(iters, Real(0.999999), Real(1e-6), out);
     DFJK_LAUNCHED();
     DFJK_CUDA_CHECK(cudaEventRecord(e1, st));
     DFJK_CUDA_CHECK(cudaEventSynchronize(e1));
     float ms = 0.f;
     DFJK_CUDA_CHECK(cudaEventElapsedTime(&ms, e0, e1));
-    tflops = 2.0 * PROBE_CHAINS * (double)iters * blocks * PROBE_THREADS / (ms * 1e-3) / 1e12;
+    tflops = 2.0 * CHAINS * (double)iters * blocks * PROBE_THREADS / (ms * 1e-3) / 1e12;
     if (pass < 3) iters = std::max<long long>(1024, (long long)(iters * 40.0 / std::max(ms, 0.01f)));
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaFree(out);
   return tflops;
+}
+
+// The best of a few occupancy / instruction-level-parallelism shapes.
+template <typename Real>
+double run_probe(cudaStream_t st) {
+  double best = 0.0;
+  best = std::max(best, run_config<Real, 8>(4, st));
+  best = std::max(best, run_config<Real, 4>(8, st));
+  best = std::max(best, run_config<Real, 16>(2, st));
+  best = std::max(best, run_config<Real, 8>(1, st));
+  return best;
 }
 
 }  // namespace

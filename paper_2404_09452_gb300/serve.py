@@ -267,17 +267,20 @@ class Server:
         self.lru = Residency(self.budget)
 
 
-def make_stream(mols, nreq, rate, repeat=0.7, seed=5000, c_of=None):
-    """Poisson arrivals; with probability `repeat` a request reuses a molecule
-    already requested (new C_occ), otherwise it introduces the next molecule of
-    the pool.  `c_of(mol_id, k)` returns the device C_occ of the k-th request
-    of that molecule."""
+def make_stream(mols, nreq, rate, repeat=0.7, seed=5000, c_of=None, active=None):
+    """Poisson arrivals; with probability `repeat` a request repeats a molecule
+    whose SCF is in progress (new C_occ), otherwise it introduces the next
+    molecule of the pool.  `active`: how many molecules are in SCF at once
+    (the last `active` introduced; None = every molecule introduced so far).
+    `c_of(mol_id, k)` returns the device C_occ of the k-th request of that
+    molecule."""
     rng = np.random.default_rng(seed)
     t = np.cumsum(rng.exponential(1.0 / rate, size=nreq))
     seen, nxt, out, count = [], 0, [], collections.Counter()
     for i in range(nreq):
-        if seen and (rng.random() < repeat or nxt >= len(mols)):
-            mid = seen[int(rng.integers(len(seen)))]
+        live = seen if active is None else seen[-active:]
+        if live and (rng.random() < repeat or nxt >= len(mols)):
+            mid = live[int(rng.integers(len(live)))]
         else:
             mid = nxt
             seen.append(mid)

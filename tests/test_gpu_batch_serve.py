@@ -156,7 +156,9 @@ def test_batch_with_a_60_atom_molecule_matches_the_oracle():
         Cnp.append(C)
         Cs.append(torch.from_numpy(C).cuda())
     prec = dfjk.DFJK_MIXED
-    budget = int(1.05 * batch.resident_bytes(big.nao, big.naux, Cs[1].shape[1], prec))
+    # the 60-atom molecule fits alone, not with the first small one: three waves
+    small = batch.resident_bytes(mols[0].nao, mols[0].naux, Cs[0].shape[1], prec)
+    budget = batch.resident_bytes(big.nao, big.naux, Cs[1].shape[1], prec) + small // 2
     E, res, st = batch.run_batch(mols, Cs, precision=prec, budget_bytes=budget, workers=2, nstreams=2,
                                  keep_results=True)
     assert st["waves"] > 1
