@@ -703,6 +703,7 @@ __global__ void __launch_bounds__(CoopShape<LC>::THREADS, 1) eri3c_coop_kernel(E
         const int n1 = t + u + v + LC;                 // level of the shifted index
         const int s1 = u + v + sh_yz;                  // (u + dy) + (v + dz)
         const int i1 = n1 * (n1 + 1) * (n1 + 2) / 6 + s1 * (s1 + 1) / 2 + v + sh_z;
+        if (LC == 1) return Rs[i1];                    // p: W = R shifted, c1 = 1, c2 = 0
         return fma(c1, Rs[i1], c2 * Rs[tuv_idx(t, u, v)]);
       };
       const Real scale = (two >= 0) ? g1 : (LC == 1 ? -g1 : g1 * g1);
