@@ -211,51 +211,6 @@ __global__ void __launch_bounds__(256) potrf_diag_kernel(double *A, int lda, dou
   }
 }
 
-// The same for NB = 32 on one warp, the block held in registers (lane i owns
-// row i), columns and rows broadcast by shuffles: no shared memory and no
-// block-wide barriers on the Cholesky's critical chain (the shared-memory
-// kernel above takes ~48 us per block, 128 barriers).
-__global__ void __launch_bounds__(32) potrf32_warp_kernel(double *A, int lda, double *Dinv, int *status) {
-  constexpr int NB = 32;
-  const int i = threadIdx.x;
-  double a[NB];
-#pragma unroll
-  for (int j = 0; j < NB; ++j) a[j] = (j <= i) ? A[(long long)i * lda + j] : 0.0;
-  bool bad = false;
-#pragma unroll
-  for (int j = 0; j < NB; ++j) {
-    double d = __shfl_sync(0xffffffffu, a[j], j);
-    if (!(d > 0.0) || !isfinite(d)) {
-      bad = true;  // every lane sees the same pivot
-      d = 1.0;
-    }
-    const double l = sqrt(d), r = 1.0 / l;
-    if (i == j) a[j] = l;
-    else if (i > j) a[j] *= r;
-#pragma unroll
-    for (int c = j + 1; c < NB; ++c) {
-      const double lc = __shfl_sync(0xffffffffu, a[j], c);  // L[c][j]
-      if (i >= c) a[c] = fma(-a[j], lc, a[c]);
-    }
-  }
-  if (bad && i == 0) atomicOr(status, STATUS_NOT_PD);
-  // X = L^-1 by forward substitution, lane c owns column c:
-  // x[k] = (delta_kc - sum_{j < k} L[k][j] x[j]) / L[k][k]
-  double x[NB];
-#pragma unroll
-  for (int k = 0; k < NB; ++k) {
-    double sum = 0.0;
-#pragma unroll
-    for (int j = 0; j < k; ++j) sum = fma(__shfl_sync(0xffffffffu, a[j], k), x[j], sum);
-    const double lkk = __shfl_sync(0xffffffffu, a[k], k);
-    x[k] = ((i == k ? 1.0 : 0.0) - sum) / lkk;
-  }
-#pragma unroll
-  for (int j = 0; j < NB; ++j) A[(long long)i * lda + j] = a[j];
-#pragma unroll
-  for (int k = 0; k < NB; ++k) Dinv[k * NB + i] = (i <= k) ? x[k] : 0.0;
-}
-
 void cholesky_f64(double *A, int n, int lda, double *Dinv, int *status, double *work,
                   cudaStream_t st) {
   (void)work;
@@ -269,8 +224,7 @@ void cholesky_f64(double *A, int n, int lda, double *Dinv, int *status, double *
   const int nb = n / NB;
   for (int k = 0; k < nb; ++k) {
     double *Akk = A + (long long)k * NB * lda + k * NB;
-    if (NB == 32) potrf32_warp_kernel<<<1, 32, 0, st>>>(Akk, lda, Dinv + (long long)k * NB * NB, status);
-    else potrf_diag_kernel<NB><<<1, 256, SMEM, st>>>(Akk, lda, Dinv + (long long)k * NB * NB, status);
+    potrf_diag_kernel<NB><<<1, 256, SMEM, st>>>(Akk, lda, Dinv + (long long)k * NB * NB, status);
     DFJK_LAUNCHED();
     const int rows = n - (k + 1) * NB;
     if (rows <= 0) continue;

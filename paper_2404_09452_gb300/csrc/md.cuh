@@ -573,8 +573,8 @@ __device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
 __device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
 
 // Which kernel evaluates a class: the cooperative one where it measured
-// faster (the classes whose one-thread kernel spills: (dp|p), (dd|p), (dd|d),
-// and in FP32 also (dp|d)); the one-thread kernel elsewhere, where every
+// faster (the classes whose one-thread kernel spills: (dp|p), (dp|d),
+// (dd|p), (dd|d)); the one-thread kernel elsewhere, where every
 // thread of a warp works on its own aux shell and the cooperative kernel's
 // per-lane Boys evaluations would cost more than they save.  DFJK_ERI_COOP=0
 // or 1 forces one kernel for every class with aux l >= 1.
@@ -585,9 +585,15 @@ inline bool eri3c_use_coop(int la, int lb, int lc, bool fp32) {
   }();
   if (lc == 0 || mode == 0) return false;
   if (mode == 1) return true;
-  if (la == 2 && lb == 2) return true;               // (dd|p), (dd|d)
-  if (la == 2 && lb == 1) return lc == 1 || fp32;    // (dp|p); (dp|d) in FP32
-  return false;
+  (void)fp32;
+  return la == 2 && lb >= 1;  // (dp|p), (dp|d), (dd|p), (dd|d)
+}
+
+// (dd|s): the cooperative kernel split over the orbital components.
+inline bool eri3c_use_coop_a(int la, int lb) {
+  const char *e = std::getenv("DFJK_ERI_COOP");
+  if (e && e[0] == '0') return false;
+  return la == 2 && lb == 2;
 }
 
 template <int LC>
@@ -737,6 +743,135 @@ __global__ void __launch_bounds__(CoopShape<LC>::THREADS, 1) eri3c_coop_kernel(E
     for (int cb = 0; cb < NCB; ++cb)
       args.T[(col0 + ca * NCB + cb) * args.ldT + P] =
           (double)acc[ca * NCB + cb] * (comp_factor(LA, ca) * comp_factor(LB, cb) * fc);
+}
+
+// The cooperative scheme for s aux functions (LC = 0), split over the
+// components of the first orbital shell instead: the ncart(LA) threads of an
+// aux shell share R (W = R for an s function) and each contracts it with the
+// NCB component pairs of its own component a.  Used for (dd|s), whose
+// one-thread kernel spills (ncu at 20 atoms: FP64 pipe 31 % busy).
+template <int LA>
+struct CoopShapeA {
+  static constexpr int G = ncart(LA);
+  static constexpr int SPW = 32 / G;
+  static constexpr int NW = 4;
+  static constexpr int NS = NW * SPW;
+  static constexpr int THREADS = NW * 32;
+};
+
+template <int LA, int LB, typename Real>
+__global__ void __launch_bounds__(CoopShapeA<LA>::THREADS, 1) eri3c_coop_a_kernel(Eri3cArgs args, AuxArgs aux,
+                                                                                   const Real *__restrict__ boys_tab) {
+  using Sh = CoopShapeA<LA>;
+  constexpr int G = Sh::G, SPW = Sh::SPW, NS = Sh::NS;
+  constexpr int NT = nterms(LA, LB);
+  constexpr int REC = REC_HDR + NT;
+  constexpr int NCA = ncart(LA), NCB = ncart(LB);
+  constexpr int L = LA + LB;
+  constexpr int NR = ntuv(L);
+  __shared__ Real srec[REC];
+  __shared__ double sP[3];
+  __shared__ Real Rbuf[2][NS][NR];
+  __shared__ int srt[NR];
+  for (int i = threadIdx.x; i < NR; i += blockDim.x) srt[i] = c_rec.e[i];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = lane / G, ca = lane - g * G;
+  const bool lane_used = lane < SPW * G;
+  const int slot = warp * SPW + (lane_used ? g : 0);
+  const int as = blockIdx.y * NS + slot;
+  const bool active = lane_used && as < args.naux_shells;
+  const int sc = active ? args.aux_shells[as] : 0;
+  const double Cx = aux.center[3 * sc], Cy = aux.center[3 * sc + 1], Cz = aux.center[3 * sc + 2];
+  const int pc0 = aux.prim_off[sc], nc = active ? aux.nprim[sc] : 0;
+  // first term of component a's block in a primitive-pair record, and the
+  // (t, u, v) ranges of each of its component pairs
+  const int ax = cart_x(LA, ca), ay = cart_y(LA, ca), az = cart_z(LA, ca);
+  int k0 = 0;
+#pragma unroll
+  for (int a = 0; a < NCA; ++a)
+#pragma unroll
+    for (int cb = 0; cb < NCB; ++cb)
+      if (a < ca)
+        k0 += (cart_x(LA, a) + cart_x(LB, cb) + 1) * (cart_y(LA, a) + cart_y(LB, cb) + 1) *
+              (cart_z(LA, a) + cart_z(LB, cb) + 1);
+  Real acc[NCB];
+#pragma unroll
+  for (int i = 0; i < NCB; ++i) acc[i] = Real(0);
+  const double *rec0 = args.rec + args.rec_off[args.pairs[blockIdx.x]];
+  const int npp = args.npp[args.pairs[blockIdx.x]];
+  int ncmax = nc;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) ncmax = max(ncmax, __shfl_xor_sync(0xffffffffu, ncmax, o));
+  for (int ipp = 0; ipp < npp; ++ipp) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < REC; i += blockDim.x) {
+      const double v = rec0[(long long)ipp * REC + i];
+      srec[i] = (Real)v;
+      if (i >= 1 && i <= 3) sP[i - 1] = v;
+    }
+    __syncthreads();
+    for (int kc = 0; kc < ncmax; ++kc) {
+      const bool live = kc < nc;
+      const Real gexp = live ? (Real)aux.exps[pc0 + kc] : Real(1);
+      const Real p = srec[0];
+      const Real X = (Real)(sP[0] - Cx), Y = (Real)(sP[1] - Cy), Z = (Real)(sP[2] - Cz);
+      const Real sr = rsq(p + gexp);
+      const Real al = p * gexp * (sr * sr);
+      Real F[L + 1];
+      boys_eval<L>(al * (X * X + Y * Y + Z * Z), boys_tab, F);
+      Real *cur = Rbuf[0][slot], *nxt = Rbuf[1][slot];
+      Real pw = Real(1);
+#pragma unroll
+      for (int n = 0; n < L; ++n) pw *= Real(-2) * al;
+      if (lane_used && ca == 0) cur[0] = pw * F[L];
+      __syncwarp();
+#pragma unroll
+      for (int n = L - 1; n >= 0; --n) {
+        pw = Real(1);
+#pragma unroll
+        for (int q = 0; q < n; ++q) pw *= Real(-2) * al;
+        const int cnt = ntuv(L - n);
+        if (lane_used)
+          for (int k = ca; k < cnt; k += G) {
+            Real r;
+            if (k == 0) {
+              r = pw * F[n];
+            } else {
+              const int e = srt[k];
+              const int d = (e >> 16) & 3;
+              const Real P = d == 0 ? X : (d == 1 ? Y : Z);
+              r = fma(Real((e >> 18) & 15), cur[(e >> 8) & 255], P * cur[e & 255]);
+            }
+            nxt[k] = r;
+          }
+        __syncwarp();
+        Real *tmp = cur;
+        cur = nxt;
+        nxt = tmp;
+      }
+      const Real ps = live ? srec[4] * (Real)aux.cdiv[pc0 + kc] * sr : Real(0);
+      // this thread's component a: the (t, u, v) bounds depend on a at run
+      // time, so the terms are walked with runtime loops over small ranges
+      int k = k0;
+#pragma unroll
+      for (int cb = 0; cb < NCB; ++cb) {
+        const int bx = cart_x(LB, cb), by = cart_y(LB, cb), bz = cart_z(LB, cb);
+        Real sum = Real(0);
+        for (int t = 0; t <= ax + bx; ++t)
+          for (int u = 0; u <= ay + by; ++u)
+            for (int v = 0; v <= az + bz; ++v) sum = fma(srec[REC_HDR + k++], cur[tuv_idx_rt(t, u, v)], sum);
+        acc[cb] = fma(ps, sum, acc[cb]);
+      }
+      __syncwarp();
+    }
+  }
+  if (!active) return;
+  const long long col0 = args.pair_col[args.pairs[blockIdx.x]] - args.col_begin;
+  const int P = aux.func_off[sc];
+  const double fa = comp_factor(LA, ca);
+#pragma unroll
+  for (int cb = 0; cb < NCB; ++cb)
+    args.T[(col0 + ca * NCB + cb) * args.ldT + P] = (double)acc[cb] * (fa * comp_factor(LB, cb));
 }
 
 // ---- 2-centre metric and overlap ----------------------------------------------
