@@ -332,16 +332,18 @@ struct dfjk_ctx {
   SlicedOp Csl, Xsl;  // DFJK_MIXED build operands
   DBuf<double> uks_D, uks_J;  // spin-unrestricted build: D_a + D_b and J[D_b]
   cudaStream_t side = nullptr;  // setup: Cholesky + inverse beside the integrals
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaStream_t side2 = nullptr;  // the Cholesky's bulk trailing updates (look-ahead)
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_panel = nullptr, ev_bulk = nullptr;
   ~dfjk_ctx() {
     oz_free(Bchunk);
     oz_free(Csl);
     oz_free(Xsl);
-    if (side) {
-      cudaStreamSynchronize(side);
-      cudaStreamDestroy(side);
-    }
-    for (cudaEvent_t e : {ev_fork, ev_join})
+    for (cudaStream_t s : {side, side2})
+      if (s) {
+        cudaStreamSynchronize(s);
+        cudaStreamDestroy(s);
+      }
+    for (cudaEvent_t e : {ev_fork, ev_join, ev_panel, ev_bulk})
       if (e) cudaEventDestroy(e);
   }
 };
@@ -593,8 +595,11 @@ void make_resident(dfjk_ctx *h, cudaStream_t st) {
     int lo = 0, hi = 0;
     DFJK_CUDA_CHECK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
     DFJK_CUDA_CHECK(cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, hi));
+    DFJK_CUDA_CHECK(cudaStreamCreateWithPriority(&h->side2, cudaStreamNonBlocking, hi));
     DFJK_CUDA_CHECK(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
     DFJK_CUDA_CHECK(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+    DFJK_CUDA_CHECK(cudaEventCreateWithFlags(&h->ev_panel, cudaEventDisableTiming));
+    DFJK_CUDA_CHECK(cudaEventCreateWithFlags(&h->ev_bulk, cudaEventDisableTiming));
   }
   const cudaStream_t s2 = h->side;
   DFJK_CUDA_CHECK(cudaEventRecord(h->ev_fork, st));
@@ -611,7 +616,13 @@ void make_resident(dfjk_ctx *h, cudaStream_t st) {
     h->L.alloc((size_t)np * np);
     DFJK_CUDA_CHECK(cudaMemcpyAsync(h->L.p, h->V.p, h->V.bytes(), cudaMemcpyDeviceToDevice, s2));
     h->Dinv.alloc((size_t)(np / CHOL_NB) * CHOL_NB * CHOL_NB);
-    cholesky_f64(h->L.p, np, np, h->Dinv.p, h->status.p, nullptr, s2);
+    // look-ahead on a second stream (DFJK_CHOL_AHEAD=0: one stream)
+    static const bool ahead = [] {
+      const char *e = std::getenv("DFJK_CHOL_AHEAD");
+      return !(e && e[0] == '0');
+    }();
+    if (ahead) cholesky_f64(h->L.p, np, np, h->Dinv.p, h->status.p, nullptr, s2, h->side2, h->ev_panel, h->ev_bulk);
+    else cholesky_f64(h->L.p, np, np, h->Dinv.p, h->status.p, nullptr, s2);
     zero_upper_kernel<<<(unsigned)(((long long)np * np + 255) / 256), 256, 0, s2>>>(h->L.p, np, np);
     DFJK_LAUNCHED();
     h->Linv.alloc((size_t)np * np);

@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(256) potrf_diag_kernel(double *A, int lda, dou
 }
 
 void cholesky_f64(double *A, int n, int lda, double *Dinv, int *status, double *work,
-                  cudaStream_t st) {
+                  cudaStream_t st, cudaStream_t st2, cudaEvent_t ev_panel, cudaEvent_t ev_bulk) {
   (void)work;
   constexpr int NB = CHOL_NB;
   constexpr int SMEM = 2 * NB * (NB + 1) * (int)sizeof(double);
@@ -221,7 +221,9 @@ void cholesky_f64(double *A, int n, int lda, double *Dinv, int *status, double *
     DFJK_CUDA_CHECK(cudaFuncSetAttribute(potrf_diag_kernel<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM));
     attr = true;
   }
+  const bool ahead = st2 && ev_panel && ev_bulk;
   const int nb = n / NB;
+  bool bulk_pending = false;
   for (int k = 0; k < nb; ++k) {
     double *Akk = A + (long long)k * NB * lda + k * NB;
     potrf_diag_kernel<NB><<<1, 256, SMEM, st>>>(Akk, lda, Dinv + (long long)k * NB * NB, status);
@@ -238,15 +240,48 @@ void cholesky_f64(double *A, int n, int lda, double *Dinv, int *status, double *
     // own complete rows (with narrower tiles two CTAs would share them)
     p.tile = NB;
     gemm_f64(p, st);
-    GemmArgs t;  // A_ij -= L_ik L_jk^T on the trailing lower triangle
-    t.M = rows; t.N = rows; t.K = NB;
-    t.A = panel; t.sAm = lda; t.sAk = 1;
-    t.B = panel; t.sBn = lda; t.sBk = 1;
-    t.C = A + (long long)(k + 1) * NB * (lda + 1); t.sCm = lda; t.sCn = 1;
-    t.alpha = -1.0; t.beta = 1.0; t.lower_only = 1;
-    t.tile = 32;
-    gemm_f64(t, st);
+    if (!ahead) {
+      GemmArgs t;  // A_ij -= L_ik L_jk^T on the trailing lower triangle
+      t.M = rows; t.N = rows; t.K = NB;
+      t.A = panel; t.sAm = lda; t.sAk = 1;
+      t.B = panel; t.sBn = lda; t.sBk = 1;
+      t.C = A + (long long)(k + 1) * NB * (lda + 1); t.sCm = lda; t.sCn = 1;
+      t.alpha = -1.0; t.beta = 1.0; t.lower_only = 1;
+      t.tile = 32;
+      gemm_f64(t, st);
+      continue;
+    }
+    // look-ahead: the next block column (k + 1) is updated on the critical
+    // stream, so the next diagonal block can start, while the rest of the
+    // trailing matrix (block columns >= k + 2) is updated on the second
+    // stream; block column k + 1 also receives the second stream's earlier
+    // updates, which must have landed first
+    DFJK_CUDA_CHECK(cudaEventRecord(ev_panel, st));
+    if (bulk_pending) DFJK_CUDA_CHECK(cudaStreamWaitEvent(st, ev_bulk, 0));
+    GemmArgs c;  // A_{i,k+1} -= L_ik L_{k+1,k}^T for block rows i >= k + 1
+    c.M = rows; c.N = NB; c.K = NB;
+    c.A = panel; c.sAm = lda; c.sAk = 1;
+    c.B = panel; c.sBn = lda; c.sBk = 1;
+    c.C = A + (long long)(k + 1) * NB * (lda + 1); c.sCm = lda; c.sCn = 1;
+    c.alpha = -1.0; c.beta = 1.0;
+    c.tile = 32;
+    gemm_f64(c, st);
+    const int rest = rows - NB;
+    if (rest > 0) {
+      DFJK_CUDA_CHECK(cudaStreamWaitEvent(st2, ev_panel, 0));
+      GemmArgs t;  // A_ij -= L_ik L_jk^T for block rows and columns >= k + 2
+      t.M = rest; t.N = rest; t.K = NB;
+      t.A = panel + (long long)NB * lda; t.sAm = lda; t.sAk = 1;
+      t.B = panel + (long long)NB * lda; t.sBn = lda; t.sBk = 1;
+      t.C = A + (long long)(k + 2) * NB * (lda + 1); t.sCm = lda; t.sCn = 1;
+      t.alpha = -1.0; t.beta = 1.0; t.lower_only = 1;
+      t.tile = 32;
+      gemm_f64(t, st2);
+      DFJK_CUDA_CHECK(cudaEventRecord(ev_bulk, st2));
+      bulk_pending = true;
+    }
   }
+  if (bulk_pending) DFJK_CUDA_CHECK(cudaStreamWaitEvent(st, ev_bulk, 0));
 }
 
 __global__ void place_diag_blocks(double *Linv, int ld, const double *Dinv, int nb) {

@@ -44,8 +44,12 @@ constexpr int CHOL_NB = 32;
 // in place; Dinv (n / CHOL_NB blocks of CHOL_NB^2 doubles) receives the
 // inverse of every diagonal block of L.  A non-positive pivot sets
 // STATUS_NOT_PD in *status.
+// With st2 and two events: look-ahead -- the next block column is updated on
+// st (the critical chain of diagonal blocks and panels) while the rest of the
+// trailing matrix is updated on st2; st waits for st2 before returning.
 void cholesky_f64(double *A, int n, int lda, double *Dinv, int *status, double *work,
-                  cudaStream_t st);
+                  cudaStream_t st, cudaStream_t st2 = nullptr, cudaEvent_t ev_panel = nullptr,
+                  cudaEvent_t ev_bulk = nullptr);
 // Linv = L^-1 (lower triangular), n a multiple of CHOL_NB; uses Dinv from
 // cholesky_f64 and `work` (n x n doubles).
 void tri_inverse_f64(const double *L, int n, int ld, const double *Dinv, double *Linv,
