@@ -198,8 +198,11 @@ __global__ void __launch_bounds__(256) oz_slice_tr_fused_kernel(const double *__
                                                                 __nv_bfloat16 *__restrict__ out, int mu0,
                                                                 int kblk, const int *__restrict__ pre = nullptr,
                                                                 long long pre_rows = 0, int pre_row0 = 0) {
-  constexpr int KG = 256 / R, LD = 72, MAXKB = 8;
-  __shared__ __nv_bfloat16 tile[S * R * LD];
+  // slices staged K-major, [s][k][row] with R + 1 elements per k: the writes
+  // (lanes along rows) and the reads of 8 consecutive k of one row (lanes
+  // along k chunks) both spread over the shared-memory banks
+  constexpr int KG = 256 / R, LDK = R + 1, MAXKB = 8;
+  __shared__ __nv_bfloat16 tile[S * 64 * LDK];
   __shared__ unsigned long long rmax[R][MAXKB];
   __shared__ int rexp[R][MAXKB];
   const int z = blockIdx.y, r0 = blockIdx.x * R;
@@ -259,18 +262,21 @@ __global__ void __launch_bounds__(256) oz_slice_tr_fused_kernel(const double *__
 #pragma unroll
       for (int s = S - 1; s >= 1; --s) {
         const int d = (int)(((n + 32) & 63) - 32);
-        tile[(s * R + rr) * LD + kk] = __float2bfloat16_rn((float)d);
+        tile[(s * 64 + kk) * LDK + rr] = __float2bfloat16_rn((float)d);
         n = (n - d) >> 6;
       }
-      tile[rr * LD + kk] = __float2bfloat16_rn((float)n);
+      tile[kk * LDK + rr] = __float2bfloat16_rn((float)n);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < S * R * 8; i += 256) {  // (slice, row, chunk of 8 K)
       const int s = i / (R * 8), rw = (i / 8) % R, c8 = i % 8;
       const int kc = k0 + c8 * 8;
       if (kc < kpitch) {
-        const uint4 v = *reinterpret_cast<const uint4 *>(&tile[(s * R + rw) * LD + c8 * 8]);
-        *reinterpret_cast<uint4 *>(out + oz_off(z, s, r0 + rw, kc, S, rows_pad, kpitch, nkb, kblk)) = v;
+        __align__(16) __nv_bfloat16 v[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) v[t] = tile[(s * 64 + c8 * 8 + t) * LDK + rw];
+        *reinterpret_cast<uint4 *>(out + oz_off(z, s, r0 + rw, kc, S, rows_pad, kpitch, nkb, kblk)) =
+            *reinterpret_cast<const uint4 *>(v);
       }
     }
     __syncthreads();
