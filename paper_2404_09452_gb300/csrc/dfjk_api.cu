@@ -787,20 +787,9 @@ void ensure_workspace(dfjk_ctx *h, int nocc, int nset) {
     if (mixed) {
       const int pc = build_chunk_rows(h->nao, h->naux_pad, nocc, h->tune.build_ws_mb);
       h->chunk_rows = pc;
-      const size_t mp = ((size_t)pc + OZ_BM - 1) / OZ_BM * OZ_BM, ig = ((size_t)nocc + 31) / 32;
-      if (oz_fused_x_available()) {
-        // X = B C writes X's slices (K blocks of 32 P x 32 i) and rho partials
-        // directly; rows beyond nao stay zero
-        h->X.release();
-        h->rho_work.alloc((size_t)h->nao * ig * mp);
-        oz_alloc(h->Xsl, 1, 6, h->nao, (int)(ig * mp * 32), OZ_BM);
-        DFJK_CUDA_CHECK(cudaMemset(h->Xsl.data, 0, (size_t)6 * h->Xsl.rows_pad * h->Xsl.kpitch * 2));
-        DFJK_CUDA_CHECK(cudaMemset(h->Xsl.expo, 0, (size_t)h->Xsl.rows_pad * h->Xsl.nkb * 4));
-      } else {
-        h->X.alloc((size_t)h->nao * pc * nocc);
-        h->rho_work.alloc((size_t)h->nao * pc);
-        oz_alloc(h->Xsl, 1, 6, h->nao, pc * nocc, OZ_BM);
-      }
+      h->X.alloc((size_t)h->nao * pc * nocc);
+      h->rho_work.alloc((size_t)h->nao * pc);
+      oz_alloc(h->Xsl, 1, 6, h->nao, pc * nocc, OZ_BM);
       oz_alloc(h->Bchunk, h->nao, 6, pc, h->nao, OZ_BM);
     } else {
       h->rho_work.alloc(std::max((size_t)128 * ceil_div(h->naux_pad, 256) * 256, (size_t)h->nao * h->naux_pad));
@@ -941,38 +930,25 @@ void build_one(dfjk_ctx *h, int nocc, const double *C, double *J, double *Kout, 
     const int pc_max = h->chunk_rows;
     const int nchunk = ceil_div(np, pc_max);
     const cudaStream_t sj = h->side ? h->side : st;
-    const bool fused = oz_fused_x_available();
     for (int c = 0; c < nchunk; ++c) {
       const int p0 = c * pc_max, pc = std::min(pc_max, np - p0);
-      const int mp = (pc + OZ_BM - 1) / OZ_BM * OZ_BM, ig = (nocc + 31) / 32;
-      // K of the K GEMM: (P, i) of the chunk, in K blocks of 32 P x 32 i
-      // (fused) or P-major (X in FP64, then sliced)
-      const long long kt = fused ? (long long)ig * mp * 32 : (long long)pc * nocc;
-      double *Xc = h->X.p;  // X[mu][p][i] of this chunk (unfused)
+      const long long kt = (long long)pc * nocc;  // K of the K GEMM: (P, i) of the chunk, P-major
+      double *Xc = h->X.p;                        // X[mu][p][i] of this chunk
       {
         PhaseScope ph(4, st);
         SlicedOp bv = oz_view(h->Bchunk, pc, nao);  // batch mu, rows P of the chunk, K nu
         oz_slice_f64_packed_pre(h->B.p, h->ldb, h->Bexpo.p, h->expo_rows, p0, bv, st, h->tune.pslice_rows);
         OzGemmArgs x;
         x.M = pc; x.N = nocc; x.K = nao; x.nz = nao; x.a_batched = 1;
+        x.mode = 0; x.out = Xc; x.ldo = nocc; x.out_bs = kt;
         x.status = h->status.p; x.timeout = h->opt.timeout_iters;
         x.tile_ctr = h->tctr.p;
         x.phase = 9;
-        if (fused) {  // written in the layout of the K GEMM's operand view below
-          const SlicedOp xv = oz_view(h->Xsl, nao, (int)kt);
-          x.mode = 3;
-          x.x_data = xv.data; x.x_expo = xv.expo; x.x_rows_pad = xv.rows_pad;
-          x.x_pg = mp / 32; x.x_ig = ig; x.x_nkb = xv.nkb; x.x_kblk = xv.kblk; x.x_kpitch = xv.kpitch;
-          x.x_C = C; x.x_rho = h->rho_work.p;
-        } else {
-          x.mode = 0; x.out = Xc; x.ldo = nocc; x.out_bs = kt;
-        }
         oz_gemm(bv, h->Csl, x, st);
       }
-      {  // rho of the chunk: from the X GEMM's partials, or from X
+      {
         PhaseScope ph(6, st);
-        if (fused) column_sum_f64(h->rho_work.p, mp, nao * ig, pc, h->rho.p + p0, st);
-        else rho_from_x_f64(Xc, C, nao, pc, nocc, h->rho.p + p0, h->rho_work.p, st);
+        rho_from_x_f64(Xc, C, nao, pc, nocc, h->rho.p + p0, h->rho_work.p, st);
       }
       if (c == nchunk - 1) {
         // J = B^T rho over the packed B, on the handle's side stream beside the
@@ -988,7 +964,7 @@ void build_one(dfjk_ctx *h, int nocc, const double *C, double *J, double *Kout, 
       }
       PhaseScope ph(5, st);
       SlicedOp xs = oz_view(h->Xsl, nao, (int)kt);  // rows mu, K (p, i)
-      if (!fused) oz_slice_f64(Xc, 0, kt, 1, xs, st);
+      oz_slice_f64(Xc, 0, kt, 1, xs, st);
       k_gemm_sliced(h, xs, nao, kt, Kout, c > 0, st);
     }
     mirror_lower_f64(Kout, nao, st);

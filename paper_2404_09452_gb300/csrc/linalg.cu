@@ -374,12 +374,6 @@ __global__ void column_sum_kernel(const double *__restrict__ work, int ldw, int 
   out[P] = s;
 }
 
-void column_sum_f64(const double *work, int ldw, int nrow, int n, double *out, cudaStream_t st) {
-  if (n <= 0) return;
-  column_sum_kernel<<<ceil_div(n, 256), 256, 0, st>>>(work, ldw, nrow, n, out);
-  DFJK_LAUNCHED();
-}
-
 void rho_gemv_f64(const double *B, long long ldb, int nao, int naux, const double *D,
                   double *rho, double *work, int nchunk, cudaStream_t st, int packed) {
   const long long nrows = (long long)nao * (nao + 1) / 2;

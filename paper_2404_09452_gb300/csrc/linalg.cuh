@@ -60,8 +60,6 @@ void tri_inverse_f64(const double *L, int n, int ld, const double *Dinv, double 
 // partial sums in `work` (ceil(naux/256) x nchunk) then a fixed-order reduction.
 void rho_gemv_f64(const double *B, long long ldb, int nao, int naux, const double *D,
                   double *rho, double *work, int nchunk, cudaStream_t st, int packed = 0);
-// out[j] = sum_{r < nrow} work[r ldw + j] for j < n, rows added in order.
-void column_sum_f64(const double *work, int ldw, int nrow, int n, double *out, cudaStream_t st);
 // Both triangles of a packed B: Bfull[(mu nao + nu) ldb + P] =
 // Bp[(max (max + 1) / 2 + min) ldb + P] (nao^2 rows of ldb doubles).
 void unpack_tri_f64(const double *Bp, long long ldb, int nao, double *Bfull, cudaStream_t st);

@@ -724,16 +724,14 @@ __global__ void __launch_bounds__(128, 1)
 // together and the operands of the tiles in flight stay in L2 (a static
 // round-robin lets CTAs drift apart when tiles differ in length).  Per
 // K-block: the producer fills the stage ring, the MMA warp accumulates S
-// levels in TMEM and commits `accf`; the epilogue reads the level sums,
-// combines them into int64, releases TMEM through `acce` (32 NEPI arrivals)
-// and only then converts and accumulates in FP64, so the MMA warp's next K
-// block overlaps that FP64 work.  The producer runs ahead into the next
-// K-block / tile during the drain.
-// Drain warps: 8 (the default: 4 TMEM lane quarters x 2 column halves of 32)
-// or 16 (x 4 column quarters of 16; fewer registers per thread for the level
-// sums and FP64 accumulators, at the lower per-thread register cap of 576
-// threads); DFJK_OZ_DRAIN_WARPS selects.
-constexpr int OZ_MAX_DRAIN = 16;
+// levels in TMEM and commits `accf`; the epilogue drains into FP64 registers
+// and releases TMEM through `acce` (32 NEPI arrivals).  The producer runs
+// ahead into the next K-block / tile during the drain.  (Releasing TMEM
+// before the FP64 part of the drain, so that the next K block's MMAs overlap
+// it, measured slower: holding the level sums and the accumulators together
+// spilled at this kernel's register cap.)
+// 8 drain warps: 4 TMEM lane quarters x 2 column halves of 32.
+constexpr int OZ_NEPI = 8;
 __host__ __device__ constexpr int oz_ws_threads(int nepi) { return 64 + 32 * nepi; }
 constexpr int OZ_QD = 4;  // depth of the tile queue
 
@@ -954,29 +952,26 @@ __global__ void __launch_bounds__(oz_ws_threads(NEPI), 1)
         const int eA = ka.expoA[((long long)zA * ka.rows_padA + m) * ka.nkbA + kb] - OzLev<S>::UNIT;
         // this warp's 32 column exponents, one per lane, broadcast by shuffles
         const int eBl = __ldg(ka.expoB + ((long long)zB * ka.rows_padB + nh + lane) * ka.nkbB + kb);
-        // the level sums of this warp's 32 outputs, combined exactly into one
-        // int64 each, then TMEM is released before the FP64 part: the MMA warp
-        // starts the next K block while the conversion and the scaled FP64
-        // accumulation (the slow part on this GPU's FP64 pipe) run here
-        long long Tv[NH];
 #pragma unroll
-        for (int j = 0; j < NH; ++j) Tv[j] = 0;
+        for (int c = 0; c < NH / 16; ++c) {
+          long long Tv[16];
 #pragma unroll
-        for (int c = 0; c < NH / 16; ++c)
+          for (int j = 0; j < 16; ++j) Tv[j] = 0;
 #pragma unroll
           for (int lev = 0; lev < S; ++lev) {
             float v[16];
             tc::tmem_ld16(tbase + lane_base + lev * OZ_BN + half * NH + c * 16, v);
 #pragma unroll
-            for (int j = 0; j < 16; ++j) oz_add_level<S>(Tv[c * 16 + j], lev, v[j]);
+            for (int j = 0; j < 16; ++j) oz_add_level<S>(Tv[j], lev, v[j]);
           }
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int eB = __shfl_sync(0xffffffffu, eBl, c * 16 + j);
+            acc[c * 16 + j] = fma((double)Tv[j], pow2(eA + eB), acc[c * 16 + j]);
+          }
+        }
         tc::tc_fence_before();
         tc::mbar_arrive(acce);
-#pragma unroll
-        for (int j = 0; j < NH; ++j) {
-          const int eB = __shfl_sync(0xffffffffu, eBl, j);
-          acc[j] = fma((double)Tv[j], pow2(eA + eB), acc[j]);
-        }
       }
       if (!ok) break;
       if (g.mode == 2) {
@@ -1008,55 +1003,6 @@ __global__ void __launch_bounds__(oz_ws_threads(NEPI), 1)
         __threadfence();
         __syncwarp();
         if (lane == 0) *(volatile int *)seq = z + 1;
-      } else if (g.mode == 3) {
-        if constexpr (NH == 32) {
-          // this warp's 32 rows x 32 columns are one K block of the K GEMM's
-          // operand (padding rows and columns hold exact zeros)
-          double mx = 0.0;
-#pragma unroll
-          for (int j = 0; j < NH; ++j) mx = fmax(mx, fabs(acc[j]));
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-          const int e = oz_expo_of(mx);
-          const int ig = nh >> 5, pg = (m0 >> 5) + lgrp;
-          if (ig < g.x_ig) {
-            const long long kb = (long long)ig * g.x_pg + pg;
-            if (lane == 0) g.x_expo[(long long)z * g.x_nkb + kb] = e;
-            // 8 outputs at a time: their 6 digits, then one 16-byte store per slice
-#pragma unroll
-            for (int j0 = 0; j0 < NH; j0 += 8) {
-              int dg[6][8];
-#pragma unroll
-              for (int t = 0; t < 8; ++t) {
-                long long q = oz_fixed<6>(acc[j0 + t], e);
-#pragma unroll
-                for (int sl = 5; sl >= 1; --sl) {
-                  const int d = (int)(((q + 32) & 63) - 32);
-                  dg[sl][t] = d;
-                  q = (q - d) >> 6;
-                }
-                dg[0][t] = (int)q;
-              }
-#pragma unroll
-              for (int sl = 0; sl < 6; ++sl) {
-                __nv_bfloat16 *dst =
-                    g.x_data + (g.x_kblk ? (((long long)sl * g.x_nkb + kb) * g.x_rows_pad + z) * OZ_KB
-                                         : ((long long)sl * g.x_rows_pad + z) * g.x_kpitch + kb * OZ_KB) +
-                    lane * 32 + j0;
-                __align__(16) __nv_bfloat16 v[8];
-#pragma unroll
-                for (int t = 0; t < 8; ++t) v[t] = __float2bfloat16_rn((float)dg[sl][t]);
-                *reinterpret_cast<uint4 *>(dst) = *reinterpret_cast<const uint4 *>(v);
-              }
-            }
-            double r = 0.0;
-            const double *cz = g.x_C + (long long)z * g.N;
-#pragma unroll
-            for (int j = 0; j < NH; ++j)
-              if (nh + j < g.N) r = fma(__ldg(cz + nh + j), acc[j], r);
-            g.x_rho[((long long)z * g.x_ig + ig) * (g.x_pg * 32) + m] = r;
-          }
-        }
       } else if (m < g.M) {
         const bool full = nh + NH <= g.N;
         if (g.mode == 0) {
@@ -1161,14 +1107,6 @@ static int num_sms() {
   return n;
 }
 
-static int oz_drain_warps() {
-  static const int n = [] {
-    const char *e = std::getenv("DFJK_OZ_DRAIN_WARPS");
-    return (e && std::atoi(e) == 16) ? 16 : 8;
-  }();
-  return n;
-}
-
 // Persistent warp-specialised launch (the default).
 template <int S, int NEPI>
 static void launch_oz_ws_n(const SlicedOp &A, const SlicedOp &B, const OzGemmArgs &g, cudaStream_t st) {
@@ -1203,8 +1141,7 @@ static void launch_oz_ws_n(const SlicedOp &A, const SlicedOp &B, const OzGemmArg
 
 template <int S>
 static void launch_oz_ws(const SlicedOp &A, const SlicedOp &B, const OzGemmArgs &g, cudaStream_t st) {
-  if (oz_drain_warps() == 16) launch_oz_ws_n<S, 16>(A, B, g, st);
-  else launch_oz_ws_n<S, 8>(A, B, g, st);
+  launch_oz_ws_n<S, OZ_NEPI>(A, B, g, st);
 }
 
 template <int S>
@@ -1231,10 +1168,8 @@ bool oz_simple_mode() {
   return simple;
 }
 
-bool oz_fused_x_available() { return !oz_simple_mode() && oz_drain_warps() == 8; }
-
 size_t oz_tile_seq_count(int M, int N) {
-  return (size_t)((M + OZ_BM - 1) / OZ_BM) * ((N + OZ_BN - 1) / OZ_BN) * OZ_MAX_DRAIN;
+  return (size_t)((M + OZ_BM - 1) / OZ_BM) * ((N + OZ_BN - 1) / OZ_BN) * OZ_NEPI;
 }
 
 void oz_gemm(const SlicedOp &A, const SlicedOp &B, const OzGemmArgs &g, cudaStream_t st) {
@@ -1248,12 +1183,6 @@ void oz_gemm(const SlicedOp &A, const SlicedOp &B, const OzGemmArgs &g, cudaStre
   if (g.a_batched && g.nz > A.batch) throw Error{DFJK_ERR_ARG, "oz_gemm: A batch"};
   if (g.b_batched && g.nz > B.batch) throw Error{DFJK_ERR_ARG, "oz_gemm: B batch"};
   if (g.mode == 1 && (!g.colmu || !g.colnu)) throw Error{DFJK_ERR_ARG, "oz_gemm: scatter map"};
-  if (g.mode == 3) {
-    const int mtp = (g.M + OZ_BM - 1) / OZ_BM * OZ_BM;
-    if (!oz_fused_x_available() || !g.x_data || !g.x_expo || !g.x_C || !g.x_rho || g.x_pg * 32 != mtp ||
-        g.x_ig != (g.N + 31) / 32 || g.x_nkb != g.x_ig * g.x_pg || !g.a_batched || g.nz > g.x_rows_pad)
-      throw Error{DFJK_ERR_ARG, "oz_gemm: fused X arguments"};
-  }
   if (g.nz > 65535 || (g.M + OZ_BM - 1) / OZ_BM > 2147483647) throw Error{DFJK_ERR_ARG, "oz_gemm: grid"};
   const bool simple = oz_simple_mode();
   if (simple && g.mode == 2) throw Error{DFJK_ERR_UNSUPPORTED, "oz_gemm: mode 2 needs the persistent kernel"};

@@ -63,18 +63,6 @@ struct OzGemmArgs {
   int mode = 0;          // 0: out[z out_bs + m ldo + n] = C; 1: whitening scatter;
                          // 2: split-K in order, out[m ldo + n] (+)= C of split z
                          //    after splits 0..z-1 (persistent kernel only)
-  // mode 3 (X = B C of the mixed build, batch z = mu, rows m = P of the chunk,
-  // columns n = i): instead of X in FP64, the epilogue writes the K GEMM's
-  // operand -- the 6 slices of X[mu][(P, i)] in K blocks of 32 P x 32 i, one
-  // block per drain warp (block kb = (i / 32) x_pg + P / 32, offset
-  // (P % 32) 32 + i % 32, exponent from the block's maximum) -- and rho
-  // partials sum_{i of the block} C[mu][i] X[mu][P][i]
-  __nv_bfloat16 *x_data = nullptr;  // slice planes [6][x_nkb][x_rows_pad][1024]
-  int *x_expo = nullptr;            // [x_rows_pad][x_nkb]
-  int x_rows_pad = 0, x_nkb = 0, x_pg = 0, x_ig = 0;  // x_pg = P groups of 32, x_ig = i groups of 32
-  int x_kblk = 1, x_kpitch = 0;     // layout of the slice planes (SlicedOp kblk, kpitch)
-  const double *x_C = nullptr;      // C [mu][i], nocc columns (= N)
-  double *x_rho = nullptr;          // rho partials [mu][x_ig][x_pg 32]
   int *tile_seq = nullptr;  // mode 2: per (tile, drain warp) split counters
   int accumulate = 0;    // mode 2: split 0 also adds onto out (a later chunk of
                          // the reduction range, in chunk order)
@@ -114,8 +102,6 @@ void oz_slice_f64_packed_pre(const double *B, long long ldb, const int *pre, int
 
 // True when DFJK_OZ_SIMPLE=1 selects the one-tile-per-CTA kernel (no mode 2).
 bool oz_simple_mode();
-// True when the persistent kernel runs mode 3 (its default 8 drain warps).
-bool oz_fused_x_available();
 // Counters mode 2 needs for a launch of M x N (ints).
 size_t oz_tile_seq_count(int M, int N);
 
