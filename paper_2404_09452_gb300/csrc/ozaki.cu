@@ -7,10 +7,11 @@
 // int64 + FP64 in registers.
 //
 // Kernel layout (one CTA per SM: 512 TMEM columns, ~200 KB shared memory):
-//   tile 128 (M, one TMEM lane per row) x 64 (N) ; K stages of 32 (64-byte
-//   swizzled rows) ; 2-3 stage TMA ring ; thread 0 issues TMA and MMA ; after
-//   each K-block of 1024 every thread drains its TMEM row: S level
-//   accumulators -> two int64 groups -> FP64 register accumulators.
+//   tile 128 (M, one TMEM lane per row) x 64 (N) ; K stages of 16 (32-byte
+//   swizzled rows) ; 4-5 stage TMA ring ; one thread issues TMA, one MMA ;
+//   S level accumulators of 64 TMEM columns, filled two levels per MMA
+//   (oz_mma_step) ; after each K-block of 1024 the epilogue drains every TMEM
+//   row: level sums -> int64 -> FP64 register accumulators.
 #include <cuda.h>
 
 #include <algorithm>
@@ -483,15 +484,65 @@ void oz_slice_f64(const double *src, long long sz, long long sr, long long sk, S
 // independent of the caller's timeout, which may be tiny in tests.
 constexpr long long OZ_CLEANUP_POLLS = 1LL << 24;
 
+// K per pipeline stage (one MMA deep; rows of 32 bytes).
+constexpr int OZ_KS = 16;
+
+// A stage: the S slices of the A tile, then a zero tile and the S slices of
+// the B tile, so that B_{q}, B_{q+1} (q >= -1, B_{-1} the zero tile) form one
+// 128-row K-major operand (oz_mma_step).
 template <int S>
 struct OzCfg {
-  static constexpr int NST = (S <= 6) ? 3 : 2;
-  static constexpr int A_TILE = OZ_BM * OZ_BK * 2;
-  static constexpr int B_TILE = OZ_BN * OZ_BK * 2;
-  static constexpr int STAGE = S * (A_TILE + B_TILE);
+  static constexpr int NST = (S <= 6) ? 5 : 4;
+  static constexpr int A_TILE = OZ_BM * OZ_KS * 2;
+  static constexpr int B_TILE = OZ_BN * OZ_KS * 2;
+  static constexpr int ZERO = S * A_TILE;          // offset of the zero tile
+  static constexpr int STAGE = S * A_TILE + (S + 1) * B_TILE;
+  static constexpr int LOAD = S * (A_TILE + B_TILE);  // bytes TMA writes per stage
   static constexpr int SMEM = NST * STAGE + 1024 + 256;
-  static_assert(S * OZ_BN <= 512, "TMEM holds S level accumulators of 64 columns");
+  static_assert(S % 2 == 0 && S * OZ_BN <= 512, "TMEM holds S level accumulators of 64 columns");
+  static_assert(SMEM <= 232448, "shared memory per CTA");
 };
+
+// The MMAs of one K step of 16.  Level l (TMEM columns 64 l .. 64 l + 63)
+// accumulates the slice products A_s B_t with s + t = l.  For each A slice s
+// and each even level pair (r, r + 1) with r >= s - 1, one 128 x 128 MMA
+// multiplies A_s by the stacked slices [B_{r-s}, B_{r-s+1}] (B_{-1} is the
+// zero tile) into columns 64 r .. 64 r + 127: both levels at once, so A_s is
+// read from shared memory once per pair of levels instead of once per level
+// (12 MMAs for S = 6 and 20 for S = 8 where one per product would be 21 and
+// 36 of half the width; the zero products cost 14% and 11% more tensor
+// work).  Every MMA has the same shape and writes one of S / 2 disjoint
+// column ranges, so the MMAs into one range are ordered by the tensor pipe.
+// The first K step of a K-block starts each range (s = 0 comes first and
+// covers every range).
+template <int S>
+__device__ __forceinline__ void oz_mma_step(uint32_t tbase, uint32_t sa, uint32_t &reg_init) {
+  using Cfg = OzCfg<S>;
+  constexpr uint32_t IDESC = tc::idesc_bf16(OZ_BM, 2 * OZ_BN);
+  const uint32_t sz = sa + Cfg::ZERO;
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    const uint64_t ad = tc::sdesc_k_sw32(sa + s * Cfg::A_TILE);
+#pragma unroll
+    for (int r = s & ~1; r < S; r += 2) {
+      const uint64_t bd = tc::sdesc_k_sw32(sz + (r - s + 1) * Cfg::B_TILE);
+      tc::mma_bf16(tbase + r * OZ_BN, ad, bd, IDESC, (reg_init >> r) & 1u);
+      reg_init |= 1u << r;
+    }
+  }
+}
+
+// Zeroes the zero tile of every stage (all threads of the CTA; a barrier
+// follows before the first MMA).
+template <int S>
+__device__ __forceinline__ void oz_zero_tiles(uint8_t *smem) {
+  using Cfg = OzCfg<S>;
+  for (int i = threadIdx.x; i < Cfg::NST * (Cfg::B_TILE / 16); i += blockDim.x) {
+    const int st = i / (Cfg::B_TILE / 16), o = i % (Cfg::B_TILE / 16);
+    *reinterpret_cast<uint4 *>(smem + st * Cfg::STAGE + Cfg::ZERO + o * 16) = make_uint4(0, 0, 0, 0);
+  }
+  tc::fence_proxy_async_smem();
+}
 
 struct OzKernelArgs {
   OzGemmArgs g;
@@ -564,6 +615,7 @@ __global__ void __launch_bounds__(128, 1)
   const int zA = g.a_batched ? z : 0, zB = g.b_batched ? z : 0;
 
   if (warp == 0) tc::tmem_alloc(tmem_holder, 512);
+  oz_zero_tiles<S>(smem);
   if (tid == 0) {
     for (int i = 0; i < Cfg::NST; ++i) {
       tc::mbar_init(&full[i], 1);
@@ -582,14 +634,13 @@ __global__ void __launch_bounds__(128, 1)
 #pragma unroll
   for (int j = 0; j < OZ_BN; ++j) acc[j] = 0.0;
   const int m = m0 + tid;
-  constexpr uint32_t IDESC = tc::idesc_bf16(OZ_BM, OZ_BN);
   uint32_t gstage = 0;  // stages consumed so far (thread 0)
   bool ok = true;
   int kbi = 0;
   for (int kb = kb0; kb < kb1; ++kb, ++kbi) {
     const int kstart = kb * OZ_KB;
     const int kstop = min(kend, kstart + OZ_KB);
-    const int nst = (kstop - kstart + OZ_BK - 1) / OZ_BK;
+    const int nst = (kstop - kstart + OZ_KS - 1) / OZ_KS;
     if (tid == 0) {
       uint32_t lev_init = 0;
       constexpr int dist = Cfg::NST - 1;
@@ -603,14 +654,14 @@ __global__ void __launch_bounds__(128, 1)
             break;
           }
           uint8_t *stp = smem + slot * Cfg::STAGE;
-          tc::mbar_expect_tx(&full[slot], Cfg::STAGE);
-          const int kc = kstart + j * OZ_BK;
+          tc::mbar_expect_tx(&full[slot], Cfg::LOAD);
+          const int kc = kstart + j * OZ_KS;
 #pragma unroll
           for (int s = 0; s < S; ++s)
             oz_tma(stp + s * Cfg::A_TILE, &tmA, &full[slot], kc, m0, zA * S + s, ka.kblkA);
 #pragma unroll
           for (int t = 0; t < S; ++t)
-            oz_tma(stp + S * Cfg::A_TILE + t * Cfg::B_TILE, &tmB, &full[slot], kc, n0, zB * S + t, ka.kblkB);
+            oz_tma(stp + Cfg::ZERO + (t + 1) * Cfg::B_TILE, &tmB, &full[slot], kc, n0, zB * S + t, ka.kblkB);
           ++issued;
         }
         if (j >= dist) {
@@ -621,20 +672,7 @@ __global__ void __launch_bounds__(128, 1)
           }
           ++consumed;
           tc::tc_fence_after();
-          const uint32_t sa = tc::smem_u32(smem + slot * Cfg::STAGE);
-          const uint32_t sb = sa + S * Cfg::A_TILE;
-#pragma unroll
-          for (int kk = 0; kk < OZ_BK / 16; ++kk)
-#pragma unroll
-            for (int s = 0; s < S; ++s)
-#pragma unroll
-              for (int t = 0; t < S - s; ++t) {
-                const int lev = s + t;
-                const uint64_t ad = tc::sdesc_k_sw64(sa + s * Cfg::A_TILE + kk * 32);
-                const uint64_t bd = tc::sdesc_k_sw64(sb + t * Cfg::B_TILE + kk * 32);
-                tc::mma_bf16(tbase + lev * OZ_BN, ad, bd, IDESC, (lev_init >> lev) & 1u);
-                lev_init |= 1u << lev;
-              }
+          oz_mma_step<S>(tbase, tc::smem_u32(smem + slot * Cfg::STAGE), lev_init);
           tc::mma_commit(&empty[slot]);
         }
       }
@@ -782,6 +820,7 @@ __global__ void __launch_bounds__(oz_ws_threads(NEPI), 1)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   constexpr int OZ_WS_THREADS = oz_ws_threads(NEPI);
   if (warp == 1) tc::tmem_alloc(tmem_holder, 512);
+  oz_zero_tiles<S>(smem);
   if (tid == 0) {
     for (int i = 0; i < Cfg::NST; ++i) {
       tc::mbar_init(&full[i], 1);
@@ -825,7 +864,7 @@ __global__ void __launch_bounds__(oz_ws_threads(NEPI), 1)
         const int zA = g.a_batched ? z : 0, zB = g.b_batched ? z : 0;
         for (int kb = kb0; kb < kb1 && ok; ++kb) {
           const int kstart = kb * OZ_KB, kstop = min(kend, kstart + OZ_KB);
-          for (int kc = kstart; kc < kstop; kc += OZ_BK, ++gs) {
+          for (int kc = kstart; kc < kstop; kc += OZ_KS, ++gs) {
             const uint32_t slot = gs % Cfg::NST;
             if (gs >= (uint32_t)Cfg::NST && !tc::mbar_wait(&empty[slot], ((gs / Cfg::NST) - 1) & 1, lim)) {
               ok = false;
@@ -836,13 +875,13 @@ __global__ void __launch_bounds__(oz_ws_threads(NEPI), 1)
               break;
             }
             uint8_t *stp = smem + slot * Cfg::STAGE;
-            tc::mbar_expect_tx(&full[slot], Cfg::STAGE);
+            tc::mbar_expect_tx(&full[slot], Cfg::LOAD);
 #pragma unroll
             for (int s = 0; s < S; ++s)
               oz_tma(stp + s * Cfg::A_TILE, &tmA, &full[slot], kc, m0, zA * S + s, ka.kblkA);
 #pragma unroll
             for (int q = 0; q < S; ++q)
-              oz_tma(stp + S * Cfg::A_TILE + q * Cfg::B_TILE, &tmB, &full[slot], kc, n0, zB * S + q, ka.kblkB);
+              oz_tma(stp + Cfg::ZERO + (q + 1) * Cfg::B_TILE, &tmB, &full[slot], kc, n0, zB * S + q, ka.kblkB);
           }
         }
       }
@@ -856,7 +895,6 @@ __global__ void __launch_bounds__(oz_ws_threads(NEPI), 1)
     }
   } else if (warp == 1) {
     if (lane == 0) {  // ---- MMA issuer
-      constexpr uint32_t IDESC = tc::idesc_bf16(OZ_BM, OZ_BN);
       uint32_t gs = 0, kbi = 0, qi = 0;
       bool ok = true;
       while (ok) {
@@ -879,27 +917,14 @@ __global__ void __launch_bounds__(oz_ws_threads(NEPI), 1)
           tc::tc_fence_after();
           const int kstart = kb * OZ_KB, kstop = min(kend, kstart + OZ_KB);
           uint32_t lev_init = 0;
-          for (int kc = kstart; kc < kstop; kc += OZ_BK, ++gs) {
+          for (int kc = kstart; kc < kstop; kc += OZ_KS, ++gs) {
             const uint32_t slot = gs % Cfg::NST;
             if (!tc::mbar_wait(&full[slot], (gs / Cfg::NST) & 1, lim) || *abort_flag) {
               ok = false;
               break;
             }
             tc::tc_fence_after();
-            const uint32_t sa = tc::smem_u32(smem + slot * Cfg::STAGE);
-            const uint32_t sb = sa + S * Cfg::A_TILE;
-#pragma unroll
-            for (int kk = 0; kk < OZ_BK / 16; ++kk)
-#pragma unroll
-              for (int s = 0; s < S; ++s)
-#pragma unroll
-                for (int q = 0; q < S - s; ++q) {
-                  const int lev = s + q;
-                  const uint64_t ad = tc::sdesc_k_sw64(sa + s * Cfg::A_TILE + kk * 32);
-                  const uint64_t bd = tc::sdesc_k_sw64(sb + q * Cfg::B_TILE + kk * 32);
-                  tc::mma_bf16(tbase + lev * OZ_BN, ad, bd, IDESC, (lev_init >> lev) & 1u);
-                  lev_init |= 1u << lev;
-                }
+            oz_mma_step<S>(tbase, tc::smem_u32(smem + slot * Cfg::STAGE), lev_init);
             tc::mma_commit(&empty[slot]);
           }
           if (ok) tc::mma_commit(accf);
@@ -1077,20 +1102,20 @@ static CUtensorMap make_map(const SlicedOp &op, int box_rows) {
   if (!op.kblk) {  // (k, row, batch x slice)
     cuuint64_t dims[3] = {(cuuint64_t)op.K, (cuuint64_t)op.rows_pad, (cuuint64_t)op.batch * op.S};
     cuuint64_t strides[2] = {(cuuint64_t)op.kpitch * 2, (cuuint64_t)op.rows_pad * op.kpitch * 2};
-    cuuint32_t box[3] = {OZ_BK, (cuuint32_t)box_rows, 1};
+    cuuint32_t box[3] = {OZ_KS, (cuuint32_t)box_rows, 1};
     cuuint32_t estr[3] = {1, 1, 1};
     r = encode_fn()(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, op.data, dims, strides, box, estr,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   } else {  // (k within block, row, K block, batch x slice); padding of the last block is zero
     cuuint64_t dims[4] = {(cuuint64_t)OZ_KB, (cuuint64_t)op.rows_pad, (cuuint64_t)op.nkb,
                           (cuuint64_t)op.batch * op.S};
     cuuint64_t strides[3] = {(cuuint64_t)OZ_KB * 2, (cuuint64_t)op.rows_pad * OZ_KB * 2,
                              (cuuint64_t)op.nkb * op.rows_pad * OZ_KB * 2};
-    cuuint32_t box[4] = {OZ_BK, (cuuint32_t)box_rows, 1, 1};
+    cuuint32_t box[4] = {OZ_KS, (cuuint32_t)box_rows, 1, 1};
     cuuint32_t estr[4] = {1, 1, 1, 1};
     r = encode_fn()(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, op.data, dims, strides, box, estr,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   }
   if (r != CUDA_SUCCESS) throw Error{DFJK_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")"};

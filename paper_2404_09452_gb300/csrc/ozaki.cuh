@@ -19,7 +19,8 @@ namespace dfjk {
 
 constexpr int OZ_W = 6;      // bits per slice
 constexpr int OZ_KB = 1024;  // K elements per exponent block
-constexpr int OZ_BM = 128, OZ_BN = 64, OZ_BK = 32;
+constexpr int OZ_BM = 128, OZ_BN = 64;
+constexpr int OZ_BK = 32;   // K pitch granularity of the slice planes
 
 // Slices of an operand: planes [batch][S][rows_pad][kpitch] (BF16, K
 // contiguous) and exponents [batch][rows_pad][nkb] (int32).

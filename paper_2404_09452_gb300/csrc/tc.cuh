@@ -133,6 +133,24 @@ __device__ __forceinline__ uint64_t sdesc_k_sw64(uint32_t saddr) {
   return d;
 }
 
+// Shared-memory matrix descriptor for a K-major operand whose rows are 32
+// bytes (16 BF16) with the 32-byte swizzle TMA writes (CU_TENSOR_MAP_SWIZZLE_32B):
+// core matrices of 8 rows x 32 bytes, 256 bytes apart along M/N.
+__device__ __forceinline__ uint64_t sdesc_k_sw32(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFF) >> 4);   // start address
+  d |= (uint64_t)1 << 16;                     // leading byte offset (unused here)
+  d |= (uint64_t)(256 >> 4) << 32;            // stride byte offset
+  d |= (uint64_t)1 << 46;                     // descriptor version
+  d |= (uint64_t)6 << 61;                     // SWIZZLE_32B
+  return d;
+}
+// Proxy fence: shared-memory writes of this thread become visible to the
+// async proxy (TMA, tensor core) after a following barrier.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
 // Instruction descriptor for kind::f16: D F32, A/B BF16, both K-major, M x N.
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
