@@ -49,6 +49,31 @@ __device__ __forceinline__ long long oz_fixed(double x, int e) {
   return u < 0 ? -n : n;
 }
 
+// The S balanced base-64 digits of n (|n| <= 2^(6S)), n = sum_s d_s
+// 64^(S-1-s) with d_s in [-32, 31] for s >= 1, as FP32 bit patterns whose
+// high halves are the digits' BF16 patterns.  Adding 32 (1 + 64 + ... +
+// 64^(S-2)) turns the low S - 1 digits into plain 6-bit fields u_s = d_s + 32
+// and leaves d_0 in the top bits; a digit becomes an exact float through the
+// 1.5 2^23 bias (an integer add into the mantissa and one FP32 subtract), so
+// no conversion instructions are needed.
+template <int S>
+__device__ __forceinline__ void oz_digits(long long n, uint32_t (&f)[S]) {
+  constexpr long long C = 32 * (((1LL << (6 * (S - 1))) - 1) / 63);
+  const long long m = n + C;
+  const unsigned long long um = (unsigned long long)m;
+  f[0] = __float_as_uint(__int_as_float(0x4B400000 + (int)(m >> (6 * (S - 1)))) - 12582912.0f);
+#pragma unroll
+  for (int s = 1; s < S; ++s) {
+    const uint32_t u = (uint32_t)(um >> (6 * (S - 1 - s))) & 63u;
+    f[s] = __float_as_uint(__uint_as_float(0x4B400000u + u) - 12582944.0f);
+  }
+}
+__device__ __forceinline__ __nv_bfloat16 oz_bf16_of(uint32_t fbits) {
+  return __ushort_as_bfloat16((unsigned short)(fbits >> 16));
+}
+// Two digits' FP32 patterns -> one word of two BF16 (a at the lower address).
+__device__ __forceinline__ uint32_t oz_pack2(uint32_t a, uint32_t b) { return __byte_perm(a, b, 0x7632); }
+
 // Element offset of slice s of (z, r, k) in a SlicedOp's data (k % 8 == 0 for
 // the 16-byte stores below, which then stay inside one 1024-wide K block).
 __device__ __forceinline__ long long oz_off(int z, int s, int r, int k, int S, int rows_pad, int kpitch,
@@ -119,28 +144,20 @@ __global__ void oz_slice_kernel(const double *__restrict__ src, long long sz, lo
   }
   const int k0 = kc * 8;
   const int e = expo[((long long)z * rows_pad + r) * nkb + k0 / OZ_KB];
-  int dig[8][S];
+  uint32_t w[S][4];
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
     const int k = k0 + j;
     const double x = (r < rows && k < K) ? src[z * sz + r * sr + (long long)k * sk] : 0.0;
-    long long n = oz_fixed<S>(x, e);
+    uint32_t f[S];
+    oz_digits<S>(oz_fixed<S>(x, e), f);
 #pragma unroll
-    for (int s = S - 1; s >= 1; --s) {
-      const int d = (int)(((n + 32) & 63) - 32);
-      dig[j][s] = d;
-      n = (n - d) >> 6;
-    }
-    dig[j][0] = (int)n;
+    for (int s = 0; s < S; ++s) w[s][j / 2] = (j & 1) ? oz_pack2(w[s][j / 2], f[s]) : f[s];
   }
 #pragma unroll
-  for (int s = 0; s < S; ++s) {
-    __align__(16) __nv_bfloat16 v[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) v[j] = __float2bfloat16_rn((float)dig[j][s]);
+  for (int s = 0; s < S; ++s)
     *reinterpret_cast<uint4 *>(out + oz_off(z, s, r, k0, S, rows_pad, kpitch, nkb, kblk)) =
-        *reinterpret_cast<const uint4 *>(v);
-  }
+        make_uint4(w[s][0], w[s][1], w[s][2], w[s][3]);
 }
 
 // Slices of a 64 (rows) x 64 (K) tile per block for row-contiguous sources:
@@ -160,14 +177,10 @@ __global__ void __launch_bounds__(256) oz_slice_tr_kernel(const double *__restri
   for (int kk = kq; kk < 64; kk += 4) {
     const int k = k0 + kk;
     const double x = (r < rows && k < K) ? src[z * sz + r + (long long)k * sk] : 0.0;
-    long long n = oz_fixed<S>(x, e);
+    uint32_t f[S];
+    oz_digits<S>(oz_fixed<S>(x, e), f);
 #pragma unroll
-    for (int s = S - 1; s >= 1; --s) {
-      const int d = (int)(((n + 32) & 63) - 32);
-      tile[(s * 64 + rr) * LD + kk] = __float2bfloat16_rn((float)d);
-      n = (n - d) >> 6;
-    }
-    tile[rr * LD + kk] = __float2bfloat16_rn((float)n);
+    for (int s = 0; s < S; ++s) tile[(s * 64 + rr) * LD + kk] = oz_bf16_of(f[s]);
   }
   __syncthreads();
   const int c8 = threadIdx.x & 7, rw = threadIdx.x >> 3;  // 8 x 16-byte chunks per row
@@ -259,14 +272,10 @@ __global__ void __launch_bounds__(256) oz_slice_tr_fused_kernel(const double *__
     for (int kk = kq; kk < 64; kk += KG) {
       const int k = k0 + kk;
       const double x = (live && k < K) ? at(k) : 0.0;
-      long long n = oz_fixed<S>(x, e);
+      uint32_t f[S];
+      oz_digits<S>(oz_fixed<S>(x, e), f);
 #pragma unroll
-      for (int s = S - 1; s >= 1; --s) {
-        const int d = (int)(((n + 32) & 63) - 32);
-        tile[(s * 64 + kk) * LDK + rr] = __float2bfloat16_rn((float)d);
-        n = (n - d) >> 6;
-      }
-      tile[kk * LDK + rr] = __float2bfloat16_rn((float)n);
+      for (int s = 0; s < S; ++s) tile[(s * 64 + kk) * LDK + rr] = oz_bf16_of(f[s]);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < S * R * 8; i += 256) {  // (slice, row, chunk of 8 K)
@@ -282,6 +291,140 @@ __global__ void __launch_bounds__(256) oz_slice_tr_fused_kernel(const double *__
     }
     __syncthreads();
   }
+}
+
+// Slicing of the packed mu >= nu triangle reading each stored element once.
+// A block owns a 32 x 32 tile of the pair triangle (mu block >= nu block) and
+// R rows P, and stages the tile's FP64 values in shared memory (pairs with
+// mu < nu on the diagonal tiles are read from (nu, mu)); consecutive pairs of
+// one mu are rows of B ldb doubles apart, R contiguous doubles each.
+// MODE 2: writes the slices of batch mu at K index nu and, off the diagonal,
+// of batch nu at K index mu, with exponents from `pre`; tiles beyond nao (up
+// to the K pitch) write the zero padding.  MODE 1: per (mu, P, 1024-block of
+// nu) maxima of |x|, folded across tiles with atomicMax on the encoded
+// exponent (0 for an all-zero block, else exponent + OZ_EXPO_BIAS; larger
+// |x| never has a smaller exponent).
+constexpr int OZ_EXPO_BIAS = 4096;
+constexpr int OZ_TT = 32;  // tile edge in AO indices
+
+__host__ __device__ constexpr int oz_sym_smem(int R) { return OZ_TT * OZ_TT * (R + 1) * 8 + 2 * OZ_TT * R * 4; }
+
+template <int R, int MODE>
+__global__ void __launch_bounds__(256) oz_slice_sym_kernel(const double *__restrict__ B, long long ldb, int nao,
+                                                           int rows, int p0, int rows_pad, int kpitch, int nkb,
+                                                           int kblk, const int *__restrict__ pre, int pre_rows,
+                                                           int *__restrict__ expo_out, __nv_bfloat16 *__restrict__ out) {
+  constexpr int RP = R + 1;
+  extern __shared__ __align__(16) uint8_t sym_smem[];
+  double *tile = reinterpret_cast<double *>(sym_smem);  // [mu_l][nu_l][P], P stride 1, nu stride RP
+  int *eD = reinterpret_cast<int *>(tile + OZ_TT * OZ_TT * RP);  // [mu_l][P]: batch mu, K block of nu0
+  int *eT = eD + OZ_TT * R;                                    // [nu_l][P]: batch nu, K block of mu0
+  // grid x: row groups (fastest, so that the blocks reading the neighbouring
+  // rows of one pair run together and share its cache lines); grid y: tile
+  // t of the lower triangle -> (ti >= tj)
+  const long long t = blockIdx.y;
+  int ti = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+  while ((long long)(ti + 1) * (ti + 2) / 2 <= t) ++ti;
+  while ((long long)ti * (ti + 1) / 2 > t) --ti;
+  const int tj = (int)(t - (long long)ti * (ti + 1) / 2);
+  const int mu0 = ti * OZ_TT, nu0 = tj * OZ_TT, r0 = blockIdx.x * R;
+  const bool diag = ti == tj;
+  // stage the tile: R lanes per pair, 256 / R pairs per pass, 16 loads in
+  // flight per thread
+  constexpr int PER = OZ_TT * OZ_TT * R / 256, UN = PER < 16 ? PER : 16;
+  static_assert(PER % UN == 0, "tile loads");
+#pragma unroll 1
+  for (int u0 = 0; u0 < PER; u0 += UN) {
+    double v[UN];
+#pragma unroll
+    for (int u = 0; u < UN; ++u) {
+      const int i = threadIdx.x + (u0 + u) * 256;
+      const int P = i % R, q = i / R, ml = q / OZ_TT, nl = q % OZ_TT;
+      const int mu = mu0 + ml, nu = nu0 + nl, r = r0 + P;
+      v[u] = 0.0;
+      if (mu < nao && nu < nao && r < rows) {
+        const long long hi = mu > nu ? mu : nu, lo = mu > nu ? nu : mu;
+        v[u] = B[(hi * (hi + 1) / 2 + lo) * ldb + p0 + r];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < UN; ++u) {
+      const int i = threadIdx.x + (u0 + u) * 256;
+      tile[((i / R) / OZ_TT * OZ_TT + (i / R) % OZ_TT) * RP + i % R] = v[u];
+    }
+  }
+  if (MODE == 2) {
+    for (int i = threadIdx.x; i < 2 * OZ_TT * R; i += 256) {
+      const int P = i % R, l = (i / R) % OZ_TT, tr = i / (OZ_TT * R);
+      const int z = (tr ? nu0 : mu0) + l, kb = (tr ? mu0 : nu0) >> 10;
+      (tr ? eT : eD)[l * R + P] = z < nao ? pre[((long long)z * pre_rows + p0 + r0 + P) * nkb + kb] : 0;
+    }
+  }
+  __syncthreads();
+  if (MODE == 1) {
+    // thread (l, P): direct maximum over nu of row mu0 + l; transposed over mu of column nu0 + l
+    for (int i = threadIdx.x; i < 2 * OZ_TT * R; i += 256) {
+      const int P = i % R, l = (i / R) % OZ_TT, tr = i / (OZ_TT * R);
+      if (tr && diag) continue;
+      const int z = (tr ? nu0 : mu0) + l, kb = (tr ? mu0 : nu0) >> 10;
+      if (z >= nao) continue;
+      // |x| maxima on the bit patterns (non-negative doubles order like
+      // their bits), on the integer pipes
+      unsigned long long mx = 0;
+#pragma unroll 8
+      for (int o = 0; o < OZ_TT; ++o) {
+        const double x = tr ? tile[(o * OZ_TT + l) * RP + P] : tile[(l * OZ_TT + o) * RP + P];
+        mx = max(mx, (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull);
+      }
+      if (mx) atomicMax(expo_out + ((long long)z * pre_rows + r0 + P) * nkb + kb,
+                        oz_expo_of(__longlong_as_double((long long)mx)) + OZ_EXPO_BIAS);
+    }
+    return;
+  }
+  // slices: item (l, P, g) = 8 consecutive K of batch mu0 + l (direct) or nu0 + l
+  // (transposed), one 16-byte store per slice; 4 lanes cover 32 K (64 bytes)
+  for (int i = threadIdx.x; i < 2 * OZ_TT * R * 4; i += 256) {
+    const int g = i % 4, P = (i / 4) % R, l = (i / (4 * R)) % OZ_TT, tr = i / (4 * R * OZ_TT);
+    if (tr && diag) break;  // the transposed half comes last
+    const int z = (tr ? nu0 : mu0) + l;
+    if (z >= nao) continue;
+    const int e = (tr ? eT : eD)[l * R + P];
+    const int k = (tr ? mu0 : nu0) + g * 8;
+    uint32_t w[6][4];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int o = g * 8 + u;
+      uint32_t f[6];
+      oz_digits<6>(oz_fixed<6>(tr ? tile[(o * OZ_TT + l) * RP + P] : tile[(l * OZ_TT + o) * RP + P], e), f);
+#pragma unroll
+      for (int sl = 0; sl < 6; ++sl) w[sl][u / 2] = (u & 1) ? oz_pack2(w[sl][u / 2], f[sl]) : f[sl];
+    }
+#pragma unroll
+    for (int sl = 0; sl < 6; ++sl)
+      *reinterpret_cast<uint4 *>(out + oz_off(z, sl, r0 + P, k, 6, rows_pad, kpitch, nkb, kblk)) =
+          make_uint4(w[sl][0], w[sl][1], w[sl][2], w[sl][3]);
+  }
+}
+
+// expo[i] encoded as above -> exponent
+__global__ void oz_expo_decode_kernel(int *expo, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) expo[i] = expo[i] ? expo[i] - OZ_EXPO_BIAS : 0;
+}
+
+template <int R, int MODE>
+static void launch_oz_sym(dim3 grid, const double *B, long long ldb, int nao, int rows, int p0, int rows_pad,
+                          int kpitch, int nkb, int kblk, const int *pre, int pre_rows, int *expo_out,
+                          __nv_bfloat16 *out, cudaStream_t st) {
+  constexpr int SM = oz_sym_smem(R);
+  static bool attr_set = false;
+  if (!attr_set) {
+    DFJK_CUDA_CHECK(cudaFuncSetAttribute(oz_slice_sym_kernel<R, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, SM));
+    attr_set = true;
+  }
+  oz_slice_sym_kernel<R, MODE><<<grid, 256, SM, st>>>(B, ldb, nao, rows, p0, rows_pad, kpitch, nkb, kblk, pre,
+                                                       pre_rows, expo_out, out);
+  DFJK_LAUNCHED();
 }
 
 static void oz_shape(SlicedOp &op, int batch, int S, int rows, int K, int row_tile) {
@@ -327,67 +470,50 @@ void oz_free(SlicedOp &op) {
   op.expo = nullptr;
 }
 
-void oz_slice_f64_packed(const double *B, long long ldb, int mu0, SlicedOp &op, bool b_on_host, cudaStream_t st,
-                         int rows_per_block) {
-  if (op.S != 6 || op.rows_pad % 32 != 0 || op.nkb > 8)
-    throw Error{DFJK_ERR_UNSUPPORTED, "packed slicing: 6 slices, K <= 8192"};
-  if (b_on_host) {  // 32 rows (256 contiguous bytes) per K index over the host link
-    dim3 grid((unsigned)(op.rows_pad / 32), (unsigned)op.batch);
-    oz_slice_tr_fused_kernel<6, true, 32><<<grid, 256, 0, st>>>(B, 0, ldb, op.rows, op.K, op.rows_pad, op.kpitch,
-                                                                op.nkb, op.expo, op.data, mu0, op.kblk);
-  } else {
-    // rows P per block (8 contiguous doubles = 64 bytes per packed row and K
-    // index); DFJK_PSLICE_ROWS selects 16 or 32 instead
-    static const int R_env = [] {
-      const char *e = std::getenv("DFJK_PSLICE_ROWS");
-      const int v = e ? std::atoi(e) : 8;
-      return (v == 16 || v == 32) ? v : 8;
-    }();
-    const int R = (rows_per_block == 8 || rows_per_block == 16 || rows_per_block == 32) ? rows_per_block : R_env;
-    dim3 grid((unsigned)(op.rows_pad / R), (unsigned)op.batch);
-    if (R == 32)
-      oz_slice_tr_fused_kernel<6, true, 32><<<grid, 256, 0, st>>>(B, 0, ldb, op.rows, op.K, op.rows_pad, op.kpitch,
-                                                                  op.nkb, op.expo, op.data, mu0, op.kblk);
-    else if (R == 16)
-      oz_slice_tr_fused_kernel<6, true, 16><<<grid, 256, 0, st>>>(B, 0, ldb, op.rows, op.K, op.rows_pad, op.kpitch,
-                                                                  op.nkb, op.expo, op.data, mu0, op.kblk);
-    else
-      oz_slice_tr_fused_kernel<6, true, 8><<<grid, 256, 0, st>>>(B, 0, ldb, op.rows, op.K, op.rows_pad, op.kpitch,
-                                                                 op.nkb, op.expo, op.data, mu0, op.kblk);
-  }
-  DFJK_LAUNCHED();
-}
-
 void oz_expo_packed(const double *B, long long ldb, int nao, int np, int pre_rows, int *expo, cudaStream_t st) {
   const int nkb = (nao + OZ_KB - 1) / OZ_KB;
-  if (pre_rows % 32 != 0 || pre_rows < np || nkb > 8) throw Error{DFJK_ERR_UNSUPPORTED, "packed exponents: K <= 8192"};
-  dim3 grid((unsigned)(pre_rows / 32), (unsigned)nao);
-  oz_slice_tr_fused_kernel<6, true, 32, 1><<<grid, 256, 0, st>>>(B, 0, ldb, np, nao, pre_rows, 0, nkb, expo, nullptr,
-                                                                 0, 0);
+  if (pre_rows % 32 != 0 || pre_rows < np || nkb > 8 || np > ldb)
+    throw Error{DFJK_ERR_UNSUPPORTED, "packed exponents: K <= 8192"};
+  const long long n = (long long)nao * pre_rows * nkb;
+  DFJK_CUDA_CHECK(cudaMemsetAsync(expo, 0, n * sizeof(int), st));
+  const long long nb = (nao + OZ_TT - 1) / OZ_TT, tiles = nb * (nb + 1) / 2;
+  if (tiles > 65535) throw Error{DFJK_ERR_ARG, "packed exponents: grid"};
+  launch_oz_sym<8, 1>(dim3((unsigned)(pre_rows / 8), (unsigned)tiles), B, ldb, nao, np, 0, 0, 0, nkb, 0, nullptr,
+                      pre_rows, expo, nullptr, st);
+  oz_expo_decode_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(expo, n);
   DFJK_LAUNCHED();
 }
 
 void oz_slice_f64_packed_pre(const double *B, long long ldb, const int *pre, int pre_rows, int p0, SlicedOp &op,
                              cudaStream_t st, int rows_per_block) {
-  // every row a block touches, padding included, has a precomputed exponent
-  if (op.S != 6 || op.rows_pad % 32 != 0 || op.nkb > 8 || p0 % 32 != 0 || p0 + op.rows_pad > pre_rows)
+  // every row a block touches, padding included, has a precomputed exponent;
+  // batch = nao, K = nao
+  if (op.S != 6 || op.rows_pad % 32 != 0 || op.nkb > 8 || p0 % 32 != 0 || p0 + op.rows_pad > pre_rows ||
+      op.batch != op.K || op.kpitch % OZ_TT != 0 || p0 + op.rows > ldb)
     throw Error{DFJK_ERR_UNSUPPORTED, "packed slicing: 6 slices, K <= 8192, exponent rows"};
+  // rows P per block: 8 (default), 4 or 16 (DFJK_PSLICE_ROWS or the tuning table)
   static const int R_env = [] {
     const char *e = std::getenv("DFJK_PSLICE_ROWS");
-    const int v = e ? std::atoi(e) : 32;
-    return (v == 8 || v == 16) ? v : 32;
+    const int v = e ? std::atoi(e) : 8;
+    return (v == 4 || v == 16) ? v : 8;
   }();
-  const int R = (rows_per_block == 8 || rows_per_block == 16 || rows_per_block == 32) ? rows_per_block : R_env;
-  dim3 grid((unsigned)(op.rows_pad / R), (unsigned)op.batch);
-#define OZ_PRE(RR)                                                                                           \
-  oz_slice_tr_fused_kernel<6, true, RR, 2><<<grid, 256, 0, st>>>(B + p0, 0, ldb, op.rows, op.K, op.rows_pad,   \
-                                                                  op.kpitch, op.nkb, op.expo, op.data, 0,     \
-                                                                  op.kblk, pre, pre_rows, p0)
-  if (R == 32) OZ_PRE(32);
-  else if (R == 16) OZ_PRE(16);
-  else OZ_PRE(8);
-#undef OZ_PRE
-  DFJK_LAUNCHED();
+  const int R = (rows_per_block == 4 || rows_per_block == 8 || rows_per_block == 16) ? rows_per_block : R_env;
+  // exponents of the chunk's rows, copied for the GEMM
+  DFJK_CUDA_CHECK(cudaMemcpy2DAsync(op.expo, (size_t)op.rows_pad * op.nkb * sizeof(int), pre + (size_t)p0 * op.nkb,
+                                    (size_t)pre_rows * op.nkb * sizeof(int), (size_t)op.rows_pad * op.nkb * sizeof(int),
+                                    (size_t)op.batch, cudaMemcpyDeviceToDevice, st));
+  const long long nb = op.kpitch / OZ_TT, tiles = nb * (nb + 1) / 2;
+  if (tiles > 65535) throw Error{DFJK_ERR_ARG, "packed slicing: grid"};
+  const dim3 grid((unsigned)(op.rows_pad / R), (unsigned)tiles);
+  if (R == 4)
+    launch_oz_sym<4, 2>(grid, B, ldb, op.batch, op.rows, p0, op.rows_pad, op.kpitch, op.nkb, op.kblk, pre, pre_rows,
+                        nullptr, op.data, st);
+  else if (R == 16)
+    launch_oz_sym<16, 2>(grid, B, ldb, op.batch, op.rows, p0, op.rows_pad, op.kpitch, op.nkb, op.kblk, pre, pre_rows,
+                         nullptr, op.data, st);
+  else
+    launch_oz_sym<8, 2>(grid, B, ldb, op.batch, op.rows, p0, op.rows_pad, op.kpitch, op.nkb, op.kblk, pre, pre_rows,
+                        nullptr, op.data, st);
 }
 
 void oz_slice_f64(const double *src, long long sz, long long sr, long long sk, SlicedOp &op,

@@ -81,23 +81,21 @@ struct OzGemmArgs {
                                // run concurrently need distinct counters
 };
 
-// Slices of B stored as the packed mu >= nu triangle (row mu (mu + 1) / 2 + nu,
-// ldb doubles per row, P contiguous): batch z is mu = mu0 + z, rows P, K nu.
-// b_on_host: B is in host memory (wider row groups per block for the host link).
-// rows_per_block: rows P per block for device memory (8, 16 or 32; 0 = the
-// default, 8, or DFJK_PSLICE_ROWS).
-void oz_slice_f64_packed(const double *B, long long ldb, int mu0, SlicedOp &op, bool b_on_host, cudaStream_t st,
-                         int rows_per_block = 0);
+// B stored as the packed mu >= nu triangle: row mu (mu + 1) / 2 + nu, ldb
+// doubles per row, P contiguous.  Its slices for the X GEMM are batch mu,
+// rows P, K nu, with one exponent per (mu, P, 1024-block of nu).  Both
+// functions below read each stored element once (32 x 32 tiles of the pair
+// triangle, each written for batch mu and for batch nu).
 
-// Exponents of the slices of a packed B (the same per-(mu, P, 1024-block of
-// nu) exponents oz_slice_f64_packed computes), for every mu and the rows P <
-// pre_rows (rows np..pre_rows-1 get 0): expo[(mu pre_rows + P) nkb + kb].  B
-// does not change between builds, so a handle computes them once.
+// The exponents for every mu and the rows P < pre_rows (rows np..pre_rows-1
+// get 0): expo[(mu pre_rows + P) nkb + kb].  B does not change between
+// builds, so a handle computes them once.
 void oz_expo_packed(const double *B, long long ldb, int nao, int np, int pre_rows, int *expo, cudaStream_t st);
-// oz_slice_f64_packed for the chunk of rows P [p0, p0 + op.rows) of all mu
-// (mu0 = 0, batch = nao), reading B once: the exponents come from `pre`
-// (oz_expo_packed) and are copied into op.expo.  p0 % 32 == 0 and
-// p0 + op.rows_pad <= pre_rows.
+// The slices of the chunk of rows P [p0, p0 + op.rows) for all mu (batch = K
+// = nao), with the exponents from `pre` (oz_expo_packed), which are also
+// copied into op.expo.  p0 % 32 == 0 and p0 + op.rows_pad <= pre_rows.
+// rows_per_block: rows P per block (4, 8 or 16; 0 = the default, 8, or
+// DFJK_PSLICE_ROWS).
 void oz_slice_f64_packed_pre(const double *B, long long ldb, const int *pre, int pre_rows, int p0, SlicedOp &op,
                              cudaStream_t st, int rows_per_block = 0);
 
