@@ -497,6 +497,59 @@ void make_resident(dfjk_ctx *h, cudaStream_t st) {
   // a2: metric
   compute_metric(h, tab, st);
 
+  // a3: Cholesky and inverse of the metric, on a side stream: they depend on
+  // the metric alone, so they run beside the shell-pair kernels, the host's
+  // pair bookkeeping and the 3-centre integrals; the first whitening waits
+  // for them
+  const bool mixed = h->opt.precision == DFJK_MIXED;
+  if (!h->side) {
+    // highest priority: the Cholesky chain is a sequence of small launches on
+    // the critical path, its blocks go first whenever the integrals free an SM
+    int lo = 0, hi = 0;
+    DFJK_CUDA_CHECK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    DFJK_CUDA_CHECK(cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, hi));
+    DFJK_CUDA_CHECK(cudaStreamCreateWithPriority(&h->side2, cudaStreamNonBlocking, hi));
+    DFJK_CUDA_CHECK(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+    DFJK_CUDA_CHECK(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+    DFJK_CUDA_CHECK(cudaEventCreateWithFlags(&h->ev_panel, cudaEventDisableTiming));
+    DFJK_CUDA_CHECK(cudaEventCreateWithFlags(&h->ev_bulk, cudaEventDisableTiming));
+  }
+  const cudaStream_t s2 = h->side;
+  DFJK_CUDA_CHECK(cudaEventRecord(h->ev_fork, st));
+  DFJK_CUDA_CHECK(cudaStreamWaitEvent(s2, h->ev_fork, 0));
+  struct OzLocal {  // slice buffers that live only during setup
+    SlicedOp op;
+    ~OzLocal() { oz_free(op); }
+  } linv8_, t8_;
+  SlicedOp &Linv8 = linv8_.op, &T8 = t8_.op;
+  DBuf<double> inv_work;
+  StreamDrain drain_side{s2};  // destroyed before the buffers above
+  {
+    PhaseScope ph1(1, s2);
+    h->L.alloc((size_t)np * np);
+    DFJK_CUDA_CHECK(cudaMemcpyAsync(h->L.p, h->V.p, h->V.bytes(), cudaMemcpyDeviceToDevice, s2));
+    h->Dinv.alloc((size_t)(np / CHOL_NB) * CHOL_NB * CHOL_NB);
+    // look-ahead on a second stream (DFJK_CHOL_AHEAD=0: one stream)
+    static const bool ahead = [] {
+      const char *e = std::getenv("DFJK_CHOL_AHEAD");
+      return !(e && e[0] == '0');
+    }();
+    if (ahead) cholesky_f64(h->L.p, np, np, h->Dinv.p, h->status.p, nullptr, s2, h->side2, h->ev_panel, h->ev_bulk);
+    else cholesky_f64(h->L.p, np, np, h->Dinv.p, h->status.p, nullptr, s2);
+    zero_upper_kernel<<<(unsigned)(((long long)np * np + 255) / 256), 256, 0, s2>>>(h->L.p, np, np);
+    DFJK_LAUNCHED();
+    h->Linv.alloc((size_t)np * np);
+    inv_work.alloc((size_t)np * np);
+    tri_inverse_f64(h->L.p, np, np, h->Dinv.p, h->Linv.p, inv_work.p, s2);
+  }
+  if (mixed) {  // L^-1 as the B operand of the whitening (rows P, K Q), 8 slices
+    PhaseScope ph3(3, s2);
+    oz_alloc(Linv8, 1, 8, np, np, OZ_BN);
+    oz_slice_f64(h->Linv.p, 0, np, 1, Linv8, s2);
+  }
+  DFJK_CUDA_CHECK(cudaEventRecord(h->ev_join, s2));
+
+
   // a0: shell pairs, primitive-pair records, Schwarz factors
   enumerate_pairs(h);
   const int npair = h->cls_begin[6];
@@ -585,56 +638,6 @@ void make_resident(dfjk_ctx *h, cudaStream_t st) {
   h->colmu.upload(cmu, st);
   h->colnu.upload(cnu, st);
 
-  // a3: Cholesky and inverse of the metric, on a side stream: they do not
-  // depend on the 3-centre integrals, so they run while the first slab's
-  // integrals are computed; the first whitening waits for them
-  const bool mixed = h->opt.precision == DFJK_MIXED;
-  if (!h->side) {
-    // highest priority: the Cholesky chain is a sequence of small launches on
-    // the critical path, its blocks go first whenever the integrals free an SM
-    int lo = 0, hi = 0;
-    DFJK_CUDA_CHECK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
-    DFJK_CUDA_CHECK(cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, hi));
-    DFJK_CUDA_CHECK(cudaStreamCreateWithPriority(&h->side2, cudaStreamNonBlocking, hi));
-    DFJK_CUDA_CHECK(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
-    DFJK_CUDA_CHECK(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
-    DFJK_CUDA_CHECK(cudaEventCreateWithFlags(&h->ev_panel, cudaEventDisableTiming));
-    DFJK_CUDA_CHECK(cudaEventCreateWithFlags(&h->ev_bulk, cudaEventDisableTiming));
-  }
-  const cudaStream_t s2 = h->side;
-  DFJK_CUDA_CHECK(cudaEventRecord(h->ev_fork, st));
-  DFJK_CUDA_CHECK(cudaStreamWaitEvent(s2, h->ev_fork, 0));
-  struct OzLocal {  // slice buffers that live only during setup
-    SlicedOp op;
-    ~OzLocal() { oz_free(op); }
-  } linv8_, t8_;
-  SlicedOp &Linv8 = linv8_.op, &T8 = t8_.op;
-  DBuf<double> inv_work;
-  StreamDrain drain_side{s2};  // destroyed before the buffers above
-  {
-    PhaseScope ph1(1, s2);
-    h->L.alloc((size_t)np * np);
-    DFJK_CUDA_CHECK(cudaMemcpyAsync(h->L.p, h->V.p, h->V.bytes(), cudaMemcpyDeviceToDevice, s2));
-    h->Dinv.alloc((size_t)(np / CHOL_NB) * CHOL_NB * CHOL_NB);
-    // look-ahead on a second stream (DFJK_CHOL_AHEAD=0: one stream)
-    static const bool ahead = [] {
-      const char *e = std::getenv("DFJK_CHOL_AHEAD");
-      return !(e && e[0] == '0');
-    }();
-    if (ahead) cholesky_f64(h->L.p, np, np, h->Dinv.p, h->status.p, nullptr, s2, h->side2, h->ev_panel, h->ev_bulk);
-    else cholesky_f64(h->L.p, np, np, h->Dinv.p, h->status.p, nullptr, s2);
-    zero_upper_kernel<<<(unsigned)(((long long)np * np + 255) / 256), 256, 0, s2>>>(h->L.p, np, np);
-    DFJK_LAUNCHED();
-    h->Linv.alloc((size_t)np * np);
-    inv_work.alloc((size_t)np * np);
-    tri_inverse_f64(h->L.p, np, np, h->Dinv.p, h->Linv.p, inv_work.p, s2);
-  }
-  if (mixed) {  // L^-1 as the B operand of the whitening (rows P, K Q), 8 slices
-    PhaseScope ph3(3, s2);
-    oz_alloc(Linv8, 1, 8, np, np, OZ_BN);
-    oz_slice_f64(h->Linv.p, 0, np, 1, Linv8, s2);
-  }
-  DFJK_CUDA_CHECK(cudaEventRecord(h->ev_join, s2));
   bool joined = false;
 
   // a4 + a5: 3-centre integrals in column slabs, whitened into B
