@@ -328,8 +328,10 @@ uint64_t dfjk_launch_count(void);
  * of B), 5 K = sum X X^T, 6 D, rho and J, 7 energies; in
  * DFJK_MIXED also the tensor-core GEMM launches alone: 8 whitening, 9 X = B C,
  * 10 K (each also counted inside phases 3, 4, 5); 11 the 3-centre integrals
- * of the shell pairs evaluated in FP32 (phase 2 then holds the FP64 ones).  */
-#define DFJK_NPHASE 12
+ * of the shell pairs evaluated in FP32 (phase 2 then holds the FP64 ones);
+ * 12 the whole setup and 13 the whole build, each from its first to its last
+ * operation on the call's stream (the time between them is host work).      */
+#define DFJK_NPHASE 14
 int dfjk_set_timing(int32_t enable);
 
 /* Frees the device blocks the library keeps cached for reuse after handles

@@ -328,6 +328,7 @@ struct dfjk_ctx {
   // build workspace
   int ws_nocc = -1;
   DBuf<double> D, rho, rho_work, X, Kpart, en_work, e;
+  DBuf<int> rowmap;  // DFJK_MIXED: row of B for AO pair (mu, nu), -1 if screened
   int ksplit = 1;
   SlicedOp Csl, Xsl;  // DFJK_MIXED build operands
   DBuf<double> uks_D, uks_J;  // spin-unrestricted build: D_a + D_b and J[D_b]
@@ -392,6 +393,8 @@ void enumerate_pairs(dfjk_ctx *h) {
 // Device bytes of a handle's resident data: B (packed triangle in the mixed
 // path, both triangles in the FP64 path; none when B is in host memory) and
 // the metric, its Cholesky factor and inverse.
+// Before screening: the mixed path's B holds one row per kept AO pair, at
+// most the nao (nao + 1) / 2 of the triangle (the bound used here).
 size_t resident_estimate(const dfjk_ctx *h) {
   const size_t np2 = (size_t)h->naux_pad * h->naux_pad;
   const bool mixed = h->opt.precision == DFJK_MIXED;
@@ -488,6 +491,7 @@ void make_resident(dfjk_ctx *h, cudaStream_t st) {
   if (h->opt.hbm_budget_bytes > 0 && resident_estimate(h) > h->opt.hbm_budget_bytes)
     throw Error{DFJK_ERR_BUDGET, "resident data (" + std::to_string(resident_estimate(h)) +
                                      " bytes) exceeds hbm_budget_bytes"};
+  PhaseScope span(12, st);
   upload_bases(h, st);
   h->status.alloc(1);
   if (!h->tctr.p) h->tctr.alloc(1);
@@ -637,14 +641,21 @@ void make_resident(dfjk_ctx *h, cudaStream_t st) {
   h->pair_col.upload(h->pair_col_h, st);
   h->colmu.upload(cmu, st);
   h->colnu.upload(cnu, st);
+  if (mixed) {
+    h->rowmap.alloc((size_t)h->nao * h->nao);
+    build_rowmap(h->colmu.p, h->colnu.p, h->ncol, h->nao, h->rowmap.p, st);
+  }
 
   bool joined = false;
 
   // a4 + a5: 3-centre integrals in column slabs, whitened into B
+  // mixed: one row per kept column (the whitening writes every row); FP64:
+  // both triangles of every AO pair, zero for the screened ones
   h->ldb = np;
   h->lean = mixed;
-  h->B.alloc((h->lean ? (size_t)h->nao * (h->nao + 1) / 2 : (size_t)h->nao * h->nao) * np, h->opt.b_on_host != 0);
-  DFJK_CUDA_CHECK(cudaMemsetAsync(h->B.p, 0, h->B.bytes(), st));
+  h->B.alloc((h->lean ? (size_t)std::max<long long>(h->ncol, 1) : (size_t)h->nao * h->nao) * np,
+             h->opt.b_on_host != 0);
+  if (!h->lean) DFJK_CUDA_CHECK(cudaMemsetAsync(h->B.p, 0, h->B.bytes(), st));
   // bytes of one T slab: 4 GiB, or 2 GiB in the mixed path, whose slab also
   // has an 8-slice copy (twice the bytes) during the whitening
   const long long slab_budget = mixed ? (2LL << 30) : (4LL << 30);
@@ -703,11 +714,10 @@ void make_resident(dfjk_ctx *h, cudaStream_t st) {
       g.nao = h->nao; g.ldo = h->ldb; g.out = h->B.p;
       gemm_f64(g, st);
     } else {  // the same product on the tensor cores, 8 slices per operand
-      OzGemmArgs g;
+      OzGemmArgs g;  // B row c0 + m = whitened column c0 + m
       g.M = ncols; g.N = np; g.K = np; g.k_upto_n = 1;
-      g.mode = 1; g.out = h->B.p; g.colmu = h->colmu.p + c0; g.colnu = h->colnu.p + c0;
-      g.packed = h->lean ? 1 : 0;
-      g.nao = h->nao; g.ldb = h->ldb; g.status = h->status.p; g.timeout = h->opt.timeout_iters;
+      g.mode = 0; g.out = h->B.p + c0 * h->ldb; g.ldo = h->ldb;
+      g.status = h->status.p; g.timeout = h->opt.timeout_iters;
       g.tile_ctr = h->tctr.p;
       g.phase = 8;
       oz_gemm(T8, Linv8, g, st);
@@ -724,7 +734,7 @@ void make_resident(dfjk_ctx *h, cudaStream_t st) {
     PhaseScope ph(3, st);
     h->expo_rows = (np + OZ_BM - 1) / OZ_BM * OZ_BM;
     h->Bexpo.alloc((size_t)h->nao * h->expo_rows * ((h->nao + OZ_KB - 1) / OZ_KB));
-    oz_expo_packed(h->B.p, h->ldb, h->nao, np, h->expo_rows, h->Bexpo.p, st);
+    oz_expo_packed(h->B.p, h->ldb, h->rowmap.p, h->nao, np, h->expo_rows, h->Bexpo.p, st);
   }
   int status = 0;
   DFJK_CUDA_CHECK(cudaMemcpyAsync(&status, h->status.p, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -738,6 +748,7 @@ void make_resident(dfjk_ctx *h, cudaStream_t st) {
 void release_device(dfjk_ctx *h) {
   h->B.release();
   h->Bexpo.release();
+  h->rowmap.release();
   oz_free(h->Bchunk);
   h->V.release();
   h->L.release();
@@ -905,7 +916,7 @@ void build_one(dfjk_ctx *h, int nocc, const double *C, double *J, double *Kout, 
     {  // rho from X (5x smaller than B), then J over B
       PhaseScope ph(6, st);
       rho_from_x_f64(h->X.p, C, nao, np, nocc, h->rho.p, h->rho_work.p, st);
-      j_gemv_f64(h->B.p, h->ldb, nao, np, h->rho.p, J, h->lean ? 1 : 0, st);
+      j_gemv_f64(h->B.p, h->ldb, nao, np, h->rho.p, J, h->lean ? h->rowmap.p : nullptr, st);
     }
     GemmArgs k;  // K[mu][nu] = sum_(P,i) X[mu][(P,i)] X[nu][(P,i)]
     k.M = nao; k.N = nao; k.K = (int)kt;
@@ -940,7 +951,7 @@ void build_one(dfjk_ctx *h, int nocc, const double *C, double *J, double *Kout, 
       {
         PhaseScope ph(4, st);
         SlicedOp bv = oz_view(h->Bchunk, pc, nao);  // batch mu, rows P of the chunk, K nu
-        oz_slice_f64_packed_pre(h->B.p, h->ldb, h->Bexpo.p, h->expo_rows, p0, bv, st, h->tune.pslice_rows);
+        oz_slice_f64_packed_pre(h->B.p, h->ldb, h->rowmap.p, h->Bexpo.p, h->expo_rows, p0, bv, st, h->tune.pslice_rows);
         OzGemmArgs x;
         x.M = pc; x.N = nocc; x.K = nao; x.nz = nao; x.a_batched = 1;
         x.mode = 0; x.out = Xc; x.ldo = nocc; x.out_bs = kt;
@@ -962,7 +973,7 @@ void build_one(dfjk_ctx *h, int nocc, const double *C, double *J, double *Kout, 
           DFJK_CUDA_CHECK(cudaStreamWaitEvent(sj, h->ev_fork, 0));
         }
         PhaseScope ph(6, sj);
-        j_gemv_f64(h->B.p, h->ldb, nao, np, h->rho.p, J, 1, sj);
+        j_gemv_f64(h->B.p, h->ldb, nao, np, h->rho.p, J, h->rowmap.p, sj);
         if (h->side) DFJK_CUDA_CHECK(cudaEventRecord(h->ev_join, sj));
       }
       PhaseScope ph(5, st);
@@ -1080,7 +1091,7 @@ int dfjk_query(dfjk_handle h, int32_t *nao, int32_t *naux, int32_t *npair_kept, 
   if (nao) *nao = h->nao;
   if (naux) *naux = h->naux;
   if (npair_kept) *npair_kept = h->npair_kept;
-  if (bytes) *bytes = h->B.device_bytes() + h->Bexpo.bytes() + h->V.bytes() +
+  if (bytes) *bytes = h->B.device_bytes() + h->Bexpo.bytes() + h->rowmap.bytes() + h->V.bytes() +
                       h->L.bytes() + h->Linv.bytes() + h->rec.bytes();
   return DFJK_OK;
 }
@@ -1161,9 +1172,12 @@ int dfjk_build(dfjk_handle h, int32_t nset, int32_t nocc, const double *C, doubl
     if (!h->resident) make_resident(h, st);
     ensure_workspace(h, nocc, nset);
     const size_t nao2 = (size_t)h->nao * h->nao;
-    for (int s = 0; s < nset; ++s) {
-      const double *Cs = C + (size_t)s * h->nao * nocc;
-      build_one(h, nocc, Cs, J + s * nao2, K + s * nao2, h->e.p + 2 * s, st);
+    {
+      PhaseScope span(13, st);
+      for (int s = 0; s < nset; ++s) {
+        const double *Cs = C + (size_t)s * h->nao * nocc;
+        build_one(h, nocc, Cs, J + s * nao2, K + s * nao2, h->e.p + 2 * s, st);
+      }
     }
     // energies go to host or device memory as the pointers are (detected per call)
     cudaPointerAttributes pa{}, pb{};
@@ -1270,13 +1284,13 @@ int dfjk_build_density(dfjk_handle h, int32_t nset, const double *D, double *J, 
     }
     if (!h->rho_work.p || h->rho_work.n < (size_t)128 * ceil_div(np, 256) * 256)
       h->rho_work.alloc((size_t)128 * ceil_div(np, 256) * 256);
-    // the GEMMs below take B in both triangles: a packed B is expanded into a
-    // temporary copy for the duration of the call
+    // the GEMMs below take B in both triangles of every pair: a B of kept
+    // rows only is expanded into a temporary copy for the duration of the call
     DBuf<double> Bfull;
     const double *Bf = h->B.p;
     if (h->lean) {
       Bfull.alloc(nao2 * h->ldb);
-      unpack_tri_f64(h->B.p, h->ldb, nao, Bfull.p, st);
+      unpack_rows_f64(h->B.p, h->ldb, nao, h->rowmap.p, Bfull.p, st);
       Bf = Bfull.p;
     }
     DBuf<double> W;  // W[mu][sigma][P] = sum_lambda D[sigma][lambda] B[mu][lambda][P]
@@ -1367,7 +1381,7 @@ static void jk_gradient(dfjk_ctx *h, const double *Din, int nocc, const double *
   work.alloc(std::max<size_t>((size_t)128 * ceil_div(np, 256) * 256, (size_t)16 * np));
   d.alloc(np);
   DFJK_CUDA_CHECK(cudaMemsetAsync(d.p, 0, d.bytes(), st));
-  rho_gemv_f64(h->B.p, h->ldb, nao, np, D, rho.p, work.p, 128, st, h->lean ? 1 : 0);
+  rho_gemv_f64(h->B.p, h->ldb, nao, np, D, rho.p, work.p, 128, st, h->lean ? h->rowmap.p : nullptr);
   fitted_coefficients(h->Linv.p, h->naux, np, rho.p, work.p, d.p, st);
   DBuf<double> gam, W;
   std::deque<SlicedOp> ops;  // slices of the tensor-core GEMMs, freed after the final sync
@@ -1418,7 +1432,7 @@ static void jk_gradient(dfjk_ctx *h, const double *Din, int nocc, const double *
       for (int p0 = 0; p0 < np; p0 += pcm) {
         const int pc = std::min(pcm, np - p0);
         SlicedOp bv = oz_view(bck, pc, nao);
-        oz_slice_f64_packed_pre(h->B.p, h->ldb, h->Bexpo.p, h->expo_rows, p0, bv, st, h->tune.pslice_rows);
+        oz_slice_f64_packed_pre(h->B.p, h->ldb, h->rowmap.p, h->Bexpo.p, h->expo_rows, p0, bv, st, h->tune.pslice_rows);
         tc_gemm(bv, csl, pc, nocc, nao, nao, X.p + (size_t)p0 * nocc, nocc, (long long)np * nocc, 0);
       }
       // Xt[P][j][i] = sum_mu X[mu][P][j] C[mu][i]  (symmetric in i, j)
@@ -1719,7 +1733,7 @@ int dfjk_get_B(dfjk_handle h, double *Bout, void *stream) {
     for (int i = 0; i < h->naux; ++i) ident[i] = i;
     DBuf<int> perm;
     perm.upload(ident, st);
-    gather_B_f64(h->B.p, h->ldb, h->nao, perm.p, h->naux, Bout, h->lean ? 1 : 0, st);
+    gather_B_f64(h->B.p, h->ldb, h->nao, perm.p, h->naux, Bout, h->lean ? h->rowmap.p : nullptr, st);
     DFJK_CUDA_CHECK(cudaStreamSynchronize(st));
     return DFJK_OK;
   } catch (const Error &e) {
@@ -1734,11 +1748,16 @@ int dfjk_get_B_columns(dfjk_handle h, int32_t ncol, const int32_t *mu, const int
     if (!h->resident) throw Error{DFJK_ERR_STATE, "handle evicted"};
     if (ncol == 0) return DFJK_OK;
     cudaStream_t st = S(stream);
-    std::vector<int> rows(ncol), ident(h->naux);
+    std::vector<int> rows(ncol), ident(h->naux), map;
+    if (h->lean) {  // rows of the kept pairs (-1: screened, zero)
+      map.resize((size_t)h->nao * h->nao);
+      DFJK_CUDA_CHECK(cudaMemcpyAsync(map.data(), h->rowmap.p, map.size() * sizeof(int), cudaMemcpyDeviceToHost, st));
+      DFJK_CUDA_CHECK(cudaStreamSynchronize(st));
+    }
     for (int c = 0; c < ncol; ++c) {
       if (mu[c] < 0 || mu[c] >= h->nao || nu[c] < 0 || nu[c] >= h->nao) throw Error{DFJK_ERR_ARG, "AO index"};
-      const long long hi = std::max(mu[c], nu[c]), lo = std::min(mu[c], nu[c]);
-      rows[c] = (int)(h->lean ? hi * (hi + 1) / 2 + lo : (long long)mu[c] * h->nao + nu[c]);
+      const long long e = (long long)mu[c] * h->nao + nu[c];
+      rows[c] = h->lean ? map[e] : (int)e;
     }
     for (int i = 0; i < h->naux; ++i) ident[i] = i;
     DBuf<int> r, p;

@@ -343,7 +343,7 @@ __global__ void __launch_bounds__(256) rho_partial_kernel(const double *__restri
                                                           long long ldb, int nao, int naux,
                                                           const double *__restrict__ D,
                                                           double *__restrict__ work, int ldw,
-                                                          long long rows_per, int packed) {
+                                                          long long rows_per, const int *__restrict__ rowmap) {
   const int P = blockIdx.x * 256 + threadIdx.x;
   const long long nrows = (long long)nao * (nao + 1) / 2;
   const long long r0 = (long long)blockIdx.y * rows_per;
@@ -354,8 +354,8 @@ __global__ void __launch_bounds__(256) rho_partial_kernel(const double *__restri
     tri_row(r0, mu, nu);
     for (long long r = r0; r < r1; ++r) {
       const double w = D[(long long)mu * nao + nu] * (mu == nu ? 1.0 : 2.0);
-      const long long row = packed ? r : (long long)mu * nao + nu;
-      if (P < naux) acc = fma(w, B[row * ldb + P], acc);
+      const long long row = rowmap ? rowmap[(long long)mu * nao + nu] : (long long)mu * nao + nu;
+      if (P < naux && row >= 0) acc = fma(w, B[row * ldb + P], acc);
       if (++nu > mu) {
         ++mu;
         nu = 0;
@@ -375,11 +375,11 @@ __global__ void column_sum_kernel(const double *__restrict__ work, int ldw, int 
 }
 
 void rho_gemv_f64(const double *B, long long ldb, int nao, int naux, const double *D,
-                  double *rho, double *work, int nchunk, cudaStream_t st, int packed) {
+                  double *rho, double *work, int nchunk, cudaStream_t st, const int *rowmap) {
   const long long nrows = (long long)nao * (nao + 1) / 2;
   const long long rows_per = (nrows + nchunk - 1) / nchunk;
   const int gx = ceil_div(naux, 256), ldw = gx * 256;
-  rho_partial_kernel<<<dim3(gx, nchunk), 256, 0, st>>>(B, ldb, nao, naux, D, work, ldw, rows_per, packed);
+  rho_partial_kernel<<<dim3(gx, nchunk), 256, 0, st>>>(B, ldb, nao, naux, D, work, ldw, rows_per, rowmap);
   DFJK_LAUNCHED();
   column_sum_kernel<<<ceil_div(naux, 256), 256, 0, st>>>(work, ldw, nchunk, naux, rho);
   DFJK_LAUNCHED();
@@ -414,16 +414,18 @@ void rho_from_x_f64(const double *X, const double *C, int nao, int np, int nocc,
 __global__ void __launch_bounds__(256) j_gemv_kernel(const double *__restrict__ B, long long ldb,
                                                      int nao, int naux,
                                                      const double *__restrict__ rho,
-                                                     double *__restrict__ J, int packed) {
+                                                     double *__restrict__ J, const int *__restrict__ rowmap) {
   const long long r = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   const long long nrows = (long long)nao * (nao + 1) / 2;
   if (r >= nrows) return;
   int mu, nu;
   tri_row(r, mu, nu);
-  const double *row = B + (packed ? r : (long long)mu * nao + nu) * ldb;
+  const long long br = rowmap ? rowmap[(long long)mu * nao + nu] : (long long)mu * nao + nu;
+  const double *row = B + (br < 0 ? 0 : br) * ldb;
   double s = 0.0;
-  if ((naux & 1) == 0 && (ldb & 1) == 0) {  // 16-byte loads, two partial sums, 4 loads in flight
+  if (br < 0) {  // a screened pair: no row stored, J is 0
+  } else if ((naux & 1) == 0 && (ldb & 1) == 0) {  // 16-byte loads, two partial sums, 4 loads in flight
     const double2 *row2 = reinterpret_cast<const double2 *>(row);
     const double2 *rho2 = reinterpret_cast<const double2 *>(rho);
     double s1 = 0.0;
@@ -446,28 +448,50 @@ __global__ void __launch_bounds__(256) j_gemv_kernel(const double *__restrict__ 
 }
 
 void j_gemv_f64(const double *B, long long ldb, int nao, int naux, const double *rho, double *J,
-                int packed, cudaStream_t st) {
+                const int *rowmap, cudaStream_t st) {
   const long long nrows = (long long)nao * (nao + 1) / 2;
-  j_gemv_kernel<<<(unsigned)((nrows + 7) / 8), 256, 0, st>>>(B, ldb, nao, naux, rho, J, packed);
+  j_gemv_kernel<<<(unsigned)((nrows + 7) / 8), 256, 0, st>>>(B, ldb, nao, naux, rho, J, rowmap);
   DFJK_LAUNCHED();
 }
 
-// Bfull[(mu nao + nu) ldb + P] = Bp[(max (max + 1) / 2 + min) ldb + P]: one
-// block per (mu, nu) pair, threads along P (coalesced).
-__global__ void __launch_bounds__(256) unpack_tri_kernel(const double *__restrict__ Bp, long long ldb, int nao,
-                                                         double *__restrict__ Bf) {
+// Bfull[(mu nao + nu) ldb + P] = Bc[rowmap[mu nao + nu] ldb + P] (0 where the
+// map is -1): one block per (mu, nu) pair, threads along P (coalesced).
+__global__ void __launch_bounds__(256) unpack_rows_kernel(const double *__restrict__ Bc, long long ldb, int nao,
+                                                          const int *__restrict__ rowmap, double *__restrict__ Bf) {
   const long long e = blockIdx.x;  // mu nao + nu
-  const int mu = (int)(e / nao), nu = (int)(e % nao);
-  const long long hi = mu > nu ? mu : nu, lo = mu > nu ? nu : mu;
-  const double *src = Bp + (hi * (hi + 1) / 2 + lo) * ldb;
+  const int row = rowmap[e];
   double *dst = Bf + e * ldb;
+  if (row < 0) {
+    for (long long P = threadIdx.x; P < ldb; P += 256) dst[P] = 0.0;
+    return;
+  }
+  const double *src = Bc + (long long)row * ldb;
   for (long long P = threadIdx.x; P < ldb; P += 256) dst[P] = src[P];
 }
 
-void unpack_tri_f64(const double *Bp, long long ldb, int nao, double *Bfull, cudaStream_t st) {
+void unpack_rows_f64(const double *Bc, long long ldb, int nao, const int *rowmap, double *Bfull, cudaStream_t st) {
   const long long n2 = (long long)nao * nao;
   if (n2 == 0) return;
-  unpack_tri_kernel<<<(unsigned)n2, 256, 0, st>>>(Bp, ldb, nao, Bfull);
+  unpack_rows_kernel<<<(unsigned)n2, 256, 0, st>>>(Bc, ldb, nao, rowmap, Bfull);
+  DFJK_LAUNCHED();
+}
+
+// rowmap[mu nao + nu] = rowmap[nu nao + mu] = m for every column m with
+// colmu[m] >= 0 (the map is -1 elsewhere).
+__global__ void build_rowmap_kernel(const int *__restrict__ colmu, const int *__restrict__ colnu, long long ncol,
+                                    int nao, int *__restrict__ rowmap) {
+  const long long m = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= ncol) return;
+  const int mu = colmu[m], nu = colnu[m];
+  if (mu < 0) return;
+  rowmap[(long long)mu * nao + nu] = (int)m;
+  rowmap[(long long)nu * nao + mu] = (int)m;
+}
+
+void build_rowmap(const int *colmu, const int *colnu, long long ncol, int nao, int *rowmap, cudaStream_t st) {
+  DFJK_CUDA_CHECK(cudaMemsetAsync(rowmap, 0xFF, (size_t)nao * nao * sizeof(int), st));
+  if (ncol == 0) return;
+  build_rowmap_kernel<<<(unsigned)((ncol + 255) / 256), 256, 0, st>>>(colmu, colnu, ncol, nao, rowmap);
   DFJK_LAUNCHED();
 }
 
@@ -606,7 +630,7 @@ __global__ void gather2d_kernel(const double *in, long long ldi, const int *pr, 
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (long long)nr * nc) return;
   const int i = (int)(e / nc), j = (int)(e % nc);
-  out[i * ldo + j] = in[(long long)pr[i] * ldi + pc[j]];
+  out[i * ldo + j] = pr[i] < 0 ? 0.0 : in[(long long)pr[i] * ldi + pc[j]];
 }
 
 void gather2d_f64(const double *in, long long ldi, const int *perm_r, const int *perm_c, int nr,
@@ -618,26 +642,21 @@ void gather2d_f64(const double *in, long long ldi, const int *perm_r, const int 
 }
 
 __global__ void gather_B_kernel(const double *Bint, long long ldb, int nao, const int *perm,
-                                int naux, double *out, int packed) {
+                                int naux, double *out, const int *rowmap) {
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long n2 = (long long)nao * nao;
   if (e >= n2 * naux) return;
   const int P = (int)(e / n2);
   const long long mn = e % n2;
-  long long row = mn;
-  if (packed) {
-    const long long mu = mn / nao, nu = mn % nao;
-    const long long hi = mu > nu ? mu : nu, lo = mu > nu ? nu : mu;
-    row = hi * (hi + 1) / 2 + lo;
-  }
-  out[e] = Bint[row * ldb + perm[P]];
+  const long long row = rowmap ? rowmap[mn] : mn;
+  out[e] = row < 0 ? 0.0 : Bint[row * ldb + perm[P]];
 }
 
 void gather_B_f64(const double *Bint, long long ldb, int nao, const int *perm, int naux,
-                  double *out, int packed, cudaStream_t st) {
+                  double *out, const int *rowmap, cudaStream_t st) {
   const long long n = (long long)nao * nao * naux;
   if (n == 0) return;
-  gather_B_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(Bint, ldb, nao, perm, naux, out, packed);
+  gather_B_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(Bint, ldb, nao, perm, naux, out, rowmap);
   DFJK_LAUNCHED();
 }
 

@@ -55,22 +55,27 @@ void cholesky_f64(double *A, int n, int lda, double *Dinv, int *status, double *
 void tri_inverse_f64(const double *L, int n, int ld, const double *Dinv, double *Linv,
                      double *work, cudaStream_t st);
 
-// rho[P] = sum_{mu >= nu} w D[mu][nu] B[row ldb + P], w = 2 off the diagonal,
-// row = mu nao + nu (both triangles stored) or mu (mu + 1) / 2 + nu (packed);
+// B storage: rows of ldb doubles (P contiguous), row(mu, nu) = mu nao + nu
+// (both triangles stored, rowmap null) or rowmap[mu nao + nu] (the kept AO
+// pairs only; -1 for a screened pair, whose B is zero).
+//
+// rho[P] = sum_{mu >= nu} w D[mu][nu] B[row ldb + P], w = 2 off the diagonal;
 // partial sums in `work` (ceil(naux/256) x nchunk) then a fixed-order reduction.
 void rho_gemv_f64(const double *B, long long ldb, int nao, int naux, const double *D,
-                  double *rho, double *work, int nchunk, cudaStream_t st, int packed = 0);
-// Both triangles of a packed B: Bfull[(mu nao + nu) ldb + P] =
-// Bp[(max (max + 1) / 2 + min) ldb + P] (nao^2 rows of ldb doubles).
-void unpack_tri_f64(const double *Bp, long long ldb, int nao, double *Bfull, cudaStream_t st);
+                  double *rho, double *work, int nchunk, cudaStream_t st, const int *rowmap = nullptr);
+// Both triangles of a row-mapped B: Bfull[(mu nao + nu) ldb + P] (nao^2 rows).
+void unpack_rows_f64(const double *Bc, long long ldb, int nao, const int *rowmap, double *Bfull, cudaStream_t st);
+// The row map of the kept columns: rowmap[mu nao + nu] = rowmap[nu nao + mu] =
+// m for colmu[m] >= 0, -1 elsewhere (nao^2 ints).
+void build_rowmap(const int *colmu, const int *colnu, long long ncol, int nao, int *rowmap, cudaStream_t st);
 // rho[P] = sum_{mu,i} C[mu][i] X[mu][P][i]  (= sum_{mu nu} B[mu][nu][P] D[mu][nu]
 // since X_P = B_P C and D = C C^T); per-mu partials in `part` (nao x np).
 void rho_from_x_f64(const double *X, const double *C, int nao, int np, int nocc, double *rho,
                     double *part, cudaStream_t st);
-// J[mu][nu] = J[nu][mu] = sum_P B[row(mu, nu) ldb + P] rho[P] for mu >= nu, with
-// row = mu nao + nu (full storage) or mu (mu + 1) / 2 + nu (packed triangle).
+// J[mu][nu] = J[nu][mu] = sum_P B[row(mu, nu) ldb + P] rho[P] for mu >= nu
+// (0 for a screened pair).
 void j_gemv_f64(const double *B, long long ldb, int nao, int naux, const double *rho, double *J,
-                int packed, cudaStream_t st);
+                const int *rowmap, cudaStream_t st);
 // out[mu][nu] = out[nu][mu] = sum_s part[s][mu][nu] (mu >= nu), summed in
 // split order; add = 1 starts the sum from the current out[mu][nu].
 void reduce_sym_f64(const double *part, int nsplit, int n, double *out, cudaStream_t st, int add = 0);
@@ -85,12 +90,13 @@ void max_sqrt_diag(const double *V, int n, int ld, double *out, cudaStream_t st)
 void screen_pairs(const double *q, int n, const double *maxdiag, double thresh, int *keep,
                   cudaStream_t st);
 void fill_f64(double *p, long long n, double v, cudaStream_t st);
-// out[i][j] = in[perm_r[i] * ldi + perm_c[j]] for an n_r x n_c gather.
+// out[i][j] = in[perm_r[i] * ldi + perm_c[j]] for an n_r x n_c gather (0 where
+// perm_r[i] < 0).
 void gather2d_f64(const double *in, long long ldi, const int *perm_r, const int *perm_c, int nr,
                   int nc, double *out, long long ldo, cudaStream_t st);
 // B user-order copy: out[P][mu][nu] = Bint[row(mu, nu) ldb + perm[P]] (row as
-// for j_gemv_f64; packed storage holds the mu >= nu triangle).
+// above).
 void gather_B_f64(const double *Bint, long long ldb, int nao, const int *perm, int naux,
-                  double *out, int packed, cudaStream_t st);
+                  double *out, const int *rowmap, cudaStream_t st);
 
 }  // namespace dfjk

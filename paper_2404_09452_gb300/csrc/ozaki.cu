@@ -195,23 +195,16 @@ __global__ void __launch_bounds__(256) oz_slice_tr_kernel(const double *__restri
     }
 }
 
-// Row-contiguous sources, exponents and slices in one kernel: a block owns 8
+// Row-contiguous sources, exponents and slices in one kernel: a block owns R
 // rows of one batch and walks all of K twice, first for the per-(row, K-block)
-// maxima, then for the slices.  8 rows x K doubles per block (58 KB for
-// K = 900) keeps the second read in L2 with every SM's blocks in flight; lanes
-// run along the rows (64 contiguous bytes per K index, four K indices per
-// warp load).
-// MODE 0: both passes.  MODE 1: exponents only (pass 1; no slices).  MODE 2:
-// slices only, with the exponents of row r taken from a precomputed array
-// pre[(z pre_rows + pre_row0 + r) nkb + kb] (and copied to `expo` for the
-// GEMM), so the source is read once.
-template <int S, bool PACKED, int R = 8, int MODE = 0>
+// maxima, then for the slices.  R rows x K doubles per block (58 KB for R = 8
+// and K = 900) keeps the second read in L2 with every SM's blocks in flight;
+// lanes run along the rows (8 R contiguous bytes per K index).
+template <int S, int R = 8>
 __global__ void __launch_bounds__(256) oz_slice_tr_fused_kernel(const double *__restrict__ src, long long sz,
                                                                 long long sk, int rows, int K, int rows_pad,
                                                                 int kpitch, int nkb, int *__restrict__ expo,
-                                                                __nv_bfloat16 *__restrict__ out, int mu0,
-                                                                int kblk, const int *__restrict__ pre = nullptr,
-                                                                long long pre_rows = 0, int pre_row0 = 0) {
+                                                                __nv_bfloat16 *__restrict__ out, int kblk) {
   // slices staged K-major, [s][k][row] with R + 1 elements per k: the writes
   // (lanes along rows) and the reads of 8 consecutive k of one row (lanes
   // along k chunks) both spread over the shared-memory banks
@@ -223,48 +216,31 @@ __global__ void __launch_bounds__(256) oz_slice_tr_fused_kernel(const double *__
   const int rr = threadIdx.x % R, kq = threadIdx.x / R;  // KG groups along K
   const int r = r0 + rr;
   const bool live = r < rows;
-  // element (z, r, k): src[z sz + k sk + r], or for a packed mu >= nu triangle
-  // (mu = mu0 + z, nu = k) src[row(max, min) sk + r]
-  const long long mu = (long long)mu0 + z;
-  auto at = [&](int k) -> double {
-    if (PACKED) {
-      const long long hi = mu > k ? mu : k, lo = mu > k ? k : mu;
-      return src[(hi * (hi + 1) / 2 + lo) * sk + r];
-    }
-    return src[z * sz + (long long)k * sk + r];
-  };
-  if (MODE == 2) {
-    if (threadIdx.x < R * nkb) {
-      const int q = threadIdx.x / nkb, kb = threadIdx.x % nkb;
-      const int e = pre[((long long)z * pre_rows + pre_row0 + r0 + q) * nkb + kb];
-      rexp[q][kb] = e;
-      expo[((long long)z * rows_pad + r0 + q) * nkb + kb] = e;
-    }
-    __syncthreads();
-  }
-  if (MODE != 2 && threadIdx.x < R * MAXKB) rmax[threadIdx.x / MAXKB][threadIdx.x % MAXKB] = 0ull;
+  auto at = [&](int k) -> double { return src[z * sz + (long long)k * sk + r]; };
+  if (threadIdx.x < R * MAXKB) rmax[threadIdx.x / MAXKB][threadIdx.x % MAXKB] = 0ull;
   __syncthreads();
-  // pass 1: |x| maxima per K block (non-negative doubles order like their bits)
-  for (int kb = 0; kb < nkb && MODE != 2; ++kb) {
-    double mx = 0.0;
+  // pass 1: |x| maxima per K block, on the bit patterns (non-negative doubles
+  // order like their bits)
+  for (int kb = 0; kb < nkb; ++kb) {
+    unsigned long long mx = 0;
     if (live) {
       const int k1 = min(K, (kb + 1) * OZ_KB);
 #pragma unroll 4
-      for (int k = kb * OZ_KB + kq; k < k1; k += KG) mx = fmax(mx, fabs(at(k)));
+      for (int k = kb * OZ_KB + kq; k < k1; k += KG)
+        mx = max(mx, (unsigned long long)__double_as_longlong(at(k)) & 0x7FFFFFFFFFFFFFFFull);
     }
     // lanes with the same row in a warp (32 / R of them)
 #pragma unroll
-    for (int o = R; o < 32; o <<= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if ((threadIdx.x & 31) < R) atomicMax(&rmax[rr][kb], (unsigned long long)__double_as_longlong(mx));
+    for (int o = R; o < 32; o <<= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) < R) atomicMax(&rmax[rr][kb], mx);
   }
   __syncthreads();
-  if (MODE != 2 && threadIdx.x < R * nkb) {
+  if (threadIdx.x < R * nkb) {
     const int q = threadIdx.x / nkb, kb = threadIdx.x % nkb;
     const int e = oz_expo_of(__longlong_as_double((long long)rmax[q][kb]));
     rexp[q][kb] = e;
     expo[((long long)z * rows_pad + r0 + q) * nkb + kb] = e;
   }
-  if (MODE == 1) return;
   __syncthreads();
   // pass 2: slices, 64 K at a time, staged [s][row][k] and written along K
   for (int k0 = 0; k0 < kpitch; k0 += 64) {
@@ -310,9 +286,10 @@ constexpr int OZ_TT = 32;  // tile edge in AO indices
 __host__ __device__ constexpr int oz_sym_smem(int R) { return OZ_TT * OZ_TT * (R + 1) * 8 + 2 * OZ_TT * R * 4; }
 
 template <int R, int MODE>
-__global__ void __launch_bounds__(256) oz_slice_sym_kernel(const double *__restrict__ B, long long ldb, int nao,
-                                                           int rows, int p0, int rows_pad, int kpitch, int nkb,
-                                                           int kblk, const int *__restrict__ pre, int pre_rows,
+__global__ void __launch_bounds__(256) oz_slice_sym_kernel(const double *__restrict__ B, long long ldb,
+                                                           const int *__restrict__ rowmap, int nao, int rows,
+                                                           int p0, int rows_pad, int kpitch, int nkb, int kblk,
+                                                           const int *__restrict__ pre, int pre_rows,
                                                            int *__restrict__ expo_out, __nv_bfloat16 *__restrict__ out) {
   constexpr int RP = R + 1;
   extern __shared__ __align__(16) uint8_t sym_smem[];
@@ -343,8 +320,8 @@ __global__ void __launch_bounds__(256) oz_slice_sym_kernel(const double *__restr
       const int mu = mu0 + ml, nu = nu0 + nl, r = r0 + P;
       v[u] = 0.0;
       if (mu < nao && nu < nao && r < rows) {
-        const long long hi = mu > nu ? mu : nu, lo = mu > nu ? nu : mu;
-        v[u] = B[(hi * (hi + 1) / 2 + lo) * ldb + p0 + r];
+        const int row = rowmap[(long long)mu * nao + nu];
+        if (row >= 0) v[u] = B[(long long)row * ldb + p0 + r];
       }
     }
 #pragma unroll
@@ -361,7 +338,7 @@ __global__ void __launch_bounds__(256) oz_slice_sym_kernel(const double *__restr
     }
   }
   __syncthreads();
-  if (MODE == 1) {
+  if constexpr (MODE == 1) {
     // thread (l, P): direct maximum over nu of row mu0 + l; transposed over mu of column nu0 + l
     for (int i = threadIdx.x; i < 2 * OZ_TT * R; i += 256) {
       const int P = i % R, l = (i / R) % OZ_TT, tr = i / (OZ_TT * R);
@@ -380,7 +357,7 @@ __global__ void __launch_bounds__(256) oz_slice_sym_kernel(const double *__restr
                         oz_expo_of(__longlong_as_double((long long)mx)) + OZ_EXPO_BIAS);
     }
     return;
-  }
+  } else {
   // slices: item (l, P, g) = 8 consecutive K of batch mu0 + l (direct) or nu0 + l
   // (transposed), one 16-byte store per slice; 4 lanes cover 32 K (64 bytes)
   for (int i = threadIdx.x; i < 2 * OZ_TT * R * 4; i += 256) {
@@ -404,6 +381,7 @@ __global__ void __launch_bounds__(256) oz_slice_sym_kernel(const double *__restr
       *reinterpret_cast<uint4 *>(out + oz_off(z, sl, r0 + P, k, 6, rows_pad, kpitch, nkb, kblk)) =
           make_uint4(w[sl][0], w[sl][1], w[sl][2], w[sl][3]);
   }
+  }
 }
 
 // expo[i] encoded as above -> exponent
@@ -413,8 +391,8 @@ __global__ void oz_expo_decode_kernel(int *expo, long long n) {
 }
 
 template <int R, int MODE>
-static void launch_oz_sym(dim3 grid, const double *B, long long ldb, int nao, int rows, int p0, int rows_pad,
-                          int kpitch, int nkb, int kblk, const int *pre, int pre_rows, int *expo_out,
+static void launch_oz_sym(dim3 grid, const double *B, long long ldb, const int *rowmap, int nao, int rows, int p0,
+                          int rows_pad, int kpitch, int nkb, int kblk, const int *pre, int pre_rows, int *expo_out,
                           __nv_bfloat16 *out, cudaStream_t st) {
   constexpr int SM = oz_sym_smem(R);
   static bool attr_set = false;
@@ -422,8 +400,8 @@ static void launch_oz_sym(dim3 grid, const double *B, long long ldb, int nao, in
     DFJK_CUDA_CHECK(cudaFuncSetAttribute(oz_slice_sym_kernel<R, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, SM));
     attr_set = true;
   }
-  oz_slice_sym_kernel<R, MODE><<<grid, 256, SM, st>>>(B, ldb, nao, rows, p0, rows_pad, kpitch, nkb, kblk, pre,
-                                                       pre_rows, expo_out, out);
+  oz_slice_sym_kernel<R, MODE><<<grid, 256, SM, st>>>(B, ldb, rowmap, nao, rows, p0, rows_pad, kpitch, nkb, kblk,
+                                                       pre, pre_rows, expo_out, out);
   DFJK_LAUNCHED();
 }
 
@@ -470,7 +448,8 @@ void oz_free(SlicedOp &op) {
   op.expo = nullptr;
 }
 
-void oz_expo_packed(const double *B, long long ldb, int nao, int np, int pre_rows, int *expo, cudaStream_t st) {
+void oz_expo_packed(const double *B, long long ldb, const int *rowmap, int nao, int np, int pre_rows, int *expo,
+                    cudaStream_t st) {
   const int nkb = (nao + OZ_KB - 1) / OZ_KB;
   if (pre_rows % 32 != 0 || pre_rows < np || nkb > 8 || np > ldb)
     throw Error{DFJK_ERR_UNSUPPORTED, "packed exponents: K <= 8192"};
@@ -478,14 +457,14 @@ void oz_expo_packed(const double *B, long long ldb, int nao, int np, int pre_row
   DFJK_CUDA_CHECK(cudaMemsetAsync(expo, 0, n * sizeof(int), st));
   const long long nb = (nao + OZ_TT - 1) / OZ_TT, tiles = nb * (nb + 1) / 2;
   if (tiles > 65535) throw Error{DFJK_ERR_ARG, "packed exponents: grid"};
-  launch_oz_sym<8, 1>(dim3((unsigned)(pre_rows / 8), (unsigned)tiles), B, ldb, nao, np, 0, 0, 0, nkb, 0, nullptr,
-                      pre_rows, expo, nullptr, st);
+  launch_oz_sym<8, 1>(dim3((unsigned)(pre_rows / 8), (unsigned)tiles), B, ldb, rowmap, nao, np, 0, 0, 0, nkb, 0,
+                      nullptr, pre_rows, expo, nullptr, st);
   oz_expo_decode_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(expo, n);
   DFJK_LAUNCHED();
 }
 
-void oz_slice_f64_packed_pre(const double *B, long long ldb, const int *pre, int pre_rows, int p0, SlicedOp &op,
-                             cudaStream_t st, int rows_per_block) {
+void oz_slice_f64_packed_pre(const double *B, long long ldb, const int *rowmap, const int *pre, int pre_rows, int p0,
+                             SlicedOp &op, cudaStream_t st, int rows_per_block) {
   // every row a block touches, padding included, has a precomputed exponent;
   // batch = nao, K = nao
   if (op.S != 6 || op.rows_pad % 32 != 0 || op.nkb > 8 || p0 % 32 != 0 || p0 + op.rows_pad > pre_rows ||
@@ -506,13 +485,13 @@ void oz_slice_f64_packed_pre(const double *B, long long ldb, const int *pre, int
   if (tiles > 65535) throw Error{DFJK_ERR_ARG, "packed slicing: grid"};
   const dim3 grid((unsigned)(op.rows_pad / R), (unsigned)tiles);
   if (R == 4)
-    launch_oz_sym<4, 2>(grid, B, ldb, op.batch, op.rows, p0, op.rows_pad, op.kpitch, op.nkb, op.kblk, pre, pre_rows,
+    launch_oz_sym<4, 2>(grid, B, ldb, rowmap, op.batch, op.rows, p0, op.rows_pad, op.kpitch, op.nkb, op.kblk, pre, pre_rows,
                         nullptr, op.data, st);
   else if (R == 16)
-    launch_oz_sym<16, 2>(grid, B, ldb, op.batch, op.rows, p0, op.rows_pad, op.kpitch, op.nkb, op.kblk, pre, pre_rows,
+    launch_oz_sym<16, 2>(grid, B, ldb, rowmap, op.batch, op.rows, p0, op.rows_pad, op.kpitch, op.nkb, op.kblk, pre, pre_rows,
                          nullptr, op.data, st);
   else
-    launch_oz_sym<8, 2>(grid, B, ldb, op.batch, op.rows, p0, op.rows_pad, op.kpitch, op.nkb, op.kblk, pre, pre_rows,
+    launch_oz_sym<8, 2>(grid, B, ldb, rowmap, op.batch, op.rows, p0, op.rows_pad, op.kpitch, op.nkb, op.kblk, pre, pre_rows,
                         nullptr, op.data, st);
 }
 
@@ -531,8 +510,8 @@ void oz_slice_f64(const double *src, long long sz, long long sr, long long sk, S
     const int R = (op.rows_pad % rows_per_block == 0) ? rows_per_block : 8;
     dim3 grid((unsigned)(op.rows_pad / R), (unsigned)op.batch);
 #define OZ_FUSED(SS, RR)                                                                                      \
-  oz_slice_tr_fused_kernel<SS, false, RR><<<grid, 256, 0, st>>>(src, sz, sk, op.rows, op.K, op.rows_pad, op.kpitch, \
-                                                                 op.nkb, op.expo, op.data, 0, op.kblk)
+  oz_slice_tr_fused_kernel<SS, RR><<<grid, 256, 0, st>>>(src, sz, sk, op.rows, op.K, op.rows_pad, op.kpitch,   \
+                                                          op.nkb, op.expo, op.data, op.kblk)
     if (op.S == 6) {
       if (R == 32) OZ_FUSED(6, 32);
       else if (R == 16) OZ_FUSED(6, 16);
@@ -684,12 +663,6 @@ __device__ __forceinline__ void oz_tma(void *dst, const CUtensorMap *map, uint64
                                        int plane, int kblk) {
   if (kblk) tc::tma_load_4d(dst, map, bar, kc & (OZ_KB - 1), row0, kc >> 10, plane);
   else tc::tma_load_3d(dst, map, bar, kc, row0, plane);
-}
-
-// Row of (mu, nu) in a packed symmetric triangle: max (max + 1) / 2 + min.
-__device__ __forceinline__ long long tri_row_of(int mu, int nu) {
-  const long long hi = mu > nu ? mu : nu, lo = mu > nu ? nu : mu;
-  return hi * (hi + 1) / 2 + lo;
 }
 
 __device__ __forceinline__ double pow2(int e) {
@@ -852,25 +825,10 @@ __global__ void __launch_bounds__(128, 1)
   }
 
   if (ok && m < g.M) {
-    if (g.mode == 0) {
-      double *o = g.out + (long long)z * g.out_bs + (long long)m * g.ldo;
+    double *o = g.out + (long long)z * g.out_bs + (long long)m * g.ldo;
 #pragma unroll
-      for (int j = 0; j < OZ_BN; ++j)
-        if (n0 + j < g.N) o[n0 + j] = acc[j];
-    } else {
-      const int mu = g.colmu[m], nu = g.colnu[m];
-      if (mu >= 0) {
-        const bool two = mu != nu && !g.packed;
-        double *o1 = g.out + (g.packed ? tri_row_of(mu, nu) : (long long)mu * g.nao + nu) * g.ldb;
-        double *o2 = g.out + ((long long)nu * g.nao + mu) * g.ldb;
-#pragma unroll
-        for (int j = 0; j < OZ_BN; ++j)
-          if (n0 + j < g.N) {
-            o1[n0 + j] = acc[j];
-            if (two) o2[n0 + j] = acc[j];
-          }
-      }
-    }
+    for (int j = 0; j < OZ_BN; ++j)
+      if (n0 + j < g.N) o[n0 + j] = acc[j];
   }
   __syncthreads();
   if (warp == 0) tc::tmem_dealloc(tbase, 512);
@@ -1156,38 +1114,14 @@ __global__ void __launch_bounds__(oz_ws_threads(NEPI), 1)
         if (lane == 0) *(volatile int *)seq = z + 1;
       } else if (m < g.M) {
         const bool full = nh + NH <= g.N;
-        if (g.mode == 0) {
-          double *o = g.out + (long long)z * g.out_bs + (long long)m * g.ldo + nh;
-          if (full && ((uintptr_t)o & 15) == 0) {
+        double *o = g.out + (long long)z * g.out_bs + (long long)m * g.ldo + nh;
+        if (full && ((uintptr_t)o & 15) == 0) {
 #pragma unroll
-            for (int j = 0; j < NH; j += 2) *reinterpret_cast<double2 *>(o + j) = make_double2(acc[j], acc[j + 1]);
-          } else {
-#pragma unroll
-            for (int j = 0; j < NH; ++j)
-              if (nh + j < g.N) o[j] = acc[j];
-          }
+          for (int j = 0; j < NH; j += 2) *reinterpret_cast<double2 *>(o + j) = make_double2(acc[j], acc[j + 1]);
         } else {
-          const int mu = g.colmu[m], nu = g.colnu[m];
-          if (mu >= 0) {
-            const bool two = mu != nu && !g.packed;
-            double *o1 = g.out + (g.packed ? tri_row_of(mu, nu) : (long long)mu * g.nao + nu) * g.ldb + nh;
-            double *o2 = g.out + ((long long)nu * g.nao + mu) * g.ldb + nh;
-            if (full && (((uintptr_t)o1 | (uintptr_t)o2) & 15) == 0) {
 #pragma unroll
-              for (int j = 0; j < NH; j += 2) {
-                const double2 v = make_double2(acc[j], acc[j + 1]);
-                *reinterpret_cast<double2 *>(o1 + j) = v;
-                if (two) *reinterpret_cast<double2 *>(o2 + j) = v;
-              }
-            } else {
-#pragma unroll
-              for (int j = 0; j < NH; ++j)
-                if (nh + j < g.N) {
-                  o1[j] = acc[j];
-                  if (two) o2[j] = acc[j];
-                }
-            }
-          }
+          for (int j = 0; j < NH; ++j)
+            if (nh + j < g.N) o[j] = acc[j];
         }
       }
     }
@@ -1333,7 +1267,7 @@ void oz_gemm(const SlicedOp &A, const SlicedOp &B, const OzGemmArgs &g, cudaStre
     throw Error{DFJK_ERR_ARG, "oz_gemm: tiles exceed the padded operands"};
   if (g.a_batched && g.nz > A.batch) throw Error{DFJK_ERR_ARG, "oz_gemm: A batch"};
   if (g.b_batched && g.nz > B.batch) throw Error{DFJK_ERR_ARG, "oz_gemm: B batch"};
-  if (g.mode == 1 && (!g.colmu || !g.colnu)) throw Error{DFJK_ERR_ARG, "oz_gemm: scatter map"};
+  if (g.mode != 0 && g.mode != 2) throw Error{DFJK_ERR_ARG, "oz_gemm: mode"};
   if (g.nz > 65535 || (g.M + OZ_BM - 1) / OZ_BM > 2147483647) throw Error{DFJK_ERR_ARG, "oz_gemm: grid"};
   const bool simple = oz_simple_mode();
   if (simple && g.mode == 2) throw Error{DFJK_ERR_UNSUPPORTED, "oz_gemm: mode 2 needs the persistent kernel"};

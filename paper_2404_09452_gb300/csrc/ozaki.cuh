@@ -61,18 +61,14 @@ struct OzGemmArgs {
   int kb_per_split = 0;  // >0: z selects K-blocks [z kb_per_split, (z+1) kb_per_split)
   int k_upto_n = 0;      // K limited to < end of the N tile (B lower triangular)
   int lower_only = 0;    // skip tiles strictly above the diagonal
-  int mode = 0;          // 0: out[z out_bs + m ldo + n] = C; 1: whitening scatter;
+  int mode = 0;          // 0: out[z out_bs + m ldo + n] = C;
                          // 2: split-K in order, out[m ldo + n] (+)= C of split z
                          //    after splits 0..z-1 (persistent kernel only)
   int *tile_seq = nullptr;  // mode 2: per (tile, drain warp) split counters
   int accumulate = 0;    // mode 2: split 0 also adds onto out (a later chunk of
                          // the reduction range, in chunk order)
-  int packed = 0;        // mode 1: out holds the mu >= nu triangle, row mu (mu + 1) / 2 + nu
   double *out = nullptr;
   long long ldo = 0, out_bs = 0;
-  const int *colmu = nullptr, *colnu = nullptr;  // mode 1: row m -> AO pair
-  int nao = 0;
-  long long ldb = 0;
   int *status = nullptr;       // STATUS_TIMEOUT on an expired wait
   long long timeout = 1 << 26; // polls per mbarrier wait
   int phase = -1;              // phase timer id of this launch (-1: none)
@@ -81,23 +77,26 @@ struct OzGemmArgs {
                                // run concurrently need distinct counters
 };
 
-// B stored as the packed mu >= nu triangle: row mu (mu + 1) / 2 + nu, ldb
-// doubles per row, P contiguous.  Its slices for the X GEMM are batch mu,
+// B stored by rows of ldb doubles (P contiguous), one row per kept AO pair:
+// rowmap[mu nao + nu] = rowmap[nu nao + mu] is the row of pair (mu, nu), -1 for
+// a screened pair (B is zero there).  Its slices for the X GEMM are batch mu,
 // rows P, K nu, with one exponent per (mu, P, 1024-block of nu).  Both
-// functions below read each stored element once (32 x 32 tiles of the pair
-// triangle, each written for batch mu and for batch nu).
+// functions below read each stored row once (32 x 32 tiles of the mu >= nu
+// pair triangle, each written for batch mu and for batch nu) and skip the
+// screened pairs.
 
 // The exponents for every mu and the rows P < pre_rows (rows np..pre_rows-1
 // get 0): expo[(mu pre_rows + P) nkb + kb].  B does not change between
 // builds, so a handle computes them once.
-void oz_expo_packed(const double *B, long long ldb, int nao, int np, int pre_rows, int *expo, cudaStream_t st);
+void oz_expo_packed(const double *B, long long ldb, const int *rowmap, int nao, int np, int pre_rows, int *expo,
+                    cudaStream_t st);
 // The slices of the chunk of rows P [p0, p0 + op.rows) for all mu (batch = K
 // = nao), with the exponents from `pre` (oz_expo_packed), which are also
 // copied into op.expo.  p0 % 32 == 0 and p0 + op.rows_pad <= pre_rows.
 // rows_per_block: rows P per block (4, 8 or 16; 0 = the default, 8, or
 // DFJK_PSLICE_ROWS).
-void oz_slice_f64_packed_pre(const double *B, long long ldb, const int *pre, int pre_rows, int p0, SlicedOp &op,
-                             cudaStream_t st, int rows_per_block = 0);
+void oz_slice_f64_packed_pre(const double *B, long long ldb, const int *rowmap, const int *pre, int pre_rows, int p0,
+                             SlicedOp &op, cudaStream_t st, int rows_per_block = 0);
 
 // True when DFJK_OZ_SIMPLE=1 selects the one-tile-per-CTA kernel (no mode 2).
 bool oz_simple_mode();

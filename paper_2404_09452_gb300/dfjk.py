@@ -69,7 +69,7 @@ EXPORTS = [
 ]
 
 PHASES = ["pairs+metric", "cholesky", "eri3c", "whiten", "X=BC", "K", "rho+J", "energies",
-          "tc:whiten", "tc:X=BC", "tc:K", "eri3c32"]
+          "tc:whiten", "tc:X=BC", "tc:K", "eri3c32", "setup", "build"]
 
 
 class DfjkError(RuntimeError):
