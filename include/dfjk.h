@@ -176,9 +176,16 @@ int dfjk_query_tuning(dfjk_handle h, int32_t *vals);
 
 /* Layout of a handle's setup: the number of 3-centre column slabs (T is
  * built and whitened slab by slab, at most 4 GiB each, 2 GiB in the mixed
- * path) and whether B is kept as the packed mu >= nu triangle (1 for every
- * DFJK_MIXED handle, 0 for DFJK_FP64).  Either output pointer may be NULL.   */
+ * path) and whether B holds rows for the Schwarz-kept AO pairs only (1 for
+ * every DFJK_MIXED handle; 0 for DFJK_FP64, whose B has both triangles of
+ * every pair).  Either output pointer may be NULL.                           */
 int dfjk_query_setup(dfjk_handle h, int32_t *nslab, int32_t *lean);
+
+/* Aux-row chunking of the DFJK_MIXED build (the build slices B, forms X and
+ * adds its K contribution chunk by chunk of rows P, one X and one K GEMM
+ * launch per chunk): rows per chunk and the number of chunks, both 0 before
+ * the handle's first build and for DFJK_FP64.  Either pointer may be NULL.   */
+int dfjk_query_build(dfjk_handle h, int32_t *chunk_rows, int32_t *nchunk);
 
 /* Device bytes a molecule with nao AOs and naux aux functions takes at the
  * given precision, before any setup (no device work): `resident` = what a

@@ -1162,6 +1162,14 @@ int dfjk_query_setup(dfjk_handle h, int32_t *nslab, int32_t *lean) {
   return DFJK_OK;
 }
 
+int dfjk_query_build(dfjk_handle h, int32_t *chunk_rows, int32_t *nchunk) {
+  if (!h) return fail(Error{DFJK_ERR_ARG, "null handle"});
+  const bool mixed = h->opt.precision == DFJK_MIXED && h->chunk_rows > 0;
+  if (chunk_rows) *chunk_rows = mixed ? h->chunk_rows : 0;
+  if (nchunk) *nchunk = mixed ? ceil_div(h->naux_pad, h->chunk_rows) : 0;
+  return DFJK_OK;
+}
+
 int dfjk_build(dfjk_handle h, int32_t nset, int32_t nocc, const double *C, double *J, double *K,
                double *EJ, double *EK, void *stream) {
   try {

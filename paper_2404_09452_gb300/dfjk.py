@@ -37,6 +37,7 @@ EXPORTS = [
     "dfjk_query",
     "dfjk_query_precision",
     "dfjk_query_setup",
+    "dfjk_query_build",
     "dfjk_query_pair_classes",
     "dfjk_query_tuning",
     "dfjk_estimate_bytes",
@@ -136,6 +137,7 @@ def load_library(path: str = LIB_PATH):
     lib.dfjk_query_pair_classes.argtypes = [vp, vp, vp]
     lib.dfjk_fma_rate.argtypes = [i32, vp, vp]
     lib.dfjk_query_tuning.argtypes = [vp, vp]
+    lib.dfjk_query_build.argtypes = [vp, vp, vp]
     lib.dfjk_overlap.argtypes = [vp, vp, vp]
     lib.dfjk_coulomb_gradient.argtypes = [vp, vp, vp, vp]
     lib.dfjk_jk_gradient.argtypes = [vp, i32, vp, ctypes.c_double, ctypes.c_double, vp, vp]
@@ -269,6 +271,13 @@ class Handle:
         # launch shapes from the tuning table (0 = default): slicing rows,
         # packed-B slicing rows, K range MB, build work-buffer cap MB
         self.tuning = list(tv)
+
+    def build_chunks(self):
+        """(rows per aux chunk, chunks) of the mixed build; (0, 0) before the
+        first build and for DFJK_FP64."""
+        r, n = ctypes.c_int32(), ctypes.c_int32()
+        _check(load_library().dfjk_query_build(self.h, ctypes.byref(r), ctypes.byref(n)))
+        return r.value, n.value
 
     def close(self):
         if getattr(self, "h", None):
