@@ -80,9 +80,10 @@ typedef enum {
                     kept in both triangles, nao^2 naux_pad doubles            */
   DFJK_MIXED = 1 /* integrals (FP64; FP32 for the pairs below
                     fp32_pair_thresh), Cholesky and inverse, rho, J and the
-                    energies in FP64.  B is kept in FP64 as the packed
-                    mu >= nu triangle, nao (nao + 1) / 2 naux_pad doubles (8
-                    bytes per stored element, half the FP64 path's bytes).
+                    energies in FP64.  B is kept in FP64 for the
+                    Schwarz-kept AO pairs only, one row of naux_pad doubles
+                    per kept column (a quarter of the mu >= nu pairs at 60
+                    atoms, fewer for larger molecules).
                     The whitening, X = B C and K run on the tensor cores as
                     exact sliced products: each FP64 operand row is cut into 6
                     (8 for the whitening) 6-bit integer slices stored as BF16
@@ -170,7 +171,7 @@ int dfjk_query_precision(dfjk_handle h, int32_t *npair_fp32, double *fp32_thresh
 int dfjk_query_pair_classes(dfjk_handle h, int64_t *prim_pairs_fp64, int64_t *prim_pairs_fp32);
 
 /* The launch-shape choices a handle took from its tuning table, vals[4] =
- * {slicing rows per block, packed-B slicing rows per block, K GEMM split-K
+ * {slicing rows per block, B slicing rows per block, K GEMM split-K
  * range in MB, build work-buffer cap in MB}; 0 = the built-in default.       */
 int dfjk_query_tuning(dfjk_handle h, int32_t *vals);
 
@@ -190,7 +191,9 @@ int dfjk_query_build(dfjk_handle h, int32_t *chunk_rows, int32_t *nchunk);
 /* Device bytes a molecule with nao AOs and naux aux functions takes at the
  * given precision, before any setup (no device work): `resident` = what a
  * handle holds between builds (B and the metric, its Cholesky factor and
- * inverse), `build_ws` = the work buffers a build at nocc occupied orbitals
+ * inverse; for DFJK_MIXED an upper bound that counts every mu >= nu pair as
+ * kept, dfjk_query gives a set-up handle's actual bytes), `build_ws` = the
+ * work buffers a build at nocc occupied orbitals
  * adds (kept by the handle for its next builds), `setup_ws` = the transient
  * peak of the setup beyond the resident data (released when it returns).
  * Used to admit molecules under a memory budget (batching, serving).
@@ -218,8 +221,9 @@ int dfjk_build(dfjk_handle h, int32_t nset, int32_t nocc, const double *C_occ,
  *   J, K : device, nset x nao x nao FP64.
  *   E_J, E_K : nset doubles each, Tr(D J)/2 and Tr(D K)/2, host or device.
  * Uses a work buffer of nao^2 naux_pad doubles for the duration of the call,
- * and for a DFJK_MIXED handle (B packed) a second one holding B in both
- * triangles; synchronises the stream before returning.  Errors:
+ * and for a DFJK_MIXED handle (B of the kept pairs only) a second one holding
+ * B in both triangles of every pair; synchronises the stream before
+ * returning.  Errors:
  * DFJK_ERR_ARG, _OOM, _CUDA.                            */
 int dfjk_build_density(dfjk_handle h, int32_t nset, const double *D, double *J, double *K,
                        double *E_J, double *E_K, void *stream);

@@ -19,9 +19,10 @@ from . import dfjk
 
 def resident_bytes(nao: int, naux: int, nocc: int, precision: int) -> int:
     """Device bytes one molecule holds while set up and built, as the library
-    states them (dfjk_estimate_bytes): its resident data (B -- the packed
-    mu >= nu triangle in the mixed path, both triangles in the FP64 path --
-    and the metric, its Cholesky factor and inverse) plus the larger of the
+    states them (dfjk_estimate_bytes) from its sizes alone: its resident data
+    (B -- in the mixed path bounded by every mu >= nu pair, of which the setup
+    keeps the Schwarz-significant ones, both triangles in the FP64 path -- and
+    the metric, its Cholesky factor and inverse) plus the larger of the
     build's work buffers and the setup's transient peak."""
     e = dfjk.estimate_bytes(nao, naux, nocc, precision)
     return int(e["resident"] + max(e["build_ws"], e["setup_ws"]))

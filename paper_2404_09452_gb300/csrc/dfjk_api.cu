@@ -313,16 +313,16 @@ struct dfjk_ctx {
   DBuf<int> tctr;  // tile counter of the tensor-core GEMM launches (stream-ordered)
   DBuf<int> kseq;  // split counters of the ordered split-K GEMM
   // whitened tensor B, P contiguous: DFJK_FP64 keeps both triangles,
-  // B[(mu nao + nu) ldb + P]; DFJK_MIXED keeps the packed mu >= nu triangle,
-  // B[(mu (mu + 1) / 2 + nu) ldb + P], and slices it per build, chunk by chunk
-  // of rows P (Bchunk: batch mu, rows P of the chunk, K nu), just before
-  // X = B C of that chunk
+  // B[(mu nao + nu) ldb + P]; DFJK_MIXED keeps one row per kept column m (the
+  // whitening's output order), B[m ldb + P], found through rowmap, and slices
+  // it per build, chunk by chunk of rows P (Bchunk: batch mu, rows P of the
+  // chunk, K nu), just before X = B C of that chunk
   BStore B;
   long long ldb = 0;
-  bool lean = false;    // B packed (the mixed path)
+  bool lean = false;    // B of the kept pairs only (the mixed path)
   SlicedOp Bchunk;
   int chunk_rows = 0;   // rows P per build chunk (mixed path)
-  DBuf<int> Bexpo;      // slice exponents of the packed B, [mu][expo_rows][nkb]
+  DBuf<int> Bexpo;      // slice exponents of B's slices, [mu][expo_rows][nkb]
   int expo_rows = 0;    // rows P of Bexpo (naux_pad rounded up to 128)
   Tuning tune;          // launch-shape choices (tuning table entry or defaults)
   // build workspace
@@ -390,11 +390,11 @@ void enumerate_pairs(dfjk_ctx *h) {
   h->cls_begin[6] = (int)h->pa_h.size();
 }
 
-// Device bytes of a handle's resident data: B (packed triangle in the mixed
-// path, both triangles in the FP64 path; none when B is in host memory) and
-// the metric, its Cholesky factor and inverse.
-// Before screening: the mixed path's B holds one row per kept AO pair, at
-// most the nao (nao + 1) / 2 of the triangle (the bound used here).
+// Device bytes of a handle's resident data: B (none when B is in host
+// memory) and the metric, its Cholesky factor and inverse.  Before screening:
+// the mixed path's B holds one row per kept AO pair, at most the
+// nao (nao + 1) / 2 of the triangle (the bound used here); the FP64 path's
+// holds both triangles of every pair.
 size_t resident_estimate(const dfjk_ctx *h) {
   const size_t np2 = (size_t)h->naux_pad * h->naux_pad;
   const bool mixed = h->opt.precision == DFJK_MIXED;
@@ -930,7 +930,7 @@ void build_one(dfjk_ctx *h, int nocc, const double *C, double *J, double *Kout, 
     gemm_f64(k, st);
     reduce_sym_f64(h->Kpart.p, ceil_div(kt, k.k_split), nao, Kout, st);
   } else {
-    // The mixed path keeps B as the packed mu >= nu triangle (FP64) and works
+    // The mixed path keeps B for the kept AO pairs (FP64) and works
     // through the aux index in chunks of rows P: per chunk, the 6 slices of
     // B[mu][nu][P in chunk] (all mu, nu), X_P = B_P C for P in the chunk,
     // rho of the chunk from X, the slices of X and its contribution to K
@@ -965,7 +965,7 @@ void build_one(dfjk_ctx *h, int nocc, const double *C, double *J, double *Kout, 
         rho_from_x_f64(Xc, C, nao, pc, nocc, h->rho.p + p0, h->rho_work.p, st);
       }
       if (c == nchunk - 1) {
-        // J = B^T rho over the packed B, on the handle's side stream beside the
+        // J = B^T rho over the kept rows of B, on the handle's side stream beside the
         // last K GEMM: both only read finished data, and the HBM-bound GEMV
         // fits next to the tensor-bound GEMM on the SMs
         if (h->side) {
@@ -1418,7 +1418,7 @@ static void jk_gradient(dfjk_ctx *h, const double *Din, int nocc, const double *
     oz_gemm(A, Bo, o, st);
   };
   if (ck != 0.0) {
-    // exact sliced tensor-core GEMMs when the handle is mixed (B packed),
+    // exact sliced tensor-core GEMMs when the handle is mixed (B of the kept pairs),
     // FP64 CUDA-core GEMMs otherwise (B in both triangles)
     const bool tc = h->opt.precision == DFJK_MIXED;
     const long long no2 = (long long)nocc * nocc;
@@ -1431,7 +1431,7 @@ static void jk_gradient(dfjk_ctx *h, const double *Din, int nocc, const double *
     if (tc) {
       const SlicedOp &csl = slice(C, 0, 1, nocc, 1, nocc, nao, OZ_BN);  // rows i, K nu
       const SlicedOp &cn = slice(C, 0, nocc, 1, 1, nao, nocc, OZ_BN);   // rows mu, K i
-      // X[mu][P][i] = sum_nu B[(mu,nu)][P] C[nu][i], slicing the packed B chunk
+      // X[mu][P][i] = sum_nu B[(mu,nu)][P] C[nu][i], slicing B chunk
       // by chunk of rows P as the build does
       const int pcm = build_chunk_rows(nao, np, nocc, h->tune.build_ws_mb);
       ops.emplace_back();

@@ -269,7 +269,8 @@ __global__ void __launch_bounds__(256) oz_slice_tr_fused_kernel(const double *__
   }
 }
 
-// Slicing of the packed mu >= nu triangle reading each stored element once.
+// Slicing of B (rows of the kept AO pairs, found through rowmap) reading each
+// stored row once.
 // A block owns a 32 x 32 tile of the pair triangle (mu block >= nu block) and
 // R rows P, and stages the tile's FP64 values in shared memory (pairs with
 // mu < nu on the diagonal tiles are read from (nu, mu)); consecutive pairs of

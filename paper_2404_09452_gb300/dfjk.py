@@ -269,7 +269,7 @@ class Handle:
         tv = (ctypes.c_int32 * 4)()
         _check(lib.dfjk_query_tuning(h, tv))
         # launch shapes from the tuning table (0 = default): slicing rows,
-        # packed-B slicing rows, K range MB, build work-buffer cap MB
+        # B slicing rows, K range MB, build work-buffer cap MB
         self.tuning = list(tv)
 
     def build_chunks(self):

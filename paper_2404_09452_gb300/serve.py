@@ -25,6 +25,12 @@ from . import dfjk
 from .batch import resident_bytes
 
 
+def setup_bytes(h, mol, nocc: int, precision: int) -> int:
+    """Device bytes a set-up molecule holds from now on: its handle's resident
+    data (dfjk_query) plus the work buffers of a build at nocc."""
+    return int(h.device_bytes + dfjk.estimate_bytes(mol.nao, mol.naux, nocc, precision)["build_ws"])
+
+
 @dataclass
 class Request:
     rid: int
@@ -74,6 +80,13 @@ class Residency:
         if mol_id in self.bytes:
             self.used -= self.bytes.pop(mol_id)
 
+    def resize(self, mol_id, need: int):
+        """Charges a resident molecule `need` bytes instead of its current charge
+        (after its setup, when its actual size is known)."""
+        if mol_id in self.bytes:
+            self.used += need - self.bytes[mol_id]
+            self.bytes[mol_id] = need
+
 
 @dataclass
 class Stats:
@@ -102,21 +115,26 @@ class Server:
     miss reserves the molecule's bytes (evicting idle molecules in LRU order)
     and runs its setup on a worker thread with a stream of its own, so that
     hits keep being admitted and completions keep being retired while the
-    setup runs.  Builds of one molecule are serialised (its work buffers are
-    shared)."""
+    setup runs.  The reservation is the library's bound from the molecule's
+    sizes alone (every AO pair kept); once the setup is done the molecule is
+    charged what its handle holds (only the Schwarz-kept pairs of B) plus the
+    build's work buffers.  Builds of one molecule are serialised (its work
+    buffers are shared)."""
 
     def __init__(self, mols, precision=dfjk.DFJK_MIXED, budget_bytes=150 << 30, slots=8,
                  keep_outputs=False, setup_workers=2, backend=None):
-        """`backend`: (torch, handle class, bytes function) to use instead of
-        torch, dfjk.Handle and resident_bytes (host-logic tests on CPU)."""
+        """`backend`: (torch, handle class, bytes function[, set-up bytes
+        function]) to use instead of torch, dfjk.Handle, resident_bytes and
+        setup_bytes (host-logic tests on CPU)."""
         import threading
         from concurrent.futures import ThreadPoolExecutor
 
         if backend is None:
             import torch
 
-            backend = (torch, dfjk.Handle, resident_bytes)
-        torch, self._handle_cls, self._bytes_fn = backend
+            backend = (torch, dfjk.Handle, resident_bytes, setup_bytes)
+        torch, self._handle_cls, self._bytes_fn = backend[:3]
+        self._actual_fn = backend[3] if len(backend) > 3 else None
         self.torch = torch
         self.mols = mols
         self.precision = precision
@@ -159,7 +177,7 @@ class Server:
         if not ok:
             return False
         self.busy.add(mol_id)
-        self.setting_up[mol_id] = self._pool.submit(self._setup, mol_id)
+        self.setting_up[mol_id] = (self._pool.submit(self._setup, mol_id), nocc)
         self.stats.misses += 1
         return True
 
@@ -175,13 +193,17 @@ class Server:
                 waiting.append(pending.popleft())
             progressed = False
             # setups that finished: their molecules become resident and idle
-            for mid, fut in list(self.setting_up.items()):
+            for mid, (fut, nocc) in list(self.setting_up.items()):
                 if fut.done():
                     del self.setting_up[mid]
                     self.busy.discard(mid)
                     progressed = True
                     try:
-                        self.resident[mid] = fut.result()
+                        h = self.resident[mid] = fut.result()
+                        if self._actual_fn is not None:
+                            actual = self._actual_fn(h, self.mols[mid], nocc, self.precision)
+                            if actual < self.lru.bytes.get(mid, 0):
+                                self.lru.resize(mid, actual)
                     except dfjk.DfjkError as e:
                         # the molecule cannot be set up (device memory, budget):
                         # its waiting requests fail, its reservation is returned
@@ -254,7 +276,7 @@ class Server:
         return requests
 
     def close(self):
-        for fut in self.setting_up.values():
+        for fut, _ in self.setting_up.values():
             try:
                 fut.result().close()
             except dfjk.DfjkError:

@@ -1,6 +1,6 @@
 """Autotuner of the launch shapes that do not change what the build
 computes: rows per block of the slicing kernels (T, C and X slices; the
-per-build slices of the packed B), the K GEMM's split-K range and the mixed
+per-build slices of B), the K GEMM's split-K range and the mixed
 build's work-buffer cap (which sets the aux-row chunk).
 
 For each range of nao it times setup + build of a representative synthetic

@@ -143,7 +143,7 @@ def test_build_batch_captured_in_a_cuda_graph():
 
 def test_batch_with_a_60_atom_molecule_matches_the_oracle():
     """A multi-wave batch whose largest member is the 60-atom workload
-    molecule (mixed path: B packed, built in four aux-row chunks): that
+    molecule (mixed path: B of the kept pairs, built in four aux-row chunks): that
     member's J, K and energies against the FP64 CPU oracle at full size, and
     a small member against the oracle too."""
     from oracle import oracle as O

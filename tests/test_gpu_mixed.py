@@ -160,7 +160,7 @@ def test_chunked_build_matches_one_chunk_and_oracle(tmp_path):
 
 def test_config_120_atoms_mixed_vs_fp64_gpu():
     """The 120-atom mixed configuration (nao 1800, naux 4320, nocc 360; B kept
-    as the packed triangle, sliced per build in chunks of aux rows) against the
+    for the kept pairs only, sliced per build in chunks of aux rows) against the
     FP64 GPU path at the same size."""
     m = I.molecule(120, seed=1003)
     nocc = I.default_nocc(m.nao)

@@ -130,3 +130,33 @@ def test_hits_are_admitted_while_a_miss_sets_up():
     big = reqs[1]
     hits_done = [r.done for r in reqs if r.mol_id == 0 and r.rid >= 2]
     assert max(hits_done) < big.done  # every hit finished before the miss
+
+
+def test_setup_recharges_the_actual_bytes():
+    """A miss reserves the bound from the molecule's sizes; after the setup the
+    molecule is charged its actual bytes, so that two molecules whose bounds
+    do not fit the budget together (60 + 60 > 100) stay resident together
+    (30 + 60, then 30 + 30)."""
+    C = types.SimpleNamespace(shape=(0, 8))
+    mols = [_Mol(5), _Mol(6)]
+    # alternating requests of two molecules
+    reqs = [serve.Request(i, 0.001 * i, i % 2, C) for i in range(40)]
+
+    def run(actual):
+        log = {"setups": 0, "builds": 0, "setting_up": set()}
+        lock = threading.Lock()
+        backend = (_fake_torch(log), _make_handle_cls(log, lock), lambda *a: 60)
+        if actual is not None:
+            backend = backend + (actual,)
+        srv = serve.Server(mols, budget_bytes=100, slots=2, setup_workers=1, backend=backend)
+        srv.run([serve.Request(r.rid, r.arrival, r.mol_id, C) for r in reqs])
+        st = srv.stats.summary()
+        used = srv.lru.used
+        srv.close()
+        assert st["requests"] == 40 and st["failed"] == 0
+        return st["misses"], used
+
+    misses, used = run(lambda h, mol, nocc, p: 30)
+    assert misses == 2 and used == 60  # both resident, charged 30 each
+    misses_bound, _ = run(None)
+    assert misses_bound > 2  # charged the bound, they evict each other
