@@ -284,7 +284,9 @@ __global__ void __launch_bounds__(256) oz_slice_tr_fused_kernel(const double *__
 constexpr int OZ_EXPO_BIAS = 4096;
 constexpr int OZ_TT = 32;  // tile edge in AO indices
 
-__host__ __device__ constexpr int oz_sym_smem(int R) { return OZ_TT * OZ_TT * (R + 1) * 8 + 2 * OZ_TT * R * 4; }
+__host__ __device__ constexpr int oz_sym_smem(int R) {
+  return OZ_TT * OZ_TT * (R + 1) * 8 + 2 * OZ_TT * R * 4 + OZ_TT * OZ_TT * 4;
+}
 
 template <int R, int MODE>
 __global__ void __launch_bounds__(256) oz_slice_sym_kernel(const double *__restrict__ B, long long ldb,
@@ -297,6 +299,7 @@ __global__ void __launch_bounds__(256) oz_slice_sym_kernel(const double *__restr
   double *tile = reinterpret_cast<double *>(sym_smem);  // [mu_l][nu_l][P], P stride 1, nu stride RP
   int *eD = reinterpret_cast<int *>(tile + OZ_TT * OZ_TT * RP);  // [mu_l][P]: batch mu, K block of nu0
   int *eT = eD + OZ_TT * R;                                    // [nu_l][P]: batch nu, K block of mu0
+  int *tmap = eT + OZ_TT * R;                                  // [mu_l][nu_l]: row of B, -1 if none
   // grid x: row groups (fastest, so that the blocks reading the neighbouring
   // rows of one pair run together and share its cache lines); grid y: tile
   // t of the lower triangle -> (ti >= tj)
@@ -307,6 +310,17 @@ __global__ void __launch_bounds__(256) oz_slice_sym_kernel(const double *__restr
   const int tj = (int)(t - (long long)ti * (ti + 1) / 2);
   const int mu0 = ti * OZ_TT, nu0 = tj * OZ_TT, r0 = blockIdx.x * R;
   const bool diag = ti == tj;
+  // the tile's rows of B (one load per pair, 32 consecutive nu per mu), so
+  // that the loads of B below do not wait on the map
+  bool any = false;
+  for (int q = threadIdx.x; q < OZ_TT * OZ_TT; q += 256) {
+    const int mu = mu0 + q / OZ_TT, nu = nu0 + q % OZ_TT;
+    const int row = (mu < nao && nu < nao) ? rowmap[(long long)mu * nao + nu] : -1;
+    tmap[q] = row;
+    any |= row >= 0;
+  }
+  any = __syncthreads_or(any);
+  if (MODE == 1 && !any) return;  // every pair of the tile screened: maxima 0
   // stage the tile: R lanes per pair, 256 / R pairs per pass, 16 loads in
   // flight per thread
   constexpr int PER = OZ_TT * OZ_TT * R / 256, UN = PER < 16 ? PER : 16;
@@ -317,13 +331,9 @@ __global__ void __launch_bounds__(256) oz_slice_sym_kernel(const double *__restr
 #pragma unroll
     for (int u = 0; u < UN; ++u) {
       const int i = threadIdx.x + (u0 + u) * 256;
-      const int P = i % R, q = i / R, ml = q / OZ_TT, nl = q % OZ_TT;
-      const int mu = mu0 + ml, nu = nu0 + nl, r = r0 + P;
-      v[u] = 0.0;
-      if (mu < nao && nu < nao && r < rows) {
-        const int row = rowmap[(long long)mu * nao + nu];
-        if (row >= 0) v[u] = B[(long long)row * ldb + p0 + r];
-      }
+      const int P = i % R, q = i / R, r = r0 + P;
+      const int row = tmap[q];
+      v[u] = (row >= 0 && r < rows) ? B[(long long)row * ldb + p0 + r] : 0.0;
     }
 #pragma unroll
     for (int u = 0; u < UN; ++u) {
