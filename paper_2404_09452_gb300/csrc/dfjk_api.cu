@@ -233,7 +233,7 @@ static void read_basis(const dfjk_basis *b, int natom, const double *coords, Hos
 // built-in default (or the corresponding environment variable).
 struct Tuning {
   int slice_rows = 0;   // DFJK_SLICE_ROWS: 8, 16, 32
-  int pslice_rows = 0;  // DFJK_PSLICE_ROWS: 4, 8, 16
+  int pslice_rows = 0;  // DFJK_PSLICE_ROWS: 4, 8, 16 (default 4)
   int k_range_mb = 0;   // DFJK_K_RANGE_MB
   int build_ws_mb = 0;  // DFJK_BUILD_WS_MB
 };

@@ -468,7 +468,9 @@ void oz_expo_packed(const double *B, long long ldb, const int *rowmap, int nao, 
   DFJK_CUDA_CHECK(cudaMemsetAsync(expo, 0, n * sizeof(int), st));
   const long long nb = (nao + OZ_TT - 1) / OZ_TT, tiles = nb * (nb + 1) / 2;
   if (tiles > 65535) throw Error{DFJK_ERR_ARG, "packed exponents: grid"};
-  launch_oz_sym<8, 1>(dim3((unsigned)(pre_rows / 8), (unsigned)tiles), B, ldb, rowmap, nao, np, 0, 0, 0, nkb, 0,
+  // 4 rows P per block: 46 KB of shared memory, 4 blocks per SM (8 rows: 80 KB,
+  // 2 blocks, latency-bound)
+  launch_oz_sym<4, 1>(dim3((unsigned)(pre_rows / 4), (unsigned)tiles), B, ldb, rowmap, nao, np, 0, 0, 0, nkb, 0,
                       nullptr, pre_rows, expo, nullptr, st);
   oz_expo_decode_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(expo, n);
   DFJK_LAUNCHED();
@@ -481,11 +483,13 @@ void oz_slice_f64_packed_pre(const double *B, long long ldb, const int *rowmap, 
   if (op.S != 6 || op.rows_pad % 32 != 0 || op.nkb > 8 || p0 % 32 != 0 || p0 + op.rows_pad > pre_rows ||
       op.batch != op.K || op.kpitch % OZ_TT != 0 || p0 + op.rows > ldb)
     throw Error{DFJK_ERR_UNSUPPORTED, "packed slicing: 6 slices, K <= 8192, exponent rows"};
-  // rows P per block: 8 (default), 4 or 16 (DFJK_PSLICE_ROWS or the tuning table)
+  // rows P per block: 4 (default: 4 blocks per SM; 8 rows fit 2 and were
+  // latency-bound, 2.36 against 1.96 ms per 60-atom chunk), 8 or 16
+  // (DFJK_PSLICE_ROWS or the tuning table)
   static const int R_env = [] {
     const char *e = std::getenv("DFJK_PSLICE_ROWS");
-    const int v = e ? std::atoi(e) : 8;
-    return (v == 4 || v == 16) ? v : 8;
+    const int v = e ? std::atoi(e) : 4;
+    return (v == 8 || v == 16) ? v : 4;
   }();
   const int R = (rows_per_block == 4 || rows_per_block == 8 || rows_per_block == 16) ? rows_per_block : R_env;
   // exponents of the chunk's rows, copied for the GEMM

@@ -93,7 +93,7 @@ void oz_expo_packed(const double *B, long long ldb, const int *rowmap, int nao, 
 // The slices of the chunk of rows P [p0, p0 + op.rows) for all mu (batch = K
 // = nao), with the exponents from `pre` (oz_expo_packed), which are also
 // copied into op.expo.  p0 % 32 == 0 and p0 + op.rows_pad <= pre_rows.
-// rows_per_block: rows P per block (4, 8 or 16; 0 = the default, 8, or
+// rows_per_block: rows P per block (4, 8 or 16; 0 = the default, 4, or
 // DFJK_PSLICE_ROWS).
 void oz_slice_f64_packed_pre(const double *B, long long ldb, const int *rowmap, const int *pre, int pre_rows, int p0,
                              SlicedOp &op, cudaStream_t st, int rows_per_block = 0);

@@ -28,7 +28,7 @@ from . import dfjk, inputs
 BUCKETS = [(0, 150, 6), (150, 300, 14), (300, 600, 30), (600, 1200, 60), (1200, 2400, 110)]
 CHOICES = {
     "slice_rows": [16, 8, 32],
-    "pslice_rows": [8, 4, 16],
+    "pslice_rows": [4, 8, 16],
     "k_range_mb": [64, 32, 128],
     "build_ws_mb": [8192, 4096],
 }
