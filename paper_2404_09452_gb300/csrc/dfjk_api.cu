@@ -374,18 +374,17 @@ void enumerate_pairs(dfjk_ctx *h) {
   h->pa_h.clear();
   h->pb_h.clear();
   h->npp_h.clear();
+  std::vector<int> by_l[3];  // orbital shells of each l, ascending
+  for (int a = 0; a < h->orb.nshell; ++a) by_l[h->orb.l[a]].push_back(a);
   for (int c = 0; c < 6; ++c) {
     h->cls_begin[c] = (int)h->pa_h.size();
-    for (int a = 0; a < h->orb.nshell; ++a) {
-      if (h->orb.l[a] != cls[c][0]) continue;
-      for (int b = 0; b < h->orb.nshell; ++b) {
-        if (h->orb.l[b] != cls[c][1]) continue;
-        if (cls[c][0] == cls[c][1] && b > a) continue;
+    for (int a : by_l[cls[c][0]])
+      for (int b : by_l[cls[c][1]]) {
+        if (cls[c][0] == cls[c][1] && b > a) break;
         h->pa_h.push_back(a);
         h->pb_h.push_back(b);
         h->npp_h.push_back(h->orb.nprim[a] * h->orb.nprim[b]);
       }
-    }
   }
   h->cls_begin[6] = (int)h->pa_h.size();
 }
@@ -461,17 +460,16 @@ void compute_metric(dfjk_ctx *h, const double *tab, cudaStream_t st) {
     DFJK_LAUNCHED();
   }
   static const int cls[6][2] = {{0, 0}, {1, 0}, {1, 1}, {2, 0}, {2, 1}, {2, 2}};
+  std::vector<int> by_l[3];  // aux shells of each l, ascending
+  for (int p = 0; p < h->aux.nshell; ++p) by_l[h->aux.l[p]].push_back(p);
   for (int c = 0; c < 6; ++c) {
     std::vector<int> sp, sq;
-    for (int p = 0; p < h->aux.nshell; ++p) {
-      if (h->aux.l[p] != cls[c][0]) continue;
-      for (int q = 0; q < h->aux.nshell; ++q) {
-        if (h->aux.l[q] != cls[c][1]) continue;
-        if (cls[c][0] == cls[c][1] && q > p) continue;
+    for (int p : by_l[cls[c][0]])
+      for (int q : by_l[cls[c][1]]) {
+        if (cls[c][0] == cls[c][1] && q > p) break;
         sp.push_back(p);
         sq.push_back(q);
       }
-    }
     if (sp.empty()) continue;
     DBuf<int> dp, dq;
     dp.upload(sp, st);

@@ -187,24 +187,39 @@ def _stream(stream=None):
     return ctypes.c_void_p(s.cuda_stream)
 
 
+# numpy layout of dfjk_shell (atom, l, nprim, pad, exps*, coefs*)
+_SHELL_DTYPE = np.dtype({"names": ["atom", "l", "nprim", "exps", "coefs"],
+                         "formats": [np.int32, np.int32, np.int32, np.uint64, np.uint64],
+                         "offsets": [0, 4, 8, 16, 24], "itemsize": 32})
+
+
 class _BasisHolder:
-    """Keeps the numpy arrays alive while C holds pointers into them."""
+    """A dfjk_basis for `basis`, with the arrays it points into kept alive:
+    every shell's exponents and coefficients in two contiguous arrays and the
+    shell records in one structured array (no per-shell ctypes objects)."""
 
     def __init__(self, basis):
+        assert ctypes.sizeof(Shell) == _SHELL_DTYPE.itemsize
         shells = list(basis.shells)
-        self.arrays = []
-        arr = (Shell * max(1, len(shells)))()
-        for i, s in enumerate(shells):
-            e = np.ascontiguousarray(s.exps, dtype=np.float64)
-            c = np.ascontiguousarray(s.coefs, dtype=np.float64)
-            self.arrays += [e, c]
-            arr[i].atom = int(s.atom)
-            arr[i].l = int(s.l)
-            arr[i].nprim = len(e)
-            arr[i].exps = e.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
-            arr[i].coefs = c.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
-        self.shells = arr
-        self.c = BasisC(len(shells), ctypes.cast(arr, ctypes.POINTER(Shell)))
+        n = len(shells)
+        nprim = np.fromiter((len(s.exps) for s in shells), dtype=np.int64, count=n)
+        off = np.zeros(n + 1, dtype=np.int64)
+        np.cumsum(nprim, out=off[1:])
+        self.exps = np.ascontiguousarray(np.concatenate([np.asarray(s.exps, dtype=np.float64) for s in shells])
+                                         if n else np.zeros(1), dtype=np.float64)
+        self.coefs = np.ascontiguousarray(np.concatenate([np.asarray(s.coefs, dtype=np.float64) for s in shells])
+                                          if n else np.zeros(1), dtype=np.float64)
+        if n and (self.coefs.size != off[-1] or self.exps.size != off[-1]):
+            raise ValueError("every shell needs as many coefficients as exponents")
+        rec = np.zeros(max(1, n), dtype=_SHELL_DTYPE)
+        if n:
+            rec["atom"][:n] = np.fromiter((s.atom for s in shells), dtype=np.int32, count=n)
+            rec["l"][:n] = np.fromiter((s.l for s in shells), dtype=np.int32, count=n)
+            rec["nprim"][:n] = nprim
+            rec["exps"][:n] = self.exps.ctypes.data + 8 * off[:n]
+            rec["coefs"][:n] = self.coefs.ctypes.data + 8 * off[:n]
+        self.rec = rec
+        self.c = BasisC(n, ctypes.cast(rec.ctypes.data, ctypes.POINTER(Shell)))
 
 
 def default_options(precision: int = DFJK_FP64, schwarz_thresh: float = 1e-12,
