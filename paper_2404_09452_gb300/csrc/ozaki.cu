@@ -356,16 +356,21 @@ __global__ void __launch_bounds__(256) oz_slice_sym_kernel(const double *__restr
       if (tr && diag) continue;
       const int z = (tr ? nu0 : mu0) + l, kb = (tr ? mu0 : nu0) >> 10;
       if (z >= nao) continue;
-      // |x| maxima on the bit patterns (non-negative doubles order like
-      // their bits), on the integer pipes
-      unsigned long long mx = 0;
+      // maxima of the high words of |x| (sign cleared): the exponent lives
+      // there and non-negative doubles order like their bits, so 32-bit
+      // integer maxima suffice (values whose high word is 0, below 2^-1042,
+      // count as zero)
+      unsigned int mx = 0;
 #pragma unroll 8
       for (int o = 0; o < OZ_TT; ++o) {
         const double x = tr ? tile[(o * OZ_TT + l) * RP + P] : tile[(l * OZ_TT + o) * RP + P];
-        mx = max(mx, (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull);
+        mx = max(mx, (unsigned int)__double2hiint(x) & 0x7FFFFFFFu);
       }
-      if (mx) atomicMax(expo_out + ((long long)z * pre_rows + r0 + P) * nkb + kb,
-                        oz_expo_of(__longlong_as_double((long long)mx)) + OZ_EXPO_BIAS);
+      if (mx) {
+        const int ex = (int)(mx >> 20);  // biased exponent, as oz_expo_of takes it
+        atomicMax(expo_out + ((long long)z * pre_rows + r0 + P) * nkb + kb,
+                  (ex == 0 ? -1021 : ex - 1022) + OZ_EXPO_BIAS);
+      }
     }
     return;
   } else {

@@ -242,3 +242,36 @@ def test_config_120_atoms_sampled_B_columns_vs_oracle():
     print(f"mol120 sampled B columns: {len(cols_mu)} columns, max|dB| {err:.2e}, max|B| {np.abs(Bref).max():.2e}")
     assert err < 1e-6 * max(1.0, np.abs(Bref).max())
     h.close()
+
+
+def test_B_holds_the_kept_pairs_only():
+    """The mixed handle stores B for the Schwarz-kept AO pairs only (rows found
+    through a row map): a screened pair reads back as exact zeros through both
+    accessors, a kept one as the FP64 handle's column, and the handle holds
+    fewer bytes than the FP64 handle with both triangles of every pair."""
+    m = I.molecule(12, seed=1012)
+    thr = 1e-5  # screens a good share of the pairs of this molecule
+    hm = dfjk.Handle(m, precision=dfjk.DFJK_MIXED, schwarz_thresh=thr)
+    hf = dfjk.Handle(m, precision=dfjk.DFJK_FP64, schwarz_thresh=thr)
+    ncart = [(s.l + 1) * (s.l + 2) // 2 for s in m.orb.shells]
+    off = np.concatenate([[0], np.cumsum(ncart)])
+    mask = hm.pair_mask().cpu().numpy()
+    kept, screened = [], []
+    for a in range(len(ncart)):
+        for b in range(a + 1):
+            (kept if mask[a, b] else screened).append((off[a], off[b] + ncart[b] - 1))
+    assert screened and kept
+    mu = np.array([p[0] for p in kept + screened], dtype=np.int32)
+    nu = np.array([p[1] for p in kept + screened], dtype=np.int32)
+    Bm = hm.B_columns(mu, nu).cpu().numpy()
+    Bf = hf.B_columns(mu, nu).cpu().numpy()
+    nk = len(kept)
+    assert not Bm[nk:].any() and not Bf[nk:].any()
+    assert np.abs(Bm[:nk] - Bf[:nk]).max() <= 1e-8 * max(1.0, np.abs(Bf).max())
+    Bfull_m, Bfull_f = hm.B().cpu().numpy(), hf.B().cpu().numpy()
+    assert np.abs(Bfull_m - Bfull_f).max() <= 1e-8 * max(1.0, np.abs(Bfull_f).max())
+    for (a, b) in screened[:20]:
+        assert not Bfull_m[:, a, b].any() and not Bfull_m[:, b, a].any()
+    assert hm.device_bytes < hf.device_bytes
+    hm.close()
+    hf.close()
