@@ -141,6 +141,7 @@ class Server:
         self.budget = budget_bytes
         self.keep = keep_outputs
         self.resident = {}  # mol_id -> Handle (set up, ready)
+        self.nocc_of = {}  # mol_id -> the largest nocc it is charged for
         self.setting_up = {}  # mol_id -> Future of its Handle
         self.lru = Residency(budget_bytes)
         self.busy = set()  # mol_ids with a build or a setup in flight
@@ -177,6 +178,7 @@ class Server:
         if not ok:
             return False
         self.busy.add(mol_id)
+        self.nocc_of[mol_id] = nocc
         self.setting_up[mol_id] = (self._pool.submit(self._setup, mol_id), nocc)
         self.stats.misses += 1
         return True
@@ -232,6 +234,15 @@ class Server:
                     if not self.free_slots:
                         continue
                     h = self.resident[mid]
+                    nocc = int(req.C.shape[1])
+                    if nocc > self.nocc_of.get(mid, 0):
+                        # a larger build work buffer: charge it (later
+                        # admissions evict to make room)
+                        self.nocc_of[mid] = nocc
+                        grown = (self._actual_fn(h, self.mols[mid], nocc, self.precision)
+                                 if self._actual_fn is not None else self._bytes(mid, nocc))
+                        if grown > self.lru.bytes.get(mid, 0):
+                            self.lru.resize(mid, grown)
                     slot = self.free_slots.pop()
                     s = self.streams[slot]
                     with torch.cuda.stream(s):
@@ -286,6 +297,7 @@ class Server:
         for h in self.resident.values():
             h.close()
         self.resident.clear()
+        self.nocc_of.clear()
         self.lru = Residency(self.budget)
 
 

@@ -160,3 +160,25 @@ def test_setup_recharges_the_actual_bytes():
     assert misses == 2 and used == 60  # both resident, charged 30 each
     misses_bound, _ = run(None)
     assert misses_bound > 2  # charged the bound, they evict each other
+
+
+def test_a_larger_nocc_raises_the_charge():
+    """A later request with more occupied orbitals (a larger build work
+    buffer) raises its molecule's charge."""
+    log = {"setups": 0, "builds": 0, "setting_up": set()}
+    lock = threading.Lock()
+    mols = [_Mol(5)]
+    small, large = types.SimpleNamespace(shape=(0, 8)), types.SimpleNamespace(shape=(0, 16))
+    reqs = [serve.Request(0, 0.0, 0, small), serve.Request(1, 0.01, 0, large)]
+    charged = []
+
+    def actual(h, mol, nocc, p):
+        charged.append(nocc)
+        return 10 * nocc
+
+    srv = serve.Server(mols, budget_bytes=10 ** 6, slots=1, setup_workers=1,
+                       backend=(_fake_torch(log), _make_handle_cls(log, lock), lambda *a: 1000, actual))
+    srv.run(reqs)
+    used = srv.lru.used
+    srv.close()
+    assert charged == [8, 16] and used == 160 and log["setups"] == 1
