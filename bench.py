@@ -102,20 +102,31 @@ def eri_roofline(h, m, ms64, ms32, fp64_peak, fp32_peak):
     return out
 
 
-def recorded_traffic(key: str, workload: str):
-    """DRAM bytes (read + write) per launch of the tensor-core GEMM `key`, from the
-    ncu capture summarised in profiles/traffic_mol60.md, or None when there is
-    no capture for this workload or the kernel source changed since (the
-    summary records the sha256 of csrc/ozaki.cu it was taken with)."""
+def gemm_source_sha() -> str:
+    """sha256 of the tensor-core GEMM's source: csrc/ozaki.cu from its
+    '// ---- GEMM' section marker to the end (the kernels, their tensor maps and
+    launch code; the slicing kernels come before the marker)."""
     import hashlib
 
     src = os.path.join(ROOT, "paper_2404_09452_gb300", "csrc", "ozaki.cu")
-    if not os.path.exists(TRAFFIC_FILE) or not os.path.exists(src):
+    if not os.path.exists(src):
+        return ""
+    text = open(src, "rb").read()
+    at = text.find(b"// ---- GEMM")
+    return hashlib.sha256(text[at:] if at >= 0 else text).hexdigest()
+
+
+def recorded_traffic(key: str, workload: str):
+    """DRAM bytes (read + write) per launch of the tensor-core GEMM `key`, from the
+    ncu capture summarised in profiles/traffic_mol60.md, or None when there is
+    no capture for this workload or the GEMM source changed since (the summary
+    records gemm_source_sha() at capture time)."""
+    if not os.path.exists(TRAFFIC_FILE):
         return None
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    sha = gemm_source_sha()
     for line in open(TRAFFIC_FILE):
         f = line.split()
-        # traffic-per-launch <kernel> <workload> <bytes> <sha256 of ozaki.cu>
+        # traffic-per-launch <kernel> <workload> <bytes> <gemm_source_sha()>
         if len(f) == 5 and f[0] == "traffic-per-launch" and f[1] == key and f[2] == workload and f[4] == sha:
             return int(f[3])
     return None
