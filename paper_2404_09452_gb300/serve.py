@@ -7,10 +7,11 @@ a miss evicts the least recently used idle molecules and recomputes B with
 Requests that arrive while others are on the GPU are admitted as soon as a
 build slot and their molecule are free: each build runs on one of `slots`
 CUDA streams, so builds of different molecules overlap on the device.
-Builds of the same molecule are serialised (its work buffers are shared).  Latency is measured from arrival to the host observing completion
-of the build's event.  The paper's SCF loop (Sec. "Compatibility", the
-`kernel()` call) repeats J/K builds for one molecule with new orbitals; the
-~70 % repeat rate of the request stream models that.
+Builds of the same molecule are serialised (its work buffers are shared).
+Latency is measured from arrival to the host observing completion of the
+build's event.  The paper's SCF loop (Sec. "Improved Compatibility with
+PySCF", the `kernel()` call) repeats J/K builds for one molecule with new
+orbitals; the ~70 % repeat rate of the request stream models that.
 """
 
 from __future__ import annotations
